@@ -1,0 +1,725 @@
+/*
+ * vrt_oracle.c -- TEST INFRASTRUCTURE ONLY (see vrt_oracle.h).
+ *
+ * A plain FP64 transcription of the Vectorial Ray Tracing (VRT) step of
+ * Chavez-Islas et al., Sec. II.  Nothing here is blocked, fused or reordered
+ * for speed: every step evaluates the medium, picks one of the cases of
+ * Sec. II in a fixed order and advances the ray point.  Built with
+ * -O2 -ffp-contract=off so that every product and sum is rounded on its own.
+ *
+ * Readings of the paper taken here (the paper's flowchart figure is missing):
+ *   - the ray direction is carried as state; it equals the normalised
+ *     difference of successive points (Eq. 6) in exact arithmetic;
+ *   - n_prev is the index sampled at the previous point, n_{i-1} = n(P_{i-1})
+ *     (Sec. II, after Eq. 3), whatever case that point took; a total internal
+ *     reflection steps Delta L_0 / n_{i-1} (Sec. II (v)), every other case
+ *     Delta L_0 / n_i, so every full step adds exactly Delta L_0 of optical
+ *     path, and a step cut short at the boundary a fraction t adds t Delta L_0;
+ *   - case order: boundary crossing, zero or non-finite gradient, tangent
+ *     incidence (N.I == 0 exactly), TIR (D <= 0), refraction;
+ *   - a boundary crossing ends the step at the exact FP64 intersection with
+ *     the enclosing surface (counted as a step); the boundary normal replaces
+ *     grad n there (Sec. II (i)) with mu = n_{i-1} / n_ext; on reflection the
+ *     boundary point becomes the previous point, with n sampled there;
+ *   - the exterior is one straight segment in the homogeneous index n_ext,
+ *     not counted as steps; a point exactly on the surface is outside;
+ *   - layered shells: n is the centre value of the level of an underlying
+ *     smooth field; inside one shell the gradient is taken as zero (case iii),
+ *     at a level change the normal is grad of the smooth field;
+ *   - every updated direction is renormalised.
+ */
+#include "vrt_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { EXIT_MISS = -1, EXIT_ENTRY_REFLECT = -2, EXIT_MAXSTEPS = -3, EXIT_INVALID = -4 };
+
+static double dot3(const double* a, const double* b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+static double norm3(const double* a) { return sqrt(dot3(a, a)); }
+
+static void normalize3(double* a) {
+  double l = norm3(a);
+  a[0] = a[0] / l;
+  a[1] = a[1] / l;
+  a[2] = a[2] / l;
+}
+
+static int finite3(const double* a) {
+  return isfinite(a[0]) && isfinite(a[1]) && isfinite(a[2]);
+}
+
+static double ipow(double x, int e) {
+  double r = 1.0;
+  for (int i = 0; i < e; ++i) r = r * x;
+  return r;
+}
+
+/* ---------------------------------------------------------------- medium */
+
+/* Polynomial p and its gradient in physical coordinates: a direct sum over
+ * the monomials x'^i y'^j z'^k, graded by total degree s = i+j+k, and within
+ * one degree ordered by i descending, then j descending. */
+static void poly_eval(const orc_medium* m, const double* P, double* p, double* gp) {
+  double x = (P[0] - m->off[0]) / m->scale[0];
+  double y = (P[1] - m->off[1]) / m->scale[1];
+  double z = (P[2] - m->off[2]) / m->scale[2];
+  double v = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+  int idx = 0;
+  for (int s = 0; s <= m->degree; ++s) {
+    for (int i = s; i >= 0; --i) {
+      for (int j = s - i; j >= 0; --j) {
+        int k = s - i - j;
+        double c = m->coeffs[idx++];
+        v += c * (ipow(x, i) * ipow(y, j) * ipow(z, k));
+        if (i > 0) gx += c * ((double)i * ipow(x, i - 1) * ipow(y, j) * ipow(z, k));
+        if (j > 0) gy += c * ((double)j * ipow(x, i) * ipow(y, j - 1) * ipow(z, k));
+        if (k > 0) gz += c * ((double)k * ipow(x, i) * ipow(y, j) * ipow(z, k - 1));
+      }
+    }
+  }
+  *p = v;
+  gp[0] = gx / m->scale[0];
+  gp[1] = gy / m->scale[1];
+  gp[2] = gz / m->scale[2];
+}
+
+/* Catmull-Rom cubic convolution weights (Keys 1981, a = -1/2) for the taps at
+ * offsets -1, 0, 1, 2 around the cell containing fraction t, and their
+ * derivatives with respect to t. */
+static void cr_weights(double t, double* w, double* dw) {
+  double t2 = t * t, t3 = t2 * t;
+  w[0] = (-t3 + 2.0 * t2 - t) / 2.0;
+  w[1] = (3.0 * t3 - 5.0 * t2 + 2.0) / 2.0;
+  w[2] = (-3.0 * t3 + 4.0 * t2 + t) / 2.0;
+  w[3] = (t3 - t2) / 2.0;
+  dw[0] = (-3.0 * t2 + 4.0 * t - 1.0) / 2.0;
+  dw[1] = (9.0 * t2 - 10.0 * t) / 2.0;
+  dw[2] = (-9.0 * t2 + 8.0 * t + 1.0) / 2.0;
+  dw[3] = (3.0 * t2 - 2.0 * t) / 2.0;
+}
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* Tricubic interpolant of the vertex-centred samples (x fastest) and its
+ * analytic gradient; taps beyond the grid repeat the edge sample. */
+static void grid_eval(const orc_medium* m, const double* P, double* f, double* gf) {
+  int n[3] = {m->nx, m->ny, m->nz};
+  int base[3];
+  double w[3][4], dw[3][4];
+  for (int a = 0; a < 3; ++a) {
+    double u = (P[a] - m->origin[a]) / m->spacing[a];
+    if (!(u > -2.0)) u = -2.0; /* also catches NaN */
+    if (u > (double)n[a] + 1.0) u = (double)n[a] + 1.0;
+    double fl = floor(u);
+    base[a] = (int)fl;
+    cr_weights(u - fl, w[a], dw[a]);
+  }
+  double v = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+  for (int c = 0; c < 4; ++c) {
+    int kk = clampi(base[2] - 1 + c, 0, n[2] - 1);
+    for (int b = 0; b < 4; ++b) {
+      int jj = clampi(base[1] - 1 + b, 0, n[1] - 1);
+      for (int a = 0; a < 4; ++a) {
+        int ii = clampi(base[0] - 1 + a, 0, n[0] - 1);
+        double s = (double)m->grid[((int64_t)kk * n[1] + jj) * n[0] + ii];
+        v += w[0][a] * w[1][b] * w[2][c] * s;
+        gx += dw[0][a] * w[1][b] * w[2][c] * s;
+        gy += w[0][a] * dw[1][b] * w[2][c] * s;
+        gz += w[0][a] * w[1][b] * dw[2][c] * s;
+      }
+    }
+  }
+  *f = v;
+  gf[0] = gx / m->spacing[0];
+  gf[1] = gy / m->spacing[1];
+  gf[2] = gz / m->spacing[2];
+}
+
+/* The smooth field n(x,y,z) and grad n (before any quantisation). */
+static void field_eval(const orc_medium* m, const double* P, double* f, double* g) {
+  if (m->kind == 1) {
+    grid_eval(m, P, f, g);
+    return;
+  }
+  double p, gp[3];
+  poly_eval(m, P, &p, gp);
+  if (m->form == 0) {
+    *f = p;
+    g[0] = gp[0];
+    g[1] = gp[1];
+    g[2] = gp[2];
+  } else if (m->form == 1) {
+    double n = sqrt(p);
+    *f = n;
+    g[0] = gp[0] / (2.0 * n);
+    g[1] = gp[1] / (2.0 * n);
+    g[2] = gp[2] / (2.0 * n);
+  } else {
+    *f = m->form_c / p;
+    double q = -m->form_c / (p * p);
+    g[0] = q * gp[0];
+    g[1] = q * gp[1];
+    g[2] = q * gp[2];
+  }
+}
+
+/* Layered shells: level k = clamp(floor(L (f - lo) / (hi - lo)), 0, L-1) and
+ * index lo + (k + 1/2) (hi - lo) / L.  u returns the unclamped level
+ * coordinate for the margin bookkeeping. */
+static void level_of(const orc_medium* m, double f, int* k, double* n, double* u) {
+  double L = (double)m->n_levels;
+  double uu = L * (f - m->level_lo) / (m->level_hi - m->level_lo);
+  double fl = floor(uu);
+  int kk;
+  if (!(fl >= 0.0)) kk = 0;
+  else if (fl > L - 1.0) kk = m->n_levels - 1;
+  else kk = (int)fl;
+  *k = kk;
+  *u = uu;
+  *n = m->level_lo + ((double)kk + 0.5) * (m->level_hi - m->level_lo) / L;
+}
+
+int orc_medium_eval(const orc_medium* m, const double* P, double* n, double* g) {
+  double f;
+  field_eval(m, P, &f, g);
+  if (m->n_levels > 0) {
+    int k;
+    double u;
+    level_of(m, f, &k, n, &u);
+  } else {
+    *n = f;
+  }
+  return 0;
+}
+
+/* -------------------------------------------------------------- boundary */
+
+static int inside(const orc_medium* m, const double* P) {
+  const double* b = m->b;
+  if (m->bkind == 0) {
+    return P[0] > b[0] && P[0] < b[3] && P[1] > b[1] && P[1] < b[4] && P[2] > b[2] &&
+           P[2] < b[5];
+  } else if (m->bkind == 1) {
+    double r[3] = {P[0] - b[0], P[1] - b[1], P[2] - b[2]};
+    return dot3(r, r) < b[3] * b[3];
+  } else {
+    double x = P[0] - b[0], y = P[1] - b[1];
+    return x * x + y * y < b[2] * b[2] && P[2] > b[3] && P[2] < b[4];
+  }
+}
+
+/* Relative distance of a point to the enclosing surface, in units of the
+ * geometric step h. */
+static double boundary_margin(const orc_medium* m, const double* P, double h) {
+  const double* b = m->b;
+  if (m->bkind == 0) {
+    double r = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+      double d1 = fabs(P[a] - b[a]), d2 = fabs(b[3 + a] - P[a]);
+      if (d1 < r) r = d1;
+      if (d2 < r) r = d2;
+    }
+    return r / h;
+  } else if (m->bkind == 1) {
+    double r[3] = {P[0] - b[0], P[1] - b[1], P[2] - b[2]};
+    return fabs(dot3(r, r) - b[3] * b[3]) / (2.0 * b[3] * h);
+  } else {
+    double x = P[0] - b[0], y = P[1] - b[1];
+    double r = fabs(x * x + y * y - b[2] * b[2]) / (2.0 * b[2] * h);
+    double d1 = fabs(P[2] - b[3]) / h, d2 = fabs(b[4] - P[2]) / h;
+    if (d1 < r) r = d1;
+    if (d2 < r) r = d2;
+    return r;
+  }
+}
+
+/* Both roots of a t^2 + b t + c = 0 (a > 0) in the cancellation-free form;
+ * returns 0 when there is no real root. */
+static int quad_roots(double a, double b, double c, double* t1, double* t2) {
+  double disc = b * b - 4.0 * a * c;
+  if (disc < 0.0) return 0;
+  double sq = sqrt(disc);
+  double q = b >= 0.0 ? -(b + sq) / 2.0 : (sq - b) / 2.0;
+  double r1, r2;
+  if (q == 0.0) {
+    r1 = 0.0;
+    r2 = 0.0;
+  } else {
+    r1 = q / a;
+    r2 = c / q;
+  }
+  *t1 = r1 < r2 ? r1 : r2;
+  *t2 = r1 < r2 ? r2 : r1;
+  return 1;
+}
+
+/* First intersection of the ray P0 + t d (t >= 0) with the enclosing surface
+ * from outside.  Returns 1 on a hit with t, the entry face and the outward
+ * unit normal there; the entry point is written to Pb. */
+static int enter(const orc_medium* m, const double* P0, const double* d, double* t,
+                 double* Pb, double* N, int* face) {
+  const double* b = m->b;
+  if (m->bkind == 0) {
+    double tn = -INFINITY, tf = INFINITY;
+    int axis = -1, hi_side = 0;
+    for (int a = 0; a < 3; ++a) {
+      if (d[a] == 0.0) {
+        if (!(P0[a] > b[a] && P0[a] < b[3 + a])) return 0;
+        continue;
+      }
+      double t1 = (b[a] - P0[a]) / d[a], t2 = (b[3 + a] - P0[a]) / d[a];
+      double lo = t1 < t2 ? t1 : t2, hi = t1 < t2 ? t2 : t1;
+      if (lo > tn) {
+        tn = lo;
+        axis = a;
+        hi_side = d[a] < 0.0;
+      }
+      if (hi < tf) tf = hi;
+    }
+    if (axis < 0 || !(tn >= 0.0 && tn < tf)) return 0;
+    *t = tn;
+    for (int a = 0; a < 3; ++a) Pb[a] = P0[a] + tn * d[a];
+    Pb[axis] = hi_side ? b[3 + axis] : b[axis];
+    N[0] = N[1] = N[2] = 0.0;
+    N[axis] = hi_side ? 1.0 : -1.0;
+    *face = 2 * axis + hi_side;
+    return 1;
+  } else if (m->bkind == 1) {
+    double r[3] = {P0[0] - b[0], P0[1] - b[1], P0[2] - b[2]};
+    double t1, t2;
+    if (!quad_roots(dot3(d, d), 2.0 * dot3(r, d), dot3(r, r) - b[3] * b[3], &t1, &t2)) return 0;
+    if (!(t1 >= 0.0)) return 0;
+    *t = t1;
+    for (int a = 0; a < 3; ++a) Pb[a] = P0[a] + t1 * d[a];
+    double q[3] = {Pb[0] - b[0], Pb[1] - b[1], Pb[2] - b[2]};
+    normalize3(q);
+    N[0] = q[0];
+    N[1] = q[1];
+    N[2] = q[2];
+    *face = 0;
+    return 1;
+  } else {
+    double x = P0[0] - b[0], y = P0[1] - b[1];
+    double a2 = d[0] * d[0] + d[1] * d[1];
+    double s1 = -INFINITY, s2 = INFINITY;
+    if (a2 > 0.0) {
+      if (!quad_roots(a2, 2.0 * (x * d[0] + y * d[1]), x * x + y * y - b[2] * b[2], &s1, &s2))
+        return 0;
+      if (!(s1 < s2)) return 0;
+    } else if (!(x * x + y * y < b[2] * b[2])) {
+      return 0;
+    }
+    double z1 = -INFINITY, z2 = INFINITY;
+    if (d[2] != 0.0) {
+      double u1 = (b[3] - P0[2]) / d[2], u2 = (b[4] - P0[2]) / d[2];
+      z1 = u1 < u2 ? u1 : u2;
+      z2 = u1 < u2 ? u2 : u1;
+    } else if (!(P0[2] > b[3] && P0[2] < b[4])) {
+      return 0;
+    }
+    int side = s1 > z1;
+    double tn = side ? s1 : z1, tf = s2 < z2 ? s2 : z2;
+    if (!(tn >= 0.0 && tn < tf)) return 0;
+    *t = tn;
+    for (int a = 0; a < 3; ++a) Pb[a] = P0[a] + tn * d[a];
+    if (side) {
+      N[0] = Pb[0] - b[0];
+      N[1] = Pb[1] - b[1];
+      N[2] = 0.0;
+      normalize3(N);
+      *face = 0;
+    } else {
+      int top = d[2] < 0.0;
+      Pb[2] = top ? b[4] : b[3];
+      N[0] = N[1] = 0.0;
+      N[2] = top ? 1.0 : -1.0;
+      *face = top ? 2 : 1;
+    }
+    return 1;
+  }
+}
+
+/* Crossing of the segment from P (inside, or on the surface) to Q (outside):
+ * the fraction t in [0, 1], the crossing point, the face and the outward
+ * unit normal there. */
+static void exit_root(const orc_medium* m, const double* P, const double* Q, double* t,
+                      double* Pb, double* N, int* face) {
+  const double* b = m->b;
+  double D[3] = {Q[0] - P[0], Q[1] - P[1], Q[2] - P[2]};
+  double best = INFINITY;
+  int bf = 0;
+  if (m->bkind == 0) {
+    for (int a = 0; a < 3; ++a) {
+      if (Q[a] <= b[a]) {
+        double ta = (b[a] - P[a]) / D[a];
+        if (ta < best) {
+          best = ta;
+          bf = 2 * a;
+        }
+      }
+      if (Q[a] >= b[3 + a]) {
+        double ta = (b[3 + a] - P[a]) / D[a];
+        if (ta < best) {
+          best = ta;
+          bf = 2 * a + 1;
+        }
+      }
+    }
+  } else if (m->bkind == 1) {
+    double r[3] = {P[0] - b[0], P[1] - b[1], P[2] - b[2]};
+    double t1, t2;
+    quad_roots(dot3(D, D), 2.0 * dot3(r, D), dot3(r, r) - b[3] * b[3], &t1, &t2);
+    best = t2;
+    bf = 0;
+  } else {
+    double x = P[0] - b[0], y = P[1] - b[1];
+    double qx = Q[0] - b[0], qy = Q[1] - b[1];
+    if (qx * qx + qy * qy >= b[2] * b[2]) {
+      double t1, t2;
+      quad_roots(D[0] * D[0] + D[1] * D[1], 2.0 * (x * D[0] + y * D[1]),
+                 x * x + y * y - b[2] * b[2], &t1, &t2);
+      best = t2;
+      bf = 0;
+    }
+    if (Q[2] <= b[3]) {
+      double ta = (b[3] - P[2]) / D[2];
+      if (ta < best) {
+        best = ta;
+        bf = 1;
+      }
+    }
+    if (Q[2] >= b[4]) {
+      double ta = (b[4] - P[2]) / D[2];
+      if (ta < best) {
+        best = ta;
+        bf = 2;
+      }
+    }
+  }
+  if (!(best > 0.0)) best = 0.0;
+  if (best > 1.0) best = 1.0;
+  *t = best;
+  *face = bf;
+  for (int a = 0; a < 3; ++a) Pb[a] = P[a] + best * D[a];
+  N[0] = N[1] = N[2] = 0.0;
+  if (m->bkind == 0) {
+    int a = bf / 2;
+    Pb[a] = (bf & 1) ? b[3 + a] : b[a];
+    N[a] = (bf & 1) ? 1.0 : -1.0;
+  } else if (m->bkind == 1) {
+    N[0] = Pb[0] - b[0];
+    N[1] = Pb[1] - b[1];
+    N[2] = Pb[2] - b[2];
+    normalize3(N);
+  } else if (bf == 0) {
+    N[0] = Pb[0] - b[0];
+    N[1] = Pb[1] - b[1];
+    normalize3(N);
+  } else {
+    Pb[2] = bf == 2 ? b[4] : b[3];
+    N[2] = bf == 2 ? 1.0 : -1.0;
+  }
+}
+
+/* ------------------------------------------------------------ local rules */
+
+/* Vectorial Snell law, Eq. 8-9: R = mu I + gamma N with
+ * gamma = -mu (N.I) + sgn(N.I) sqrt(D), D = 1 - mu^2 (1 - (N.I)^2), the
+ * positive root; for D <= 0 (Sec. II (v)) the reflection I - 2 (I.N) N.
+ * Returns 1 on total internal reflection.  R is renormalised. */
+static int refract_or_reflect(const double* I, const double* N, double mu, double* R,
+                              double* margin) {
+  double c = dot3(N, I);
+  double D = 1.0 - mu * mu * (1.0 - c * c);
+  /* distance of |N.I| from its critical value sqrt(1 - 1/mu^2), i.e.
+   * D / (mu^2 (|c| + c_crit)); no critical angle exists for mu <= 1 */
+  if (mu > 1.0) {
+    double cc = sqrt(1.0 - 1.0 / (mu * mu));
+    *margin = fabs(D) / (mu * mu * (fabs(c) + cc));
+  } else {
+    *margin = INFINITY;
+  }
+  if (D <= 0.0) {
+    for (int a = 0; a < 3; ++a) R[a] = I[a] - 2.0 * c * N[a];
+    normalize3(R);
+    return 1;
+  }
+  double s = c > 0.0 ? 1.0 : (c < 0.0 ? -1.0 : 0.0);
+  double gamma = -mu * c + s * sqrt(D);
+  for (int a = 0; a < 3; ++a) R[a] = mu * I[a] + gamma * N[a];
+  normalize3(R);
+  return 0;
+}
+
+/* Neumaier-compensated running sum. */
+typedef struct {
+  double s, c;
+} nsum;
+
+static void nsum_add(nsum* a, double x) {
+  double t = a->s + x;
+  if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+  else a->c += (x - t) + a->s;
+  a->s = t;
+}
+
+static double minf(double a, double b) { return a < b ? a : b; }
+
+typedef struct {
+  double P[3], d[3], opl;
+  int exit_id, steps, tir_int, tir_bnd;
+  double mg[ORC_NM];
+} ray_out;
+
+/* Index n_i, gradient and level at P.  For layered media *lvl receives the
+ * level and *u the level coordinate; otherwise *lvl = -1. */
+static void sample(const orc_medium* m, const double* P, double* n, double* g, int* lvl,
+                   double* u) {
+  double f;
+  field_eval(m, P, &f, g);
+  if (m->n_levels > 0) {
+    level_of(m, f, lvl, n, u);
+  } else {
+    *n = f;
+    *lvl = -1;
+    *u = 0.5;
+  }
+}
+
+static void trace_one(const orc_medium* m, const orc_params* prm, const double* o,
+                      const double* d0, ray_out* out, double* path, int64_t cap,
+                      int64_t* plen) {
+  double P[3] = {o[0], o[1], o[2]}, d[3] = {d0[0], d0[1], d0[2]};
+  nsum opl = {0.0, 0.0};
+  int64_t np = 0;
+  memset(out, 0, sizeof(*out));
+  for (int k = 0; k < ORC_NM; ++k) out->mg[k] = INFINITY;
+  out->exit_id = EXIT_INVALID;
+  for (int a = 0; a < 3; ++a) {
+    out->P[a] = o[a];
+    out->d[a] = d0[a];
+  }
+  if (!finite3(P) || !finite3(d) || norm3(d) == 0.0) return;
+  normalize3(d);
+
+  double n_prev, g[3], u, Dm; /* n_prev holds n_{i-1} */
+  int lvl_prev;
+  if (inside(m, P)) {
+    sample(m, P, &n_prev, g, &lvl_prev, &u);
+  } else {
+    double t, Pb[3], NB[3];
+    int face;
+    if (!enter(m, P, d, &t, Pb, NB, &face)) {
+      out->exit_id = EXIT_MISS;
+      for (int a = 0; a < 3; ++a) out->d[a] = d[a];
+      return;
+    }
+    nsum_add(&opl, m->n_ext * t);
+    for (int a = 0; a < 3; ++a) P[a] = Pb[a];
+    double n_b;
+    sample(m, P, &n_b, g, &lvl_prev, &u);
+    double R[3];
+    int tir = refract_or_reflect(d, NB, m->n_ext / n_b, R, &Dm);
+    out->mg[ORC_M_CRIT] = minf(out->mg[ORC_M_CRIT], fabs(Dm));
+    for (int a = 0; a < 3; ++a) d[a] = R[a];
+    if (tir) {
+      out->exit_id = EXIT_ENTRY_REFLECT;
+      goto done;
+    }
+    n_prev = n_b;
+  }
+  if (!(isfinite(n_prev) && n_prev > 0.0)) {
+    out->exit_id = EXIT_INVALID;
+    goto done;
+  }
+  if (path && np < cap) {
+    for (int a = 0; a < 3; ++a) path[3 * np + a] = P[a];
+    ++np;
+  }
+
+  double dopl = prm->dopl;
+  double h = dopl / n_prev; /* Eq. 3 */
+  double Q[3];
+  for (int a = 0; a < 3; ++a) Q[a] = P[a] + h * d[a]; /* Eq. 2 */
+  int steps = 0;
+  out->exit_id = EXIT_MAXSTEPS;
+  while (steps < prm->max_steps) {
+    out->mg[ORC_M_BND] = minf(out->mg[ORC_M_BND], boundary_margin(m, Q, h));
+    if (!inside(m, Q)) {
+      /* Sec. II (i): the step ends on the enclosing surface, where the
+       * surface normal replaces grad n. */
+      double t, Pb[3], NB[3], R[3];
+      int face;
+      exit_root(m, P, Q, &t, Pb, NB, &face);
+      nsum_add(&opl, t * dopl);
+      ++steps;
+      for (int a = 0; a < 3; ++a) P[a] = Pb[a];
+      if (path && np < cap) {
+        for (int a = 0; a < 3; ++a) path[3 * np + a] = P[a];
+        ++np;
+      }
+      int tir = refract_or_reflect(d, NB, n_prev / m->n_ext, R, &Dm);
+      out->mg[ORC_M_CRIT] = minf(out->mg[ORC_M_CRIT], fabs(Dm));
+      for (int a = 0; a < 3; ++a) d[a] = R[a];
+      if (tir) {
+        ++out->tir_bnd;
+        /* Sec. II (v): step Delta L_0 / n_{i-1}; then n(P_b) is the new n_{i-1}. */
+        h = dopl / n_prev;
+        sample(m, P, &n_prev, g, &lvl_prev, &u);
+        if (!(isfinite(n_prev) && n_prev > 0.0)) {
+          out->exit_id = EXIT_INVALID;
+          break;
+        }
+        for (int a = 0; a < 3; ++a) Q[a] = P[a] + h * d[a];
+        continue;
+      }
+      out->exit_id = face;
+      break;
+    }
+    for (int a = 0; a < 3; ++a) P[a] = Q[a];
+    nsum_add(&opl, dopl);
+    ++steps;
+    if (path && np < cap) {
+      for (int a = 0; a < 3; ++a) path[3 * np + a] = P[a];
+      ++np;
+    }
+
+    double n_i;
+    int lvl_i;
+    sample(m, P, &n_i, g, &lvl_i, &u);
+    if (lvl_i >= 0) out->mg[ORC_M_LEVEL] = minf(out->mg[ORC_M_LEVEL], fabs(u - floor(u + 0.5)));
+    if (!(isfinite(n_i) && n_i > 0.0)) {
+      out->exit_id = EXIT_INVALID;
+      break;
+    }
+    double gn = norm3(g);
+    int homogeneous = (lvl_i >= 0 && lvl_i == lvl_prev) || gn == 0.0 || !isfinite(gn);
+    if (homogeneous) {
+      /* Sec. II (ii)/(iii): undefined or vanishing gradient, straight step. */
+      n_prev = n_i;
+      lvl_prev = lvl_i;
+      h = dopl / n_i;
+    } else {
+      double N[3] = {g[0] / gn, g[1] / gn, g[2] / gn}; /* Eq. 5 */
+      double c = dot3(N, d);
+      double mu = n_prev / n_i;
+      out->mg[ORC_M_TAN] = minf(out->mg[ORC_M_TAN], fabs(c));
+      if (c == 0.0) {
+        /* Sec. II (iv): tangential incidence, circular arc of curvature
+         * (dn / h) / n_i along N, with dn from one extra index sample. */
+        double hi = dopl / n_i;
+        double Pn[3] = {P[0] + hi * N[0], P[1] + hi * N[1], P[2] + hi * N[2]};
+        double n2, g2[3], u2;
+        int l2;
+        sample(m, Pn, &n2, g2, &l2, &u2);
+        double k = (n2 - n_i) / (2.0 * n_i);
+        double w = 1.0 - k * k;
+        double a0 = w > 0.0 ? sqrt(w) : 0.0;
+        for (int a = 0; a < 3; ++a) d[a] = a0 * d[a] + k * N[a];
+        normalize3(d);
+        n_prev = n_i;
+        lvl_prev = lvl_i;
+        h = hi;
+      } else {
+        double R[3];
+        int tir = refract_or_reflect(d, N, mu, R, &Dm);
+        out->mg[ORC_M_CRIT] = minf(out->mg[ORC_M_CRIT], fabs(Dm));
+        for (int a = 0; a < 3; ++a) d[a] = R[a];
+        if (tir) {
+          /* Sec. II (v): reflected step of length Delta L_0 / n_{i-1}. */
+          ++out->tir_int;
+          h = dopl / n_prev;
+        } else {
+          h = dopl / n_i;
+        }
+        n_prev = n_i;
+        lvl_prev = lvl_i;
+      }
+    }
+    for (int a = 0; a < 3; ++a) Q[a] = P[a] + h * d[a];
+  }
+  out->steps = steps;
+done:
+  for (int a = 0; a < 3; ++a) {
+    out->P[a] = P[a];
+    out->d[a] = d[a];
+  }
+  out->opl = opl.s + opl.c;
+  if (plen) *plen = np;
+}
+
+/* ------------------------------------------------------------ batch API */
+
+typedef struct {
+  const orc_medium* m;
+  const orc_params* p;
+  int64_t n;
+  const double *o, *d;
+  double *P_out, *d_out, *opl, *margins;
+  int32_t *exit_id, *steps, *tir_int, *tir_bnd;
+  int tid, nt;
+} job;
+
+static void store(const job* j, int64_t i, const ray_out* r) {
+  for (int a = 0; a < 3; ++a) {
+    j->P_out[3 * i + a] = r->P[a];
+    j->d_out[3 * i + a] = r->d[a];
+  }
+  j->opl[i] = r->opl;
+  j->exit_id[i] = r->exit_id;
+  j->steps[i] = r->steps;
+  j->tir_int[i] = r->tir_int;
+  j->tir_bnd[i] = r->tir_bnd;
+  if (j->margins)
+    for (int k = 0; k < ORC_NM; ++k) j->margins[ORC_NM * i + k] = r->mg[k];
+}
+
+static void* worker(void* arg) {
+  job* j = (job*)arg;
+  ray_out r;
+  for (int64_t i = j->tid; i < j->n; i += j->nt) {
+    trace_one(j->m, j->p, j->o + 3 * i, j->d + 3 * i, &r, NULL, 0, NULL);
+    store(j, i, &r);
+  }
+  return NULL;
+}
+
+int orc_trace_batch(const orc_medium* m, const orc_params* p, int64_t n, const double* o,
+                    const double* d, double* P_out, double* d_out, double* opl,
+                    int32_t* exit_id, int32_t* steps, int32_t* tir_int, int32_t* tir_bnd,
+                    double* margins, int32_t nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > 256) nthreads = 256;
+  job jobs[256];
+  pthread_t th[256];
+  for (int t = 0; t < nthreads; ++t) {
+    job j = {m, p, n, o, d, P_out, d_out, opl, margins, exit_id, steps, tir_int, tir_bnd, t,
+             nthreads};
+    jobs[t] = j;
+  }
+  if (nthreads == 1) {
+    worker(&jobs[0]);
+    return 0;
+  }
+  for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, worker, &jobs[t]);
+  for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+  return 0;
+}
+
+int orc_trace_path(const orc_medium* m, const orc_params* p, const double* o, const double* d,
+                   double* P_out, double* d_out, double* opl, int32_t* exit_id,
+                   int32_t* steps, int32_t* tir_int, int32_t* tir_bnd, double* margins,
+                   double* path, int64_t cap, int64_t* path_len) {
+  ray_out r;
+  *path_len = 0;
+  trace_one(m, p, o, d, &r, path, cap, path_len);
+  job j = {m, p, 1, o, d, P_out, d_out, opl, margins, exit_id, steps, tir_int, tir_bnd, 0, 1};
+  store(&j, 0, &r);
+  return 0;
+}

@@ -1,0 +1,391 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form, exact rational arithmetic, a value printed in the paper, an invariant
+or a convergence order.  No GPU is used.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_22655_b300 import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _one(medium, o, d, dopl, max_steps):
+    r = oracle.trace(medium, np.asarray(o, float)[None], np.asarray(d, float)[None], dopl, max_steps, threads=1)
+    return {k: v[0] for k, v in r.items()}
+
+
+# ------------------------------------------------------- homogeneous media
+
+
+def test_homogeneous_normal_incidence_steps_and_opl():
+    """Case (iii): straight steps of dL0/n; exact step count ceil(n L / dL0),
+    OPL = n_ext * 1 + n L, and normal incidence leaves R = I (Eq. 8-9)."""
+    n, L, dopl = 1.5, 0.8227, 0.01
+    m = W.homogeneous_box(n, lo=(-1, -1, 0), hi=(1, 1, L))
+    r = _one(m, (0, 0, -1), (0, 0, 1), dopl, 10000)
+    assert r["exit_id"] == 5
+    assert r["steps"] == math.ceil(n * L / dopl) == 124
+    assert r["opl"] == pytest.approx(1.0 + n * L, rel=1e-14)
+    np.testing.assert_allclose(r["P"], [0, 0, L], atol=1e-15)
+    np.testing.assert_array_equal(r["d"], [0, 0, 1])
+
+
+@pytest.mark.parametrize("theta_deg", [5.0, 30.0, 60.0])
+def test_homogeneous_slab_oblique(theta_deg):
+    """Snell at both faces of a parallel slab: lateral shift L tan(theta_in),
+    exit direction equal to the input direction, OPL = outside + n L / cos."""
+    n, L, dopl = 1.5, 1.0, 1e-3
+    m = W.homogeneous_box(n, lo=(-10, -10, 0), hi=(10, 10, L))
+    th = math.radians(theta_deg)
+    d0 = np.array([math.sin(th), 0.0, math.cos(th)])
+    o = np.array([0.0, 0.0, -1.0])
+    r = _one(m, o, d0, dopl, 100000)
+    th_in = math.asin(math.sin(th) / n)
+    x_entry = math.tan(th)
+    assert r["exit_id"] == 5
+    np.testing.assert_allclose(r["P"], [x_entry + L * math.tan(th_in), 0, L], atol=1e-12)
+    np.testing.assert_allclose(r["d"], d0, atol=1e-14)
+    assert r["opl"] == pytest.approx(1.0 / math.cos(th) + n * L / math.cos(th_in), rel=1e-13)
+
+
+def test_entry_refraction_vector_snell():
+    """Eq. 1: n_ext N x I = n N x R at the entry face (max_steps = 0 stops
+    right after the boundary refraction)."""
+    n = 1.7
+    m = W.homogeneous_box(n, lo=(-10, -10, 0), hi=(10, 10, 5))
+    d0 = np.array([0.3, -0.5, 0.8])
+    d0 /= np.linalg.norm(d0)
+    r = _one(m, (0, 0, -1), d0, 1e-3, 0)
+    assert r["exit_id"] == oracle.EXIT_MAXSTEPS and r["steps"] == 0
+    N = np.array([0, 0, -1.0])
+    np.testing.assert_allclose(1.0 * np.cross(N, d0), n * np.cross(N, r["d"]), atol=1e-15)
+    assert np.dot(r["d"], [0, 0, 1]) > 0  # positive root of Eq. 9: transmitted, not reflected
+
+
+@pytest.mark.parametrize("sign", [+1, -1])
+def test_critical_angle_split(sign):
+    """Sec. II (v): at the +x wall of a homogeneous box (n = 1.5, air
+    outside) a ray 1e-6 rad beyond the critical angle is reflected, one 1e-6
+    rad short of it leaves with n sin(a) = sin(a_out)."""
+    n = 1.5
+    m = W.homogeneous_box(n, lo=(-1, -1, -50), hi=(1, 1, 50))
+    ac = math.asin(1.0 / n)
+    a = ac + sign * 1e-6  # incidence angle on the x wall
+    d0 = np.array([math.cos(a), 0.0, math.sin(a)])
+    r = _one(m, (0, 0, 0), d0, 1e-3, 200000)
+    if sign > 0:
+        assert r["tir_boundary"] >= 1 and r["exit_id"] != 1
+    else:
+        assert r["exit_id"] == 1 and r["tir_boundary"] == 0
+        assert r["d"][2] == pytest.approx(n * math.sin(a), rel=1e-12)
+
+
+def test_boundary_reflection_law():
+    """Sec. II (v) reflection I - 2 (I.N) N at the +x wall, then Snell out of
+    the +z face: the exit direction has d_x = -n cos(a); checked in closed
+    form together with the exit point."""
+    n = 1.5
+    m = W.homogeneous_box(n, lo=(-1, -1, 0), hi=(1, 1, 3))
+    a = math.radians(70.0)  # incidence angle on the x wall, beyond critical (41.8 deg)
+    d0 = np.array([math.cos(a), 0.0, math.sin(a)])
+    r = _one(m, (0, 0, 0.1), d0, 1e-4, 200000)
+    assert r["tir_boundary"] == 1 and r["exit_id"] == 5
+    # after reflection the ray heads (-cos a, 0, sin a); at the z face the
+    # tangential component is scaled by n
+    dx = -n * math.cos(a)
+    np.testing.assert_allclose(r["d"], [dx, 0, math.sqrt(1 - dx * dx)], atol=1e-12)
+    # geometry: wall at x=1 reached after dz = tan(a); top at z = 3
+    z_wall = 0.1 + math.tan(a)
+    x_exit = 1.0 - (3.0 - z_wall) / math.tan(a)
+    np.testing.assert_allclose(r["P"], [x_exit, 0, 3.0], atol=1e-12)
+
+
+def test_miss_entry_reflect_invalid_and_zero_steps():
+    m = W.luneburg_medium()
+    r = _one(m, (2, 0, -1.5), (0, 0, 1), 1e-3, 10)
+    assert r["exit_id"] == oracle.EXIT_MISS and r["steps"] == 0 and r["opl"] == 0
+    dense = W.homogeneous_box(1.0, lo=(-1, -1, 0), hi=(1, 1, 1), n_ext=1.5)
+    a = math.radians(70.0)
+    r = _one(dense, (0, 0, -0.1), (math.sin(a), 0, math.cos(a)), 1e-3, 10)
+    assert r["exit_id"] == oracle.EXIT_ENTRY_REFLECT
+    assert r["d"][2] == pytest.approx(-math.cos(a), abs=1e-15)
+    r = _one(m, (0, 0, -1.5), (float("nan"), 0, 1), 1e-3, 10)
+    assert r["exit_id"] == oracle.EXIT_INVALID
+    r = _one(m, (0, 0, 0.2), (0, 1, 0), 1e-3, 0)
+    assert r["exit_id"] == oracle.EXIT_MAXSTEPS and r["steps"] == 0
+    np.testing.assert_array_equal(r["P"], [0, 0, 0.2])
+
+
+# ----------------------------------------------------- smooth GRIN media
+
+
+def _luneburg_errors(dopl, idx):
+    wl = W.luneburg_workload()
+    rays = wl.rays.subset(idx)
+    r = oracle.trace(wl.medium, rays.origins, rays.dirs, dopl, 200000)
+    o = rays.origins
+    pe = np.stack([o[:, 0], o[:, 1], -np.sqrt(1 - o[:, 0] ** 2 - o[:, 1] ** 2)], 1)
+    ep = np.linalg.norm(r["P"] - [0, 0, 1], axis=1)
+    ed = np.linalg.norm(r["d"] + pe, axis=1)
+    eo = np.abs(r["opl"] - (1.5 + math.pi / 2))
+    return r, ep, ed, eo
+
+
+def test_luneburg_focus_closed_form():
+    """Ray equation with n^2 = 2 - r^2: r(t) = P_e cos t + z sin t, so every
+    ray leaves at (0, 0, 1) along -P_e with total OPL 1.5 + pi/2 from
+    z = -1.5.  VRT is first order (Sec. III), so errors are O(dL0)."""
+    r, ep, ed, eo = _luneburg_errors(1e-3, slice(0, 4096, 5))
+    assert (r["exit_id"] == 0).all()
+    assert ep.max() < 3e-3 and ed.max() < 3e-3 and eo.max() < 3e-3
+
+
+def test_luneburg_first_order_convergence():
+    """Halving dL0 roughly halves the mean exit error (first order, Sec. III)."""
+    idx = slice(0, 4096, 97)
+    e = [np.mean(_luneburg_errors(h, idx)[1]) for h in (1e-3, 5e-4, 2.5e-4)]
+    for a, b in zip(e, e[1:]):
+        assert 1.5 < a / b < 3.0
+
+
+def test_bouguer_invariant_spherical_symmetry():
+    """With N = grad n / |grad n| radial, Eq. 1 gives n_{i-1} (P_i x I_i) =
+    n_i (P_i x R_i), and P_{i+1} x R_i = P_i x R_i: the discrete scheme keeps
+    n(P_i) |P_i x R_i| (the Bouguer invariant of spherically symmetric media)
+    exactly, up to rounding, on every segment of a refracting ray."""
+    m = W.luneburg_medium()
+    for h in (2e-3, 1e-3):
+        res, path = oracle.trace_path(m, (0.3, 0.4, -1.5), (0, 0, 1), h, 100000)
+        assert res["tir_internal"][0] == 0
+        seg = np.diff(path, axis=0)
+        dirs = seg / np.linalg.norm(seg, axis=1, keepdims=True)
+        n, _ = oracle.medium_eval(m, path[:-1])
+        inv = n * np.linalg.norm(np.cross(path[:-1], dirs), axis=1)
+        assert inv[0] == pytest.approx(0.5, abs=1e-15)  # n = 1 at entry, impact parameter 0.5
+        assert np.abs(inv - inv[0]).max() < 1e-12
+
+
+def test_maxwell_fisheye_conjugate_point():
+    """Maxwell fish-eye n = n0 / (1 + r^2): all rays from P0 pass through
+    -P0 / |P0|^2."""
+    m = W.fisheye_medium(n0=2.0, a=1.0, r_bound=20.0)
+    p0 = np.array([0.5, 0.0, 0.0])
+    target = -p0 / np.dot(p0, p0)
+    for th in (0.7, 1.3, 2.1):
+        d0 = np.array([math.cos(th), math.sin(th) * 0.6, math.sin(th) * 0.8])
+        res, path = oracle.trace_path(m, p0, d0, 1e-4, 400000)
+        dist = np.linalg.norm(path - target, axis=1).min()
+        assert dist < 2e-3, (th, dist)
+
+
+def test_fiber_helix_matches_paper_rmse():
+    """Sec. IV: the parabolic-index fiber ray from P0 = (4, -2.6128, -3.0288)
+    through (4, 0, 0) is a helix of radius 4; with dL0 = 1e-4 the paper prints
+    a transverse RMSE (Eq. 23) of 5.0892e-5.  The analytic helix is
+    x = 4 cos(a t), y = 4 sin(a t), z = b t with a = n_c sqrt(2 Delta) / R and
+    b = sqrt(n(4)^2 - k^2), k the transverse optical momentum of the launched
+    ray; the interior length follows from the printed point count."""
+    g = json.load(open(os.path.join(GOLD, "helix_e1.json")))
+    R, nc, D = g["R"], g["nc"], g["Delta"]
+    m = W.fiber_medium(nc=nc, delta=D, radius=R, length=52.1)
+    p0, pi = np.array(g["P0"]), np.array(g["PI"])
+    d0 = (pi - p0) / np.linalg.norm(pi - p0)
+    assert math.degrees(math.acos(d0[2])) == pytest.approx(g["angle_to_z_deg"], abs=5e-3)
+    alpha = nc * math.sqrt(2 * D) / R
+    n4 = nc * math.sqrt(1 - 2 * D * 16 / R ** 2)
+    # transverse optical momentum is conserved through the z = 0 face and the
+    # axial one, b, inside (n has no z dependence)
+    kt = m.n_ext * math.sqrt(1 - d0[2] ** 2)
+    assert kt == pytest.approx(4 * alpha, rel=1e-5)  # helical condition at rho = 4
+    beta = math.sqrt(n4 ** 2 - kt ** 2)
+
+    def rmse(h):
+        res, path = oracle.trace_path(m, p0, d0, h, 3_000_000)
+        t = path[:, 2] / beta
+        e2 = (path[:, 0] - 4 * np.cos(alpha * t)) ** 2 + (path[:, 1] - 4 * np.sin(alpha * t)) ** 2
+        return math.sqrt(e2.mean()), path
+
+    e1, path = rmse(g["dL0"])
+    rho = np.hypot(path[:, 0], path[:, 1])
+    assert np.abs(rho - 4.0).max() < 1e-4
+    assert 0.8 * g["rmse"] < e1 < 1.25 * g["rmse"]
+    e2, _ = rmse(2 * g["dL0"])
+    assert 1.6 < e2 / e1 < 2.4
+
+
+# ------------------------------------------------------------- evaluators
+
+
+def _exact_poly(coeffs, degree, off, scale, P):
+    """Exact rational value and gradient of the normalised polynomial."""
+    x = [(Fraction(P[a]) - Fraction(off[a])) / Fraction(scale[a]) for a in range(3)]
+    v = Fraction(0)
+    g = [Fraction(0)] * 3
+    for c, (i, j, k) in zip(coeffs, W.monomial_exponents(degree)):
+        c = Fraction(c)
+        v += c * x[0] ** i * x[1] ** j * x[2] ** k
+        if i:
+            g[0] += c * i * x[0] ** (i - 1) * x[1] ** j * x[2] ** k
+        if j:
+            g[1] += c * j * x[0] ** i * x[1] ** (j - 1) * x[2] ** k
+        if k:
+            g[2] += c * k * x[0] ** i * x[1] ** j * x[2] ** (k - 1)
+    return float(v), [float(g[a] / Fraction(scale[a])) for a in range(3)]
+
+
+def test_polynomial_evaluator_exact():
+    m = W.freeform_block_medium()
+    pts = np.stack([W.uniform(5, 1, 20, -5, 5), W.uniform(5, 2, 20, -5, 5), W.uniform(5, 3, 20, 0, 20)], 1)
+    n, g = oracle.medium_eval(m, pts)
+    for i in range(len(pts)):
+        v, ge = _exact_poly(m.coeffs, 4, m.off, m.scale, pts[i])
+        assert n[i] == pytest.approx(v, rel=1e-14, abs=1e-15)
+        np.testing.assert_allclose(g[i], ge, rtol=1e-12, atol=1e-15)
+
+
+def test_sqrt_and_recip_forms_central_differences():
+    for m in (W.luneburg_medium(), W.fisheye_medium()):
+        pts = np.array([[0.1, -0.2, 0.3], [0.5, 0.4, -0.2], [-0.3, 0.1, 0.6]])
+        n, g = oracle.medium_eval(m, pts)
+        h = 1e-6
+        for a in range(3):
+            e = np.zeros(3)
+            e[a] = h
+            fd = (oracle.medium_eval(m, pts + e)[0] - oracle.medium_eval(m, pts - e)[0]) / (2 * h)
+            np.testing.assert_allclose(g[:, a], fd, rtol=1e-7, atol=1e-9)
+    m = W.luneburg_medium()
+    n, _ = oracle.medium_eval(m, pts)
+    np.testing.assert_allclose(n, np.sqrt(2 - (pts ** 2).sum(1)), rtol=1e-15)
+
+
+def _quadratic_grid(res=12, h=0.5):
+    q = lambda x, y, z: 1.5 + 0.01 * x - 0.02 * y + 0.015 * z + 0.003 * x * x - 0.002 * x * y + 0.001 * y * z + 0.0025 * z * z
+    x = np.arange(res) * h
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    grid = q(X, Y, Z).astype(np.float32)
+    return grid, q
+
+
+def test_tricubic_reproduces_quadratics_and_nodes():
+    """Catmull-Rom reproduces polynomials of degree <= 2 exactly away from the
+    clamped edges; at nodes it returns the samples."""
+    grid, q = _quadratic_grid()
+    h = 0.5
+    m = W.grid_medium(grid, h, size=h * 11)
+    # reference: the field the float32 samples actually hold is the quadratic
+    # rounded per sample, so compare with a grid built from exactly
+    # representable values: use the float32 samples at nodes
+    nodes = np.array([[2 * h, 3 * h, 4 * h], [5 * h, 5 * h, 7 * h]])
+    n, _ = oracle.medium_eval(m, nodes)
+    np.testing.assert_array_equal(n, [grid[4, 3, 2], grid[7, 5, 5]])
+    pts = np.stack([W.uniform(9, a, 25, 1.5 * h, 9.5 * h) for a in range(3)], 1)
+    n, g = oracle.medium_eval(m, pts)
+    x, y, z = pts.T
+    np.testing.assert_allclose(n, q(x, y, z), atol=5e-7)  # float32 sample rounding
+    gx = 0.01 + 0.006 * x - 0.002 * y
+    gy = -0.02 - 0.002 * x + 0.001 * z
+    gz = 0.015 + 0.001 * y + 0.005 * z
+    np.testing.assert_allclose(g, np.stack([gx, gy, gz], 1), atol=2e-6)
+
+
+def test_tricubic_exact_on_representable_linear_field():
+    """With samples that are exact in float32 the linear field is reproduced
+    to rounding."""
+    res, h = 10, 0.25
+    i = np.arange(res)
+    K, J, I = np.meshgrid(i, i, i, indexing="ij")
+    grid = (1.5 + (I + 2 * J - K) / 1024.0).astype(np.float32)
+    m = W.grid_medium(grid, h, size=h * (res - 1))
+    pts = np.stack([W.uniform(3, a, 30, 1.1 * h, (res - 2.1) * h) for a in range(3)], 1)
+    n, g = oracle.medium_eval(m, pts)
+    u = pts / h
+    np.testing.assert_allclose(n, 1.5 + (u[:, 0] + 2 * u[:, 1] - u[:, 2]) / 1024.0, atol=1e-14)
+    np.testing.assert_allclose(g, np.tile([1 / 1024 / h, 2 / 1024 / h, -1 / 1024 / h], (30, 1)), atol=1e-13)
+
+
+def test_constant_grid_gives_straight_rays():
+    grid = np.full((8, 8, 8), 1.25, dtype=np.float32)
+    m = W.grid_medium(grid, 1.0, size=7.0)
+    d0 = np.array([0.2, 0.1, 1.0])
+    d0 /= np.linalg.norm(d0)
+    r = _one(m, (2, 3, -1), d0, 1e-2, 100000)
+    assert r["exit_id"] == 5
+    np.testing.assert_allclose(r["d"], d0, atol=1e-14)
+
+
+# ---------------------------------------------------------- layered shells
+
+
+@pytest.mark.parametrize("levels", [2, 32])
+def test_layered_planar_shells_conserve_tangential_momentum(levels):
+    """Isoindicial shells that are planes z = const: every crossing obeys
+    Snell with N = z, so n sin(theta) is conserved and a ray leaves the
+    parallel stack along its input direction."""
+    c = W.coeffs_from_terms(1, {(0, 0, 0): 1.5, (0, 0, 1): 0.2})
+    m = W.Medium(kind=W.KIND_POLY, form=W.FORM_LINEAR, degree=1, coeffs=c, off=(0, 0, 1),
+                 scale=(1, 1, 1), n_levels=levels, level_lo=1.3, level_hi=1.7, bkind=W.BOUNDARY_BOX,
+                 bparams=(-50, -50, 0, 50, 50, 2, 0, 0), n_ext=1.0)
+    th = math.radians(35.0)
+    d0 = np.array([math.sin(th) * 0.6, math.sin(th) * 0.8, math.cos(th)])
+    r = _one(m, (0, 0, -1), d0, 1e-3, 100000)
+    assert r["exit_id"] == 5 and r["tir_internal"] == 0
+    np.testing.assert_allclose(r["d"], d0, atol=1e-13)
+
+
+def test_tangent_incidence_first_arc():
+    """Case (iv): with n = 1.5 + 0.1 x and the ray along +y, the first point
+    after the start has N.I = 0 exactly; the next point is
+    P_i + h (sqrt(1 - k^2) I + k N) with k = (n(P_i + h N) - n(P_i)) / (2 n_i)."""
+    c = W.coeffs_from_terms(1, {(0, 0, 0): 1.5, (1, 0, 0): 0.1})
+    m = W.Medium(kind=W.KIND_POLY, form=W.FORM_LINEAR, degree=1, coeffs=c, bkind=W.BOUNDARY_BOX,
+                 bparams=(-1, -1, -1, 1, 1, 1, 0, 0), n_ext=1.0)
+    dopl = 1e-2
+    r = _one(m, (0, 0, 0), (0, 1, 0), dopl, 2)
+    h = dopl / 1.5
+    k = (0.1 * h) / (2 * 1.5)
+    expect = np.array([0.0, h, 0.0]) + h * np.array([k, math.sqrt(1 - k * k), 0.0])
+    np.testing.assert_allclose(r["P"], expect, atol=1e-16)
+    assert r["margins"][oracle.M_TAN] == 0.0
+
+
+def test_layered_level_value_sets_optical_length():
+    """A field of constant 1.52 quantised into 4 shells on [1.3, 1.7] sits in
+    level 2, whose index is the level centre 1.3 + 2.5 * 0.1 = 1.55: the slab
+    then takes ceil(1.55 L / dL0) straight steps and OPL = 1 + 1.55 L."""
+    m = W.Medium(kind=W.KIND_POLY, form=W.FORM_LINEAR, degree=0, coeffs=np.array([1.52]),
+                 n_levels=4, level_lo=1.3, level_hi=1.7, bkind=W.BOUNDARY_BOX,
+                 bparams=(-1, -1, 0, 1, 1, 0.8227, 0, 0), n_ext=1.0)
+    r = _one(m, (0, 0, -1), (0, 0, 1), 0.01, 10000)
+    assert r["exit_id"] == 5
+    assert r["steps"] == math.ceil(1.55 * 0.8227 / 0.01)
+    assert r["opl"] == pytest.approx(1.0 + 1.55 * 0.8227, rel=1e-13)
+
+
+def test_internal_tir_step_length_uses_previous_index():
+    """Sec. II (v): a ray in the n = 1.6 shell meets the n = 1.4 shell at 80
+    deg (critical angle 61 deg); it is reflected at the first point past the
+    plane z = 1 and the reflected step has length dL0 / n_{i-1} = dL0 / 1.6."""
+    c = W.coeffs_from_terms(1, {(0, 0, 0): 1.5, (0, 0, 1): 0.2})
+    m = W.Medium(kind=W.KIND_POLY, form=W.FORM_LINEAR, degree=1, coeffs=c, off=(0, 0, 1),
+                 n_levels=2, level_lo=1.3, level_hi=1.7, bkind=W.BOUNDARY_BOX,
+                 bparams=(-50, -50, 0, 50, 50, 2, 0, 0), n_ext=1.0)
+    a = math.radians(80.0)
+    d0 = np.array([math.sin(a), 0.0, -math.cos(a)])
+    dopl = 1e-3
+    h = dopl / 1.6
+    k_star = math.floor(0.05 / (h * math.cos(a))) + 1  # first point below z = 1 (461)
+    assert 0.2 < 0.05 / (h * math.cos(a)) % 1 < 0.8  # far from an integer: no rounding ambiguity
+    r = _one(m, (0, 0, 1.05), d0, dopl, k_star + 1)
+    assert r["tir_internal"] == 1
+    p_k = np.array([0, 0, 1.05]) + k_star * h * d0
+    expect = p_k + h * np.array([math.sin(a), 0.0, math.cos(a)])
+    np.testing.assert_allclose(r["P"], expect, atol=1e-12)
