@@ -1,0 +1,333 @@
+"""Benchmark: batched VRT trace of the analytic freeform GRIN block.
+
+One step = one grin_trace call of the mixed-precision persistent tracer over
+the whole batch: 1,048,576 rays from a point source 5 mm before a 10x10x20 mm
+block with a degree-4 polynomial index (35 monomials), dL0 = 0.01 mm, at most
+20,000 steps per ray.  Metric: ray-steps/s (sum over rays of interior steps,
+divided by time), with the exit error of the measured run against the plain
+FP64 GPU tracer reported beside it (gate: 2e-5 relative).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference that exists
+for this method) on a bounded strided sample of the same rays.  Under
+torchrun (N > 1) every rank traces its own seeded batch of the same size
+(weak scaling, no collective on the data path) and rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ray-steps/s at ≤2e-5 rel exit error vs plain FP64 GPU path; serve p50/p99 latency"
+UNIT = "ray-steps/s"
+N_RAYS = 1 << 20
+L2_FLUSH_BYTES = 256 << 20
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+
+
+def poly_fma_count(D: int) -> int:
+    """FMAs of the nested-Horner value + gradient evaluation of a total-degree
+    D polynomial in three variables (the kernel's poly_vg)."""
+    f = 0
+    for i in range(D, -1, -1):
+        for j in range(D - i, -1, -1):
+            top = D - i - j
+            f += max(top, 0) + max(top - 1, 0)
+            if j != D - i:
+                f += 2 + (j != D - i - 1)
+        if i != D:
+            f += 3 + (i != D - 1)
+    return f
+
+
+# FP32 FLOPs of one refracting VRT step besides the polynomial (FMA = 2):
+# compensated position update 15, normalised coordinates 6, gradient scale 3,
+# n and 1/n 2, |grad|^2 + rsqrt + N 9, N.I 5, mu / 1-mu^2 / D 10, near-critical
+# band test 3, gamma 3, R = mu I + gamma N 9, renormalisation 9, step length 1.
+STEP_FIXED_FLOPS = 75
+
+
+def flops_per_step(degree_class: int) -> int:
+    return 2 * poly_fma_count(degree_class) + STEP_FIXED_FLOPS
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.rows = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def summary(self):
+        rows = getattr(self, "rows", [])
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_rate(wl, stride: int, threads: int, rays=None):
+    """ray-steps/s of the FP64 oracle on a strided sample of the workload;
+    also returns the sample's indices and oracle results."""
+    import oracle
+    rays = wl.rays if rays is None else rays
+    idx = np.arange(0, rays.n, stride)
+    sub = rays.subset(idx)
+    t0 = time.perf_counter()
+    r = oracle.trace(wl.medium, sub.origins, sub.dirs, wl.dopl, wl.max_steps, threads=threads)
+    dt = time.perf_counter() - t0
+    return float(r["steps"].sum()) / dt, len(idx), dt, idx, r
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2606_22655_b300 import workloads as W
+    wl = W.freeform_workload(N_RAYS)
+    threads = os.cpu_count() or 1
+    stride = args.ref_stride
+    for _ in range(args.warmup):
+        oracle_rate(wl, stride * 4, threads)
+    t0 = time.perf_counter()
+    total_steps = 0.0
+    for k in range(args.steps):
+        rate, n, dt, _, _ = oracle_rate(wl, stride, threads)
+        total_steps += rate * dt
+    wall = time.perf_counter() - t0
+    value = total_steps / wall
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wl.name, "rays_per_step": n, "sample_stride": stride,
+                                        "dopl_mm": wl.dopl, "max_steps": wl.max_steps},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"every {stride}th ray of the {wl.rays.n}-ray batch ({n} rays) per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2606_22655_b300 import tracer
+    from paper_2606_22655_b300 import workloads as W
+    from tests.compare import TAU32, TAU32_GEOM, compare, flagged
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = tracer.Context(local)
+    wl = W.freeform_workload(N_RAYS, ray_seed=W.BASE_SEED + 1 + 1000 * rank)
+    med = tracer.Medium(ctx, wl.medium)
+    rays = tracer.RayBatch.from_numpy(wl.rays.origins, wl.rays.dirs, device=dev, dtype=torch.float32)
+    out = tracer.empty_result(rays.count, dev)
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        tracer.trace(ctx, med, rays, wl.dopl, wl.max_steps, "mixed", stream=stream, out=out)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            flush.zero_()
+            step()
+    torch.cuda.synchronize(dev)
+    steps_per_trace = float(out["steps"].sum().item())
+
+    # timed region: K steps, L2 flushed before each (outside the kernel events)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            r0.record(stream)
+            for k in range(args.steps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                step()
+                launches += ctx.last_launches()
+                ev[k][1].record(stream)
+            r1.record(stream)
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+    region_s = r0.elapsed_time(r1) / 1e3
+    kern_s = [a.elapsed_time(b) / 1e3 for a, b in ev]
+    if ws > 1:
+        t = torch.tensor([region_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        region_s = float(t.item())
+    value = ws * steps_per_trace * args.steps / region_s
+    mean_kern = sum(kern_s) / len(kern_s)
+
+    # CPU baseline (the FP64 oracle on every 16th ray); its decision margins
+    # also flag the ill-conditioned rays for the precision gate
+    cpu = None
+    orc_idx = orc_res = None
+    if ws == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        rays32 = W.Rays(wl.rays.origins.astype(np.float32).astype(np.float64),
+                        wl.rays.dirs.astype(np.float32).astype(np.float64))
+        rate, n, dt, orc_idx, orc_res = oracle_rate(wl, 16, threads, rays32)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"every 16th ray of the {wl.rays.n}-ray batch ({n} rays, {dt:.1f} s)"}
+
+    # precision gate: this run's outputs against the plain FP64 GPU tracer
+    res32 = tracer.to_numpy(out)
+    rays64 = tracer.RayBatch.from_numpy(wl.rays.origins, wl.rays.dirs, device=dev, dtype=torch.float32)
+    out64 = tracer.empty_result(rays64.count, dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        tracer.trace(ctx, med, rays64, wl.dopl, wl.max_steps, "fp64", stream=stream, out=out64)
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    fp64_s = e0.elapsed_time(e1) / 1e3
+    out64f = tracer.empty_result(rays64.count, dev)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        tracer.trace(ctx, med, rays64, wl.dopl, wl.max_steps, "fp64-fast", stream=stream, out=out64f)
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    fast_s = e0.elapsed_time(e1) / 1e3
+    res64 = tracer.to_numpy(out64)
+    gate = compare(res32, res64, wl.l_ref)
+    gate_s = None
+    if orc_res is not None:
+        sub = lambda g: {k: v[orc_idx] for k, v in g.items()}
+        gate_s = compare(sub(res32), sub(res64), wl.l_ref, flagged(orc_res["margins"], TAU32, TAU32_GEOM))
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    hrays = tracer.RayBatch.from_numpy(wl.rays.origins, wl.rays.dirs, device="cpu", dtype=torch.float32, pin=True)
+    hout = tracer.empty_result(hrays.count, "cpu")
+    tracer.trace_host(ctx, med, hrays, wl.dopl, wl.max_steps, "mixed", stream=stream, out=hout)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e2e_steps = 0.0
+    for _ in range(args.steps):
+        tracer.trace_host(ctx, med, hrays, wl.dopl, wl.max_steps, "mixed", stream=stream, out=hout)
+        e2e_steps += float(hout["steps"].sum().item())
+    e2e_s = time.perf_counter() - t0
+    h2d = 6 * 4 * hrays.count
+    d2h = (7 * 8 + 4 * 4) * hrays.count
+
+    if rank != 0:
+        return 0
+    flops_launch = flops_per_step(4) * steps_per_trace
+    achieved = flops_launch / mean_kern / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * region_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "rays": wl.rays.n, "medium": "degree-4 polynomial, 35 monomials",
+                   "dopl_mm": wl.dopl, "max_steps": wl.max_steps, "precision": "fp32-mixed",
+                   "ray_steps_per_step": steps_per_trace,
+                   "l2": "256 MiB buffer zeroed before every step, inside the timed region"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "k_trace_mixed<4,false,false>", "kernel_ms": 1e3 * mean_kern,
+                     "flops_per_ray_step": flops_per_step(4),
+                     "peak_note": "148 SMs x 128 FP32 lanes x 2 FLOP x 2.032 GHz (derived)"},
+        "precision_gate": {
+            "vs": "plain FP64 GPU tracer on the same float32 input rays",
+            "fp64_ms": 1e3 * fp64_s, "fp64_ray_steps_per_s": float(res64["steps"].sum()) / fp64_s,
+            "speedup_vs_fp64": value / ws / (float(res64["steps"].sum()) / fp64_s),
+            "fp64_fast_ms": 1e3 * fast_s, "speedup_vs_fp64_fast": value / ws / (float(res64["steps"].sum()) / fast_s),
+            "all_rays": {"rays": gate["n"], "int_mismatch": gate["int_mismatch_unflagged"],
+                         "p99_rel_pos": gate["pos_p99"], "p99_dir": gate["dir_p99"],
+                         "max_rel_pos": gate["pos"], "max_dir": gate["dir"], "max_rel_opl": gate["opl"]},
+            "oracle_sample": None if gate_s is None else {
+                "rays": gate_s["n"], "flagged": gate_s["n_flagged"],
+                "flag_rule": f"oracle margins: critical distance or min |N.I| < {TAU32}, surface or level distance < {TAU32_GEOM}",
+                "int_mismatch_unflagged": gate_s["int_mismatch_unflagged"],
+                "max_rel_pos": gate_s["pos"], "max_dir": gate_s["dir"], "max_rel_opl": gate_s["opl"],
+                "pass": max(gate_s["pos"], gate_s["dir"], gate_s["opl"]) <= 2e-5}},
+        "e2e": {"value": e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ref-stride", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

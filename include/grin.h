@@ -1,0 +1,207 @@
+/*
+ * grin.h -- C ABI of the B300 Vectorial Ray Tracing (VRT) library.
+ *
+ * The library traces batches of independent rays through a gradient-index
+ * (GRIN) medium bounded by a closed surface in a homogeneous surround, by the
+ * method of Chavez-Islas et al., "Generalized vectorial ray tracing for
+ * optical analysis and design in freeform gradient-index media":
+ *   - each step advances the point by Delta_i = Delta L_0 / n_i along the
+ *     current direction (Sec. II, Eq. 2-3), so every full step adds Delta L_0
+ *     of optical path;
+ *   - at each new point P_i the direction is refracted by the vectorial Snell
+ *     law R = mu I + gamma N (Eq. 1, 8-9) with mu = n(P_{i-1}) / n(P_i) and
+ *     N = grad n / |grad n| (Eq. 5);
+ *   - special cases (Sec. II (i)-(v)): the enclosing-surface normal at the
+ *     boundary, straight steps where grad n is zero or undefined, a circular
+ *     arc at tangential incidence, and total internal reflection (TIR) with a
+ *     step of Delta L_0 / n_{i-1}.
+ *
+ * Conventions shared by every call:
+ *   - every function returns a grin_status (0 = success); nothing throws;
+ *   - per-ray problems (NaN or zero direction, n <= 0) are reported in the
+ *     ray's exit id (GRIN_EXIT_INVALID) and do not fail the batch; reaching
+ *     max_steps is an outcome (GRIN_EXIT_MAXSTEPS), not an error;
+ *   - ray and output arrays of grin_trace are caller-owned DEVICE memory on
+ *     the context's GPU; grin_trace_host takes HOST memory instead; media,
+ *     contexts and servers are library-owned and freed by their destroy call;
+ *   - grin_trace is asynchronous on the caller's CUDA stream (NULL = the
+ *     legacy default stream); kernel faults surface at the next synchronising
+ *     call on that stream;
+ *   - a context and its media may be used from one host thread at a time,
+ *     except the grin_serve_* calls, which are thread-safe.
+ */
+#ifndef GRIN_H
+#define GRIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct grin_ctx_s* grin_ctx;
+typedef struct grin_medium_s* grin_medium;
+typedef struct grin_server_s* grin_server;
+
+typedef enum {
+  GRIN_OK = 0,
+  GRIN_ERR_INVALID_ARG = -1,   /* a NULL pointer, bad enum or size */
+  GRIN_ERR_OOM = -2,           /* device or host allocation failed */
+  GRIN_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+  GRIN_ERR_NOT_IMPLEMENTED = -4,
+  GRIN_ERR_TIMEOUT = -5,       /* a bounded wait ran out */
+  GRIN_ERR_BUSY = -6,          /* admission refused (serving) */
+  GRIN_ERR_NOT_FOUND = -7,     /* unknown job id (serving) */
+  GRIN_ERR_CANCELLED = -8      /* job cancelled (serving) */
+} grin_status;
+
+/* Exit ids written per ray.  Non-negative ids name the face the ray left by:
+ * box faces 0..5 = -x, +x, -y, +y, -z, +z; sphere 0; cylinder side 0, the
+ * z0 end 1, the z1 end 2. */
+enum {
+  GRIN_EXIT_MISS = -1,          /* started outside and never met the surface */
+  GRIN_EXIT_ENTRY_REFLECT = -2, /* totally reflected at the entry point */
+  GRIN_EXIT_MAXSTEPS = -3,      /* max_steps interior steps taken */
+  GRIN_EXIT_INVALID = -4        /* non-finite or zero direction, n <= 0 */
+};
+
+enum { GRIN_MEDIUM_POLY = 0, GRIN_MEDIUM_GRID = 1 };
+enum { GRIN_FORM_LINEAR = 0, GRIN_FORM_SQRT = 1, GRIN_FORM_RECIP = 2 };
+enum { GRIN_BOUNDARY_BOX = 0, GRIN_BOUNDARY_SPHERE = 1, GRIN_BOUNDARY_CYLINDER = 2 };
+enum { GRIN_F32 = 0, GRIN_F64 = 1 };
+enum { GRIN_PREC_FP64 = 0, GRIN_PREC_FP32_MIXED = 1, GRIN_PREC_FP64_FAST = 2 };
+
+#define GRIN_MAX_DEGREE 6
+#define GRIN_MAX_LEVELS 65536
+
+/*
+ * Medium description (copied by grin_medium_create; the caller may free its
+ * buffers afterwards).  The index field n(x, y, z) is either
+ *   - GRIN_MEDIUM_POLY: a polynomial p of degree <= GRIN_MAX_DEGREE in the
+ *     normalised coordinates x' = (x - norm_offset) / norm_scale (the
+ *     normalisation style of the corrector lens, Sec. V), with monomials
+ *     x'^i y'^j z'^k in graded-lex order (total degree ascending; within one
+ *     degree i descending, then j descending), C(degree+3, 3) host doubles
+ *     in `coeffs`; `form` maps p to n: n = p, n = sqrt(p) (Luneburg lens,
+ *     parabolic fiber of Eq. 22) or n = form_c / p (Maxwell fish-eye);
+ *   - GRIN_MEDIUM_GRID: float32 samples grid[(k * ny + j) * nx + i] at
+ *     origin + (i, j, k) * spacing (host memory, or device memory if
+ *     grid_on_device), read by Catmull-Rom tricubic interpolation (Keys 1981)
+ *     with edge-clamped taps and its analytic gradient.
+ * n_levels > 0 turns the field into that many isoindicial shells (the
+ * discretised media of Sec. I and the abstract): level
+ * k = clamp(floor(n_levels (f - level_lo) / (level_hi - level_lo)), 0,
+ * n_levels - 1) has index level_lo + (k + 1/2)(level_hi - level_lo)/n_levels,
+ * the gradient is zero inside a shell and grad f at a level change.
+ * The enclosing surface (Sec. II (i)) is a box (lo[3], hi[3]), a sphere
+ * (centre[3], R) or a z-axis cylinder (cx, cy, R, z0, z1) in `boundary`;
+ * n_ext is the surround index.  Points exactly on the surface are outside.
+ */
+typedef struct {
+  int32_t kind;
+  int32_t form;
+  double form_c;
+  int32_t degree;
+  const double* coeffs;
+  double norm_offset[3];
+  double norm_scale[3];
+  int32_t nx, ny, nz;
+  const float* grid;
+  int32_t grid_on_device;
+  double origin[3];
+  double spacing[3];
+  int32_t n_levels;
+  double level_lo, level_hi;
+  int32_t boundary_kind;
+  double boundary[8];
+  double n_ext;
+} grin_medium_desc;
+
+/* Ray batch: structure-of-arrays origins and directions (directions need not
+ * be unit; they are normalised on entry), `count` rays of `dtype`
+ * (GRIN_F32 or GRIN_F64). */
+typedef struct {
+  const void *ox, *oy, *oz;
+  const void *dx, *dy, *dz;
+  int64_t count;
+  int32_t dtype;
+} grin_rays;
+
+/* Per-ray results, `count` entries each: the final point (the exit point on
+ * the surface for a ray that left), the final direction (refracted into the
+ * surround for a ray that left), the accumulated optical path length (the
+ * exterior approach segment included), the exit id, the number of interior
+ * steps (a step cut short at the surface counts as one), and the numbers of
+ * internal and boundary total internal reflections. */
+typedef struct {
+  double *px, *py, *pz;
+  double *dx, *dy, *dz;
+  double* opl;
+  int32_t* exit_id;
+  int32_t* steps;
+  int32_t* tir_internal;
+  int32_t* tir_boundary;
+} grin_out;
+
+/* dopl = Delta L_0 > 0 (Eq. 3); max_steps >= 0 interior steps per ray;
+ * precision:
+ *   GRIN_PREC_FP64: the plain FP64 tracer, one thread per ray, every formula
+ *     evaluated as written with unfused IEEE operations (polynomials as
+ *     monomial sums), so results do not depend on compiler contraction;
+ *   GRIN_PREC_FP64_FAST: the same steps in FP64 with Horner polynomials and
+ *     fused multiply-adds (differs from GRIN_PREC_FP64 by rounding order);
+ *   GRIN_PREC_FP32_MIXED: FP32 stepping with compensated position sums, the
+ *     index difference n_i - n_{i-1} by the trapezoid rule on grad n (exact to
+ *     O(step^3); point values for layered media), an exact step-count optical
+ *     path, FP64 for the surface root, the boundary refraction and
+ *     near-critical discriminants; persistent ray-pool kernel.
+ * flags must be 0. */
+typedef struct {
+  double dopl;
+  int32_t max_steps;
+  int32_t precision;
+  uint32_t flags;
+} grin_params;
+
+/* Context on one CUDA device (ordinal `device`); makes that device current
+ * on the calling thread. */
+int grin_ctx_create(int device, grin_ctx* out);
+int grin_ctx_destroy(grin_ctx ctx);
+
+/* Static text for a status code. */
+const char* grin_status_string(int status);
+
+/* Number of monomials of a polynomial of the given total degree. */
+int grin_poly_terms(int degree);
+
+/* Validate and copy a medium description to the device.  Errors:
+ * GRIN_ERR_INVALID_ARG for a bad kind, form, degree, grid size, spacing,
+ * scale, level range or boundary; GRIN_ERR_OOM / GRIN_ERR_CUDA on device
+ * failures (nothing is leaked). */
+int grin_medium_create(grin_ctx ctx, const grin_medium_desc* desc, grin_medium* out);
+int grin_medium_destroy(grin_medium medium);
+/* Device bytes the medium holds (its sample grid, if any). */
+int grin_medium_device_bytes(grin_medium medium, size_t* bytes);
+
+/* Trace rays->count rays (device SoA) into out (device SoA), asynchronously
+ * on `cuda_stream`.  count == 0 is a no-op.  Errors: GRIN_ERR_INVALID_ARG
+ * for NULL pointers, count < 0, dopl <= 0 or non-finite, max_steps < 0, bad
+ * precision or dtype; GRIN_ERR_CUDA if the launch fails. */
+int grin_trace(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
+               const grin_params* params, const grin_out* out, void* cuda_stream);
+
+/* Same as grin_trace with rays and out in HOST memory: the library copies the
+ * rays to context-owned device buffers, traces, copies the results back and
+ * synchronises `cuda_stream` before returning. */
+int grin_trace_host(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
+                    const grin_params* params, const grin_out* out, void* cuda_stream);
+
+/* Kernel launches made by the last grin_trace / grin_trace_host call on this
+ * context (for accounting). */
+int grin_ctx_last_launches(grin_ctx ctx, int32_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRIN_H */

@@ -1,0 +1,96 @@
+"""ctypes declarations of the C ABI in include/grin.h and the library loader.
+
+The library is the in-tree build paper_2606_22655_b300/lib/libgrin_vrt.so; if
+it is missing, loading raises (there is no fallback implementation).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libgrin_vrt.so")
+
+GRIN_OK = 0
+STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA runtime error",
+          -4: "not implemented", -5: "timed out", -6: "busy", -7: "not found", -8: "cancelled"}
+EXIT_MISS, EXIT_ENTRY_REFLECT, EXIT_MAXSTEPS, EXIT_INVALID = -1, -2, -3, -4
+F32, F64 = 0, 1
+PREC_FP64, PREC_FP32_MIXED, PREC_FP64_FAST = 0, 1, 2
+
+_d3 = ctypes.c_double * 3
+_vp = ctypes.c_void_p
+
+
+class MediumDesc(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("form", ctypes.c_int32), ("form_c", ctypes.c_double),
+        ("degree", ctypes.c_int32), ("coeffs", ctypes.POINTER(ctypes.c_double)),
+        ("norm_offset", _d3), ("norm_scale", _d3),
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("grid", _vp), ("grid_on_device", ctypes.c_int32),
+        ("origin", _d3), ("spacing", _d3),
+        ("n_levels", ctypes.c_int32), ("level_lo", ctypes.c_double), ("level_hi", ctypes.c_double),
+        ("boundary_kind", ctypes.c_int32), ("boundary", ctypes.c_double * 8),
+        ("n_ext", ctypes.c_double),
+    ]
+
+
+class Rays(ctypes.Structure):
+    _fields_ = [("ox", _vp), ("oy", _vp), ("oz", _vp), ("dx", _vp), ("dy", _vp), ("dz", _vp),
+                ("count", ctypes.c_int64), ("dtype", ctypes.c_int32)]
+
+
+class Out(ctypes.Structure):
+    _fields_ = [("px", _vp), ("py", _vp), ("pz", _vp), ("dx", _vp), ("dy", _vp), ("dz", _vp),
+                ("opl", _vp), ("exit_id", _vp), ("steps", _vp), ("tir_internal", _vp),
+                ("tir_boundary", _vp)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("dopl", ctypes.c_double), ("max_steps", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libgrin_vrt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                           "(run python -m paper_2606_22655_b300.build)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    sig = {
+        "grin_ctx_create": (ctypes.c_int, [ctypes.c_int, P(_vp)]),
+        "grin_ctx_destroy": (ctypes.c_int, [_vp]),
+        "grin_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "grin_poly_terms": (ctypes.c_int, [ctypes.c_int]),
+        "grin_medium_create": (ctypes.c_int, [_vp, P(MediumDesc), P(_vp)]),
+        "grin_medium_destroy": (ctypes.c_int, [_vp]),
+        "grin_medium_device_bytes": (ctypes.c_int, [_vp, P(ctypes.c_size_t)]),
+        "grin_trace": (ctypes.c_int, [_vp, _vp, P(Rays), P(Params), P(Out), _vp]),
+        "grin_trace_host": (ctypes.c_int, [_vp, _vp, P(Rays), P(Params), P(Out), _vp]),
+        "grin_ctx_last_launches": (ctypes.c_int, [_vp, P(ctypes.c_int32)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class GrinError(RuntimeError):
+    def __init__(self, call: str, status: int):
+        super().__init__(f"{call} failed: {STATUS.get(status, status)} ({status})")
+        self.status = status
+
+
+def check(call: str, status: int) -> None:
+    if status != GRIN_OK:
+        raise GrinError(call, status)

@@ -1,0 +1,403 @@
+// grin_capi.cu -- the C ABI declared in include/grin.h: contexts, media,
+// argument checking and dispatch to the tracing kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "grin_device.cuh"
+#include "grin_internal.h"
+
+using grin::DevMedium;
+
+namespace {
+
+constexpr int kQueueSlots = 4096;
+
+}  // namespace
+
+struct grin_ctx_s {
+  int device = 0;
+  int sm_count = 0;
+  // One 8-byte ray-queue counter per trace call, taken round robin, so calls
+  // on different streams do not share a counter while fewer than kQueueSlots
+  // are in flight.
+  unsigned long long* queues = nullptr;
+  int next_queue = 0;
+  int last_launches = 0;
+  // device staging for grin_trace_host (grown on demand)
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+};
+
+struct grin_medium_s {
+  grin_ctx ctx = nullptr;
+  DevMedium dm{};
+  float* grid_dev = nullptr;
+  size_t grid_bytes = 0;
+};
+
+extern "C" {
+
+const char* grin_status_string(int status) {
+  switch (status) {
+    case GRIN_OK: return "ok";
+    case GRIN_ERR_INVALID_ARG: return "invalid argument";
+    case GRIN_ERR_OOM: return "out of memory";
+    case GRIN_ERR_CUDA: return "CUDA runtime error";
+    case GRIN_ERR_NOT_IMPLEMENTED: return "not implemented";
+    case GRIN_ERR_TIMEOUT: return "timed out";
+    case GRIN_ERR_BUSY: return "busy";
+    case GRIN_ERR_NOT_FOUND: return "not found";
+    case GRIN_ERR_CANCELLED: return "cancelled";
+    default: return "unknown status";
+  }
+}
+
+int grin_poly_terms(int degree) {
+  if (degree < 0 || degree > GRIN_MAX_DEGREE) return 0;
+  return (degree + 1) * (degree + 2) * (degree + 3) / 6;
+}
+
+int grin_ctx_create(int device, grin_ctx* out) {
+  if (!out) return GRIN_ERR_INVALID_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess) return GRIN_ERR_CUDA;
+  if (device < 0 || device >= n) return GRIN_ERR_INVALID_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return GRIN_ERR_CUDA;
+  grin_ctx c = new (std::nothrow) grin_ctx_s;
+  if (!c) return GRIN_ERR_OOM;
+  c->device = device;
+  if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete c;
+    return GRIN_ERR_CUDA;
+  }
+  if (cudaMalloc(&c->queues, kQueueSlots * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return GRIN_ERR_OOM;
+  }
+  *out = c;
+  return GRIN_OK;
+}
+
+int grin_ctx_destroy(grin_ctx ctx) {
+  if (!ctx) return GRIN_ERR_INVALID_ARG;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  cudaFree(ctx->queues);
+  if (ctx->stage) cudaFree(ctx->stage);
+  delete ctx;
+  return GRIN_OK;
+}
+
+int grin_ctx_last_launches(grin_ctx ctx, int32_t* launches) {
+  if (!ctx || !launches) return GRIN_ERR_INVALID_ARG;
+  *launches = ctx->last_launches;
+  return GRIN_OK;
+}
+
+static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+int grin_medium_create(grin_ctx ctx, const grin_medium_desc* d, grin_medium* out) {
+  if (!ctx || !d || !out) return GRIN_ERR_INVALID_ARG;
+  *out = nullptr;
+  DevMedium m;
+  std::memset(&m, 0, sizeof(m));
+  m.kind = d->kind;
+  m.form = d->form;
+  m.n_levels = d->n_levels;
+  m.bkind = d->boundary_kind;
+  m.n_ext = d->n_ext;
+  m.form_c = d->form_c;
+  if (!finite_pos(d->n_ext)) return GRIN_ERR_INVALID_ARG;
+  if (d->kind != GRIN_MEDIUM_POLY && d->kind != GRIN_MEDIUM_GRID) return GRIN_ERR_INVALID_ARG;
+  if (d->n_levels < 0 || d->n_levels > GRIN_MAX_LEVELS) return GRIN_ERR_INVALID_ARG;
+  if (d->n_levels > 0 && !(std::isfinite(d->level_lo) && std::isfinite(d->level_hi) &&
+                           d->level_hi > d->level_lo))
+    return GRIN_ERR_INVALID_ARG;
+  for (int k = 0; k < 8; ++k)
+    if (!std::isfinite(d->boundary[k])) return GRIN_ERR_INVALID_ARG;
+  const double* b = d->boundary;
+  switch (d->boundary_kind) {
+    case GRIN_BOUNDARY_BOX:
+      if (!(b[0] < b[3] && b[1] < b[4] && b[2] < b[5])) return GRIN_ERR_INVALID_ARG;
+      break;
+    case GRIN_BOUNDARY_SPHERE:
+      if (!(b[3] > 0.0)) return GRIN_ERR_INVALID_ARG;
+      break;
+    case GRIN_BOUNDARY_CYLINDER:
+      if (!(b[2] > 0.0 && b[3] < b[4])) return GRIN_ERR_INVALID_ARG;
+      break;
+    default:
+      return GRIN_ERR_INVALID_ARG;
+  }
+  std::memcpy(m.b, b, sizeof(m.b));
+
+  std::vector<float> samples;
+  if (d->kind == GRIN_MEDIUM_POLY) {
+    if (d->degree < 0 || d->degree > GRIN_MAX_DEGREE || !d->coeffs) return GRIN_ERR_INVALID_ARG;
+    if (d->form < GRIN_FORM_LINEAR || d->form > GRIN_FORM_RECIP) return GRIN_ERR_INVALID_ARG;
+    if (d->form == GRIN_FORM_RECIP && !std::isfinite(d->form_c)) return GRIN_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; ++k) {
+      if (!std::isfinite(d->norm_offset[k]) || !std::isfinite(d->norm_scale[k]) ||
+          d->norm_scale[k] == 0.0)
+        return GRIN_ERR_INVALID_ARG;
+      m.off[k] = d->norm_offset[k];
+      m.inv_scale[k] = 1.0 / d->norm_scale[k];
+    }
+    m.pclass = d->degree <= 2 ? grin::kPoly2 : (d->degree <= 4 ? grin::kPoly4 : grin::kPoly6);
+    const int D = m.pclass;
+    // graded-lex input: kept as is (zero padded to class D) and scattered
+    // into the Horner layout of class D
+    int idx = 0;
+    for (int s = 0; s <= d->degree; ++s)
+      for (int i = s; i >= 0; --i)
+        for (int j = s - i; j >= 0; --j) {
+          double c = d->coeffs[idx];
+          if (!std::isfinite(c)) return GRIN_ERR_INVALID_ARG;
+          m.cglex[idx++] = c;
+          m.c64[grin::hidx(D, i, j, s - i - j)] = c;
+        }
+    for (int k = 0; k < 3; ++k) m.scale[k] = d->norm_scale[k];
+    const double c0 = m.c64[0];  // hidx(D, 0, 0, 0) == 0
+    float base_f = 1.0f;
+    if (d->form == GRIN_FORM_LINEAR) base_f = (float)c0;
+    else if (d->form == GRIN_FORM_SQRT && c0 > 0.0) base_f = (float)std::sqrt(c0);
+    else if (d->form == GRIN_FORM_RECIP && c0 != 0.0 && std::isfinite(d->form_c / c0))
+      base_f = (float)(d->form_c / c0);
+    if (!(std::isfinite(base_f) && base_f > 0.0f)) base_f = 1.0f;
+    m.base_f = base_f;
+    m.base = (double)base_f;
+    for (int k = 0; k < grin::kMaxTerms; ++k) m.c32[k] = (float)m.c64[k];
+    if (d->form == GRIN_FORM_LINEAR) m.c32[0] = (float)(c0 - m.base);
+    else if (d->form == GRIN_FORM_SQRT) m.c32[0] = (float)(c0 - m.base * m.base);
+  } else {
+    if (!d->grid || d->nx < 1 || d->ny < 1 || d->nz < 1) return GRIN_ERR_INVALID_ARG;
+    const int64_t cnt = (int64_t)d->nx * d->ny * d->nz;
+    if (cnt >= (int64_t(1) << 31)) return GRIN_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; ++k) {
+      if (!finite_pos(d->spacing[k]) || !std::isfinite(d->origin[k])) return GRIN_ERR_INVALID_ARG;
+      m.origin[k] = d->origin[k];
+      m.spacing[k] = d->spacing[k];
+      m.inv_spacing[k] = 1.0 / d->spacing[k];
+    }
+    m.nx = d->nx;
+    m.ny = d->ny;
+    m.nz = d->nz;
+    try {
+      samples.resize((size_t)cnt);
+    } catch (...) {
+      return GRIN_ERR_OOM;
+    }
+    if (d->grid_on_device) {
+      if (cudaMemcpy(samples.data(), d->grid, (size_t)cnt * sizeof(float), cudaMemcpyDeviceToHost) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        return GRIN_ERR_INVALID_ARG;
+      }
+    } else {
+      std::memcpy(samples.data(), d->grid, (size_t)cnt * sizeof(float));
+    }
+    float lo = INFINITY, hi = -INFINITY;
+    for (float v : samples) {
+      if (!std::isfinite(v)) return GRIN_ERR_INVALID_ARG;
+      lo = std::min(lo, v);
+      hi = std::max(hi, v);
+    }
+    // FP32 interpolation subtracts this value from every tap (exact for
+    // samples within a factor two of it), the samples stay as given
+    float base_f = (float)(0.5 * ((double)lo + (double)hi));
+    if (!(std::isfinite(base_f) && base_f != 0.0f)) base_f = 1.0f;
+    m.base_f = base_f;
+    m.base = (double)base_f;
+  }
+  if (d->n_levels > 0) {
+    m.lvl_lo = d->level_lo;
+    m.lvl_hi = d->level_hi;
+    m.lvl_span = d->level_hi - d->level_lo;
+    m.lvl_lo_rel_f = (float)(d->level_lo - m.base);
+    m.lvl_scale_f = (float)((double)d->n_levels / m.lvl_span);
+    m.lvl_step_f = (float)(m.lvl_span / (double)d->n_levels);
+  }
+  m.form_c_f = (float)m.form_c;
+  m.n_ext_f = (float)m.n_ext;
+  for (int k = 0; k < 3; ++k) {
+    m.off_f[k] = (float)m.off[k];
+    m.inv_scale_f[k] = (float)m.inv_scale[k];
+    m.origin_f[k] = (float)m.origin[k];
+    m.inv_spacing_f[k] = (float)m.inv_spacing[k];
+  }
+  for (int k = 0; k < 8; ++k) m.b_f[k] = (float)m.b[k];
+
+  grin_medium med = new (std::nothrow) grin_medium_s;
+  if (!med) return GRIN_ERR_OOM;
+  med->ctx = ctx;
+  if (d->kind == GRIN_MEDIUM_GRID) {
+    cudaSetDevice(ctx->device);
+    med->grid_bytes = samples.size() * sizeof(float);
+    if (cudaMalloc(&med->grid_dev, med->grid_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      delete med;
+      return GRIN_ERR_OOM;
+    }
+    if (cudaMemcpy(med->grid_dev, samples.data(), med->grid_bytes, cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      cudaFree(med->grid_dev);
+      delete med;
+      return GRIN_ERR_CUDA;
+    }
+    m.grid = med->grid_dev;
+  }
+  med->dm = m;
+  *out = med;
+  return GRIN_OK;
+}
+
+int grin_medium_destroy(grin_medium medium) {
+  if (!medium) return GRIN_ERR_INVALID_ARG;
+  if (medium->grid_dev) {
+    cudaSetDevice(medium->ctx->device);
+    cudaDeviceSynchronize();
+    cudaFree(medium->grid_dev);
+  }
+  delete medium;
+  return GRIN_OK;
+}
+
+int grin_medium_device_bytes(grin_medium medium, size_t* bytes) {
+  if (!medium || !bytes) return GRIN_ERR_INVALID_ARG;
+  *bytes = medium->grid_bytes;
+  return GRIN_OK;
+}
+
+static int check_trace_args(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
+                            const grin_params* p, const grin_out* out) {
+  if (!ctx || !medium || !rays || !p || !out) return GRIN_ERR_INVALID_ARG;
+  if (medium->ctx != ctx) return GRIN_ERR_INVALID_ARG;
+  if (rays->count < 0) return GRIN_ERR_INVALID_ARG;
+  if (rays->dtype != GRIN_F32 && rays->dtype != GRIN_F64) return GRIN_ERR_INVALID_ARG;
+  if (!finite_pos(p->dopl) || p->max_steps < 0 || p->flags != 0) return GRIN_ERR_INVALID_ARG;
+  if (p->precision != GRIN_PREC_FP64 && p->precision != GRIN_PREC_FP32_MIXED &&
+      p->precision != GRIN_PREC_FP64_FAST)
+    return GRIN_ERR_INVALID_ARG;
+  if (rays->count == 0) return GRIN_OK;
+  if (!rays->ox || !rays->oy || !rays->oz || !rays->dx || !rays->dy || !rays->dz)
+    return GRIN_ERR_INVALID_ARG;
+  if (!out->px || !out->py || !out->pz || !out->dx || !out->dy || !out->dz || !out->opl ||
+      !out->exit_id || !out->steps || !out->tir_internal || !out->tir_boundary)
+    return GRIN_ERR_INVALID_ARG;
+  return GRIN_OK;
+}
+
+int grin_trace(grin_ctx ctx, grin_medium medium, const grin_rays* rays, const grin_params* p,
+               const grin_out* out, void* cuda_stream) {
+  int st = check_trace_args(ctx, medium, rays, p, out);
+  if (st != GRIN_OK) return st;
+  ctx->last_launches = 0;
+  if (rays->count == 0) return GRIN_OK;
+  grin::TraceArgs a;
+  a.ox = rays->ox;
+  a.oy = rays->oy;
+  a.oz = rays->oz;
+  a.dx = rays->dx;
+  a.dy = rays->dy;
+  a.dz = rays->dz;
+  a.count = rays->count;
+  a.dtype = rays->dtype;
+  a.px = out->px;
+  a.py = out->py;
+  a.pz = out->pz;
+  a.ux = out->dx;
+  a.uy = out->dy;
+  a.uz = out->dz;
+  a.opl = out->opl;
+  a.exit_id = out->exit_id;
+  a.steps = out->steps;
+  a.tir_i = out->tir_internal;
+  a.tir_b = out->tir_boundary;
+  a.dopl = p->dopl;
+  a.max_steps = p->max_steps;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int rc;
+  if (p->precision == GRIN_PREC_FP64) {
+    rc = grin::launch_fp64(medium->dm, a, s, ctx->sm_count);
+  } else if (p->precision == GRIN_PREC_FP64_FAST) {
+    rc = grin::launch_fp64_fast(medium->dm, a, s, ctx->sm_count);
+  } else {
+    unsigned long long* q = ctx->queues + ctx->next_queue;
+    ctx->next_queue = (ctx->next_queue + 1) % kQueueSlots;
+    rc = grin::launch_mixed(medium->dm, a, q, s, ctx->sm_count);
+  }
+  if (rc < 0) return rc;
+  ctx->last_launches = rc;
+  return GRIN_OK;
+}
+
+int grin_trace_host(grin_ctx ctx, grin_medium medium, const grin_rays* rays, const grin_params* p,
+                    const grin_out* out, void* cuda_stream) {
+  int st = check_trace_args(ctx, medium, rays, p, out);
+  if (st != GRIN_OK) return st;
+  ctx->last_launches = 0;
+  const int64_t n = rays->count;
+  if (n == 0) return GRIN_OK;
+  const size_t esz = rays->dtype == GRIN_F64 ? 8 : 4;
+  const size_t in_bytes = 6 * esz * (size_t)n;
+  const size_t out_bytes = (7 * 8 + 4 * 4) * (size_t)n;
+  const size_t need = in_bytes + out_bytes + 256;
+  if (ctx->stage_bytes < need) {
+    if (ctx->stage) {
+      cudaDeviceSynchronize();
+      cudaFree(ctx->stage);
+      ctx->stage = nullptr;
+      ctx->stage_bytes = 0;
+    }
+    if (cudaMalloc(&ctx->stage, need) != cudaSuccess) {
+      cudaGetLastError();
+      return GRIN_ERR_OOM;
+    }
+    ctx->stage_bytes = need;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  char* base = (char*)ctx->stage;
+  const void* hin[6] = {rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz};
+  const void* din[6];
+  for (int k = 0; k < 6; ++k) {
+    din[k] = base + k * esz * (size_t)n;
+    if (cudaMemcpyAsync((void*)din[k], hin[k], esz * (size_t)n, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+      return GRIN_ERR_CUDA;
+  }
+  char* ob = base + in_bytes;
+  double* dd[7];
+  for (int k = 0; k < 7; ++k) dd[k] = (double*)(ob + k * 8 * (size_t)n);
+  int32_t* di[4];
+  for (int k = 0; k < 4; ++k) di[k] = (int32_t*)(ob + 56 * (size_t)n + k * 4 * (size_t)n);
+  grin_rays dr = *rays;
+  dr.ox = din[0];
+  dr.oy = din[1];
+  dr.oz = din[2];
+  dr.dx = din[3];
+  dr.dy = din[4];
+  dr.dz = din[5];
+  grin_out dout = {dd[0], dd[1], dd[2], dd[3], dd[4], dd[5], dd[6], di[0], di[1], di[2], di[3]};
+  st = grin_trace(ctx, medium, &dr, p, &dout, cuda_stream);
+  if (st != GRIN_OK) return st;
+  double* hd[7] = {out->px, out->py, out->pz, out->dx, out->dy, out->dz, out->opl};
+  int32_t* hi[4] = {out->exit_id, out->steps, out->tir_internal, out->tir_boundary};
+  for (int k = 0; k < 7; ++k)
+    if (cudaMemcpyAsync(hd[k], dd[k], 8 * (size_t)n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return GRIN_ERR_CUDA;
+  for (int k = 0; k < 4; ++k)
+    if (cudaMemcpyAsync(hi[k], di[k], 4 * (size_t)n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return GRIN_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return GRIN_ERR_CUDA;
+  return GRIN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,64 @@
+// grin_internal.h -- device-side medium record and launch entry points shared
+// by the C ABI (grin_capi.cu) and the kernels (trace_fp64.cu, trace_mixed.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "grin.h"
+
+namespace grin {
+
+// Largest supported polynomial: C(GRIN_MAX_DEGREE + 3, 3) coefficients.
+constexpr int kMaxTerms = 84;
+
+// Polynomial evaluators are instantiated for these total degrees; a medium
+// of lower degree is zero-padded to the next class.
+enum PolyClass : int32_t { kPoly2 = 2, kPoly4 = 4, kPoly6 = 6 };
+
+// Everything a kernel needs to evaluate n, grad n and the boundary, passed by
+// value as a kernel parameter (it lives in the constant bank, so every lane
+// reads the same coefficient in one broadcast).
+struct DevMedium {
+  int32_t kind;      // GRIN_MEDIUM_POLY / GRIN_MEDIUM_GRID
+  int32_t form;      // GRIN_FORM_*
+  int32_t pclass;    // PolyClass of the coefficient layout
+  int32_t n_levels;  // 0: continuous
+  int32_t bkind;     // GRIN_BOUNDARY_*
+  int32_t nx, ny, nz;
+  double form_c, n_ext;
+  // Index offset: the FP32 path carries nu = n - base so that the difference
+  // of successive indices (which drives each refraction) keeps its bits.
+  double base;
+  double off[3], inv_scale[3];
+  double origin[3], inv_spacing[3];
+  double lvl_lo, lvl_hi, lvl_span;  // level_lo, level_hi, level_hi - level_lo
+  double b[8];                    // boundary parameters (grin_medium_desc)
+  const float* grid;              // device samples (x fastest)
+  double scale[3], spacing[3];    // as given (the plain FP64 tracer divides)
+  double cglex[kMaxTerms];        // coefficients in graded-lex order, zero padded
+  double c64[kMaxTerms];          // coefficients in Horner layout (see hidx)
+  float c32[kMaxTerms];           // same, constant term shifted for nu
+  float base_f, form_c_f, n_ext_f;
+  float off_f[3], inv_scale_f[3], origin_f[3], inv_spacing_f[3];
+  float lvl_lo_rel_f, lvl_scale_f, lvl_step_f;  // lo - base, L / span, span / L
+  float b_f[8];
+};
+
+struct TraceArgs {
+  const void *ox, *oy, *oz, *dx, *dy, *dz;
+  int64_t count;
+  int32_t dtype;  // GRIN_F32 / GRIN_F64
+  double *px, *py, *pz, *ux, *uy, *uz, *opl;
+  int32_t *exit_id, *steps, *tir_i, *tir_b;
+  double dopl;
+  int32_t max_steps;
+};
+
+// Number of kernel launches made; negative grin_status on failure.
+int launch_fp64(const DevMedium& m, const TraceArgs& a, cudaStream_t s, int sm_count);
+int launch_fp64_fast(const DevMedium& m, const TraceArgs& a, cudaStream_t s, int sm_count);
+int launch_mixed(const DevMedium& m, const TraceArgs& a, unsigned long long* queue,
+                 cudaStream_t s, int sm_count);
+
+}  // namespace grin

@@ -1,0 +1,449 @@
+// trace_mixed.cu -- mixed-precision persistent ray-pool VRT tracer.
+//
+// The VRT step (Chavez-Islas et al., Sec. II; Eq. 1-9) runs in FP32:
+//   - the point is kept as an unevaluated sum ph + pl of two floats and each
+//     step's increment h d is added with Dekker's Fast2Sum, so rounding does
+//     not pile up over thousands of steps;
+//   - the unit direction is kept the same way (dh + dl): a refraction adds
+//     the small vector R - I = gamma N - (1 - mu) I, a reflection -2 c N, by
+//     Knuth's TwoSum, so the direction does not random-walk by one FP32
+//     rounding per step (that walk, a few 1e-6 after 3000 steps, would decide
+//     on which side of a turning point of n the discrete map kinks); R is a
+//     unit vector whenever I and N are, so no per-step renormalisation;
+//   - the index difference n_i - n_{i-1}, which sets 1 - mu and hence the
+//     whole deflection, is taken by the trapezoid rule on grad n along the
+//     step, (grad n_{i-1} + grad n_i) . (P_i - P_{i-1}) / 2, which equals the
+//     point difference to O(step^3) but keeps FP32 relative accuracy where
+//     the difference of two rounded indices would not (near turning points,
+//     where gamma ~ sqrt(D) amplifies any error in 1 - mu^2); layered media
+//     use the exact level values; the index itself is carried as
+//     nu = n - base;
+//   - the refraction uses gamma = sgn(c) (1 - mu^2) / (sqrt(D) + mu |c|), an
+//     algebraically equal form of Eq. 9 without the cancellation of
+//     -mu c + sgn(c) sqrt(D); D = (1 - mu^2) + mu^2 c^2;
+//   - when |D| is within a few FP32 roundings of zero (near critical or
+//     grazing incidence) the discriminant and gamma are recomputed in FP64;
+//   - the optical path is exact: dL0 times the count of full steps, plus the
+//     FP64 exterior segment and the fractions of steps cut at the surface;
+//   - everything at the enclosing surface (the entry intersection and
+//     refraction, the exit root, boundary refraction or TIR) runs in FP64.
+// Work distribution: a persistent grid sized to the resident capacity of the
+// GPU; each warp keeps 32 rays in flight and, every kStepQuantum steps, lanes
+// whose ray finished claim new rays from a global counter (one atomicAdd per
+// warp, ranks from a ballot), so long and short rays do not idle lanes.
+#include "grin_device.cuh"
+
+namespace grin {
+
+constexpr int kStepQuantum = 32;
+constexpr float kCritBand = 1.0e-5f;  // relative |D| below which FP64 decides
+
+template <int PC, bool GRID, bool LAYERED>
+struct Field32 {
+  // nu = n - base (after layering), the gradient of the smooth field, level.
+  static __device__ __forceinline__ void eval(const DevMedium& m, float px, float py, float pz,
+                                              float& nu, float& gx, float& gy, float& gz,
+                                              int& lvl) {
+    float f;
+    if (GRID) {
+      float u[3] = {(px - m.origin_f[0]) * m.inv_spacing_f[0],
+                    (py - m.origin_f[1]) * m.inv_spacing_f[1],
+                    (pz - m.origin_f[2]) * m.inv_spacing_f[2]};
+      grid_vg<float>(m, u, m.base_f, f, gx, gy, gz);
+      gx *= m.inv_spacing_f[0];
+      gy *= m.inv_spacing_f[1];
+      gz *= m.inv_spacing_f[2];
+    } else {
+      float x = (px - m.off_f[0]) * m.inv_scale_f[0];
+      float y = (py - m.off_f[1]) * m.inv_scale_f[1];
+      float z = (pz - m.off_f[2]) * m.inv_scale_f[2];
+      float q, qx, qy, qz;
+      poly_vg<PC, float>(m.c32, x, y, z, q, qx, qy, qz);
+      qx *= m.inv_scale_f[0];
+      qy *= m.inv_scale_f[1];
+      qz *= m.inv_scale_f[2];
+      if (m.form == GRIN_FORM_LINEAR) {
+        f = q;  // constant term already shifted by base
+        gx = qx;
+        gy = qy;
+        gz = qz;
+      } else if (m.form == GRIN_FORM_SQRT) {
+        // q = p - base^2: n = sqrt(q + base^2), nu = q / (n + base)
+        float n = sqrtf(fmaf(m.base_f, m.base_f, q));
+        f = q / (n + m.base_f);
+        float s = 0.5f / n;
+        gx = qx * s;
+        gy = qy * s;
+        gz = qz * s;
+      } else {
+        float n = m.form_c_f / q;
+        f = n - m.base_f;
+        float s = -n / q;
+        gx = qx * s;
+        gy = qy * s;
+        gz = qz * s;
+      }
+    }
+    if (LAYERED) {
+      float u = (f - m.lvl_lo_rel_f) * m.lvl_scale_f;
+      float fl = floorf(u);
+      int k = fl >= 0.0f ? (fl > (float)(m.n_levels - 1) ? m.n_levels - 1 : (int)fl) : 0;
+      lvl = k;
+      nu = fmaf((float)k + 0.5f, m.lvl_step_f, m.lvl_lo_rel_f);
+    } else {
+      lvl = 0;
+      nu = f;
+    }
+  }
+};
+
+struct RayF {
+  float ph[3], pl[3], d[3], dl[3];  // point and direction as hi + lo pairs
+  float gp[3];  // grad n at the previous point
+  float nu_prev, h;
+  int lvl_prev, steps, full, tir_i, tir_b;
+  double opl_x;  // exterior segment + cut steps, in optical length
+};
+
+__device__ __forceinline__ bool inside32(const DevMedium& m, const float* q) {
+  const float* b = m.b_f;
+  if (m.bkind == GRIN_BOUNDARY_BOX)
+    return q[0] > b[0] && q[0] < b[3] && q[1] > b[1] && q[1] < b[4] && q[2] > b[2] && q[2] < b[5];
+  if (m.bkind == GRIN_BOUNDARY_SPHERE) {
+    float x = q[0] - b[0], y = q[1] - b[1], z = q[2] - b[2];
+    return fmaf(x, x, fmaf(y, y, z * z)) < b[3] * b[3];
+  }
+  float x = q[0] - b[0], y = q[1] - b[1];
+  return fmaf(x, x, y * y) < b[2] * b[2] && q[2] > b[3] && q[2] < b[4];
+}
+
+__device__ __forceinline__ V3 pos64(const RayF& s) {
+  return mk((double)s.ph[0] + (double)s.pl[0], (double)s.ph[1] + (double)s.pl[1],
+            (double)s.ph[2] + (double)s.pl[2]);
+}
+
+__device__ __forceinline__ void set_pos(RayF& s, V3 p) {
+  s.ph[0] = (float)p.x;
+  s.ph[1] = (float)p.y;
+  s.ph[2] = (float)p.z;
+  s.pl[0] = (float)(p.x - (double)s.ph[0]);
+  s.pl[1] = (float)(p.y - (double)s.ph[1]);
+  s.pl[2] = (float)(p.z - (double)s.ph[2]);
+}
+
+__device__ __forceinline__ void finish(const TraceArgs& a, int64_t r, const RayF& s, V3 p, V3 d,
+                                       int exit_id) {
+  double opl = s.opl_x + a.dopl * (double)s.full;
+  store_ray(a, r, p, d, opl, exit_id, s.steps, s.tir_i, s.tir_b);
+}
+
+__device__ __forceinline__ V3 dir64(const RayF& s) {
+  return mk((double)s.d[0] + (double)s.dl[0], (double)s.d[1] + (double)s.dl[1],
+            (double)s.d[2] + (double)s.dl[2]);
+}
+
+__device__ __forceinline__ void set_dir(RayF& s, V3 d) {
+  s.d[0] = (float)d.x;
+  s.d[1] = (float)d.y;
+  s.d[2] = (float)d.z;
+  s.dl[0] = (float)(d.x - (double)s.d[0]);
+  s.dl[1] = (float)(d.y - (double)s.d[1]);
+  s.dl[2] = (float)(d.z - (double)s.d[2]);
+}
+
+// (hi, lo) += x: the carried residual lo is folded into x, then Knuth's
+// TwoSum (exact for any magnitudes) leaves hi = fl(hi + x) and the new
+// residual in lo, so hi stays the rounded value of the pair.
+__device__ __forceinline__ void add_ff(float& hi, float& lo, float x) {
+  x += lo;
+  float s = hi + x;
+  float bp = s - hi;
+  lo = (hi - (s - bp)) + (x - bp);
+  hi = s;
+}
+
+// Start ray r: FP64 entry through the surface.  Returns false when the ray
+// is already finished (its output is written).
+template <int PC, bool GRID, bool LAYERED>
+__device__ bool init_ray(const DevMedium& m, const TraceArgs& a, int64_t r, RayF& s) {
+  using F = Field32<PC, GRID, LAYERED>;
+  V3 p = mk(ld(a.ox, r, a.dtype), ld(a.oy, r, a.dtype), ld(a.oz, r, a.dtype));
+  V3 d = mk(ld(a.dx, r, a.dtype), ld(a.dy, r, a.dtype), ld(a.dz, r, a.dtype));
+  s.steps = s.full = s.tir_i = s.tir_b = 0;
+  s.opl_x = 0.0;
+  if (!finite3(p) || !finite3(d) || dot(d, d) == 0.0) {
+    finish(a, r, s, p, d, GRIN_EXIT_INVALID);
+    return false;
+  }
+  d = unit(d);
+  if (!inside64(m, p)) {
+    double t;
+    V3 pb, nb;
+    int face;
+    if (!enter64(m, p, d, t, pb, nb, face)) {
+      finish(a, r, s, p, d, GRIN_EXIT_MISS);
+      return false;
+    }
+    s.opl_x = m.n_ext * t;
+    p = pb;
+    F::eval(m, (float)p.x, (float)p.y, (float)p.z, s.nu_prev, s.gp[0], s.gp[1], s.gp[2],
+            s.lvl_prev);
+    double nb_in = (double)m.base_f + (double)s.nu_prev;
+    if (refract64(d, nb, m.n_ext / nb_in)) {
+      finish(a, r, s, p, d, GRIN_EXIT_ENTRY_REFLECT);
+      return false;
+    }
+  } else {
+    F::eval(m, (float)p.x, (float)p.y, (float)p.z, s.nu_prev, s.gp[0], s.gp[1], s.gp[2],
+            s.lvl_prev);
+  }
+  float n0 = m.base_f + s.nu_prev;
+  if (!(isfinite(n0) && n0 > 0.0f)) {
+    finish(a, r, s, p, d, GRIN_EXIT_INVALID);
+    return false;
+  }
+  if (a.max_steps <= 0) {
+    finish(a, r, s, p, d, GRIN_EXIT_MAXSTEPS);
+    return false;
+  }
+  set_pos(s, p);
+  set_dir(s, d);
+  s.h = (float)a.dopl / n0;
+  return true;
+}
+
+__device__ __forceinline__ void renorm(float* v) {
+  float r = rsqrtf(fmaf(v[0], v[0], fmaf(v[1], v[1], v[2] * v[2])));
+  v[0] *= r;
+  v[1] *= r;
+  v[2] *= r;
+}
+
+// One VRT step of an active ray; returns false when the ray finished.
+template <int PC, bool GRID, bool LAYERED>
+__device__ __forceinline__ bool step_ray(const DevMedium& m, const TraceArgs& a, int64_t r,
+                                         RayF& s, float dopl_f) {
+  using F = Field32<PC, GRID, LAYERED>;
+  float qh[3], ql[3], dv[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    dv[k] = s.h * s.d[k];
+    float y = fmaf(s.h, s.d[k], fmaf(s.h, s.dl[k], s.pl[k]));
+    float t = s.ph[k] + y;
+    ql[k] = y - (t - s.ph[k]);
+    qh[k] = t;
+  }
+  if (!inside32(m, qh)) {
+    // Sec. II (i): FP64 crossing of the enclosing surface.
+    V3 p = pos64(s), d = dir64(s);
+    V3 q = axpy((double)s.h, d, p);
+    if (!inside64(m, q)) {
+      double t;
+      V3 pb, nb;
+      int face;
+      exit64(m, p, q, t, pb, nb, face);
+      s.opl_x += a.dopl * t;
+      ++s.steps;
+      double n_prev = (double)m.base_f + (double)s.nu_prev;
+      if (refract64(d, nb, n_prev / m.n_ext)) {
+        ++s.tir_b;
+        s.h = dopl_f / (m.base_f + s.nu_prev);
+        F::eval(m, (float)pb.x, (float)pb.y, (float)pb.z, s.nu_prev, s.gp[0], s.gp[1], s.gp[2],
+                s.lvl_prev);
+        float nn = m.base_f + s.nu_prev;
+        set_pos(s, pb);
+        set_dir(s, d);
+        if (!(isfinite(nn) && nn > 0.0f)) {
+          finish(a, r, s, pb, d, GRIN_EXIT_INVALID);
+          return false;
+        }
+        if (s.steps >= a.max_steps) {
+          finish(a, r, s, pb, d, GRIN_EXIT_MAXSTEPS);
+          return false;
+        }
+        return true;
+      }
+      finish(a, r, s, pb, d, face);
+      return false;
+    }
+    // FP32 and FP64 disagree by a rounding at the surface: FP64 says
+    // inside, so this is an ordinary step.
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    s.ph[k] = qh[k];
+    s.pl[k] = ql[k];
+  }
+  ++s.full;
+  ++s.steps;
+  float nu_i, g[3];
+  int lvl_i;
+  F::eval(m, qh[0], qh[1], qh[2], nu_i, g[0], g[1], g[2], lvl_i);
+  const float n_i = m.base_f + nu_i;
+  if (!(isfinite(n_i) && n_i > 0.0f)) {
+    finish(a, r, s, pos64(s), dir64(s), GRIN_EXIT_INVALID);
+    return false;
+  }
+  const float inv_n = 1.0f / n_i;
+  float gn2 = fmaf(g[0], g[0], fmaf(g[1], g[1], g[2] * g[2]));
+  if ((LAYERED && lvl_i == s.lvl_prev) || gn2 == 0.0f || !isfinite(gn2)) {
+    s.h = dopl_f * inv_n;  // Sec. II (ii)/(iii)
+  } else {
+    float ri = rsqrtf(gn2);
+    float N[3] = {g[0] * ri, g[1] * ri, g[2] * ri};
+    float c = fmaf(N[0], s.d[0], fmaf(N[1], s.d[1], N[2] * s.d[2]));
+    if (c == 0.0f) {
+      // Sec. II (iv): circular arc from one extra index sample along N.
+      float hi = dopl_f * inv_n;
+      float nu2, g2x, g2y, g2z;
+      int l2;
+      F::eval(m, fmaf(hi, N[0], qh[0]), fmaf(hi, N[1], qh[1]), fmaf(hi, N[2], qh[2]), nu2, g2x,
+              g2y, g2z, l2);
+      float k = (nu2 - nu_i) * 0.5f * inv_n;
+      float w = fmaf(-k, k, 1.0f);
+      float a0 = w > 0.0f ? sqrtf(w) : 0.0f;
+      float nd[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) nd[j] = fmaf(a0, s.d[j], k * N[j]);
+      renorm(nd);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        s.d[j] = nd[j];
+        s.dl[j] = 0.0f;
+      }
+      s.h = hi;
+    } else {
+      float dn = nu_i - s.nu_prev;
+      if (!LAYERED) {
+        float dt = 0.5f * fmaf(s.gp[0] + g[0], dv[0],
+                               fmaf(s.gp[1] + g[1], dv[1], (s.gp[2] + g[2]) * dv[2]));
+        if (isfinite(dt)) dn = dt;
+      }
+      const float om = dn * inv_n;  // 1 - mu
+      const float mu = 1.0f - om;
+      const float omm = om * (2.0f - om);            // 1 - mu^2
+      const float mc = mu * c;
+      const float D = fmaf(mc, mc, omm);
+      bool tir;
+      float gamma = 0.0f;
+      if (fabsf(D) > kCritBand * (fabsf(omm) + mc * mc)) {
+        tir = D <= 0.0f;
+        if (!tir) gamma = (c > 0.0f ? omm : -omm) / (sqrtf(D) + fabsf(mc));
+      } else {
+        // near critical / grazing: discriminant and gamma in FP64
+        double c64 = (double)N[0] * s.d[0] + (double)N[1] * s.d[1] + (double)N[2] * s.d[2];
+        double om64 = (double)dn / (double)n_i;
+        double mu64 = 1.0 - om64;
+        double omm64 = om64 * (2.0 - om64);
+        double mc64 = mu64 * c64;
+        double D64 = fma(mc64, mc64, omm64);
+        tir = D64 <= 0.0;
+        if (!tir) gamma = (float)((c64 > 0.0 ? omm64 : -omm64) / (sqrt(D64) + fabs(mc64)));
+      }
+      if (tir) {
+        // Sec. II (v): reflect, step dL0 / n_{i-1}
+        const float c2 = -2.0f * c;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) add_ff(s.d[j], s.dl[j], c2 * N[j]);
+        ++s.tir_i;
+        s.h = dopl_f / (m.base_f + s.nu_prev);
+      } else {
+        // Eq. 8: R = mu I + gamma N = I + (gamma N - (1 - mu) I)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) add_ff(s.d[j], s.dl[j], fmaf(gamma, N[j], -om * s.d[j]));
+        s.h = dopl_f * inv_n;
+      }
+    }
+  }
+  s.nu_prev = nu_i;
+  s.lvl_prev = lvl_i;
+  s.gp[0] = g[0];
+  s.gp[1] = g[1];
+  s.gp[2] = g[2];
+  if (s.steps >= a.max_steps) {
+    finish(a, r, s, pos64(s), dir64(s), GRIN_EXIT_MAXSTEPS);
+    return false;
+  }
+  return true;
+}
+
+template <int PC, bool GRID, bool LAYERED>
+__global__ void __launch_bounds__(128) k_trace_mixed(DevMedium m, TraceArgs a,
+                                                     unsigned long long* queue) {
+  const unsigned lane = threadIdx.x & 31u;
+  const float dopl_f = (float)a.dopl;
+  RayF s;
+  bool active = false;
+  bool exhausted = false;
+  int64_t ray = 0;
+  for (;;) {
+    const unsigned need = __ballot_sync(0xffffffffu, !active);
+    if (need && !exhausted) {
+      const int leader = __ffs(need) - 1;
+      const unsigned cnt = __popc(need);
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd(queue, (unsigned long long)cnt);
+      base = __shfl_sync(0xffffffffu, base, leader);
+      exhausted = base + cnt >= (unsigned long long)a.count;
+      if (!active) {
+        const unsigned long long rr = base + __popc(need & ((1u << lane) - 1u));
+        if (rr < (unsigned long long)a.count) {
+          ray = (int64_t)rr;
+          active = init_ray<PC, GRID, LAYERED>(m, a, ray, s);
+        }
+      }
+    }
+    if (!__any_sync(0xffffffffu, active)) {
+      if (exhausted) break;
+      continue;
+    }
+#pragma unroll 1
+    for (int k = 0; k < kStepQuantum; ++k) {
+      if (active) active = step_ray<PC, GRID, LAYERED>(m, a, ray, s, dopl_f);
+    }
+  }
+}
+
+template <int PC, bool GRID, bool LAYERED>
+static int launch_t(const DevMedium& m, const TraceArgs& a, unsigned long long* queue,
+                    cudaStream_t st, int sm_count) {
+  auto kern = k_trace_mixed<PC, GRID, LAYERED>;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int64_t warps_needed = (a.count + 31) / 32;
+  int block = 128;
+  int64_t blocks = (int64_t)sm_count * per_sm;
+  // Small batches: one warp per block so that the warps spread over all SMs.
+  if (warps_needed <= (int64_t)sm_count * 4) {
+    block = 32;
+    blocks = warps_needed;
+  } else {
+    blocks = blocks < (warps_needed + 3) / 4 ? blocks : (warps_needed + 3) / 4;
+  }
+  if (cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st) != cudaSuccess) return GRIN_ERR_CUDA;
+  kern<<<(unsigned)blocks, block, 0, st>>>(m, a, queue);
+  return cudaGetLastError() == cudaSuccess ? 1 : GRIN_ERR_CUDA;
+}
+
+int launch_mixed(const DevMedium& m, const TraceArgs& a, unsigned long long* queue,
+                 cudaStream_t s, int sm_count) {
+  const bool lay = m.n_levels > 0;
+  if (m.kind == GRIN_MEDIUM_GRID)
+    return lay ? launch_t<0, true, true>(m, a, queue, s, sm_count)
+               : launch_t<0, true, false>(m, a, queue, s, sm_count);
+  switch (m.pclass) {
+    case kPoly2:
+      return lay ? launch_t<2, false, true>(m, a, queue, s, sm_count)
+                 : launch_t<2, false, false>(m, a, queue, s, sm_count);
+    case kPoly4:
+      return lay ? launch_t<4, false, true>(m, a, queue, s, sm_count)
+                 : launch_t<4, false, false>(m, a, queue, s, sm_count);
+    default:
+      return lay ? launch_t<6, false, true>(m, a, queue, s, sm_count)
+                 : launch_t<6, false, false>(m, a, queue, s, sm_count);
+  }
+}
+
+}  // namespace grin

@@ -307,11 +307,14 @@ def luneburg_workload() -> Workload:
     return Workload("luneburg_4096", luneburg_medium(), luneburg_rays(), 1e-3, 5000, 1.0)
 
 
-def freeform_workload(n_rays: int = 1 << 20, seed: int = BASE_SEED + 1) -> Workload:
+def freeform_workload(n_rays: int = 1 << 20, seed: int = BASE_SEED + 1,
+                      ray_seed: Optional[int] = None) -> Workload:
     """Analytic freeform polynomial block, point source 5 mm before the
-    entrance face, half-angle 30 deg; dL0 = 0.01 mm, at most 20000 steps."""
+    entrance face, half-angle 30 deg; dL0 = 0.01 mm, at most 20000 steps.
+    `ray_seed` (default `seed`) draws the bundle."""
     m = freeform_block_medium(seed)
-    return Workload(f"freeform_block_{n_rays}", m, point_source_rays(n_rays, seed), 0.01, 20000,
+    rays = point_source_rays(n_rays, seed if ray_seed is None else ray_seed)
+    return Workload(f"freeform_block_{n_rays}", m, rays, 0.01, 20000,
                     math.sqrt(5.0 ** 2 + 5.0 ** 2 + 10.0 ** 2))
 
 

@@ -1,0 +1,53 @@
+"""The C-ABI library loads without a GPU and exports every function that
+include/grin.h declares; the binding's struct layouts match the header."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2606_22655_b300 import _native as N
+from paper_2606_22655_b300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "grin.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(grin_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return N.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings_and_poly_terms(lib):
+    assert lib.grin_status_string(0) == b"ok"
+    assert lib.grin_status_string(-1) == b"invalid argument"
+    assert [lib.grin_poly_terms(d) for d in range(7)] == [1, 4, 10, 20, 35, 56, 84]
+    assert lib.grin_poly_terms(7) == 0
+
+
+def test_null_arguments_are_rejected_without_a_device(lib):
+    assert lib.grin_ctx_create(0, None) == -1
+    assert lib.grin_ctx_destroy(None) == -1
+    assert lib.grin_medium_destroy(None) == -1
+    assert lib.grin_trace(None, None, None, None, None, None) == -1
+    assert lib.grin_trace_host(None, None, None, None, None, None) == -1
+
+
+def test_struct_sizes_match_c_layout():
+    # sizes computed from the header's field lists with natural alignment
+    assert ctypes.sizeof(N.Rays) == 6 * 8 + 8 + 8
+    assert ctypes.sizeof(N.Out) == 11 * 8
+    assert ctypes.sizeof(N.Params) == 8 + 4 + 4 + 4 + 4
