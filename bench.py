@@ -175,7 +175,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     ctx = tracer.Context(local)
-    wl = W.freeform_workload(N_RAYS, ray_seed=W.BASE_SEED + 1 + 1000 * rank)
+    wl = W.freeform_workload(args.rays, ray_seed=W.BASE_SEED + 1 + 1000 * rank)
     med = tracer.Medium(ctx, wl.medium)
     rays = tracer.RayBatch.from_numpy(wl.rays.origins, wl.rays.dirs, device=dev, dtype=torch.float32)
     out = tracer.empty_result(rays.count, dev)
@@ -220,6 +220,14 @@ def run_ours(args):
         region_s = float(t.item())
     value = ws * steps_per_trace * args.steps / region_s
     mean_kern = sum(kern_s) / len(kern_s)
+
+    if args.profile_only:
+        if rank == 0:
+            print(json.dumps({"profile_only": True, "workload": wl.name, "value": value, "unit": UNIT,
+                              "kernel_ms": 1e3 * mean_kern, "gpu_launches": launches}), flush=True)
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
 
     # CPU baseline (the FP64 oracle on every 16th ray); its decision margins
     # also flag the ill-conditioned rays for the precision gate
@@ -287,7 +295,7 @@ def run_ours(args):
                    "l2": "256 MiB buffer zeroed before every step, inside the timed region"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "k_trace_mixed<4,false,false>", "kernel_ms": 1e3 * mean_kern,
+                     "kernel": "k_trace_mixed<Cfg<4,false,false,box,linear>,false>", "kernel_ms": 1e3 * mean_kern,
                      "flops_per_ray_step": flops_per_step(4),
                      "peak_note": "148 SMs x 128 FP32 lanes x 2 FLOP x 2.032 GHz (derived)"},
         "precision_gate": {
@@ -323,6 +331,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--ref-stride", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rays", type=int, default=N_RAYS,
+                    help="ray count (profiling of a smaller case; the line then names it)")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="timed steps only: no precision gate, e2e or CPU baseline")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -9,7 +9,9 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "lib", "libgrin_vrt.so")
+# GRIN_LIB may name another build of the same library (e.g. one compiled
+# with different launch bounds); it must export the same C ABI
+LIB_PATH = os.environ.get("GRIN_LIB") or os.path.join(HERE, "lib", "libgrin_vrt.so")
 
 GRIN_OK = 0
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA runtime error",

@@ -24,8 +24,10 @@ LIB_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIB_DIR, "libgrin_vrt.so")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# per-source extra flags: the plain FP64 tracer must not contract a*b+c
-EXTRA = {"trace_fp64.cu": ["--fmad=false"]}
+# per-source extra flags: the plain FP64 tracer must not contract a*b+c; the
+# mixed tracer takes hardware-approximate FP32 division and square root
+EXTRA = {"trace_fp64.cu": ["--fmad=false"],
+         "trace_mixed.cu": ["-prec-div=false", "-prec-sqrt=false"]}
 
 
 def _nvcc() -> str:

@@ -20,26 +20,51 @@
 //     nu = n - base;
 //   - the refraction uses gamma = sgn(c) (1 - mu^2) / (sqrt(D) + mu |c|), an
 //     algebraically equal form of Eq. 9 without the cancellation of
-//     -mu c + sgn(c) sqrt(D); D = (1 - mu^2) + mu^2 c^2;
+//     -mu c + sgn(c) sqrt(D); D = (1 - mu^2) + mu^2 c^2; refraction and
+//     reflection are selected without a branch;
 //   - when |D| is within a few FP32 roundings of zero (near critical or
 //     grazing incidence) the discriminant and gamma are recomputed in FP64;
 //   - the optical path is exact: dL0 times the count of full steps, plus the
 //     FP64 exterior segment and the fractions of steps cut at the surface;
 //   - everything at the enclosing surface (the entry intersection and
 //     refraction, the exit root, boundary refraction or TIR) runs in FP64.
+// This file is built with -prec-div=false -prec-sqrt=false: FP32 divisions
+// and square roots use the hardware approximations (a few ulp), which is far
+// inside the FP32 path's error budget and removes their slow-path branches.
+//
 // Work distribution: a persistent grid sized to the resident capacity of the
 // GPU; each warp keeps 32 rays in flight and, every kStepQuantum steps, lanes
 // whose ray finished claim new rays from a global counter (one atomicAdd per
 // warp, ranks from a ballot), so long and short rays do not idle lanes.
+//
+// Template parameters: polynomial degree class PC (or GRID), LAYERED, and the
+// boundary kind BK and index form FORM, either fixed at compile time (the
+// common box / n = p case, which drops their run-time switches from the step)
+// or -1 for "read from the medium at run time".
 #include "grin_device.cuh"
 
 namespace grin {
 
+// Resident blocks of 128 threads per SM the register allocation aims for:
+// 5 (at most 102 registers a thread) for polynomial and grid media; the
+// measured optimum between register spills and resident warps.
+#ifndef GRIN_MIXED_MIN_BLOCKS
+#define GRIN_MIXED_MIN_BLOCKS 5
+#endif
+#ifndef GRIN_MIXED_MIN_BLOCKS_GRID
+#define GRIN_MIXED_MIN_BLOCKS_GRID 5
+#endif
 constexpr int kStepQuantum = 32;
 constexpr float kCritBand = 1.0e-5f;  // relative |D| below which FP64 decides
 
-template <int PC, bool GRID, bool LAYERED>
-struct Field32 {
+#define GRIN_UNLIKELY(x) __builtin_expect(!!(x), 0)
+
+template <int PC, bool GRID, bool LAYERED, int BK, int FORM>
+struct Cfg {
+  static constexpr int kMinBlocks = GRID ? GRIN_MIXED_MIN_BLOCKS_GRID : GRIN_MIXED_MIN_BLOCKS;
+  static __device__ __forceinline__ int bk(const DevMedium& m) { return BK >= 0 ? BK : m.bkind; }
+  static __device__ __forceinline__ int form(const DevMedium& m) { return FORM >= 0 ? FORM : m.form; }
+
   // nu = n - base (after layering), the gradient of the smooth field, level.
   static __device__ __forceinline__ void eval(const DevMedium& m, float px, float py, float pz,
                                               float& nu, float& gx, float& gy, float& gz,
@@ -62,12 +87,13 @@ struct Field32 {
       qx *= m.inv_scale_f[0];
       qy *= m.inv_scale_f[1];
       qz *= m.inv_scale_f[2];
-      if (m.form == GRIN_FORM_LINEAR) {
+      const int fm = form(m);
+      if (fm == GRIN_FORM_LINEAR) {
         f = q;  // constant term already shifted by base
         gx = qx;
         gy = qy;
         gz = qz;
-      } else if (m.form == GRIN_FORM_SQRT) {
+      } else if (fm == GRIN_FORM_SQRT) {
         // q = p - base^2: n = sqrt(q + base^2), nu = q / (n + base)
         float n = sqrtf(fmaf(m.base_f, m.base_f, q));
         f = q / (n + m.base_f);
@@ -95,27 +121,29 @@ struct Field32 {
       nu = f;
     }
   }
+
+  static __device__ __forceinline__ bool inside(const DevMedium& m, const float* q) {
+    const float* b = m.b_f;
+    const int k = bk(m);
+    if (k == GRIN_BOUNDARY_BOX)
+      return q[0] > b[0] && q[0] < b[3] && q[1] > b[1] && q[1] < b[4] && q[2] > b[2] &&
+             q[2] < b[5];
+    if (k == GRIN_BOUNDARY_SPHERE) {
+      float x = q[0] - b[0], y = q[1] - b[1], z = q[2] - b[2];
+      return fmaf(x, x, fmaf(y, y, z * z)) < b[3] * b[3];
+    }
+    float x = q[0] - b[0], y = q[1] - b[1];
+    return fmaf(x, x, y * y) < b[2] * b[2] && q[2] > b[3] && q[2] < b[4];
+  }
 };
 
 struct RayF {
   float ph[3], pl[3], d[3], dl[3];  // point and direction as hi + lo pairs
-  float gp[3];  // grad n at the previous point
-  float nu_prev, h;
+  float gp[3];                      // grad n at the previous point
+  float nu_prev, inv_prev, h;       // n_{i-1} - base, 1 / n_{i-1}, step length
   int lvl_prev, steps, full, tir_i, tir_b;
   double opl_x;  // exterior segment + cut steps, in optical length
 };
-
-__device__ __forceinline__ bool inside32(const DevMedium& m, const float* q) {
-  const float* b = m.b_f;
-  if (m.bkind == GRIN_BOUNDARY_BOX)
-    return q[0] > b[0] && q[0] < b[3] && q[1] > b[1] && q[1] < b[4] && q[2] > b[2] && q[2] < b[5];
-  if (m.bkind == GRIN_BOUNDARY_SPHERE) {
-    float x = q[0] - b[0], y = q[1] - b[1], z = q[2] - b[2];
-    return fmaf(x, x, fmaf(y, y, z * z)) < b[3] * b[3];
-  }
-  float x = q[0] - b[0], y = q[1] - b[1];
-  return fmaf(x, x, y * y) < b[2] * b[2] && q[2] > b[3] && q[2] < b[4];
-}
 
 __device__ __forceinline__ V3 pos64(const RayF& s) {
   return mk((double)s.ph[0] + (double)s.pl[0], (double)s.ph[1] + (double)s.pl[1],
@@ -129,12 +157,6 @@ __device__ __forceinline__ void set_pos(RayF& s, V3 p) {
   s.pl[0] = (float)(p.x - (double)s.ph[0]);
   s.pl[1] = (float)(p.y - (double)s.ph[1]);
   s.pl[2] = (float)(p.z - (double)s.ph[2]);
-}
-
-__device__ __forceinline__ void finish(const TraceArgs& a, int64_t r, const RayF& s, V3 p, V3 d,
-                                       int exit_id) {
-  double opl = s.opl_x + a.dopl * (double)s.full;
-  store_ray(a, r, p, d, opl, exit_id, s.steps, s.tir_i, s.tir_b);
 }
 
 __device__ __forceinline__ V3 dir64(const RayF& s) {
@@ -162,11 +184,24 @@ __device__ __forceinline__ void add_ff(float& hi, float& lo, float x) {
   hi = s;
 }
 
+__device__ __forceinline__ void finish(const TraceArgs& a, int64_t r, const RayF& s, V3 p, V3 d,
+                                       int exit_id) {
+  double opl = s.opl_x + a.dopl * (double)s.full;
+  store_ray(a, r, p, d, opl, exit_id, s.steps, s.tir_i, s.tir_b);
+}
+
+// (n_{i-1} - base) -> the state's index fields; false if n is not usable.
+__device__ __forceinline__ bool set_index(const DevMedium& m, RayF& s, float nu) {
+  s.nu_prev = nu;
+  float n = m.base_f + nu;
+  s.inv_prev = 1.0f / n;
+  return isfinite(n) && n > 0.0f;
+}
+
 // Start ray r: FP64 entry through the surface.  Returns false when the ray
 // is already finished (its output is written).
-template <int PC, bool GRID, bool LAYERED>
+template <class C>
 __device__ bool init_ray(const DevMedium& m, const TraceArgs& a, int64_t r, RayF& s) {
-  using F = Field32<PC, GRID, LAYERED>;
   V3 p = mk(ld(a.ox, r, a.dtype), ld(a.oy, r, a.dtype), ld(a.oz, r, a.dtype));
   V3 d = mk(ld(a.dx, r, a.dtype), ld(a.dy, r, a.dtype), ld(a.dz, r, a.dtype));
   s.steps = s.full = s.tir_i = s.tir_b = 0;
@@ -176,6 +211,7 @@ __device__ bool init_ray(const DevMedium& m, const TraceArgs& a, int64_t r, RayF
     return false;
   }
   d = unit(d);
+  float nu;
   if (!inside64(m, p)) {
     double t;
     V3 pb, nb;
@@ -186,19 +222,16 @@ __device__ bool init_ray(const DevMedium& m, const TraceArgs& a, int64_t r, RayF
     }
     s.opl_x = m.n_ext * t;
     p = pb;
-    F::eval(m, (float)p.x, (float)p.y, (float)p.z, s.nu_prev, s.gp[0], s.gp[1], s.gp[2],
-            s.lvl_prev);
-    double nb_in = (double)m.base_f + (double)s.nu_prev;
+    C::eval(m, (float)p.x, (float)p.y, (float)p.z, nu, s.gp[0], s.gp[1], s.gp[2], s.lvl_prev);
+    double nb_in = (double)m.base_f + (double)nu;
     if (refract64(d, nb, m.n_ext / nb_in)) {
       finish(a, r, s, p, d, GRIN_EXIT_ENTRY_REFLECT);
       return false;
     }
   } else {
-    F::eval(m, (float)p.x, (float)p.y, (float)p.z, s.nu_prev, s.gp[0], s.gp[1], s.gp[2],
-            s.lvl_prev);
+    C::eval(m, (float)p.x, (float)p.y, (float)p.z, nu, s.gp[0], s.gp[1], s.gp[2], s.lvl_prev);
   }
-  float n0 = m.base_f + s.nu_prev;
-  if (!(isfinite(n0) && n0 > 0.0f)) {
+  if (!set_index(m, s, nu)) {
     finish(a, r, s, p, d, GRIN_EXIT_INVALID);
     return false;
   }
@@ -208,7 +241,7 @@ __device__ bool init_ray(const DevMedium& m, const TraceArgs& a, int64_t r, RayF
   }
   set_pos(s, p);
   set_dir(s, d);
-  s.h = (float)a.dopl / n0;
+  s.h = (float)a.dopl * s.inv_prev;
   return true;
 }
 
@@ -219,11 +252,65 @@ __device__ __forceinline__ void renorm(float* v) {
   v[2] *= r;
 }
 
-// One VRT step of an active ray; returns false when the ray finished.
-template <int PC, bool GRID, bool LAYERED>
-__device__ __forceinline__ bool step_ray(const DevMedium& m, const TraceArgs& a, int64_t r,
-                                         RayF& s, float dopl_f) {
-  using F = Field32<PC, GRID, LAYERED>;
+// The step would end outside the surface (by FP32): FP64 crossing
+// (Sec. II (i)).  Returns 0 if FP64 puts the end inside after all (take the
+// ordinary step), 1 if the ray reflected and goes on, 2 if it finished.
+template <class C>
+__device__ __forceinline__ int surface_event(const DevMedium& m, const TraceArgs& a, int64_t r,
+                                             RayF& s, float dopl_f) {
+  V3 p = pos64(s), d = dir64(s);
+  V3 q = axpy((double)s.h, d, p);
+  if (inside64(m, q)) return 0;
+  double t;
+  V3 pb, nb;
+  int face;
+  exit64(m, p, q, t, pb, nb, face);
+  s.opl_x += a.dopl * t;
+  ++s.steps;
+  double n_prev = (double)m.base_f + (double)s.nu_prev;
+  if (refract64(d, nb, n_prev / m.n_ext)) {
+    ++s.tir_b;
+    s.h = dopl_f * s.inv_prev;
+    float nu;
+    C::eval(m, (float)pb.x, (float)pb.y, (float)pb.z, nu, s.gp[0], s.gp[1], s.gp[2], s.lvl_prev);
+    bool ok = set_index(m, s, nu);
+    set_pos(s, pb);
+    set_dir(s, d);
+    if (!ok) {
+      finish(a, r, s, pb, d, GRIN_EXIT_INVALID);
+      return 2;
+    }
+    if (s.steps >= a.max_steps) {
+      finish(a, r, s, pb, d, GRIN_EXIT_MAXSTEPS);
+      return 2;
+    }
+    return 1;
+  }
+  finish(a, r, s, pb, d, face);
+  return 2;
+}
+
+// Near critical or grazing incidence: D and gamma from the same FP32 inputs
+// in FP64.  Returns true on total internal reflection.
+__device__ __forceinline__ bool crit64(const float* N, const float* d, float dn, float n_i,
+                                       float& gamma) {
+  double c64 = (double)N[0] * d[0] + (double)N[1] * d[1] + (double)N[2] * d[2];
+  double om64 = (double)dn / (double)n_i;
+  double mu64 = 1.0 - om64;
+  double omm64 = om64 * (2.0 - om64);
+  double mc64 = mu64 * c64;
+  double D64 = fma(mc64, mc64, omm64);
+  if (D64 <= 0.0) return true;
+  gamma = (float)((c64 > 0.0 ? omm64 : -omm64) / (sqrt(D64) + fabs(mc64)));
+  return false;
+}
+
+// One VRT step of an active ray, every case tested in order; returns false
+// when the ray finished.  Taken only when the fast step below meets a case
+// it does not handle.
+template <class C, bool LAYERED>
+__device__ __noinline__ bool step_slow(const DevMedium& m, const TraceArgs& a, int64_t r,
+                                       RayF& s, float dopl_f) {
   float qh[3], ql[3], dv[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -233,41 +320,10 @@ __device__ __forceinline__ bool step_ray(const DevMedium& m, const TraceArgs& a,
     ql[k] = y - (t - s.ph[k]);
     qh[k] = t;
   }
-  if (!inside32(m, qh)) {
-    // Sec. II (i): FP64 crossing of the enclosing surface.
-    V3 p = pos64(s), d = dir64(s);
-    V3 q = axpy((double)s.h, d, p);
-    if (!inside64(m, q)) {
-      double t;
-      V3 pb, nb;
-      int face;
-      exit64(m, p, q, t, pb, nb, face);
-      s.opl_x += a.dopl * t;
-      ++s.steps;
-      double n_prev = (double)m.base_f + (double)s.nu_prev;
-      if (refract64(d, nb, n_prev / m.n_ext)) {
-        ++s.tir_b;
-        s.h = dopl_f / (m.base_f + s.nu_prev);
-        F::eval(m, (float)pb.x, (float)pb.y, (float)pb.z, s.nu_prev, s.gp[0], s.gp[1], s.gp[2],
-                s.lvl_prev);
-        float nn = m.base_f + s.nu_prev;
-        set_pos(s, pb);
-        set_dir(s, d);
-        if (!(isfinite(nn) && nn > 0.0f)) {
-          finish(a, r, s, pb, d, GRIN_EXIT_INVALID);
-          return false;
-        }
-        if (s.steps >= a.max_steps) {
-          finish(a, r, s, pb, d, GRIN_EXIT_MAXSTEPS);
-          return false;
-        }
-        return true;
-      }
-      finish(a, r, s, pb, d, face);
-      return false;
-    }
-    // FP32 and FP64 disagree by a rounding at the surface: FP64 says
-    // inside, so this is an ordinary step.
+  if (GRIN_UNLIKELY(!C::inside(m, qh))) {
+    int rc = surface_event<C>(m, a, r, s, dopl_f);
+    if (rc == 2) return false;
+    if (rc == 1) return true;
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -278,26 +334,26 @@ __device__ __forceinline__ bool step_ray(const DevMedium& m, const TraceArgs& a,
   ++s.steps;
   float nu_i, g[3];
   int lvl_i;
-  F::eval(m, qh[0], qh[1], qh[2], nu_i, g[0], g[1], g[2], lvl_i);
+  C::eval(m, qh[0], qh[1], qh[2], nu_i, g[0], g[1], g[2], lvl_i);
   const float n_i = m.base_f + nu_i;
-  if (!(isfinite(n_i) && n_i > 0.0f)) {
+  if (GRIN_UNLIKELY(!(isfinite(n_i) && n_i > 0.0f))) {
     finish(a, r, s, pos64(s), dir64(s), GRIN_EXIT_INVALID);
     return false;
   }
   const float inv_n = 1.0f / n_i;
   float gn2 = fmaf(g[0], g[0], fmaf(g[1], g[1], g[2] * g[2]));
-  if ((LAYERED && lvl_i == s.lvl_prev) || gn2 == 0.0f || !isfinite(gn2)) {
+  if (GRIN_UNLIKELY((LAYERED && lvl_i == s.lvl_prev) || gn2 == 0.0f || !isfinite(gn2))) {
     s.h = dopl_f * inv_n;  // Sec. II (ii)/(iii)
   } else {
     float ri = rsqrtf(gn2);
     float N[3] = {g[0] * ri, g[1] * ri, g[2] * ri};
     float c = fmaf(N[0], s.d[0], fmaf(N[1], s.d[1], N[2] * s.d[2]));
-    if (c == 0.0f) {
+    if (GRIN_UNLIKELY(c == 0.0f)) {
       // Sec. II (iv): circular arc from one extra index sample along N.
       float hi = dopl_f * inv_n;
       float nu2, g2x, g2y, g2z;
       int l2;
-      F::eval(m, fmaf(hi, N[0], qh[0]), fmaf(hi, N[1], qh[1]), fmaf(hi, N[2], qh[2]), nu2, g2x,
+      C::eval(m, fmaf(hi, N[0], qh[0]), fmaf(hi, N[1], qh[1]), fmaf(hi, N[2], qh[2]), nu2, g2x,
               g2y, g2z, l2);
       float k = (nu2 - nu_i) * 0.5f * inv_n;
       float w = fmaf(-k, k, 1.0f);
@@ -319,56 +375,116 @@ __device__ __forceinline__ bool step_ray(const DevMedium& m, const TraceArgs& a,
                                fmaf(s.gp[1] + g[1], dv[1], (s.gp[2] + g[2]) * dv[2]));
         if (isfinite(dt)) dn = dt;
       }
-      const float om = dn * inv_n;  // 1 - mu
+      const float om = dn * inv_n;           // 1 - mu
       const float mu = 1.0f - om;
-      const float omm = om * (2.0f - om);            // 1 - mu^2
+      const float omm = om * (2.0f - om);    // 1 - mu^2
       const float mc = mu * c;
       const float D = fmaf(mc, mc, omm);
-      bool tir;
-      float gamma = 0.0f;
-      if (fabsf(D) > kCritBand * (fabsf(omm) + mc * mc)) {
-        tir = D <= 0.0f;
-        if (!tir) gamma = (c > 0.0f ? omm : -omm) / (sqrtf(D) + fabsf(mc));
-      } else {
-        // near critical / grazing: discriminant and gamma in FP64
-        double c64 = (double)N[0] * s.d[0] + (double)N[1] * s.d[1] + (double)N[2] * s.d[2];
-        double om64 = (double)dn / (double)n_i;
-        double mu64 = 1.0 - om64;
-        double omm64 = om64 * (2.0 - om64);
-        double mc64 = mu64 * c64;
-        double D64 = fma(mc64, mc64, omm64);
-        tir = D64 <= 0.0;
-        if (!tir) gamma = (float)((c64 > 0.0 ? omm64 : -omm64) / (sqrt(D64) + fabs(mc64)));
-      }
-      if (tir) {
-        // Sec. II (v): reflect, step dL0 / n_{i-1}
-        const float c2 = -2.0f * c;
+      bool tir = D <= 0.0f;
+      float gamma = (c > 0.0f ? omm : -omm) / (sqrtf(fmaxf(D, 0.0f)) + fabsf(mc));
+      if (GRIN_UNLIKELY(fabsf(D) <= kCritBand * (fabsf(omm) + mc * mc)))
+        tir = crit64(N, s.d, dn, n_i, gamma);
+      // Eq. 8, R = I + (gamma N - (1 - mu) I), or Sec. II (v), R = I - 2 c N
+      // with a step of dL0 / n_{i-1}
+      const float kn = tir ? -2.0f * c : gamma;
+      const float kd = tir ? 0.0f : -om;
 #pragma unroll
-        for (int j = 0; j < 3; ++j) add_ff(s.d[j], s.dl[j], c2 * N[j]);
-        ++s.tir_i;
-        s.h = dopl_f / (m.base_f + s.nu_prev);
-      } else {
-        // Eq. 8: R = mu I + gamma N = I + (gamma N - (1 - mu) I)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) add_ff(s.d[j], s.dl[j], fmaf(gamma, N[j], -om * s.d[j]));
-        s.h = dopl_f * inv_n;
-      }
+      for (int j = 0; j < 3; ++j) add_ff(s.d[j], s.dl[j], fmaf(kn, N[j], kd * s.d[j]));
+      s.h = dopl_f * (tir ? s.inv_prev : inv_n);
+      s.tir_i += tir ? 1 : 0;
     }
   }
   s.nu_prev = nu_i;
+  s.inv_prev = inv_n;
   s.lvl_prev = lvl_i;
   s.gp[0] = g[0];
   s.gp[1] = g[1];
   s.gp[2] = g[2];
-  if (s.steps >= a.max_steps) {
+  if (GRIN_UNLIKELY(s.steps >= a.max_steps)) {
     finish(a, r, s, pos64(s), dir64(s), GRIN_EXIT_MAXSTEPS);
     return false;
   }
   return true;
 }
 
-template <int PC, bool GRID, bool LAYERED>
-__global__ void __launch_bounds__(128) k_trace_mixed(DevMedium m, TraceArgs a,
+// The common step: the end point is inside, n is usable, and N.I is nonzero
+// and not near critical (or, in a layered medium, the level did not change).
+// Everything is computed without a branch and one flag routes the rare cases
+// (surface crossing, invalid n, zero or undefined gradient, tangency,
+// near-critical D, the step limit) to step_slow, which redoes the step from
+// the unchanged state.
+template <class C, bool LAYERED>
+__device__ __forceinline__ bool step_ray(const DevMedium& m, const TraceArgs& a, int64_t r,
+                                         RayF& s, float dopl_f) {
+  float qh[3], ql[3], dv[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    dv[k] = s.h * s.d[k];
+    float y = fmaf(s.h, s.d[k], fmaf(s.h, s.dl[k], s.pl[k]));
+    float t = s.ph[k] + y;
+    ql[k] = y - (t - s.ph[k]);
+    qh[k] = t;
+  }
+  const bool in = C::inside(m, qh);
+  float nu_i, g[3];
+  int lvl_i;
+  C::eval(m, qh[0], qh[1], qh[2], nu_i, g[0], g[1], g[2], lvl_i);
+  const float n_i = m.base_f + nu_i;
+  const float inv_n = 1.0f / n_i;
+  const float gn2 = fmaf(g[0], g[0], fmaf(g[1], g[1], g[2] * g[2]));
+  const bool homog = LAYERED && lvl_i == s.lvl_prev;
+  const float ri = rsqrtf(gn2);
+  float N[3] = {g[0] * ri, g[1] * ri, g[2] * ri};
+  const float c = fmaf(N[0], s.d[0], fmaf(N[1], s.d[1], N[2] * s.d[2]));
+  float dn = nu_i - s.nu_prev;
+  if (!LAYERED)
+    dn = 0.5f * fmaf(s.gp[0] + g[0], dv[0], fmaf(s.gp[1] + g[1], dv[1], (s.gp[2] + g[2]) * dv[2]));
+  const float om = dn * inv_n;         // 1 - mu
+  const float mu = 1.0f - om;
+  const float omm = om * (2.0f - om);  // 1 - mu^2
+  const float mc = mu * c;
+  const float D = fmaf(mc, mc, omm);
+  const bool tir = D <= 0.0f;
+  const float gamma = (c > 0.0f ? omm : -omm) / (sqrtf(fmaxf(D, 0.0f)) + fabsf(mc));
+  const bool special =
+      !in || !(n_i > 0.0f) || !isfinite(n_i) || s.steps + 1 >= a.max_steps ||
+      (!homog && (!(gn2 > 0.0f) || !isfinite(gn2) || c == 0.0f || !isfinite(dn) ||
+                  fabsf(D) <= kCritBand * (fabsf(omm) + mc * mc)));
+  if (GRIN_UNLIKELY(special)) {
+    // out of line, on a copy: only the copy's address escapes, the live
+    // state stays in registers
+    RayF t = s;
+    bool alive = step_slow<C, LAYERED>(m, a, r, t, dopl_f);
+    s = t;
+    return alive;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    s.ph[k] = qh[k];
+    s.pl[k] = ql[k];
+  }
+  ++s.full;
+  ++s.steps;
+  // Eq. 8, R = I + (gamma N - (1 - mu) I); Sec. II (v), R = I - 2 c N with a
+  // step of dL0 / n_{i-1}; inside one shell of a layered medium, straight on
+  const bool refl = !homog && tir;
+  const float kn = homog ? 0.0f : (tir ? -2.0f * c : gamma);
+  const float kd = (homog || tir) ? 0.0f : -om;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) add_ff(s.d[j], s.dl[j], fmaf(kn, N[j], kd * s.d[j]));
+  s.h = dopl_f * (refl ? s.inv_prev : inv_n);
+  s.tir_i += refl ? 1 : 0;
+  s.nu_prev = nu_i;
+  s.inv_prev = inv_n;
+  s.lvl_prev = lvl_i;
+  s.gp[0] = g[0];
+  s.gp[1] = g[1];
+  s.gp[2] = g[2];
+  return true;
+}
+
+template <class C, bool LAYERED>
+__global__ void __launch_bounds__(128, C::kMinBlocks) k_trace_mixed(DevMedium m, TraceArgs a,
                                                      unsigned long long* queue) {
   const unsigned lane = threadIdx.x & 31u;
   const float dopl_f = (float)a.dopl;
@@ -389,7 +505,7 @@ __global__ void __launch_bounds__(128) k_trace_mixed(DevMedium m, TraceArgs a,
         const unsigned long long rr = base + __popc(need & ((1u << lane) - 1u));
         if (rr < (unsigned long long)a.count) {
           ray = (int64_t)rr;
-          active = init_ray<PC, GRID, LAYERED>(m, a, ray, s);
+          active = init_ray<C>(m, a, ray, s);
         }
       }
     }
@@ -399,15 +515,16 @@ __global__ void __launch_bounds__(128) k_trace_mixed(DevMedium m, TraceArgs a,
     }
 #pragma unroll 1
     for (int k = 0; k < kStepQuantum; ++k) {
-      if (active) active = step_ray<PC, GRID, LAYERED>(m, a, ray, s, dopl_f);
+      if (active) active = step_ray<C, LAYERED>(m, a, ray, s, dopl_f);
     }
   }
 }
 
-template <int PC, bool GRID, bool LAYERED>
+template <int PC, bool GRID, bool LAYERED, int BK, int FORM>
 static int launch_t(const DevMedium& m, const TraceArgs& a, unsigned long long* queue,
                     cudaStream_t st, int sm_count) {
-  auto kern = k_trace_mixed<PC, GRID, LAYERED>;
+  using C = Cfg<PC, GRID, LAYERED, BK, FORM>;
+  auto kern = k_trace_mixed<C, LAYERED>;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0) != cudaSuccess ||
       per_sm < 1)
@@ -427,22 +544,22 @@ static int launch_t(const DevMedium& m, const TraceArgs& a, unsigned long long* 
   return cudaGetLastError() == cudaSuccess ? 1 : GRIN_ERR_CUDA;
 }
 
+template <int PC, bool GRID>
+static int launch_pc(const DevMedium& m, const TraceArgs& a, unsigned long long* q,
+                     cudaStream_t s, int sm) {
+  if (m.n_levels > 0) return launch_t<PC, GRID, true, -1, -1>(m, a, q, s, sm);
+  const bool fast = m.bkind == GRIN_BOUNDARY_BOX && (GRID || m.form == GRIN_FORM_LINEAR);
+  return fast ? launch_t<PC, GRID, false, GRIN_BOUNDARY_BOX, GRIN_FORM_LINEAR>(m, a, q, s, sm)
+              : launch_t<PC, GRID, false, -1, -1>(m, a, q, s, sm);
+}
+
 int launch_mixed(const DevMedium& m, const TraceArgs& a, unsigned long long* queue,
                  cudaStream_t s, int sm_count) {
-  const bool lay = m.n_levels > 0;
-  if (m.kind == GRIN_MEDIUM_GRID)
-    return lay ? launch_t<0, true, true>(m, a, queue, s, sm_count)
-               : launch_t<0, true, false>(m, a, queue, s, sm_count);
+  if (m.kind == GRIN_MEDIUM_GRID) return launch_pc<0, true>(m, a, queue, s, sm_count);
   switch (m.pclass) {
-    case kPoly2:
-      return lay ? launch_t<2, false, true>(m, a, queue, s, sm_count)
-                 : launch_t<2, false, false>(m, a, queue, s, sm_count);
-    case kPoly4:
-      return lay ? launch_t<4, false, true>(m, a, queue, s, sm_count)
-                 : launch_t<4, false, false>(m, a, queue, s, sm_count);
-    default:
-      return lay ? launch_t<6, false, true>(m, a, queue, s, sm_count)
-                 : launch_t<6, false, false>(m, a, queue, s, sm_count);
+    case kPoly2: return launch_pc<2, false>(m, a, queue, s, sm_count);
+    case kPoly4: return launch_pc<4, false>(m, a, queue, s, sm_count);
+    default: return launch_pc<6, false>(m, a, queue, s, sm_count);
   }
 }
 
