@@ -175,7 +175,12 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     ctx = tracer.Context(local)
-    wl = W.freeform_workload(args.rays, ray_seed=W.BASE_SEED + 1 + 1000 * rank)
+    if args.workload == "freeform":
+        wl = W.freeform_workload(args.rays, ray_seed=W.BASE_SEED + 1 + 1000 * rank)
+    elif args.workload == "luneburg":
+        wl = W.luneburg_workload()
+    else:
+        wl = W.blob_workload(n_rays=args.rays, res=256, n_levels=32 if args.workload == "layered" else 0)
     med = tracer.Medium(ctx, wl.medium)
     rays = tracer.RayBatch.from_numpy(wl.rays.origins, wl.rays.dirs, device=dev, dtype=torch.float32)
     out = tracer.empty_result(rays.count, dev)
@@ -333,6 +338,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rays", type=int, default=N_RAYS,
                     help="ray count (profiling of a smaller case; the line then names it)")
+    ap.add_argument("--workload", choices=["freeform", "grid", "layered", "luneburg"], default="freeform",
+                    help="freeform (the benchmark), or another medium for profiling")
     ap.add_argument("--profile-only", action="store_true",
                     help="timed steps only: no precision gate, e2e or CPU baseline")
     args = ap.parse_args()

@@ -141,8 +141,9 @@ struct RayF {
   float ph[3], pl[3], d[3], dl[3];  // point and direction as hi + lo pairs
   float gp[3];                      // grad n at the previous point
   float nu_prev, inv_prev, h;       // n_{i-1} - base, 1 / n_{i-1}, step length
+  float frac;                       // sum of the fractions of steps cut at the surface
   int lvl_prev, steps, full, tir_i, tir_b;
-  double opl_x;  // exterior segment + cut steps, in optical length
+  double opl_x;  // exterior segment, in optical length
 };
 
 __device__ __forceinline__ V3 pos64(const RayF& s) {
@@ -186,7 +187,7 @@ __device__ __forceinline__ void add_ff(float& hi, float& lo, float x) {
 
 __device__ __forceinline__ void finish(const TraceArgs& a, int64_t r, const RayF& s, V3 p, V3 d,
                                        int exit_id) {
-  double opl = s.opl_x + a.dopl * (double)s.full;
+  double opl = s.opl_x + a.dopl * ((double)s.full + (double)s.frac);
   store_ray(a, r, p, d, opl, exit_id, s.steps, s.tir_i, s.tir_b);
 }
 
@@ -198,14 +199,188 @@ __device__ __forceinline__ bool set_index(const DevMedium& m, RayF& s, float nu)
   return isfinite(n) && n > 0.0f;
 }
 
-// Start ray r: FP64 entry through the surface.  Returns false when the ray
-// is already finished (its output is written).
+__device__ __forceinline__ void renorm(float* v) {
+  float r = rsqrtf(fmaf(v[0], v[0], fmaf(v[1], v[1], v[2] * v[2])));
+  v[0] *= r;
+  v[1] *= r;
+  v[2] *= r;
+}
+
+__device__ __forceinline__ V3 v3f(const float* v) { return mk((double)v[0], (double)v[1], (double)v[2]); }
+
+// Box entry in FP32.  With an axis-aligned face the incidence cosine is one
+// direction component, the crossing a slab parameter and the reflection a
+// sign flip, so FP32 carries them to its own rounding; the entry point is
+// an ordinary FP32 product, accurate to one rounding of the ray's origin.
+template <class C>
+__device__ bool init_ray_box32(const DevMedium& m, const TraceArgs& a, int64_t r, RayF& s, V3 p64,
+                               V3 d64) {
+  const float* b = m.b_f;
+  float o[3] = {(float)p64.x, (float)p64.y, (float)p64.z};
+  float d[3] = {(float)d64.x, (float)d64.y, (float)d64.z};
+  float dd = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
+  if (!finite3(p64) || !finite3(d64) || !(dd > 0.0f) || !isfinite(dd)) {
+    finish(a, r, s, p64, d64, GRIN_EXIT_INVALID);
+    return false;
+  }
+  renorm(d);
+  float nu;
+  const bool in = o[0] > b[0] && o[0] < b[3] && o[1] > b[1] && o[1] < b[4] && o[2] > b[2] &&
+                  o[2] < b[5];
+  if (!in) {
+    float tn = -INFINITY, tf = INFINITY;
+    int axis = -1, hi = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (d[k] == 0.0f) {
+        if (!(o[k] > b[k] && o[k] < b[3 + k])) axis = -2;
+        continue;
+      }
+      float t1 = (b[k] - o[k]) / d[k], t2 = (b[3 + k] - o[k]) / d[k];
+      float lo = fminf(t1, t2), up = fmaxf(t1, t2);
+      if (lo > tn) {
+        tn = lo;
+        if (axis != -2) axis = k;
+        hi = d[k] < 0.0f;
+      }
+      tf = fminf(tf, up);
+    }
+    if (axis < 0 || !(tn >= 0.0f && tn < tf)) {
+      finish(a, r, s, p64, v3f(d), GRIN_EXIT_MISS);
+      return false;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) o[k] = fmaf(tn, d[k], o[k]);
+    o[axis] = hi ? b[3 + axis] : b[axis];
+    s.opl_x = m.n_ext * (double)tn;
+    C::eval(m, o[0], o[1], o[2], nu, s.gp[0], s.gp[1], s.gp[2], s.lvl_prev);
+    // Snell at the face: N = outward axis, c = N.I, mu = n_ext / n(P_b)
+    const float mu = m.n_ext_f / (m.base_f + nu);
+    const float c = hi ? d[axis] : -d[axis];
+    const float D = 1.0f - mu * mu * fmaf(-c, c, 1.0f);
+    if (D <= 0.0f) {
+      d[axis] = -d[axis];
+      finish(a, r, s, v3f(o), v3f(d), GRIN_EXIT_ENTRY_REFLECT);
+      return false;
+    }
+    const float gamma = fmaf(-mu, c, copysignf(sqrtf(D), c));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] *= mu;
+    d[axis] += hi ? gamma : -gamma;
+    renorm(d);
+  } else {
+    C::eval(m, o[0], o[1], o[2], nu, s.gp[0], s.gp[1], s.gp[2], s.lvl_prev);
+  }
+  if (!set_index(m, s, nu)) {
+    finish(a, r, s, v3f(o), v3f(d), GRIN_EXIT_INVALID);
+    return false;
+  }
+  if (a.max_steps <= 0) {
+    finish(a, r, s, v3f(o), v3f(d), GRIN_EXIT_MAXSTEPS);
+    return false;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    s.ph[k] = o[k];
+    s.pl[k] = 0.0f;
+    s.d[k] = d[k];
+    s.dl[k] = 0.0f;
+  }
+  s.h = (float)a.dopl * s.inv_prev;
+  return true;
+}
+
+// Box crossing in FP32 (see init_ray_box32): the fraction of the step to
+// the first face beyond, from the compensated point; Snell or reflection
+// with the face normal.  Same return codes as surface_event.
+template <class C>
+__device__ __forceinline__ int surface_event_box32(const DevMedium& m, const TraceArgs& a,
+                                                   int64_t r, RayF& s, float dopl_f,
+                                                   const float* qh) {
+  const float* b = m.b_f;
+  float dv[3];
+  float best = INFINITY;
+  int bf = -1;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    dv[k] = fmaf(s.h, s.d[k], s.h * s.dl[k]);
+    if (qh[k] <= b[k]) {
+      float t = ((b[k] - s.ph[k]) - s.pl[k]) / dv[k];
+      if (t < best) {
+        best = t;
+        bf = 2 * k;
+      }
+    }
+    if (qh[k] >= b[3 + k]) {
+      float t = ((b[3 + k] - s.ph[k]) - s.pl[k]) / dv[k];
+      if (t < best) {
+        best = t;
+        bf = 2 * k + 1;
+      }
+    }
+  }
+  if (bf < 0 || best > 1.0f) return 0;  // the compensated end point is inside
+  best = fmaxf(best, 0.0f);
+  s.frac += best;
+  ++s.steps;
+  const int axis = bf >> 1, hi = bf & 1;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float y = fmaf(best, dv[k], s.pl[k]);
+    float t = s.ph[k] + y;
+    s.pl[k] = y - (t - s.ph[k]);
+    s.ph[k] = t;
+  }
+  s.ph[axis] = hi ? b[3 + axis] : b[axis];
+  s.pl[axis] = 0.0f;
+  // Sec. II (i): N = outward face normal, mu = n_{i-1} / n_ext
+  const float mu = (m.base_f + s.nu_prev) / m.n_ext_f;
+  const float c = hi ? s.d[axis] : -s.d[axis];
+  const float D = 1.0f - mu * mu * fmaf(-c, c, 1.0f);
+  bool tir = D <= 0.0f;
+  if (GRIN_UNLIKELY(fabsf(D) <= kCritBand)) {
+    double mu64 = ((double)m.base_f + (double)s.nu_prev) / m.n_ext;
+    double c64 = (double)c + (double)(hi ? s.dl[axis] : -s.dl[axis]);
+    tir = 1.0 - mu64 * mu64 * (1.0 - c64 * c64) <= 0.0;
+  }
+  if (tir) {
+    // Sec. II (v): reflection flips the normal component exactly
+    s.d[axis] = -s.d[axis];
+    s.dl[axis] = -s.dl[axis];
+    ++s.tir_b;
+    s.h = dopl_f * s.inv_prev;
+    float nu;
+    C::eval(m, s.ph[0], s.ph[1], s.ph[2], nu, s.gp[0], s.gp[1], s.gp[2], s.lvl_prev);
+    if (!set_index(m, s, nu)) {
+      finish(a, r, s, pos64(s), dir64(s), GRIN_EXIT_INVALID);
+      return 2;
+    }
+    if (s.steps >= a.max_steps) {
+      finish(a, r, s, pos64(s), dir64(s), GRIN_EXIT_MAXSTEPS);
+      return 2;
+    }
+    return 1;
+  }
+  float R[3];
+  const float gamma = fmaf(-mu, c, copysignf(sqrtf(fmaxf(D, 0.0f)), c));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) R[k] = mu * (s.d[k] + s.dl[k]);
+  R[axis] += hi ? gamma : -gamma;
+  renorm(R);
+  finish(a, r, s, pos64(s), v3f(R), bf);
+  return 2;
+}
+
+// Start ray r: entry through the surface (FP64, or FP32 for a box).
+// Returns false when the ray is already finished (its output is written).
 template <class C>
 __device__ bool init_ray(const DevMedium& m, const TraceArgs& a, int64_t r, RayF& s) {
   V3 p = mk(ld(a.ox, r, a.dtype), ld(a.oy, r, a.dtype), ld(a.oz, r, a.dtype));
   V3 d = mk(ld(a.dx, r, a.dtype), ld(a.dy, r, a.dtype), ld(a.dz, r, a.dtype));
   s.steps = s.full = s.tir_i = s.tir_b = 0;
   s.opl_x = 0.0;
+  s.frac = 0.0f;
+  if (C::bk(m) == GRIN_BOUNDARY_BOX) return init_ray_box32<C>(m, a, r, s, p, d);
   if (!finite3(p) || !finite3(d) || dot(d, d) == 0.0) {
     finish(a, r, s, p, d, GRIN_EXIT_INVALID);
     return false;
@@ -245,19 +420,14 @@ __device__ bool init_ray(const DevMedium& m, const TraceArgs& a, int64_t r, RayF
   return true;
 }
 
-__device__ __forceinline__ void renorm(float* v) {
-  float r = rsqrtf(fmaf(v[0], v[0], fmaf(v[1], v[1], v[2] * v[2])));
-  v[0] *= r;
-  v[1] *= r;
-  v[2] *= r;
-}
 
-// The step would end outside the surface (by FP32): FP64 crossing
-// (Sec. II (i)).  Returns 0 if FP64 puts the end inside after all (take the
+// The step would end outside the surface (by FP32): crossing (Sec. II (i)),
+// in FP32 for a box, else in FP64.  Returns 0 if FP64 puts the end inside after all (take the
 // ordinary step), 1 if the ray reflected and goes on, 2 if it finished.
 template <class C>
 __device__ __forceinline__ int surface_event(const DevMedium& m, const TraceArgs& a, int64_t r,
-                                             RayF& s, float dopl_f) {
+                                             RayF& s, float dopl_f, const float* qh) {
+  if (C::bk(m) == GRIN_BOUNDARY_BOX) return surface_event_box32<C>(m, a, r, s, dopl_f, qh);
   V3 p = pos64(s), d = dir64(s);
   V3 q = axpy((double)s.h, d, p);
   if (inside64(m, q)) return 0;
@@ -265,7 +435,7 @@ __device__ __forceinline__ int surface_event(const DevMedium& m, const TraceArgs
   V3 pb, nb;
   int face;
   exit64(m, p, q, t, pb, nb, face);
-  s.opl_x += a.dopl * t;
+  s.frac += (float)t;
   ++s.steps;
   double n_prev = (double)m.base_f + (double)s.nu_prev;
   if (refract64(d, nb, n_prev / m.n_ext)) {
@@ -321,7 +491,7 @@ __device__ __noinline__ bool step_slow(const DevMedium& m, const TraceArgs& a, i
     qh[k] = t;
   }
   if (GRIN_UNLIKELY(!C::inside(m, qh))) {
-    int rc = surface_event<C>(m, a, r, s, dopl_f);
+    int rc = surface_event<C>(m, a, r, s, dopl_f, qh);
     if (rc == 2) return false;
     if (rc == 1) return true;
   }
