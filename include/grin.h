@@ -201,6 +201,33 @@ int grin_trace_host(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
  * context (for accounting). */
 int grin_ctx_last_launches(grin_ctx ctx, int32_t* launches);
 
+/* Largest batch grin_trace_host_static accepts. */
+#define GRIN_STATIC_MAX_RAYS 65536
+
+/* Trace without allocating anything, for callers that may not call
+ * cudaMalloc (a plug-in whose host application owns the GPU memory budget,
+ * a loop that must not allocate after start-up, a caller whose device
+ * memory is all in its own pool).  The paper has no counterpart: this is a
+ * deployment variant of grin_trace_host.
+ *   - No context and no grin_medium: `desc` is read directly; only
+ *     polynomial media (GRIN_MEDIUM_POLY) are accepted, since they live
+ *     entirely in the kernel's parameters; others give GRIN_ERR_INVALID_ARG.
+ *   - rays and out are HOST buffers as for grin_trace_host; at most
+ *     GRIN_STATIC_MAX_RAYS rays (GRIN_ERR_INVALID_ARG beyond).
+ *   - The device side uses one fixed array of about 7.5 MiB that every GPU
+ *     loading the library reserves until the process exits; it holds the
+ *     staged rays, the results and the ray-queue counter (cleared on the
+ *     stream before each launch).  It is shared by all calls and keeps the
+ *     last call's contents: calls whose GPU work overlaps (other streams or
+ *     threads) race on it and must be serialised by the caller.
+ *   - Runs on the calling thread's current device.  The first call on each
+ *     device looks the array's address up (cudaGetSymbolAddress); make that
+ *     first call before any stream capture.
+ *   - Synchronises `cuda_stream` before returning; same statuses as
+ *     grin_trace_host. */
+int grin_trace_host_static(const grin_medium_desc* desc, const grin_rays* rays,
+                           const grin_params* params, const grin_out* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

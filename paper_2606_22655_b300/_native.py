@@ -19,6 +19,7 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA runtim
 EXIT_MISS, EXIT_ENTRY_REFLECT, EXIT_MAXSTEPS, EXIT_INVALID = -1, -2, -3, -4
 F32, F64 = 0, 1
 PREC_FP64, PREC_FP32_MIXED, PREC_FP64_FAST = 0, 1, 2
+STATIC_MAX_RAYS = 65536
 
 _d3 = ctypes.c_double * 3
 _vp = ctypes.c_void_p
@@ -78,6 +79,7 @@ def load() -> ctypes.CDLL:
         "grin_trace": (ctypes.c_int, [_vp, _vp, P(Rays), P(Params), P(Out), _vp]),
         "grin_trace_host": (ctypes.c_int, [_vp, _vp, P(Rays), P(Params), P(Out), _vp]),
         "grin_ctx_last_launches": (ctypes.c_int, [_vp, P(ctypes.c_int32)]),
+        "grin_trace_host_static": (ctypes.c_int, [P(MediumDesc), P(Rays), P(Params), P(Out), _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
