@@ -64,6 +64,30 @@ def flops_per_step(degree_class: int) -> int:
     return 2 * poly_fma_count(degree_class) + STEP_FIXED_FLOPS
 
 
+KERNEL_SOURCES = ["paper_2606_22655_b300/csrc/trace_mixed.cu", "paper_2606_22655_b300/csrc/grin_device.cuh",
+                  "paper_2606_22655_b300/csrc/grin_internal.h"]
+PROFILE = "profiles/k_trace_mixed_freeform_block_1048576.md"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, or None if the
+    kernel sources changed since that capture."""
+    import hashlib
+    import re
+    try:
+        text = open(os.path.join(ROOT, PROFILE)).read()
+        h = hashlib.sha256()
+        for f in KERNEL_SOURCES:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+    except OSError:
+        return None
+    sha = re.search(r"kernel_source_sha: ([0-9a-f]+)", text)
+    tb = re.search(r"traffic_bytes_per_launch: (\d+)", text)
+    if not sha or not tb or sha.group(1) != h.hexdigest()[:16]:
+        return None
+    return int(tb.group(1))
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -299,7 +323,8 @@ def run_ours(args):
                    "ray_steps_per_step": steps_per_trace,
                    "l2": "256 MiB buffer zeroed before every step, inside the timed region"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": profiled_traffic() if args.rays == N_RAYS and args.workload == "freeform" else None,
                      "kernel": "k_trace_mixed<Cfg<4,false,false,box,linear>,false>", "kernel_ms": 1e3 * mean_kern,
                      "flops_per_ray_step": flops_per_step(4),
                      "peak_note": "148 SMs x 128 FP32 lanes x 2 FLOP x 2.032 GHz (derived)"},
