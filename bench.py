@@ -155,6 +155,70 @@ def oracle_rate(wl, stride: int, threads: int, rays=None):
     return float(r["steps"].sum()) / dt, len(idx), dt, idx, r
 
 
+def serve_load(ctx, dev_index: int, rates, jobs_per_rate: int, seed: int = 7):
+    """Poisson arrivals of trace jobs into one grin_serve server; per rate:
+    p50/p99 latency (submit to results in host memory) and ray-steps/s.
+    Jobs draw a medium from {Luneburg lens, freeform block, 128^3 blob grid,
+    its 32-shell layered version} and a ray count log-uniform in
+    [1e3, 1e6]; dL0 is the medium's own."""
+    import torch
+    from paper_2606_22655_b300 import tracer
+    from paper_2606_22655_b300 import workloads as W
+    pool = [W.luneburg_workload(), W.freeform_workload(1 << 20),
+            W.blob_workload(n_rays=1 << 20, res=128), W.blob_workload(n_rays=1 << 20, res=128, n_levels=32)]
+    media = [tracer.Medium(ctx, wl.medium) for wl in pool]
+    rays = [tracer.RayBatch.from_numpy(wl.rays.origins, wl.rays.dirs, device="cpu", dtype=torch.float32, pin=True)
+            for wl in pool]
+    n_out = 24
+    outs = [tracer.empty_result(1 << 20, "cpu") for _ in range(n_out)]
+    srv = tracer.Server(ctx, 16 << 30)
+    results = []
+    for ri, rate in enumerate(rates):
+        rng = np.random.default_rng(seed + ri)
+        kinds = rng.integers(0, len(pool), jobs_per_rate)
+        counts = np.exp(rng.uniform(np.log(1e3), np.log(1e6), jobs_per_rate)).astype(np.int64)
+        counts = np.minimum(counts, [pool[k].rays.n for k in kinds])
+        gaps = rng.exponential(1.0 / rate, jobs_per_rate)
+        t0 = time.perf_counter()
+        inflight, lat, steps = [], [], 0.0
+        next_t = t0
+        free = list(range(n_out))
+        for j in range(jobs_per_rate):
+            next_t += gaps[j]
+            while True:
+                now = time.perf_counter()
+                done = [x for x in inflight if srv.poll(x[0])[0] >= 2]
+                for x in done:
+                    st, l = srv.poll(x[0])
+                    lat.append(l)
+                    steps += float(outs[x[1]]["steps"][: x[2]].sum())
+                    free.append(x[1])
+                    inflight.remove(x)
+                if now >= next_t and free:
+                    break
+                time.sleep(0.0002)
+            k = int(kinds[j]); n = int(counts[j]); ob = free.pop()
+            sub = tracer.RayBatch(*[t[:n] for t in rays[k].tensors()])
+            out = {key: v[:n] for key, v in outs[ob].items()}
+            jid, _ = srv.submit(media[k], sub, pool[k].dopl, pool[k].max_steps, out=out)
+            inflight.append((jid, ob, n))
+        for x in inflight:
+            srv.wait(x[0], 600)
+            st, l = srv.poll(x[0])
+            lat.append(l)
+            steps += float(outs[x[1]]["steps"][: x[2]].sum())
+        wall = time.perf_counter() - t0
+        lat = np.array(lat)
+        results.append({"rate_jobs_per_s": rate, "jobs": jobs_per_rate, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                        "p99_ms": 1e3 * float(np.percentile(lat, 99)), "ray_steps_per_s": steps / wall,
+                        "wall_s": wall})
+    st = srv.stats()
+    srv.close()
+    return {"media": ["luneburg", "freeform_block", "grid_128", "layered_128"],
+            "ray_count": "log-uniform [1e3, 1e6]", "arrivals": "Poisson", "step_quantum": 1024,
+            "sweep": results, "ticks": st["ticks"], "failed": st["failed"]}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -309,6 +373,10 @@ def run_ours(args):
     h2d = 6 * 4 * hrays.count
     d2h = (7 * 8 + 4 * 4) * hrays.count
 
+    serve = None
+    if ws == 1 and not args.no_serve:
+        serve = serve_load(ctx, local, rates=[10.0, 40.0, 160.0, 640.0], jobs_per_rate=args.serve_jobs)
+
     if rank != 0:
         return 0
     flops_launch = flops_per_step(4) * steps_per_trace
@@ -346,6 +414,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
+        "serve": serve,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -361,6 +430,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--ref-stride", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-latency sweep")
+    ap.add_argument("--serve-jobs", type=int, default=60, help="jobs per arrival rate in the sweep")
     ap.add_argument("--rays", type=int, default=N_RAYS,
                     help="ray count (profiling of a smaller case; the line then names it)")
     ap.add_argument("--workload", choices=["freeform", "grid", "layered", "luneburg"], default="freeform",

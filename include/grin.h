@@ -201,6 +201,62 @@ int grin_trace_host(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
  * context (for accounting). */
 int grin_ctx_last_launches(grin_ctx ctx, int32_t* launches);
 
+/* ------------------------------------------------------------ serving
+ *
+ * A server batches trace jobs continuously on one GPU.  A job is a batch of
+ * rays through one medium (host buffers, like grin_trace_host) traced by the
+ * mixed-precision tracer.  A scheduler thread owns the GPU work:
+ *   - admission: queued jobs are admitted first come, first served, when
+ *     their device footprint (rays in, results out, resident ray state) fits
+ *     in what is left of the server's device arena (hbm_budget_bytes, taken
+ *     once at creation) and resident ray slots are free;
+ *   - ticks: every tick advances each running job's slots by step_quantum
+ *     steps; a slot whose ray ends takes the job's next ray; the ray state
+ *     stays on the device between ticks, so a small job submitted while a
+ *     large one runs finishes after a few ticks instead of after it;
+ *   - completion: when all of a job's rays have ended its results are copied
+ *     to the caller's host buffers and the job becomes GRIN_JOB_DONE.
+ * Per-ray results do not depend on the other jobs in flight (bitwise equal
+ * to grin_trace_host with the mixed tracer).  The caller keeps its host
+ * buffers alive until the job is DONE, FAILED or CANCELLED.  All grin_serve_*
+ * calls are thread-safe. */
+enum { GRIN_JOB_QUEUED = 0, GRIN_JOB_RUNNING = 1, GRIN_JOB_DONE = 2, GRIN_JOB_FAILED = 3,
+       GRIN_JOB_CANCELLED = 4 };
+
+typedef struct {
+  size_t hbm_budget_bytes;   /* device arena for job data (> 0) */
+  int32_t step_quantum;      /* steps per slot per tick; 0 = 1024 */
+  int32_t max_slots_per_job; /* resident slots one job may hold; 0 = a quarter of the GPU's */
+} grin_serve_config;
+
+typedef struct {
+  uint64_t submitted, done, failed, cancelled;
+  uint64_t ticks;
+  double ray_steps;          /* summed over finished jobs */
+  size_t arena_bytes, arena_in_use;
+  int32_t slots_total, slots_in_use, jobs_queued, jobs_running;
+} grin_serve_counters;
+
+/* Create a server on the context's device.  Errors: GRIN_ERR_INVALID_ARG,
+ * GRIN_ERR_OOM if the arena cannot be allocated. */
+int grin_serve_create(grin_ctx ctx, const grin_serve_config* config, grin_server* out);
+/* Stop the scheduler; queued and running jobs end as CANCELLED. */
+int grin_serve_destroy(grin_server server);
+/* Queue a job (precision must be GRIN_PREC_FP32_MIXED; medium from the
+ * server's context; rays and out are host buffers).  GRIN_ERR_BUSY if the
+ * job could never fit the arena. */
+int grin_serve_submit(grin_server server, grin_medium medium, const grin_rays* rays,
+                      const grin_params* params, const grin_out* out, uint64_t* job_id);
+/* State of a job and its latency: submit to completion once DONE, else the
+ * time since submission.  GRIN_ERR_NOT_FOUND for an unknown id. */
+int grin_serve_poll(grin_server server, uint64_t job_id, int32_t* state, double* latency_s);
+/* Wait up to timeout_s seconds for the job to end (DONE, FAILED or
+ * CANCELLED); GRIN_ERR_TIMEOUT if it has not. */
+int grin_serve_wait(grin_server server, uint64_t job_id, double timeout_s, int32_t* state);
+/* Cancel a queued or running job (takes effect at the next tick). */
+int grin_serve_cancel(grin_server server, uint64_t job_id);
+int grin_serve_stats(grin_server server, grin_serve_counters* stats);
+
 /* Largest batch grin_trace_host_static accepts. */
 #define GRIN_STATIC_MAX_RAYS 65536
 

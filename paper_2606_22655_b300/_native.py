@@ -55,6 +55,21 @@ class Params(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32)]
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("step_quantum", ctypes.c_int32),
+                ("max_slots_per_job", ctypes.c_int32)]
+
+
+class ServeCounters(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("done", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("cancelled", ctypes.c_uint64), ("ticks", ctypes.c_uint64), ("ray_steps", ctypes.c_double),
+                ("arena_bytes", ctypes.c_size_t), ("arena_in_use", ctypes.c_size_t),
+                ("slots_total", ctypes.c_int32), ("slots_in_use", ctypes.c_int32),
+                ("jobs_queued", ctypes.c_int32), ("jobs_running", ctypes.c_int32)]
+
+
+JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED, JOB_CANCELLED = 0, 1, 2, 3, 4
+
 _lib = None
 
 
@@ -80,6 +95,13 @@ def load() -> ctypes.CDLL:
         "grin_trace_host": (ctypes.c_int, [_vp, _vp, P(Rays), P(Params), P(Out), _vp]),
         "grin_ctx_last_launches": (ctypes.c_int, [_vp, P(ctypes.c_int32)]),
         "grin_trace_host_static": (ctypes.c_int, [P(MediumDesc), P(Rays), P(Params), P(Out), _vp]),
+        "grin_serve_create": (ctypes.c_int, [_vp, P(ServeConfig), P(_vp)]),
+        "grin_serve_destroy": (ctypes.c_int, [_vp]),
+        "grin_serve_submit": (ctypes.c_int, [_vp, _vp, P(Rays), P(Params), P(Out), P(ctypes.c_uint64)]),
+        "grin_serve_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, P(ctypes.c_int32), P(ctypes.c_double)]),
+        "grin_serve_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_double, P(ctypes.c_int32)]),
+        "grin_serve_cancel": (ctypes.c_int, [_vp, ctypes.c_uint64]),
+        "grin_serve_stats": (ctypes.c_int, [_vp, P(ServeCounters)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -14,32 +14,7 @@
 
 using grin::DevMedium;
 
-namespace {
-
-constexpr int kQueueSlots = 4096;
-
-}  // namespace
-
-struct grin_ctx_s {
-  int device = 0;
-  int sm_count = 0;
-  // One 8-byte ray-queue counter per trace call, taken round robin, so calls
-  // on different streams do not share a counter while fewer than kQueueSlots
-  // are in flight.
-  unsigned long long* queues = nullptr;
-  int next_queue = 0;
-  int last_launches = 0;
-  // device staging for grin_trace_host (grown on demand)
-  void* stage = nullptr;
-  size_t stage_bytes = 0;
-};
-
-struct grin_medium_s {
-  grin_ctx ctx = nullptr;
-  DevMedium dm{};
-  float* grid_dev = nullptr;
-  size_t grid_bytes = 0;
-};
+using grin::kQueueSlots;
 
 extern "C" {
 

@@ -61,4 +61,33 @@ int launch_fp64_fast(const DevMedium& m, const TraceArgs& a, cudaStream_t s, int
 int launch_mixed(const DevMedium& m, const TraceArgs& a, unsigned long long* queue,
                  cudaStream_t s, int sm_count);
 
+// Serving: bytes of one resident ray slot, and one tick over a job's slots
+// (nslots a multiple of 128; counters = {next ray, finished rays}).
+size_t serve_slot_bytes();
+int launch_serve_tick(const DevMedium& m, const TraceArgs& a, void* slots, int nslots,
+                      unsigned long long* counters, int quantum, cudaStream_t s);
+
+constexpr int kQueueSlots = 4096;
+
 }  // namespace grin
+
+struct grin_ctx_s {
+  int device = 0;
+  int sm_count = 0;
+  // One 8-byte ray-queue counter per trace call, taken round robin, so calls
+  // on different streams do not share a counter while fewer than kQueueSlots
+  // are in flight.
+  unsigned long long* queues = nullptr;
+  int next_queue = 0;
+  int last_launches = 0;
+  // device staging for grin_trace_host (grown on demand)
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+};
+
+struct grin_medium_s {
+  grin_ctx ctx = nullptr;
+  grin::DevMedium dm{};
+  float* grid_dev = nullptr;
+  size_t grid_bytes = 0;
+};

@@ -733,4 +733,102 @@ int launch_mixed(const DevMedium& m, const TraceArgs& a, unsigned long long* que
   }
 }
 
+// ------------------------------------------------------------- serving
+//
+// One tick of the continuous-batching server: the job's resident slots (one
+// per thread) each run up to `quantum` steps, claiming the job's next ray
+// from counters[0] whenever their ray ends; finished rays are counted into
+// counters[1].  The full per-ray FP32 state stays in HBM between ticks, so
+// the arithmetic of a ray does not depend on how its steps are split into
+// ticks: results are bitwise those of grin_trace.
+
+struct SlotState {
+  RayF s;
+  long long ray;
+  int active;
+  int pad;
+};
+
+template <class C, bool LAYERED>
+__global__ void __launch_bounds__(128, C::kMinBlocks) k_serve_tick(DevMedium m, TraceArgs a,
+                                                                   SlotState* slots,
+                                                                   unsigned long long* counters,
+                                                                   int quantum) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned lane = threadIdx.x & 31u;
+  const float dopl_f = (float)a.dopl;
+  SlotState* me = slots + t;
+  RayF s = me->s;
+  bool active = me->active != 0;
+  int64_t ray = me->ray;
+  bool exhausted = false;
+  unsigned done = 0;
+  for (int k = 0; k < quantum; k += kStepQuantum) {
+    const unsigned need = __ballot_sync(0xffffffffu, !active);
+    if (need && !exhausted) {
+      const int leader = __ffs(need) - 1;
+      const unsigned cnt = __popc(need);
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd(counters, (unsigned long long)cnt);
+      base = __shfl_sync(0xffffffffu, base, leader);
+      exhausted = base + cnt >= (unsigned long long)a.count;
+      if (!active) {
+        const unsigned long long rr = base + __popc(need & ((1u << lane) - 1u));
+        if (rr < (unsigned long long)a.count) {
+          ray = (int64_t)rr;
+          active = init_ray<C>(m, a, ray, s);
+          if (!active) ++done;
+        }
+      }
+    }
+    if (!__any_sync(0xffffffffu, active)) {
+      if (exhausted) break;
+      continue;
+    }
+#pragma unroll 1
+    for (int j = 0; j < kStepQuantum; ++j) {
+      if (active) {
+        active = step_ray<C, LAYERED>(m, a, ray, s, dopl_f);
+        if (!active) ++done;
+      }
+    }
+  }
+  me->s = s;
+  me->active = active ? 1 : 0;
+  me->ray = ray;
+  done = __reduce_add_sync(0xffffffffu, done);
+  if (lane == 0 && done) atomicAdd(counters + 1, (unsigned long long)done);
+}
+
+size_t serve_slot_bytes() { return sizeof(SlotState); }
+
+template <int PC, bool GRID, bool LAYERED, int BK, int FORM>
+static int tick_t(const DevMedium& m, const TraceArgs& a, void* slots, int nslots,
+                  unsigned long long* counters, int quantum, cudaStream_t st) {
+  using C = Cfg<PC, GRID, LAYERED, BK, FORM>;
+  k_serve_tick<C, LAYERED><<<nslots / 128, 128, 0, st>>>(m, a, (SlotState*)slots, counters, quantum);
+  return cudaGetLastError() == cudaSuccess ? 1 : GRIN_ERR_CUDA;
+}
+
+template <int PC, bool GRID>
+static int tick_pc(const DevMedium& m, const TraceArgs& a, void* slots, int nslots,
+                   unsigned long long* counters, int quantum, cudaStream_t st) {
+  if (m.n_levels > 0) return tick_t<PC, GRID, true, -1, -1>(m, a, slots, nslots, counters, quantum, st);
+  const bool fast = m.bkind == GRIN_BOUNDARY_BOX && (GRID || m.form == GRIN_FORM_LINEAR);
+  return fast ? tick_t<PC, GRID, false, GRIN_BOUNDARY_BOX, GRIN_FORM_LINEAR>(m, a, slots, nslots,
+                                                                             counters, quantum, st)
+              : tick_t<PC, GRID, false, -1, -1>(m, a, slots, nslots, counters, quantum, st);
+}
+
+int launch_serve_tick(const DevMedium& m, const TraceArgs& a, void* slots, int nslots,
+                      unsigned long long* counters, int quantum, cudaStream_t s) {
+  if (nslots <= 0 || nslots % 128 != 0 || quantum <= 0) return GRIN_ERR_INVALID_ARG;
+  if (m.kind == GRIN_MEDIUM_GRID) return tick_pc<0, true>(m, a, slots, nslots, counters, quantum, s);
+  switch (m.pclass) {
+    case kPoly2: return tick_pc<2, false>(m, a, slots, nslots, counters, quantum, s);
+    case kPoly4: return tick_pc<4, false>(m, a, slots, nslots, counters, quantum, s);
+    default: return tick_pc<6, false>(m, a, slots, nslots, counters, quantum, s);
+  }
+}
+
 }  // namespace grin

@@ -222,3 +222,66 @@ def to_numpy(res: Dict[str, torch.Tensor]) -> Dict[str, np.ndarray]:
     return dict(P=np.stack([h["px"], h["py"], h["pz"]], 1), d=np.stack([h["dx"], h["dy"], h["dz"]], 1),
                 opl=h["opl"], exit_id=h["exit_id"], steps=h["steps"], tir_internal=h["tir_internal"],
                 tir_boundary=h["tir_boundary"])
+
+
+class Server:
+    """grin_serve_*: continuous batching of trace jobs (mixed precision,
+    host buffers).  Buffers handed to submit() are kept referenced here until
+    the job has ended."""
+
+    def __init__(self, ctx: Context, hbm_budget_bytes: int, step_quantum: int = 0,
+                 max_slots_per_job: int = 0):
+        self.ctx = ctx
+        cfg = N.ServeConfig(int(hbm_budget_bytes), int(step_quantum), int(max_slots_per_job))
+        h = ctypes.c_void_p()
+        N.check("grin_serve_create", ctx.lib.grin_serve_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, medium: Medium, rays: RayBatch, dopl: float, max_steps: int,
+               out: Optional[Dict[str, torch.Tensor]] = None):
+        """Queue a job; returns (job id, result dict filled when it is DONE)."""
+        if out is None:
+            out = empty_result(rays.count, "cpu")
+        rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, "mixed")
+        jid = ctypes.c_uint64()
+        N.check("grin_serve_submit", self.ctx.lib.grin_serve_submit(
+            self.handle, medium.handle, ctypes.byref(rs), ctypes.byref(ps), ctypes.byref(os_), ctypes.byref(jid)))
+        self._keep[jid.value] = (rays, out)
+        return jid.value, out
+
+    def poll(self, job_id: int):
+        st, lat = ctypes.c_int32(), ctypes.c_double()
+        N.check("grin_serve_poll", self.ctx.lib.grin_serve_poll(self.handle, job_id, ctypes.byref(st), ctypes.byref(lat)))
+        if st.value >= N.JOB_DONE:
+            self._keep.pop(job_id, None)
+        return st.value, lat.value
+
+    def wait(self, job_id: int, timeout_s: float = 60.0) -> int:
+        st = ctypes.c_int32()
+        rc = self.ctx.lib.grin_serve_wait(self.handle, job_id, float(timeout_s), ctypes.byref(st))
+        if rc == -5:
+            return -5
+        N.check("grin_serve_wait", rc)
+        self._keep.pop(job_id, None)
+        return st.value
+
+    def cancel(self, job_id: int) -> None:
+        N.check("grin_serve_cancel", self.ctx.lib.grin_serve_cancel(self.handle, job_id))
+
+    def stats(self) -> Dict[str, float]:
+        c = N.ServeCounters()
+        N.check("grin_serve_stats", self.ctx.lib.grin_serve_stats(self.handle, ctypes.byref(c)))
+        return {k: getattr(c, k) for k, _ in N.ServeCounters._fields_}
+
+    def close(self) -> None:
+        if self.handle:
+            N.check("grin_serve_destroy", self.ctx.lib.grin_serve_destroy(self.handle))
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,139 @@
+"""The continuous-batching server (grin_serve_*), through the C ABI.
+
+Each job's results must be bitwise those of grin_trace_host with the mixed
+tracer, whether the job runs alone or among others of different media and
+sizes; admission respects the device arena; cancellation and bounded waits
+leave the server usable.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2606_22655_b300 import _native as N
+from paper_2606_22655_b300 import tracer
+from paper_2606_22655_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("px", "py", "pz", "dx", "dy", "dz", "opl", "exit_id", "steps", "tir_internal", "tir_boundary")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = tracer.Context(0)
+    yield c
+    c.close()
+
+
+def host_rays(wl, n=None, dtype=torch.float32):
+    o, d = wl.rays.origins, wl.rays.dirs
+    if n is not None:
+        o, d = o[:n], d[:n]
+    return tracer.RayBatch.from_numpy(o, d, device="cpu", dtype=dtype)
+
+
+def same(a, b):
+    for k in KEYS:
+        np.testing.assert_array_equal(a[k].numpy(), b[k].numpy(), err_msg=k)
+
+
+@pytest.fixture(scope="module")
+def jobs(ctx):
+    wls = [W.freeform_workload(30000), W.luneburg_workload(), W.blob_workload(n_rays=3000, res=64),
+           W.blob_workload(n_rays=2000, res=64, n_levels=32), W.freeform_workload(700, ray_seed=5)]
+    out = []
+    for wl in wls:
+        med = tracer.Medium(ctx, wl.medium)
+        rays = host_rays(wl)
+        ref = tracer.trace_host(ctx, med, rays, wl.dopl, wl.max_steps, "mixed")
+        out.append((wl, med, rays, ref))
+    return out
+
+
+def test_alone_equals_trace_host(ctx, jobs):
+    srv = tracer.Server(ctx, 1 << 30)
+    for wl, med, rays, ref in jobs:
+        jid, res = srv.submit(med, rays, wl.dopl, wl.max_steps)
+        assert srv.wait(jid, 120) == N.JOB_DONE
+        same(res, ref)
+    st = srv.stats()
+    assert st["done"] == len(jobs) and st["failed"] == 0
+    srv.close()
+
+
+def test_mix_equals_alone(ctx, jobs):
+    srv = tracer.Server(ctx, 1 << 30, step_quantum=256)
+    handles = []
+    for rep in range(2):
+        for wl, med, rays, ref in jobs:
+            handles.append((srv.submit(med, rays, wl.dopl, wl.max_steps), ref))
+    for (jid, res), ref in handles:
+        assert srv.wait(jid, 120) == N.JOB_DONE
+        same(res, ref)
+    st = srv.stats()
+    assert st["done"] == 2 * len(jobs)
+    total = sum(int(ref["steps"].sum()) for _, ref in handles)
+    assert st["ray_steps"] == total
+    srv.close()
+
+
+def test_admission_by_arena(ctx, jobs):
+    wl, med, rays, ref = jobs[0]
+    # room for one 30000-ray job at a time (rays, results and slots)
+    budget = 30000 * (24 + 72) + 30080 * 160 + 4096
+    srv = tracer.Server(ctx, budget)
+    ids = [srv.submit(med, rays, wl.dopl, wl.max_steps) for _ in range(3)]
+    for jid, res in ids:
+        assert srv.wait(jid, 120) == N.JOB_DONE
+        same(res, ref)
+    big = host_rays(W.freeform_workload(200000))
+    with pytest.raises(N.GrinError) as e:
+        srv.submit(med, big, wl.dopl, wl.max_steps)
+    assert e.value.status == -6  # BUSY: could never fit
+    srv.close()
+
+
+def test_cancel_and_wait_timeout_leave_server_usable(ctx, jobs):
+    srv = tracer.Server(ctx, 1 << 31, step_quantum=64)
+    wl = W.freeform_workload(1 << 20)
+    med = tracer.Medium(ctx, wl.medium)
+    jid, _ = srv.submit(med, host_rays(wl), wl.dopl, wl.max_steps)
+    assert srv.wait(jid, 0.001) == -5  # timed out, job still in flight
+    srv.cancel(jid)
+    assert srv.wait(jid, 60) == N.JOB_CANCELLED
+    wl2, med2, rays2, ref2 = jobs[1]
+    jid2, res2 = srv.submit(med2, rays2, wl2.dopl, wl2.max_steps)
+    assert srv.wait(jid2, 60) == N.JOB_DONE
+    same(res2, ref2)
+    st = srv.stats()
+    assert st["cancelled"] == 1 and st["arena_in_use"] == 0
+    with pytest.raises(N.GrinError) as e:
+        srv.poll(123456789)
+    assert e.value.status == -7
+    srv.close()
+
+
+def test_submit_argument_errors(ctx, jobs):
+    srv = tracer.Server(ctx, 1 << 28)
+    wl, med, rays, ref = jobs[0]
+    for dopl, ms in ((0.0, 10), (1e-3, -1)):
+        with pytest.raises(N.GrinError) as e:
+            srv.submit(med, rays, dopl, ms)
+        assert e.value.status == -1
+    other = tracer.Context(0)
+    foreign = tracer.Medium(other, wl.medium)
+    with pytest.raises(N.GrinError):
+        srv.submit(foreign, rays, wl.dopl, wl.max_steps)
+    empty = tracer.RayBatch(*[torch.empty(0) for _ in range(6)])
+    jid, _ = srv.submit(med, empty, wl.dopl, wl.max_steps)
+    assert srv.poll(jid)[0] == N.JOB_DONE
+    nan = host_rays(wl, 64)
+    nan.dx[:8] = float("nan")
+    jid, res = srv.submit(med, nan, wl.dopl, wl.max_steps)
+    assert srv.wait(jid, 60) == N.JOB_DONE
+    assert (res["exit_id"][:8] == N.EXIT_INVALID).all() and (res["exit_id"][8:] >= 0).all()
+    srv.close()
+    foreign.close()
+    other.close()
