@@ -219,6 +219,33 @@ def serve_load(ctx, dev_index: int, rates, jobs_per_rate: int, seed: int = 7):
             "sweep": results, "ticks": st["ticks"], "failed": st["failed"]}
 
 
+def adjoint_timing(ctx, dev):
+    """One gradient of the image-plane design loss (16 target spots on
+    z = 30 mm) with respect to the 128^3 blob grid: 262,144 collimated rays,
+    dL0 = 0.02 mm (up to 2000 steps), checkpoints every 64 steps; the
+    FP64 forward sweep with checkpoints plus the backward sweep."""
+    import torch
+    from paper_2606_22655_b300 import tracer
+    from paper_2606_22655_b300 import workloads as W
+    wl = W.blob_workload(n_rays=1 << 18, res=128)
+    med = tracer.Medium(ctx, wl.medium)
+    rays = tracer.RayBatch.from_numpy(wl.rays.origins, wl.rays.dirs, device=dev, dtype=torch.float64)
+    n = rays.count
+    g = {k: torch.randn(n, dtype=torch.float64, device=dev) * 1e-3 for k in tracer.OUT_FIELDS}
+    out, grad = tracer.trace_adjoint(ctx, med, rays, 0.02, 2000, g, wl.medium.grid.size, 64)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out, grad = tracer.trace_adjoint(ctx, med, rays, 0.02, 2000, g, wl.medium.grid.size, 64)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    t = e0.elapsed_time(e1) / 1e3
+    steps = float(out["steps"].sum())
+    return {"workload": "grid_128 adjoint, 262144 rays, dL0 0.02 mm, K=64", "seconds": t,
+            "forward_ray_steps": steps, "ray_steps_per_s_fwd_plus_bwd": steps / t,
+            "precision": "fp64", "gradient_params": int(wl.medium.grid.size)}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -373,6 +400,9 @@ def run_ours(args):
     h2d = 6 * 4 * hrays.count
     d2h = (7 * 8 + 4 * 4) * hrays.count
 
+    adjoint = None
+    if ws == 1 and not args.no_serve:
+        adjoint = adjoint_timing(ctx, dev)
     serve = None
     if ws == 1 and not args.no_serve:
         serve = serve_load(ctx, local, rates=[10.0, 40.0, 160.0, 640.0], jobs_per_rate=args.serve_jobs)
@@ -415,6 +445,7 @@ def run_ours(args):
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
         "serve": serve,
+        "adjoint": adjoint,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:

@@ -201,6 +201,45 @@ int grin_trace_host(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
  * context (for accounting). */
 int grin_ctx_last_launches(grin_ctx ctx, int32_t* launches);
 
+/* ------------------------------------------------------------ adjoint
+ *
+ * Gradient of a loss of the exit states with respect to the medium
+ * parameters, for direct design (the design use of VRT, Sec. VI): reverse
+ * mode through the discrete VRT map of the plain FP64 tracer with its
+ * branch decisions held fixed (refraction or TIR at each point, surface
+ * crossings, exit).  The forward sweep saves the ray state every
+ * checkpoint_every steps in `workspace`; the backward sweep recomputes each
+ * segment from its checkpoint and carries the adjoint back through it.
+ * Supported media: box boundary, not layered, and either a polynomial with
+ * n = p (gradient w.r.t. its C(degree+3,3) graded-lex coefficients) or a
+ * grid (gradient w.r.t. its nx*ny*nz samples, x fastest); others give
+ * GRIN_ERR_NOT_IMPLEMENTED. */
+
+/* dL/d(exit state): device FP64 arrays of `count` entries each (the same
+ * fields as grin_out; any may be NULL for zero). */
+typedef struct {
+  const double *px, *py, *pz;
+  const double *dx, *dy, *dz;
+  const double* opl;
+} grin_out_grad;
+
+/* Device bytes of workspace grin_trace_adjoint needs. */
+int grin_trace_adjoint_workspace_size(grin_medium medium, int64_t ray_count,
+                                      const grin_params* params, int32_t checkpoint_every,
+                                      size_t* bytes);
+
+/* Forward sweep (writes `out`, bitwise the results of grin_trace with
+ * GRIN_PREC_FP64) then backward sweep, adding dL/d(parameters) into the
+ * device FP64 array dL_dmedium (the caller zeroes it).  params->precision
+ * must be GRIN_PREC_FP64; 1 <= checkpoint_every <= 64; rays, out, dL_dout
+ * and workspace are device memory; asynchronous on cuda_stream.  Rays that
+ * miss, reflect at entry or are invalid contribute nothing. */
+int grin_trace_adjoint(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
+                       const grin_params* params, const grin_out* out,
+                       const grin_out_grad* dL_dout, double* dL_dmedium,
+                       int32_t checkpoint_every, void* workspace, size_t workspace_bytes,
+                       void* cuda_stream);
+
 /* ------------------------------------------------------------ serving
  *
  * A server batches trace jobs continuously on one GPU.  A job is a batch of

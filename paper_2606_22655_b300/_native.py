@@ -55,6 +55,10 @@ class Params(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32)]
 
 
+class OutGrad(ctypes.Structure):
+    _fields_ = [("px", _vp), ("py", _vp), ("pz", _vp), ("dx", _vp), ("dy", _vp), ("dz", _vp), ("opl", _vp)]
+
+
 class ServeConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("step_quantum", ctypes.c_int32),
                 ("max_slots_per_job", ctypes.c_int32)]
@@ -95,6 +99,10 @@ def load() -> ctypes.CDLL:
         "grin_trace_host": (ctypes.c_int, [_vp, _vp, P(Rays), P(Params), P(Out), _vp]),
         "grin_ctx_last_launches": (ctypes.c_int, [_vp, P(ctypes.c_int32)]),
         "grin_trace_host_static": (ctypes.c_int, [P(MediumDesc), P(Rays), P(Params), P(Out), _vp]),
+        "grin_trace_adjoint_workspace_size": (ctypes.c_int, [_vp, ctypes.c_int64, P(Params), ctypes.c_int32,
+                                                             P(ctypes.c_size_t)]),
+        "grin_trace_adjoint": (ctypes.c_int, [_vp, _vp, P(Rays), P(Params), P(Out), P(OutGrad), _vp, ctypes.c_int32,
+                                              _vp, ctypes.c_size_t, _vp]),
         "grin_serve_create": (ctypes.c_int, [_vp, P(ServeConfig), P(_vp)]),
         "grin_serve_destroy": (ctypes.c_int, [_vp]),
         "grin_serve_submit": (ctypes.c_int, [_vp, _vp, P(Rays), P(Params), P(Out), P(ctypes.c_uint64)]),

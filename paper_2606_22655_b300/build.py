@@ -26,7 +26,7 @@ INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # per-source extra flags: the plain FP64 tracer must not contract a*b+c; the
 # mixed tracer takes hardware-approximate FP32 division and square root
-EXTRA = {"trace_fp64.cu": ["--fmad=false"],
+EXTRA = {"trace_fp64.cu": ["--fmad=false"], "adjoint.cu": ["--fmad=false"],
          "trace_mixed.cu": ["-prec-div=false", "-prec-sqrt=false"]}
 
 

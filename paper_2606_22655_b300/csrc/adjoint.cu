@@ -1,0 +1,715 @@
+// adjoint.cu -- reverse-mode derivative of the traced exit states with
+// respect to the medium parameters (polynomial coefficients of n = p, or grid
+// samples), for the direct-design use of VRT (Chavez-Islas et al., Sec. VI).
+//
+// The derivative is that of the discrete map the plain FP64 tracer computes
+// (Sec. II, Eq. 1-9), with every branch decision (refraction, TIR, surface
+// crossing, exit) held at the one the forward sweep took.  Forward: the plain
+// step (plain_fp64.cuh, this file is built with --fmad=false like
+// trace_fp64.cu, so the decisions are the plain tracer's, which are the
+// oracle's), saving the ray state (P, I, n_{i-1}, step length) every K
+// steps.  Backward: for each K-step segment, last first, the segment is
+// recomputed from its checkpoint with the input state of every step kept in
+// thread-local memory, then the adjoint state
+// (dL/dP, dL/dI, dL/dn_{i-1}, dL/dh) is carried back through each step:
+//   normal step   P' = P + h I; n, grad n at P'; N = grad n / |grad n|;
+//                 c = N.I; mu = n_{i-1} / n; D = 1 - mu^2 (1 - c^2);
+//                 R = mu I + gamma N (gamma = -mu c + sgn(c) sqrt(D)) or, on
+//                 TIR, R = I - 2 c N; I' = R / |R|; h' = dL0 / n (TIR:
+//                 dL0 / n_{i-1}); n'_{i-1} = n;
+//   surface cross fraction t = (b - P_a) / (h I_a) of the step to the face,
+//                 P_b = P + t h I; exit refraction with the face normal, or
+//                 reflection (the normal component flips) and n'_{i-1} =
+//                 n(P_b);
+//   entry         the refraction at the entry point through mu = n_ext / n.
+// Parameters enter through n, grad n (first and, for dL/dP, second
+// derivatives of the interpolant or polynomial) at every point sampled.
+// Supported: box boundaries; polynomial media with n = p, or grid media;
+// continuous (not layered) fields.
+#include "plain_fp64.cuh"
+
+namespace grin {
+namespace adj {
+
+constexpr int kMaxK = 64;
+constexpr int kCk = 8;  // checkpoint words: P[3], I[3], n_{i-1}, h
+enum Kind : int { kNormal = 0, kCrossReflect = 1, kExit = 2 };
+
+struct St {
+  double P[3], d[3], n_prev, h;
+  int lvl, steps, full, ti, tb, exit_id;
+  double frac, opl_ext;
+  bool done;
+};
+
+// One iteration of the plain tracer's loop (trace_fp64.cu), on St.
+template <int PC, bool GRID>
+__device__ __forceinline__ int advance(const DevMedium& m, double dopl, St& s, int& face) {
+  using namespace plain;
+  double Q[3];
+  for (int k = 0; k < 3; ++k) Q[k] = s.P[k] + s.h * s.d[k];
+  double g[3];
+  if (!inside(m, Q)) {
+    double t, Pb[3], NB[3];
+    leave(m, s.P, Q, t, Pb, NB, face);
+    s.frac += t;
+    ++s.steps;
+    for (int k = 0; k < 3; ++k) s.P[k] = Pb[k];
+    if (snell(s.d, NB, s.n_prev / m.n_ext)) {
+      ++s.tb;
+      s.h = dopl / s.n_prev;
+      sample<PC, GRID, false>(m, s.P, s.n_prev, g, s.lvl);
+      if (!(isfinite(s.n_prev) && s.n_prev > 0.0)) {
+        s.exit_id = GRIN_EXIT_INVALID;
+        s.done = true;
+      }
+      return kCrossReflect;
+    }
+    s.exit_id = face;
+    s.done = true;
+    return kExit;
+  }
+  for (int k = 0; k < 3; ++k) s.P[k] = Q[k];
+  ++s.full;
+  ++s.steps;
+  double n_i;
+  int lvl_i;
+  sample<PC, GRID, false>(m, s.P, n_i, g, lvl_i);
+  if (!(isfinite(n_i) && n_i > 0.0)) {
+    s.exit_id = GRIN_EXIT_INVALID;
+    s.done = true;
+    return kNormal;
+  }
+  double gn = sqrt(dot3(g, g));
+  if (gn == 0.0 || !isfinite(gn)) {
+    s.h = dopl / n_i;
+  } else {
+    double N[3] = {g[0] / gn, g[1] / gn, g[2] / gn};
+    double c = dot3(N, s.d);
+    if (c == 0.0) {
+      double hi = dopl / n_i;
+      double Pn[3] = {s.P[0] + hi * N[0], s.P[1] + hi * N[1], s.P[2] + hi * N[2]};
+      double n2, g2[3];
+      int l2;
+      sample<PC, GRID, false>(m, Pn, n2, g2, l2);
+      double k = (n2 - n_i) / (2.0 * n_i);
+      double w = 1.0 - k * k;
+      double a0 = w > 0.0 ? sqrt(w) : 0.0;
+      for (int q = 0; q < 3; ++q) s.d[q] = a0 * s.d[q] + k * N[q];
+      normalize3(s.d);
+      s.h = hi;
+    } else if (snell(s.d, N, s.n_prev / n_i)) {
+      ++s.ti;
+      s.h = dopl / s.n_prev;
+    } else {
+      s.h = dopl / n_i;
+    }
+  }
+  s.n_prev = n_i;
+  s.lvl = lvl_i;
+  return kNormal;
+}
+
+// Start of a ray as in the plain tracer; false if it never steps (miss,
+// entry reflection, invalid).  Also returns the entry data the backward
+// sweep needs.
+template <int PC, bool GRID>
+__device__ bool start(const DevMedium& m, const TraceArgs& a, int64_t r, St& s, bool& entered,
+                      double* d_in, double* NB) {
+  using namespace plain;
+  s.P[0] = ld(a.ox, r, a.dtype);
+  s.P[1] = ld(a.oy, r, a.dtype);
+  s.P[2] = ld(a.oz, r, a.dtype);
+  s.d[0] = ld(a.dx, r, a.dtype);
+  s.d[1] = ld(a.dy, r, a.dtype);
+  s.d[2] = ld(a.dz, r, a.dtype);
+  s.steps = s.full = s.ti = s.tb = 0;
+  s.frac = 0.0;
+  s.opl_ext = 0.0;
+  s.done = false;
+  s.exit_id = GRIN_EXIT_MAXSTEPS;
+  entered = false;
+  if (!finite3(s.P) || !finite3(s.d) || sqrt(dot3(s.d, s.d)) == 0.0) {
+    s.exit_id = GRIN_EXIT_INVALID;
+    return false;
+  }
+  normalize3(s.d);
+  double g[3];
+  if (inside(m, s.P)) {
+    sample<PC, GRID, false>(m, s.P, s.n_prev, g, s.lvl);
+  } else {
+    double t, Pb[3];
+    int face;
+    if (!enter(m, s.P, s.d, t, Pb, NB, face)) {
+      s.exit_id = GRIN_EXIT_MISS;
+      return false;
+    }
+    entered = true;
+    s.opl_ext = m.n_ext * t;
+    for (int k = 0; k < 3; ++k) {
+      s.P[k] = Pb[k];
+      d_in[k] = s.d[k];
+    }
+    sample<PC, GRID, false>(m, s.P, s.n_prev, g, s.lvl);
+    if (snell(s.d, NB, m.n_ext / s.n_prev)) {
+      s.exit_id = GRIN_EXIT_ENTRY_REFLECT;
+      return false;
+    }
+  }
+  if (!(isfinite(s.n_prev) && s.n_prev > 0.0)) {
+    s.exit_id = GRIN_EXIT_INVALID;
+    return false;
+  }
+  s.h = a.dopl / s.n_prev;
+  return true;
+}
+
+// ------------------------------------------------------ field derivatives
+
+// n, grad n and the Hessian (xx, yy, zz, xy, xz, yz) at P.
+template <int PC, bool GRID>
+__device__ void field_h(const DevMedium& m, const double* P, double& n, double* g, double* H) {
+  for (int k = 0; k < 3; ++k) g[k] = 0.0;
+  for (int k = 0; k < 6; ++k) H[k] = 0.0;
+  n = 0.0;
+  if (GRID) {
+    const int nn[3] = {m.nx, m.ny, m.nz};
+    int b0[3];
+    double w[3][4], dw[3][4], ddw[3][4];
+    for (int a = 0; a < 3; ++a) {
+      double u = (P[a] - m.origin[a]) / m.spacing[a];
+      if (!(u > -2.0)) u = -2.0;
+      if (u > (double)nn[a] + 1.0) u = (double)nn[a] + 1.0;
+      double fl = floor(u), t = u - fl;
+      b0[a] = (int)fl;
+      plain::keys(t, w[a], dw[a]);
+      ddw[a][0] = 2.0 - 3.0 * t;
+      ddw[a][1] = 9.0 * t - 5.0;
+      ddw[a][2] = 4.0 - 9.0 * t;
+      ddw[a][3] = 3.0 * t - 1.0;
+    }
+    for (int c = 0; c < 4; ++c) {
+      int kk = min(max(b0[2] - 1 + c, 0), nn[2] - 1);
+      for (int b = 0; b < 4; ++b) {
+        int jj = min(max(b0[1] - 1 + b, 0), nn[1] - 1);
+        const float* row = m.grid + (kk * nn[1] + jj) * nn[0];
+        for (int a = 0; a < 4; ++a) {
+          int ii = min(max(b0[0] - 1 + a, 0), nn[0] - 1);
+          double s = (double)row[ii];
+          n += w[0][a] * w[1][b] * w[2][c] * s;
+          g[0] += dw[0][a] * w[1][b] * w[2][c] * s;
+          g[1] += w[0][a] * dw[1][b] * w[2][c] * s;
+          g[2] += w[0][a] * w[1][b] * dw[2][c] * s;
+          H[0] += ddw[0][a] * w[1][b] * w[2][c] * s;
+          H[1] += w[0][a] * ddw[1][b] * w[2][c] * s;
+          H[2] += w[0][a] * w[1][b] * ddw[2][c] * s;
+          H[3] += dw[0][a] * dw[1][b] * w[2][c] * s;
+          H[4] += dw[0][a] * w[1][b] * dw[2][c] * s;
+          H[5] += w[0][a] * dw[1][b] * dw[2][c] * s;
+        }
+      }
+    }
+    const double* sp = m.spacing;
+    for (int k = 0; k < 3; ++k) g[k] /= sp[k];
+    H[0] /= sp[0] * sp[0];
+    H[1] /= sp[1] * sp[1];
+    H[2] /= sp[2] * sp[2];
+    H[3] /= sp[0] * sp[1];
+    H[4] /= sp[0] * sp[2];
+    H[5] /= sp[1] * sp[2];
+  } else {
+    double x[3];
+    for (int k = 0; k < 3; ++k) x[k] = (P[k] - m.off[k]) / m.scale[k];
+    double pw[3][PC + 1];
+    for (int k = 0; k < 3; ++k) {
+      pw[k][0] = 1.0;
+      for (int e = 1; e <= PC; ++e) pw[k][e] = pw[k][e - 1] * x[k];
+    }
+    int idx = 0;
+    for (int s = 0; s <= PC; ++s)
+      for (int i = s; i >= 0; --i)
+        for (int j = s - i; j >= 0; --j) {
+          const int k = s - i - j;
+          const double c = m.cglex[idx++];
+          if (c == 0.0) continue;
+          const double X = pw[0][i], Y = pw[1][j], Z = pw[2][k];
+          const double dX = i ? i * pw[0][i - 1] : 0.0, dY = j ? j * pw[1][j - 1] : 0.0,
+                       dZ = k ? k * pw[2][k - 1] : 0.0;
+          const double ddX = i > 1 ? i * (i - 1) * pw[0][i - 2] : 0.0;
+          const double ddY = j > 1 ? j * (j - 1) * pw[1][j - 2] : 0.0;
+          const double ddZ = k > 1 ? k * (k - 1) * pw[2][k - 2] : 0.0;
+          n += c * X * Y * Z;
+          g[0] += c * dX * Y * Z;
+          g[1] += c * X * dY * Z;
+          g[2] += c * X * Y * dZ;
+          H[0] += c * ddX * Y * Z;
+          H[1] += c * X * ddY * Z;
+          H[2] += c * X * Y * ddZ;
+          H[3] += c * dX * dY * Z;
+          H[4] += c * dX * Y * dZ;
+          H[5] += c * X * dY * dZ;
+        }
+    const double* sc = m.scale;
+    for (int k = 0; k < 3; ++k) g[k] /= sc[k];
+    H[0] /= sc[0] * sc[0];
+    H[1] /= sc[1] * sc[1];
+    H[2] /= sc[2] * sc[2];
+    H[3] /= sc[0] * sc[1];
+    H[4] /= sc[0] * sc[2];
+    H[5] /= sc[1] * sc[2];
+  }
+}
+
+// theta_bar += nb dn/dtheta + gb . d(grad n)/dtheta at P.  Polynomial:
+// into the thread's accumulator acc[term]; grid: atomically into grad.
+template <int PC, bool GRID>
+__device__ void param_adj(const DevMedium& m, const double* P, double nb, const double* gb,
+                          double* acc, double* grad) {
+  if (GRID) {
+    const int nn[3] = {m.nx, m.ny, m.nz};
+    int b0[3];
+    double w[3][4], dw[3][4];
+    for (int a = 0; a < 3; ++a) {
+      double u = (P[a] - m.origin[a]) / m.spacing[a];
+      if (!(u > -2.0)) u = -2.0;
+      if (u > (double)nn[a] + 1.0) u = (double)nn[a] + 1.0;
+      double fl = floor(u);
+      b0[a] = (int)fl;
+      plain::keys(u - fl, w[a], dw[a]);
+      for (int t = 0; t < 4; ++t) dw[a][t] /= m.spacing[a];
+    }
+    for (int c = 0; c < 4; ++c) {
+      int kk = min(max(b0[2] - 1 + c, 0), nn[2] - 1);
+      for (int b = 0; b < 4; ++b) {
+        int jj = min(max(b0[1] - 1 + b, 0), nn[1] - 1);
+        for (int a = 0; a < 4; ++a) {
+          int ii = min(max(b0[0] - 1 + a, 0), nn[0] - 1);
+          double v = nb * w[0][a] * w[1][b] * w[2][c] + gb[0] * dw[0][a] * w[1][b] * w[2][c] +
+                     gb[1] * w[0][a] * dw[1][b] * w[2][c] + gb[2] * w[0][a] * w[1][b] * dw[2][c];
+          if (v != 0.0) atomicAdd(grad + ((int64_t)kk * nn[1] + jj) * nn[0] + ii, v);
+        }
+      }
+    }
+  } else {
+    double x[3];
+    for (int k = 0; k < 3; ++k) x[k] = (P[k] - m.off[k]) / m.scale[k];
+    double pw[3][PC + 1];
+    for (int k = 0; k < 3; ++k) {
+      pw[k][0] = 1.0;
+      for (int e = 1; e <= PC; ++e) pw[k][e] = pw[k][e - 1] * x[k];
+    }
+    const double gx = gb[0] / m.scale[0], gy = gb[1] / m.scale[1], gz = gb[2] / m.scale[2];
+    int idx = 0;
+    for (int s = 0; s <= PC; ++s)
+      for (int i = s; i >= 0; --i)
+        for (int j = s - i; j >= 0; --j) {
+          const int k = s - i - j;
+          const double X = pw[0][i], Y = pw[1][j], Z = pw[2][k];
+          double v = nb * X * Y * Z;
+          if (i) v += gx * i * pw[0][i - 1] * Y * Z;
+          if (j) v += gy * X * j * pw[1][j - 1] * Z;
+          if (k) v += gz * X * Y * k * pw[2][k - 1];
+          acc[idx++] += v;
+        }
+  }
+}
+
+// ------------------------------------------------------- adjoint pieces
+
+struct Adj {
+  double P[3], d[3], n, h;  // dL/dP, dL/dI, dL/dn_{i-1}, dL/dh
+};
+
+// Back through R -> R / |R| given the unit result u and |R|.
+__device__ __forceinline__ void unit_back(const double* u, double Rn, const double* ub, double* Rb) {
+  double s = plain::dot3(u, ub);
+  for (int k = 0; k < 3; ++k) Rb[k] = (ub[k] - u[k] * s) / Rn;
+}
+
+// Back through the Snell refraction R = mu I + gamma N (Eq. 8-9) at fixed
+// branch; adds into Ib, Nb and returns mub.
+__device__ __forceinline__ double snell_back(const double* I, const double* N, double mu,
+                                             const double* Rb, double* Ib, double* Nb) {
+  double c = plain::dot3(N, I);
+  double D = 1.0 - mu * mu * (1.0 - c * c);
+  double s = c > 0.0 ? 1.0 : (c < 0.0 ? -1.0 : 0.0);
+  double sq = sqrt(D);
+  double gamma = -mu * c + s * sq;
+  double mub = plain::dot3(Rb, I);
+  double gammab = plain::dot3(Rb, N);
+  for (int k = 0; k < 3; ++k) {
+    Ib[k] += mu * Rb[k];
+    Nb[k] += gamma * Rb[k];
+  }
+  mub += -c * gammab;
+  double cb = -mu * gammab;
+  double Db = sq > 0.0 ? s * gammab / (2.0 * sq) : 0.0;
+  mub += -2.0 * mu * (1.0 - c * c) * Db;
+  cb += 2.0 * mu * mu * c * Db;
+  for (int k = 0; k < 3; ++k) {
+    Nb[k] += cb * I[k];
+    Ib[k] += cb * N[k];
+  }
+  return mub;
+}
+
+// The refracted or reflected unit vector of the forward pass (plain snell
+// without the normalisation) and its length.
+__device__ __forceinline__ double fwd_R(const double* I, const double* N, double mu, bool tir,
+                                        double* R) {
+  double c = plain::dot3(N, I);
+  if (tir) {
+    for (int k = 0; k < 3; ++k) R[k] = I[k] - 2.0 * c * N[k];
+  } else {
+    double D = 1.0 - mu * mu * (1.0 - c * c);
+    double s = c > 0.0 ? 1.0 : (c < 0.0 ? -1.0 : 0.0);
+    double gamma = -mu * c + s * sqrt(D);
+    for (int k = 0; k < 3; ++k) R[k] = mu * I[k] + gamma * N[k];
+  }
+  return sqrt(plain::dot3(R, R));
+}
+
+// Back through a step that crossed face `face` of the box from state (P, I,
+// h): t = (b - P_a) / (Q_a - P_a), P_b = P + t (Q - P), Q = P + h I.  Takes
+// dL/dP_b (component a ignored: P_b,a = b) and dL/dt; adds into lam.
+__device__ void cross_back(const DevMedium& m, const double* P, const double* I, double h, int face,
+                           const double* Pbb, double tb, Adj& lam) {
+  const int ax = face >> 1;
+  const double b = (face & 1) ? m.b[3 + ax] : m.b[ax];
+  double D[3], Db[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < 3; ++k) D[k] = h * I[k];
+  const double t = (b - P[ax]) / D[ax];
+  for (int k = 0; k < 3; ++k) {
+    if (k == ax) continue;
+    tb += Pbb[k] * D[k];
+    Db[k] += t * Pbb[k];
+    lam.P[k] += Pbb[k];
+  }
+  lam.P[ax] += -tb / D[ax];
+  Db[ax] += -tb * t / D[ax];
+  for (int k = 0; k < 3; ++k) {
+    lam.h += Db[k] * I[k];
+    lam.d[k] += h * Db[k];
+  }
+}
+
+// Back through one normal step from its input state rec (P, I, n_{i-1}, h).
+template <int PC, bool GRID>
+__device__ void normal_back(const DevMedium& m, double dopl, const double* rec, Adj& lam,
+                            double* acc, double* grad) {
+  const double* P = rec;
+  const double* I = rec + 3;
+  const double n_prev = rec[6], h = rec[7];
+  double Pn[3];
+  for (int k = 0; k < 3; ++k) Pn[k] = P[k] + h * I[k];
+  double n, g[3];
+  int lvl;
+  plain::sample<PC, GRID, false>(m, Pn, n, g, lvl);
+  double gn = sqrt(plain::dot3(g, g));
+  Adj in = lam;  // adjoint of the state after the step
+  Adj out;
+  for (int k = 0; k < 3; ++k) out.P[k] = out.d[k] = 0.0;
+  out.n = out.h = 0.0;
+  double nb = in.n;
+  double gb[3] = {0.0, 0.0, 0.0};
+  if (gn == 0.0 || !isfinite(gn)) {
+    nb += -in.h * (dopl / n) / n;
+    for (int k = 0; k < 3; ++k) out.d[k] += in.d[k];
+  } else {
+    double N[3] = {g[0] / gn, g[1] / gn, g[2] / gn};
+    double c = plain::dot3(N, I);
+    double mu = n_prev / n;
+    if (c == 0.0) {
+      // tangential incidence (case iv, measure zero): the arc's direction is
+      // held fixed
+      nb += -in.h * (dopl / n) / n;
+      for (int k = 0; k < 3; ++k) out.d[k] += in.d[k];
+    } else {
+      double D = 1.0 - mu * mu * (1.0 - c * c);
+      bool tir = D <= 0.0;
+      double R[3];
+      double Rn = fwd_R(I, N, mu, tir, R);
+      double u[3] = {R[0] / Rn, R[1] / Rn, R[2] / Rn};
+      double Rb[3];
+      unit_back(u, Rn, in.d, Rb);
+      double Nb[3] = {0.0, 0.0, 0.0};
+      if (tir) {
+        out.n += -in.h * (dopl / n_prev) / n_prev;
+        double cb = -2.0 * plain::dot3(Rb, N);
+        for (int k = 0; k < 3; ++k) {
+          out.d[k] += Rb[k] + cb * N[k];
+          Nb[k] += -2.0 * c * Rb[k] + cb * I[k];
+        }
+      } else {
+        nb += -in.h * (dopl / n) / n;
+        double mub = snell_back(I, N, mu, Rb, out.d, Nb);
+        out.n += mub / n;
+        nb += -mub * mu / n;
+      }
+      double s = plain::dot3(N, Nb);
+      for (int k = 0; k < 3; ++k) gb[k] = (Nb[k] - N[k] * s) / gn;
+    }
+  }
+  // field at P': dL/dP' = in.P + nb grad n + H gb; parameters
+  double nh, gh[3], H[6];
+  field_h<PC, GRID>(m, Pn, nh, gh, H);
+  double Pb[3];
+  Pb[0] = in.P[0] + nb * gh[0] + H[0] * gb[0] + H[3] * gb[1] + H[4] * gb[2];
+  Pb[1] = in.P[1] + nb * gh[1] + H[3] * gb[0] + H[1] * gb[1] + H[5] * gb[2];
+  Pb[2] = in.P[2] + nb * gh[2] + H[4] * gb[0] + H[5] * gb[1] + H[2] * gb[2];
+  param_adj<PC, GRID>(m, Pn, nb, gb, acc, grad);
+  // P' = P + h I
+  for (int k = 0; k < 3; ++k) {
+    out.P[k] += Pb[k];
+    out.h += Pb[k] * I[k];
+    out.d[k] += h * Pb[k];
+  }
+  lam = out;
+}
+
+// Back through a surface crossing with boundary reflection.
+template <int PC, bool GRID>
+__device__ void reflect_back(const DevMedium& m, double dopl, const double* rec, int face,
+                             double fb, Adj& lam, double* acc, double* grad) {
+  const double* P = rec;
+  const double* I = rec + 3;
+  const double n_prev = rec[6], h = rec[7];
+  const int ax = face >> 1;
+  double Q[3], t, Pb[3], NB[3];
+  int f2;
+  for (int k = 0; k < 3; ++k) Q[k] = P[k] + h * I[k];
+  plain::leave(m, P, Q, t, Pb, NB, f2);
+  double R[3] = {I[0], I[1], I[2]};
+  R[ax] = -I[ax];
+  double Rn = sqrt(plain::dot3(R, R));
+  double u[3] = {R[0] / Rn, R[1] / Rn, R[2] / Rn};
+  Adj in = lam;
+  Adj out;
+  for (int k = 0; k < 3; ++k) out.P[k] = out.d[k] = 0.0;
+  out.n = -in.h * (dopl / n_prev) / n_prev;
+  out.h = 0.0;
+  // n'_{i-1} = n(P_b)
+  double nh, gh[3], H[6];
+  field_h<PC, GRID>(m, Pb, nh, gh, H);
+  double Pbb[3];
+  for (int k = 0; k < 3; ++k) Pbb[k] = in.P[k] + in.n * gh[k];
+  double zero[3] = {0.0, 0.0, 0.0};
+  param_adj<PC, GRID>(m, Pb, in.n, zero, acc, grad);
+  double Rb[3];
+  unit_back(u, Rn, in.d, Rb);
+  for (int k = 0; k < 3; ++k) out.d[k] += k == ax ? -Rb[k] : Rb[k];
+  cross_back(m, P, I, h, face, Pbb, fb, out);
+  lam = out;
+}
+
+// Back through the exit step from the seeds (dL/dP_exit, dL/dI_exit).
+__device__ void exit_back(const DevMedium& m, const double* rec, int face, const double* Pob,
+                          const double* dob, double fb, Adj& lam) {
+  const double* P = rec;
+  const double* I = rec + 3;
+  const double n_prev = rec[6], h = rec[7];
+  double N[3] = {0.0, 0.0, 0.0};
+  const int ax = face >> 1;
+  N[ax] = (face & 1) ? 1.0 : -1.0;
+  const double mu = n_prev / m.n_ext;
+  double R[3];
+  double Rn = fwd_R(I, N, mu, false, R);
+  double u[3] = {R[0] / Rn, R[1] / Rn, R[2] / Rn};
+  double Rb[3];
+  unit_back(u, Rn, dob, Rb);
+  for (int k = 0; k < 3; ++k) lam.P[k] = lam.d[k] = 0.0;
+  lam.h = 0.0;
+  double Nb[3] = {0.0, 0.0, 0.0};
+  double mub = snell_back(I, N, mu, Rb, lam.d, Nb);
+  lam.n = mub / m.n_ext;
+  cross_back(m, P, I, h, face, Pob, fb, lam);
+}
+
+// Back through the ray's start: the entry refraction (mu = n_ext / n(P_b))
+// or, for a ray starting inside, n(P_0).
+template <int PC, bool GRID>
+__device__ void entry_back(const DevMedium& m, double dopl, const St& s0, bool entered,
+                           const double* d_in, const double* NB, const Adj& lam, double* acc,
+                           double* grad) {
+  const double n0 = s0.n_prev;
+  double nb = lam.n - lam.h * (dopl / n0) / n0;
+  if (entered) {
+    double mu = m.n_ext / n0;
+    double R[3];
+    double Rn = fwd_R(d_in, NB, mu, false, R);
+    double u[3] = {R[0] / Rn, R[1] / Rn, R[2] / Rn};
+    double Rb[3], Ib[3] = {0.0, 0.0, 0.0}, Nb[3] = {0.0, 0.0, 0.0};
+    unit_back(u, Rn, lam.d, Rb);
+    double mub = snell_back(d_in, NB, mu, Rb, Ib, Nb);
+    nb += -mub * mu / n0;
+  }
+  double zero[3] = {0.0, 0.0, 0.0};
+  param_adj<PC, GRID>(m, s0.P, nb, zero, acc, grad);
+}
+
+// ---------------------------------------------------------------- kernels
+
+struct AdjArgs {
+  TraceArgs a;       // rays in; outputs of the forward sweep
+  double* ckpt;      // [ray][segment][kCk]
+  int32_t* meta;     // [ray][2]: exit id, steps
+  int k, nseg;       // checkpoint interval, segments per ray
+  const double *gpx, *gpy, *gpz, *gdx, *gdy, *gdz, *gopl;  // dL/d(outputs)
+  double* grad;      // dL/d(parameters), accumulated
+  int nterms;
+};
+
+template <int PC, bool GRID>
+__global__ void __launch_bounds__(128) k_adj_forward(DevMedium m, AdjArgs A) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= A.a.count) return;
+  St s;
+  bool entered;
+  double d_in[3], NB[3];
+  bool live = start<PC, GRID>(m, A.a, r, s, entered, d_in, NB);
+  double* ck = A.ckpt + (size_t)r * A.nseg * kCk;
+  if (live) {
+    int face = 0;
+    while (!s.done && s.steps < A.a.max_steps) {
+      if (s.steps % A.k == 0) {
+        double* c = ck + (size_t)(s.steps / A.k) * kCk;
+        for (int q = 0; q < 3; ++q) {
+          c[q] = s.P[q];
+          c[3 + q] = s.d[q];
+        }
+        c[6] = s.n_prev;
+        c[7] = s.h;
+      }
+      advance<PC, GRID>(m, A.a.dopl, s, face);
+    }
+  }
+  double opl = s.opl_ext + A.a.dopl * (double)s.full + A.a.dopl * s.frac;
+  plain::put(A.a, r, s.P, s.d, opl, s.exit_id, s.steps, s.ti, s.tb);
+  A.meta[2 * r] = s.exit_id;
+  A.meta[2 * r + 1] = s.steps;
+}
+
+template <int PC, bool GRID>
+__global__ void __launch_bounds__(128) k_adj_backward(DevMedium m, AdjArgs A) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= A.a.count) return;
+  const int exit_id = A.meta[2 * r], nsteps = A.meta[2 * r + 1];
+  if (exit_id == GRIN_EXIT_INVALID || exit_id == GRIN_EXIT_MISS ||
+      exit_id == GRIN_EXIT_ENTRY_REFLECT)
+    return;
+  const double dopl = A.a.dopl;
+  double acc[GRID ? 1 : kMaxTerms];
+  if (!GRID)
+    for (int q = 0; q < A.nterms; ++q) acc[q] = 0.0;
+  const double Pob[3] = {A.gpx[r], A.gpy[r], A.gpz[r]};
+  const double dob[3] = {A.gdx[r], A.gdy[r], A.gdz[r]};
+  const double fb = dopl * A.gopl[r];  // dL/d(sum of cut fractions)
+  Adj lam;
+  for (int q = 0; q < 3; ++q) {
+    lam.P[q] = Pob[q];
+    lam.d[q] = dob[q];
+  }
+  lam.n = lam.h = 0.0;
+  const double* ck = A.ckpt + (size_t)r * A.nseg * kCk;
+  double rec[kMaxK][kCk];
+  int kind[kMaxK], fc[kMaxK];
+  if (nsteps > 0) {
+    const int last = (nsteps - 1) / A.k;
+    for (int seg = last; seg >= 0; --seg) {
+      const int s0 = seg * A.k, s1 = min(s0 + A.k, nsteps);
+      St s;
+      const double* c = ck + (size_t)seg * kCk;
+      for (int q = 0; q < 3; ++q) {
+        s.P[q] = c[q];
+        s.d[q] = c[3 + q];
+      }
+      s.n_prev = c[6];
+      s.h = c[7];
+      s.steps = s0;
+      s.full = s.ti = s.tb = 0;
+      s.frac = 0.0;
+      s.done = false;
+      s.lvl = 0;
+      for (int i = s0; i < s1; ++i) {
+        double* rr = rec[i - s0];
+        for (int q = 0; q < 3; ++q) {
+          rr[q] = s.P[q];
+          rr[3 + q] = s.d[q];
+        }
+        rr[6] = s.n_prev;
+        rr[7] = s.h;
+        int face = 0;
+        kind[i - s0] = advance<PC, GRID>(m, dopl, s, face);
+        fc[i - s0] = face;
+      }
+      int i = s1 - 1;
+      if (seg == last && exit_id >= 0) {
+        exit_back(m, rec[i - s0], fc[i - s0], Pob, dob, fb, lam);
+        --i;
+      }
+      for (; i >= s0; --i) {
+        if (kind[i - s0] == kCrossReflect)
+          reflect_back<PC, GRID>(m, dopl, rec[i - s0], fc[i - s0], fb, lam, acc, A.grad);
+        else
+          normal_back<PC, GRID>(m, dopl, rec[i - s0], lam, acc, A.grad);
+      }
+    }
+  }
+  St s;
+  bool entered;
+  double d_in[3], NB[3];
+  start<PC, GRID>(m, A.a, r, s, entered, d_in, NB);
+  entry_back<PC, GRID>(m, dopl, s, entered, d_in, NB, lam, acc, A.grad);
+  if (!GRID)
+    for (int q = 0; q < A.nterms; ++q)
+      if (acc[q] != 0.0) atomicAdd(A.grad + q, acc[q]);
+}
+
+template <int PC, bool GRID>
+static int run_t(const DevMedium& m, const AdjArgs& A, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((A.a.count + 127) / 128);
+  k_adj_forward<PC, GRID><<<blocks, 128, 0, st>>>(m, A);
+  if (cudaGetLastError() != cudaSuccess) return GRIN_ERR_CUDA;
+  k_adj_backward<PC, GRID><<<blocks, 128, 0, st>>>(m, A);
+  return cudaGetLastError() == cudaSuccess ? 2 : GRIN_ERR_CUDA;
+}
+
+}  // namespace adj
+
+bool adjoint_supported(const DevMedium& m) {
+  if (m.n_levels > 0 || m.bkind != GRIN_BOUNDARY_BOX) return false;
+  return m.kind == GRIN_MEDIUM_GRID || (m.kind == GRIN_MEDIUM_POLY && m.form == GRIN_FORM_LINEAR);
+}
+
+size_t adjoint_workspace(int64_t rays, int32_t max_steps, int32_t k) {
+  const int64_t nseg = max_steps / k + 1;
+  return (size_t)rays * (size_t)nseg * adj::kCk * sizeof(double) + (size_t)rays * 2 * sizeof(int32_t) +
+         256;
+}
+
+int launch_adjoint(const DevMedium& m, const TraceArgs& a, int32_t k, void* ws, const double* const* gout,
+                   double* grad, int nterms, cudaStream_t st) {
+  adj::AdjArgs A;
+  A.a = a;
+  A.k = k;
+  A.nseg = a.max_steps / k + 1;
+  A.ckpt = (double*)ws;
+  A.meta = (int32_t*)((char*)ws + (size_t)a.count * A.nseg * adj::kCk * sizeof(double));
+  A.gpx = gout[0];
+  A.gpy = gout[1];
+  A.gpz = gout[2];
+  A.gdx = gout[3];
+  A.gdy = gout[4];
+  A.gdz = gout[5];
+  A.gopl = gout[6];
+  A.grad = grad;
+  A.nterms = nterms;
+  if (m.kind == GRIN_MEDIUM_GRID) return adj::run_t<0, true>(m, A, st);
+  switch (m.pclass) {
+    case kPoly2: return adj::run_t<2, false>(m, A, st);
+    case kPoly4: return adj::run_t<4, false>(m, A, st);
+    default: return adj::run_t<6, false>(m, A, st);
+  }
+}
+
+}  // namespace grin

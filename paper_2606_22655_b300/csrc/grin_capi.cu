@@ -375,4 +375,57 @@ int grin_trace_host(grin_ctx ctx, grin_medium medium, const grin_rays* rays, con
   return GRIN_OK;
 }
 
+int grin_trace_adjoint_workspace_size(grin_medium medium, int64_t ray_count, const grin_params* p,
+                                      int32_t k, size_t* bytes) {
+  if (!medium || !p || !bytes || ray_count < 0 || k < 1 || k > 64 || p->max_steps < 0)
+    return GRIN_ERR_INVALID_ARG;
+  if (!grin::adjoint_supported(medium->dm)) return GRIN_ERR_NOT_IMPLEMENTED;
+  *bytes = grin::adjoint_workspace(ray_count, p->max_steps, k);
+  return GRIN_OK;
+}
+
+int grin_trace_adjoint(grin_ctx ctx, grin_medium medium, const grin_rays* rays, const grin_params* p,
+                       const grin_out* out, const grin_out_grad* g, double* grad, int32_t k,
+                       void* ws, size_t ws_bytes, void* cuda_stream) {
+  int st = check_trace_args(ctx, medium, rays, p, out);
+  if (st != GRIN_OK) return st;
+  if (!g || !grad || !ws || k < 1 || k > 64 || p->precision != GRIN_PREC_FP64)
+    return GRIN_ERR_INVALID_ARG;
+  if (!grin::adjoint_supported(medium->dm)) return GRIN_ERR_NOT_IMPLEMENTED;
+  ctx->last_launches = 0;
+  if (rays->count == 0) return GRIN_OK;
+  if (ws_bytes < grin::adjoint_workspace(rays->count, p->max_steps, k)) return GRIN_ERR_INVALID_ARG;
+  const double* gout[7] = {g->px, g->py, g->pz, g->dx, g->dy, g->dz, g->opl};
+  for (int q = 0; q < 7; ++q)
+    if (!gout[q]) return GRIN_ERR_INVALID_ARG;
+  grin::TraceArgs a;
+  a.ox = rays->ox;
+  a.oy = rays->oy;
+  a.oz = rays->oz;
+  a.dx = rays->dx;
+  a.dy = rays->dy;
+  a.dz = rays->dz;
+  a.count = rays->count;
+  a.dtype = rays->dtype;
+  a.px = out->px;
+  a.py = out->py;
+  a.pz = out->pz;
+  a.ux = out->dx;
+  a.uy = out->dy;
+  a.uz = out->dz;
+  a.opl = out->opl;
+  a.exit_id = out->exit_id;
+  a.steps = out->steps;
+  a.tir_i = out->tir_internal;
+  a.tir_b = out->tir_boundary;
+  a.dopl = p->dopl;
+  a.max_steps = p->max_steps;
+  const grin::DevMedium& m = medium->dm;
+  int nterms = m.kind == GRIN_MEDIUM_POLY ? grin_poly_terms(m.pclass) : 0;
+  int rc = grin::launch_adjoint(m, a, k, ws, gout, grad, nterms, (cudaStream_t)cuda_stream);
+  if (rc < 0) return rc;
+  ctx->last_launches = rc;
+  return GRIN_OK;
+}
+
 }  // extern "C"

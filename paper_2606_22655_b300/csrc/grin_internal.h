@@ -69,6 +69,14 @@ int launch_serve_tick(const DevMedium& m, const TraceArgs& a, void* slots, int n
 
 constexpr int kQueueSlots = 4096;
 
+// Adjoint (adjoint.cu): supported media, workspace bytes, and the forward
+// (checkpointing) plus backward sweeps; gout = dL/d(px, py, pz, dx, dy, dz,
+// opl) device arrays; grad accumulates dL/d(parameters).
+bool adjoint_supported(const DevMedium& m);
+size_t adjoint_workspace(int64_t rays, int32_t max_steps, int32_t k);
+int launch_adjoint(const DevMedium& m, const TraceArgs& a, int32_t k, void* ws,
+                   const double* const* gout, double* grad, int nterms, cudaStream_t st);
+
 }  // namespace grin
 
 struct grin_ctx_s {

@@ -285,3 +285,96 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ adjoint
+
+
+def adjoint_workspace_bytes(medium: Medium, count: int, dopl: float, max_steps: int, k: int = 64) -> int:
+    v = ctypes.c_size_t()
+    ps = _params(dopl, max_steps, "fp64")
+    N.check("grin_trace_adjoint_workspace_size", medium.ctx.lib.grin_trace_adjoint_workspace_size(
+        medium.handle, int(count), ctypes.byref(ps), int(k), ctypes.byref(v)))
+    return int(v.value)
+
+
+def trace_adjoint(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_steps: int,
+                  grads: Dict[str, torch.Tensor], n_params: int, k: int = 64,
+                  stream: Optional[torch.cuda.Stream] = None):
+    """grin_trace_adjoint: returns (forward results, dL/d(parameters) as a
+    float64 device tensor).  `grads` holds dL/d(px, py, pz, dx, dy, dz, opl)
+    as float64 device tensors."""
+    dev = rays.ox.device
+    out = empty_result(rays.count, dev)
+    grad = torch.zeros(n_params, dtype=torch.float64, device=dev)
+    ws = torch.empty(max(adjoint_workspace_bytes(medium, rays.count, dopl, max_steps, k), 1),
+                     dtype=torch.uint8, device=dev)
+    g = {key: grads[key].contiguous().to(torch.float64) for key in OUT_FIELDS}
+    gs = N.OutGrad(*[g[key].data_ptr() for key in OUT_FIELDS])
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, "fp64")
+    N.check("grin_trace_adjoint", ctx.lib.grin_trace_adjoint(
+        ctx.handle, medium.handle, ctypes.byref(rs), ctypes.byref(ps), ctypes.byref(os_), ctypes.byref(gs),
+        ctypes.c_void_p(grad.data_ptr()), int(k), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+        ctypes.c_void_p(stream.cuda_stream)))
+    return out, grad
+
+
+def _with_params(spec, theta: torch.Tensor):
+    import copy
+    s = copy.copy(spec)
+    if spec.kind == 1:
+        s.grid = theta.detach().to(torch.float32).reshape(spec.grid.shape).contiguous()
+    else:
+        s.coeffs = theta.detach().cpu().numpy().astype(np.float64)
+    return s
+
+
+class TraceFunction(torch.autograd.Function):
+    """Exit point, direction and optical path of every ray as a function of
+    the medium parameters theta (polynomial coefficients, or grid samples);
+    backward runs grin_trace_adjoint."""
+
+    @staticmethod
+    def forward(fctx, theta, gctx, spec, rays, dopl, max_steps, k):
+        med = Medium(gctx, _with_params(spec, theta))
+        res = trace(gctx, med, rays, dopl, max_steps, "fp64")
+        fctx.save_for_backward(theta)
+        fctx.extra = (gctx, med, rays, dopl, max_steps, k)
+        P = torch.stack([res["px"], res["py"], res["pz"]], 1)
+        d = torch.stack([res["dx"], res["dy"], res["dz"]], 1)
+        fctx.mark_non_differentiable(res["exit_id"])
+        return P, d, res["opl"], res["exit_id"]
+
+    @staticmethod
+    def backward(fctx, gP, gd, gopl, gexit):
+        (theta,) = fctx.saved_tensors
+        gctx, med, rays, dopl, max_steps, k = fctx.extra
+        n = rays.count
+        z = lambda t, i: torch.zeros(n, dtype=torch.float64, device=rays.ox.device) if t is None else t[:, i]
+        grads = {"px": z(gP, 0), "py": z(gP, 1), "pz": z(gP, 2), "dx": z(gd, 0), "dy": z(gd, 1), "dz": z(gd, 2),
+                 "opl": torch.zeros(n, dtype=torch.float64, device=rays.ox.device) if gopl is None else gopl}
+        _, grad = trace_adjoint(gctx, med, rays, dopl, max_steps, grads, theta.numel(), k)
+        return grad.reshape(theta.shape).to(theta.dtype), None, None, None, None, None, None
+
+
+def traced_exit(theta: torch.Tensor, ctx: Context, spec, rays: RayBatch, dopl: float, max_steps: int,
+                k: int = 64):
+    """(P, d, opl, exit_id) differentiable in theta (see TraceFunction)."""
+    return TraceFunction.apply(theta, ctx, spec, rays, dopl, max_steps, k)
+
+
+def image_plane_loss(P, d, exit_id, targets, z_img: float, mask=None):
+    """Mean over rays of the squared distance, in the plane z = z_img, between
+    where the ray's exit line crosses the plane and its target (rays that did
+    not leave through the surface, or are False in `mask`, contribute
+    zero)."""
+    valid = exit_id >= 0
+    if mask is not None:
+        valid = valid & mask
+    sig = (z_img - P[:, 2]) / d[:, 2]
+    X = P[:, 0] + sig * d[:, 0]
+    Y = P[:, 1] + sig * d[:, 1]
+    e = (X - targets[:, 0]) ** 2 + (Y - targets[:, 1]) ** 2
+    return torch.where(valid, e, torch.zeros_like(e)).sum() / P.shape[0]

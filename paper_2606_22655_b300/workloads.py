@@ -327,3 +327,10 @@ def blob_workload(n_rays: int = 1 << 22, res: int = 256, n_levels: int = 0,
     name = ("layered" if n_levels else "grid") + f"_{res}_{n_rays}"
     return Workload(name, m, collimated_face_rays(n_rays, seed), 0.005, 20000,
                     math.sqrt(3.0) * 10.0)
+
+
+def design_targets(n_rays: int, seed: int = BASE_SEED + 4, n_spots: int = 16, half: float = 2.0) -> np.ndarray:
+    """Target spot of each ray for the image-plane design loss: n_spots spots
+    uniform in [-half, half]^2 mm, ray i aimed at spot i mod n_spots."""
+    spots = np.stack([uniform(seed, 51, n_spots, -half, half), uniform(seed, 52, n_spots, -half, half)], 1)
+    return spots[np.arange(n_rays) % n_spots]

@@ -1,0 +1,168 @@
+"""Reverse-mode adjoint (grin_trace_adjoint) against central finite
+differences of the FP64 oracle.
+
+Loss: mean squared distance, in the plane z = 30 mm, between where each
+ray's exit line crosses the plane and a seeded target spot (16 spots, ray i
+to spot i mod 16).  Parameters: the 35 coefficients of the freeform block
+(n = p) and, separately, samples of a 64^3 blob grid.  Central differences
+with h = 1e-6 of the same loss computed from oracle traces; coordinates whose
++-h traces change any integer outcome (exit id, steps, TIR counts) are
+excluded and counted.  Bound: 1e-4 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2606_22655_b300 import tracer
+from paper_2606_22655_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+Z_IMG = 30.0
+H = 1e-6
+REL = 1e-4
+INT_KEYS = ("exit_id", "steps", "tir_internal", "tir_boundary")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = tracer.Context(0)
+    yield c
+    c.close()
+
+
+def np_loss(res, targets, mask=None):
+    P, d, ex = res["P"], res["d"], res["exit_id"]
+    sig = (Z_IMG - P[:, 2]) / d[:, 2]
+    X = P[:, 0] + sig * d[:, 0]
+    Y = P[:, 1] + sig * d[:, 1]
+    e = (X - targets[:, 0]) ** 2 + (Y - targets[:, 1]) ** 2
+    keep = ex >= 0 if mask is None else (ex >= 0) & mask
+    return float(np.where(keep, e, 0.0).sum() / P.shape[0])
+
+
+def stable(a, b):
+    """Rays with identical integer outcomes in the two traces."""
+    ok = np.ones(len(a["exit_id"]), bool)
+    for k in INT_KEYS:
+        ok &= a[k] == b[k]
+    return ok
+
+
+def adjoint_grad(ctx, spec, theta0, rays, targets, dopl, max_steps, k, mask=None):
+    theta = torch.tensor(theta0, dtype=torch.float64, device="cuda", requires_grad=True)
+    rb = tracer.RayBatch.from_numpy(rays.origins, rays.dirs, device="cuda", dtype=torch.float64)
+    P, d, opl, ex = tracer.traced_exit(theta, ctx, spec, rb, dopl, max_steps, k)
+    tg = torch.tensor(targets, device="cuda")
+    mk = None if mask is None else torch.tensor(mask, device="cuda")
+    L = tracer.image_plane_loss(P, d, ex, tg, Z_IMG, mk)
+    L.backward()
+    return float(L), theta.grad.cpu().numpy()
+
+
+def per_ray_loss(res, targets):
+    P, d, ex = res["P"], res["d"], res["exit_id"]
+    sig = (Z_IMG - P[:, 2]) / d[:, 2]
+    X = P[:, 0] + sig * d[:, 0]
+    Y = P[:, 1] + sig * d[:, 1]
+    return np.where(ex >= 0, (X - targets[:, 0]) ** 2 + (Y - targets[:, 1]) ** 2, 0.0)
+
+
+def smooth_fd(trace_at, base, targets, steps):
+    """Per-ray central differences at the two perturbation sizes `steps`
+    (realised parameter deltas returned by trace_at) and the rays whose
+    differences agree to 1e-4; returns (fd per ray at the smaller size,
+    keep)."""
+    fds = []
+    keep = np.ones(len(base["exit_id"]), bool)
+    for h in steps:
+        rp, vp = trace_at(+h)
+        rm, vm = trace_at(-h)
+        keep &= stable(rp, base) & stable(rm, base)
+        fds.append((per_ray_loss(rp, targets) - per_ray_loss(rm, targets)) / (vp - vm))
+    a, b = fds
+    scale = max(np.abs(b).max(), 1e-300)
+    keep &= np.abs(a - b) <= 1e-4 * np.maximum(np.abs(b), 1e-6 * scale)
+    return b, keep
+
+
+def check_coordinates(ctx, spec, theta0, rays, targets, dopl, max_steps, coords, trace_at_factory, steps):
+    """Per coordinate: FD over the rays smooth for it, and the adjoint of the
+    loss over the same rays.  Returns the largest |adjoint - FD| / sum |FD_r|
+    and the mean fraction of rays kept."""
+    base = oracle.trace(spec, rays.origins, rays.dirs, dopl, max_steps)
+    rows = []
+    for i in coords:
+        fd_ray, keep = smooth_fd(trace_at_factory(i), base, targets, steps)
+        fd = float(fd_ray[keep].sum()) / rays.n
+        mag = float(np.abs(fd_ray[keep]).sum()) / rays.n
+        L, g = adjoint_grad(ctx, spec, theta0, rays, targets, dopl, max_steps, 64, keep)
+        assert L == pytest.approx(float(per_ray_loss(base, targets)[keep].sum()) / rays.n, rel=1e-12)
+        rows.append((int(i), fd, float(g[i]), mag, float(keep.mean())))
+    rows = [r for r in rows if r[3] > 0]
+    errs = [abs(a - f) / m_ for _, f, a, m_, _ in rows]
+    k = int(np.argmax(errs))
+    print("worst coordinate (index, fd, adjoint, sum|fd_r|, kept):", rows[k], "error", errs[k])
+    return max(errs), float(np.mean([r[4] for r in rows]))
+
+
+def test_polynomial_coefficients_against_oracle_fd(ctx):
+    m = W.freeform_block_medium()
+    rays = W.point_source_rays(384, W.BASE_SEED + 4)
+    dopl, max_steps = 0.02, 20000
+    targets = W.design_targets(rays.n)
+
+    def factory(i):
+        def at(h):
+            mm = W.Medium(**{**m.__dict__})
+            c = m.coeffs.copy()
+            c[i] += h
+            mm.coeffs = c
+            return oracle.trace(mm, rays.origins, rays.dirs, dopl, max_steps), c[i]
+        return at
+
+    worst, kept = check_coordinates(ctx, m, m.coeffs, rays, targets, dopl, max_steps,
+                                    range(len(m.coeffs)), factory, (1e-7, 1e-8))
+    assert kept > 0.5, kept
+    assert worst <= REL, (worst, kept)
+
+
+def test_grid_samples_against_oracle_fd(ctx):
+    wl = W.blob_workload(n_rays=384, res=64)
+    m = wl.medium
+    dopl, max_steps = 0.02, 20000
+    targets = W.design_targets(wl.rays.n) + 10.0  # spots around the cube's axis
+    theta0 = m.grid.astype(np.float64).ravel()
+    _, g_all = adjoint_grad(ctx, m, theta0, wl.rays, targets, dopl, max_steps, 64)
+    cand = np.flatnonzero(np.abs(g_all) > 1e-2 * np.abs(g_all).max())
+    coords = np.random.default_rng(3).choice(cand, size=min(64, cand.size), replace=False)
+    flat = m.grid.ravel()
+
+    def factory(i):
+        def at(h):
+            gr = flat.copy()
+            gr[i] = np.float32(np.float64(gr[i]) + h)
+            mm = W.Medium(**{**m.__dict__})
+            mm.grid = gr.reshape(m.grid.shape)
+            return oracle.trace(mm, wl.rays.origins, wl.rays.dirs, dopl, max_steps), float(gr[i])
+        return at
+
+    ulp = float(np.spacing(np.float32(1.5)))
+    worst, kept = check_coordinates(ctx, m, theta0, wl.rays, targets, dopl, max_steps, coords, factory,
+                                    (8 * ulp, 2 * ulp))
+    assert kept > 0.5, kept
+    assert worst <= REL, (worst, kept)
+
+
+def test_checkpoint_interval_does_not_change_the_gradient(ctx):
+    m = W.freeform_block_medium()
+    rays = W.point_source_rays(512, W.BASE_SEED + 4)
+    targets = W.design_targets(rays.n)
+    _, g64 = adjoint_grad(ctx, m, m.coeffs, rays, targets, 0.02, 20000, 64)
+    _, g7 = adjoint_grad(ctx, m, m.coeffs, rays, targets, 0.02, 20000, 7)
+    np.testing.assert_allclose(g7, g64, rtol=1e-12, atol=1e-15 * np.abs(g64).max())
