@@ -88,6 +88,29 @@ def profiled_traffic():
     return int(tb.group(1))
 
 
+def rank_ray_seed(rank: int) -> int:
+    """Each rank traces its own seeded bundle of the same size (weak scaling)."""
+    from paper_2606_22655_b300 import workloads as W
+    return W.BASE_SEED + 1 + 1000 * rank
+
+
+def aggregate(region_s: float, steps_per_trace: float, steps: int, ws: int, device=None) -> (float, float):
+    """Whole-job rate: the ray-steps every rank traced over the slowest
+    rank's time.  Two all-reduces (MAX of the time, SUM of the ray-steps),
+    both after the timed region; the data path has none.
+    Returns (seconds, ray-steps/s)."""
+    work = steps_per_trace * steps
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([region_s], dtype=torch.float64, device=device)
+        w = torch.tensor([work], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+        region_s, work = float(t.item()), float(w.item())
+    return region_s, work / region_s
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -291,7 +314,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     ctx = tracer.Context(local)
     if args.workload == "freeform":
-        wl = W.freeform_workload(args.rays, ray_seed=W.BASE_SEED + 1 + 1000 * rank)
+        wl = W.freeform_workload(args.rays, ray_seed=rank_ray_seed(rank))
     elif args.workload == "luneburg":
         wl = W.luneburg_workload()
     else:
@@ -334,11 +357,7 @@ def run_ours(args):
             torch.distributed.barrier()
     region_s = r0.elapsed_time(r1) / 1e3
     kern_s = [a.elapsed_time(b) / 1e3 for a, b in ev]
-    if ws > 1:
-        t = torch.tensor([region_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        region_s = float(t.item())
-    value = ws * steps_per_trace * args.steps / region_s
+    region_s, value = aggregate(region_s, steps_per_trace, args.steps, ws, dev)
     mean_kern = sum(kern_s) / len(kern_s)
 
     if args.profile_only:
