@@ -51,7 +51,7 @@ typedef enum {
   GRIN_ERR_CUDA = -3,          /* a CUDA runtime call failed */
   GRIN_ERR_NOT_IMPLEMENTED = -4,
   GRIN_ERR_TIMEOUT = -5,       /* a bounded wait ran out */
-  GRIN_ERR_BUSY = -6,          /* admission refused (serving) */
+  GRIN_ERR_BUSY = -6,          /* admission refused (serving); context still owns objects */
   GRIN_ERR_NOT_FOUND = -7,     /* unknown job id (serving) */
   GRIN_ERR_CANCELLED = -8      /* job cancelled (serving) */
 } grin_status;
@@ -155,8 +155,14 @@ typedef struct {
  *     index difference n_i - n_{i-1} by the trapezoid rule on grad n (exact to
  *     O(step^3); point values for layered media), an exact step-count optical
  *     path, FP64 for the surface root, the boundary refraction and
- *     near-critical discriminants; persistent ray-pool kernel.
- * flags must be 0. */
+ *     near-critical discriminants; persistent ray-pool kernel.  For
+ *     polynomial media with n = p inside a box it keeps two rays per thread
+ *     and evaluates both with packed FP32 pair instructions (same roundings,
+ *     bitwise the same results as one ray per thread).
+ * flags: 0, or GRIN_FLAG_ONE_RAY_PER_THREAD (GRIN_PREC_FP32_MIXED only: use
+ * the one-ray-per-thread kernel for every medium; ignored by the FP64
+ * tracers).  Other bits are GRIN_ERR_INVALID_ARG. */
+#define GRIN_FLAG_ONE_RAY_PER_THREAD 1u
 typedef struct {
   double dopl;
   int32_t max_steps;
@@ -165,7 +171,10 @@ typedef struct {
 } grin_params;
 
 /* Context on one CUDA device (ordinal `device`); makes that device current
- * on the calling thread. */
+ * on the calling thread.  The context owns the media and servers created on
+ * it: grin_ctx_destroy waits for the device, frees the context and returns
+ * GRIN_OK, or returns GRIN_ERR_BUSY and frees nothing while any of them has
+ * not been destroyed yet. */
 int grin_ctx_create(int device, grin_ctx* out);
 int grin_ctx_destroy(grin_ctx ctx);
 

@@ -14,12 +14,15 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("GRIN_LIB") or os.path.join(HERE, "lib", "libgrin_vrt.so")
 
 GRIN_OK = 0
+(GRIN_ERR_INVALID_ARG, GRIN_ERR_OOM, GRIN_ERR_CUDA, GRIN_ERR_NOT_IMPLEMENTED, GRIN_ERR_TIMEOUT,
+ GRIN_ERR_BUSY, GRIN_ERR_NOT_FOUND, GRIN_ERR_CANCELLED) = range(-1, -9, -1)
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA runtime error",
           -4: "not implemented", -5: "timed out", -6: "busy", -7: "not found", -8: "cancelled"}
 EXIT_MISS, EXIT_ENTRY_REFLECT, EXIT_MAXSTEPS, EXIT_INVALID = -1, -2, -3, -4
 F32, F64 = 0, 1
 PREC_FP64, PREC_FP32_MIXED, PREC_FP64_FAST = 0, 1, 2
 STATIC_MAX_RAYS = 65536
+FLAG_ONE_RAY_PER_THREAD = 1  # grin_params.flags: one-ray-per-thread mixed kernel
 
 _d3 = ctypes.c_double * 3
 _vp = ctypes.c_void_p

@@ -668,10 +668,9 @@ __global__ void __launch_bounds__(128) k_adj_backward(DevMedium m, AdjArgs A) {
 template <int PC, bool GRID>
 static int run_t(const DevMedium& m, const AdjArgs& A, cudaStream_t st) {
   const unsigned blocks = (unsigned)((A.a.count + 127) / 128);
-  k_adj_forward<PC, GRID><<<blocks, 128, 0, st>>>(m, A);
-  if (cudaGetLastError() != cudaSuccess) return GRIN_ERR_CUDA;
-  k_adj_backward<PC, GRID><<<blocks, 128, 0, st>>>(m, A);
-  return cudaGetLastError() == cudaSuccess ? 2 : GRIN_ERR_CUDA;
+  if (launch_kernel(k_adj_forward<PC, GRID>, blocks, 128, st, m, A) < 0) return GRIN_ERR_CUDA;
+  if (launch_kernel(k_adj_backward<PC, GRID>, blocks, 128, st, m, A) < 0) return GRIN_ERR_CUDA;
+  return 2;
 }
 
 }  // namespace adj

@@ -63,6 +63,7 @@ int grin_ctx_create(int device, grin_ctx* out) {
 
 int grin_ctx_destroy(grin_ctx ctx) {
   if (!ctx) return GRIN_ERR_INVALID_ARG;
+  if (ctx->children.load() != 0) return GRIN_ERR_BUSY;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   cudaFree(ctx->queues);
@@ -230,6 +231,7 @@ int grin_medium_create(grin_ctx ctx, const grin_medium_desc* d, grin_medium* out
     m.grid = med->grid_dev;
   }
   med->dm = m;
+  ++ctx->children;
   *out = med;
   return GRIN_OK;
 }
@@ -241,6 +243,7 @@ int grin_medium_destroy(grin_medium medium) {
     cudaDeviceSynchronize();
     cudaFree(medium->grid_dev);
   }
+  --medium->ctx->children;
   delete medium;
   return GRIN_OK;
 }
@@ -257,7 +260,8 @@ static int check_trace_args(grin_ctx ctx, grin_medium medium, const grin_rays* r
   if (medium->ctx != ctx) return GRIN_ERR_INVALID_ARG;
   if (rays->count < 0) return GRIN_ERR_INVALID_ARG;
   if (rays->dtype != GRIN_F32 && rays->dtype != GRIN_F64) return GRIN_ERR_INVALID_ARG;
-  if (!finite_pos(p->dopl) || p->max_steps < 0 || p->flags != 0) return GRIN_ERR_INVALID_ARG;
+  if (!finite_pos(p->dopl) || p->max_steps < 0 || (p->flags & ~GRIN_FLAG_ONE_RAY_PER_THREAD))
+    return GRIN_ERR_INVALID_ARG;
   if (p->precision != GRIN_PREC_FP64 && p->precision != GRIN_PREC_FP32_MIXED &&
       p->precision != GRIN_PREC_FP64_FAST)
     return GRIN_ERR_INVALID_ARG;
@@ -298,6 +302,7 @@ int grin_trace(grin_ctx ctx, grin_medium medium, const grin_rays* rays, const gr
   a.tir_b = out->tir_boundary;
   a.dopl = p->dopl;
   a.max_steps = p->max_steps;
+  a.flags = p->flags;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   int rc;
   if (p->precision == GRIN_PREC_FP64) {
@@ -420,6 +425,7 @@ int grin_trace_adjoint(grin_ctx ctx, grin_medium medium, const grin_rays* rays, 
   a.tir_b = out->tir_boundary;
   a.dopl = p->dopl;
   a.max_steps = p->max_steps;
+  a.flags = p->flags;
   const grin::DevMedium& m = medium->dm;
   int nterms = m.kind == GRIN_MEDIUM_POLY ? grin_poly_terms(m.pclass) : 0;
   int rc = grin::launch_adjoint(m, a, k, ws, gout, grad, nterms, (cudaStream_t)cuda_stream);

@@ -5,6 +5,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <utility>
+
 #include "grin.h"
 
 namespace grin {
@@ -53,6 +56,7 @@ struct TraceArgs {
   int32_t *exit_id, *steps, *tir_i, *tir_b;
   double dopl;
   int32_t max_steps;
+  uint32_t flags = 0;  // grin_params.flags
 };
 
 // Number of kernel launches made; negative grin_status on failure.
@@ -69,6 +73,26 @@ int launch_serve_tick(const DevMedium& m, const TraceArgs& a, void* slots, int n
 
 constexpr int kQueueSlots = 4096;
 
+// Launches kern<<<grid, block, 0, s>>>(args...) and returns 1, or
+// GRIN_ERR_CUDA if this launch failed.  cudaLaunchKernelEx reports the
+// launch's own status; the runtime's per-thread last-error slot, which any
+// earlier runtime call of the process may have left set, is not consulted
+// (and is cleared after a failed launch).
+template <typename... P, typename... A>
+inline int launch_kernel(void (*kern)(P...), unsigned grid, unsigned block, cudaStream_t s,
+                         A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  if (cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...) != cudaSuccess) {
+    cudaGetLastError();
+    return GRIN_ERR_CUDA;
+  }
+  return 1;
+}
+
 // Adjoint (adjoint.cu): supported media, workspace bytes, and the forward
 // (checkpointing) plus backward sweeps; gout = dL/d(px, py, pz, dx, dy, dz,
 // opl) device arrays; grad accumulates dL/d(parameters).
@@ -81,6 +105,9 @@ int launch_adjoint(const DevMedium& m, const TraceArgs& a, int32_t k, void* ws,
 
 struct grin_ctx_s {
   int device = 0;
+  // media and servers created on this context and not yet destroyed; the
+  // context cannot be destroyed while any remain
+  std::atomic<int> children{0};
   int sm_count = 0;
   // One 8-byte ray-queue counter per trace call, taken round robin, so calls
   // on different streams do not share a counter while fewer than kQueueSlots

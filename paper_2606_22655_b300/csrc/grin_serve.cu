@@ -370,6 +370,7 @@ int grin_serve_create(grin_ctx ctx, const grin_serve_config* cfg, grin_server* o
   s->st.arena_bytes = cfg->hbm_budget_bytes;
   s->st.slots_total = s->slots_total;
   s->thread = std::thread(scheduler, s);
+  ++ctx->children;
   *out = s;
   return GRIN_OK;
 }
@@ -385,6 +386,7 @@ int grin_serve_destroy(grin_server s) {
   cudaSetDevice(s->ctx->device);
   cudaFree(s->arena_dev);
   cudaFreeHost(s->pinned);
+  --s->ctx->children;
   delete s;
   return GRIN_OK;
 }

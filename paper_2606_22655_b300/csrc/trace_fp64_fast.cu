@@ -175,8 +175,7 @@ static int launch_t(const DevMedium& m, const TraceArgs& a, cudaStream_t s) {
   const int block = 128;
   int64_t blocks = (a.count + block - 1) / block;
   if (blocks > (1 << 30)) blocks = 1 << 30;
-  k_trace_fp64_fast<PC, GRID, LAYERED><<<(unsigned)blocks, block, 0, s>>>(m, a);
-  return cudaGetLastError() == cudaSuccess ? 1 : GRIN_ERR_CUDA;
+  return launch_kernel(k_trace_fp64_fast<PC, GRID, LAYERED>, (unsigned)blocks, block, s, m, a);
 }
 
 int launch_fp64_fast(const DevMedium& m, const TraceArgs& a, cudaStream_t s, int) {

@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import ctypes
 import dataclasses
+import weakref
 from typing import Dict, Optional
 
 import numpy as np
@@ -20,6 +21,7 @@ import torch
 from . import _native as N
 
 PRECISION = {"fp64": N.PREC_FP64, "mixed": N.PREC_FP32_MIXED, "fp64-fast": N.PREC_FP64_FAST}
+FLAG_ONE_RAY_PER_THREAD = N.FLAG_ONE_RAY_PER_THREAD
 OUT_FIELDS = ("px", "py", "pz", "dx", "dy", "dz", "opl")
 INT_FIELDS = ("exit_id", "steps", "tir_internal", "tir_boundary")
 
@@ -33,6 +35,10 @@ class Context:
         h = ctypes.c_void_p()
         N.check("grin_ctx_create", self.lib.grin_ctx_create(self.device, ctypes.byref(h)))
         self.handle = h
+        # objects the library context owns; close() ends them first (servers
+        # before the media their jobs use)
+        self._servers = weakref.WeakSet()
+        self._media = weakref.WeakSet()
 
     def last_launches(self) -> int:
         v = ctypes.c_int32()
@@ -40,7 +46,10 @@ class Context:
         return int(v.value)
 
     def close(self) -> None:
+        """Close the servers and media made on this context, then the context."""
         if self.handle:
+            for obj in list(self._servers) + list(self._media):
+                obj.close()
             N.check("grin_ctx_destroy", self.lib.grin_ctx_destroy(self.handle))
             self.handle = None
 
@@ -97,6 +106,7 @@ class Medium:
         h = ctypes.c_void_p()
         N.check("grin_medium_create", ctx.lib.grin_medium_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)))
         self.handle = h
+        ctx._media.add(self)
 
     def device_bytes(self) -> int:
         v = ctypes.c_size_t()
@@ -179,22 +189,22 @@ def _out_struct(out: Dict[str, torch.Tensor]) -> N.Out:
     return s
 
 
-def _params(dopl: float, max_steps: int, precision: str) -> N.Params:
+def _params(dopl: float, max_steps: int, precision: str, flags: int = 0) -> N.Params:
     if precision not in PRECISION:
         raise ValueError(f"precision must be one of {sorted(PRECISION)}")
-    return N.Params(float(dopl), int(max_steps), PRECISION[precision], 0)
+    return N.Params(float(dopl), int(max_steps), PRECISION[precision], int(flags))
 
 
 def trace(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_steps: int,
           precision: str = "mixed", stream: Optional[torch.cuda.Stream] = None,
-          out: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
+          out: Optional[Dict[str, torch.Tensor]] = None, flags: int = 0) -> Dict[str, torch.Tensor]:
     """grin_trace on device tensors; asynchronous on `stream` (default: the
-    current torch stream)."""
+    current torch stream).  flags: grin_params.flags (FLAG_ONE_RAY_PER_THREAD)."""
     if out is None:
         out = empty_result(rays.count, rays.ox.device)
     if stream is None:
         stream = torch.cuda.current_stream(rays.ox.device)
-    rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, precision)
+    rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, precision, flags)
     N.check("grin_trace", ctx.lib.grin_trace(ctx.handle, medium.handle, ctypes.byref(rs), ctypes.byref(ps),
                                              ctypes.byref(os_), ctypes.c_void_p(stream.cuda_stream)))
     return out
@@ -202,14 +212,14 @@ def trace(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_steps: 
 
 def trace_host(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_steps: int,
                precision: str = "mixed", stream: Optional[torch.cuda.Stream] = None,
-               out: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
+               out: Optional[Dict[str, torch.Tensor]] = None, flags: int = 0) -> Dict[str, torch.Tensor]:
     """grin_trace_host: rays and results in host memory (copies and the
     synchronisation happen inside the call)."""
     if out is None:
         out = empty_result(rays.count, "cpu")
     if stream is None:
         stream = torch.cuda.current_stream(ctx.device)
-    rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, precision)
+    rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, precision, flags)
     N.check("grin_trace_host", ctx.lib.grin_trace_host(ctx.handle, medium.handle, ctypes.byref(rs),
                                                        ctypes.byref(ps), ctypes.byref(os_),
                                                        ctypes.c_void_p(stream.cuda_stream)))
@@ -237,6 +247,7 @@ class Server:
         N.check("grin_serve_create", ctx.lib.grin_serve_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)))
         self.handle = h
         self._keep = {}
+        ctx._servers.add(self)
 
     def submit(self, medium: Medium, rays: RayBatch, dopl: float, max_steps: int,
                out: Optional[Dict[str, torch.Tensor]] = None):

@@ -291,6 +291,21 @@ def test_empty_batch_and_argument_errors(ctx):
         tracer.Medium(ctx, bad)
 
 
+def test_context_owns_media_and_servers():
+    """grin_ctx_destroy refuses (GRIN_ERR_BUSY) while a medium or server made
+    on the context exists; Context.close() ends them first."""
+    c = tracer.Context(0)
+    m = tracer.Medium(c, W.freeform_block_medium())
+    g = tracer.Medium(c, W.blob_workload(n_rays=10, res=16).medium)
+    srv = tracer.Server(c, 1 << 26)
+    assert c.lib.grin_ctx_destroy(c.handle) == tracer.N.GRIN_ERR_BUSY
+    srv.close()
+    m.close()
+    assert c.lib.grin_ctx_destroy(c.handle) == tracer.N.GRIN_ERR_BUSY  # g remains
+    c.close()
+    assert c.handle is None and g.handle is None
+
+
 def test_trace_host_equals_device(ctx):
     wl = W.freeform_workload(5000)
     med = tracer.Medium(ctx, wl.medium)
