@@ -66,19 +66,17 @@ def flops_per_step(degree_class: int) -> int:
 
 KERNEL_SOURCES = ["paper_2606_22655_b300/csrc/trace_mixed.cu", "paper_2606_22655_b300/csrc/grin_device.cuh",
                   "paper_2606_22655_b300/csrc/grin_internal.h"]
-KERNEL_PAIRS = "k_trace_mixed2<Cfg<4,false,false,box,linear>> (two rays per thread)"
-KERNEL_ONE = "k_trace_mixed<Cfg<4,false,false,box,linear>,false> (one ray per thread)"
-PROFILES = {KERNEL_PAIRS: "profiles/k_trace_mixed2_freeform_block_1048576.md",
-            KERNEL_ONE: "profiles/k_trace_mixed_freeform_block_1048576.md"}
+KERNEL = "k_trace_mixed<Cfg<4,false,false,box,linear>,false>"
+PROFILE = "profiles/k_trace_mixed_freeform_block_1048576.md"
 
 
-def profiled_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from its committed ncu summary, or
-    None if the kernel sources changed since that capture."""
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, or None if the
+    kernel sources changed since that capture."""
     import hashlib
     import re
     try:
-        text = open(os.path.join(ROOT, PROFILES[kernel])).read()
+        text = open(os.path.join(ROOT, PROFILE)).read()
         h = hashlib.sha256()
         for f in KERNEL_SOURCES:
             h.update(open(os.path.join(ROOT, f), "rb").read())
@@ -328,10 +326,8 @@ def run_ours(args):
     stream = torch.cuda.Stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
-    flags = tracer.FLAG_ONE_RAY_PER_THREAD if args.one_ray else 0
-
     def step():
-        tracer.trace(ctx, med, rays, wl.dopl, wl.max_steps, "mixed", stream=stream, out=out, flags=flags)
+        tracer.trace(ctx, med, rays, wl.dopl, wl.max_steps, "mixed", stream=stream, out=out)
 
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
@@ -385,29 +381,6 @@ def run_ours(args):
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"every 16th ray of the {wl.rays.n}-ray batch ({n} rays, {dt:.1f} s)"}
 
-    # the other thread layout of the mixed kernel on the same rays: its time
-    # and whether every output is bitwise the same
-    alt_flags = 0 if args.one_ray else tracer.FLAG_ONE_RAY_PER_THREAD
-    out_alt = tracer.empty_result(rays.count, dev)
-    alt_ms = []
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            flush.zero_()
-            e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e_a.record(stream)
-            tracer.trace(ctx, med, rays, wl.dopl, wl.max_steps, "mixed", stream=stream, out=out_alt,
-                         flags=alt_flags)
-            e_b.record(stream)
-            alt_ms.append((e_a, e_b))
-    torch.cuda.synchronize(dev)
-    alt_ms = [a.elapsed_time(b) for a, b in alt_ms]
-    variants = {
-        "timed": "one ray per thread" if args.one_ray else "two rays per thread (packed f32x2)",
-        "other": "two rays per thread (packed f32x2)" if args.one_ray else "one ray per thread",
-        "other_kernel_ms": sum(alt_ms[1:]) / len(alt_ms[1:]),
-        "timed_kernel_ms": 1e3 * mean_kern,
-        "bitwise_equal": all(torch.equal(out[k], out_alt[k]) for k in out)}
-
     # precision gate: this run's outputs against the plain FP64 GPU tracer
     res32 = tracer.to_numpy(out)
     rays64 = tracer.RayBatch.from_numpy(wl.rays.origins, wl.rays.dirs, device=dev, dtype=torch.float32)
@@ -436,13 +409,12 @@ def run_ours(args):
     # end to end through the host-buffer entry point (pinned host memory)
     hrays = tracer.RayBatch.from_numpy(wl.rays.origins, wl.rays.dirs, device="cpu", dtype=torch.float32, pin=True)
     hout = tracer.empty_result(hrays.count, "cpu")
-    tracer.trace_host(ctx, med, hrays, wl.dopl, wl.max_steps, "mixed", stream=stream, out=hout, flags=flags)
+    tracer.trace_host(ctx, med, hrays, wl.dopl, wl.max_steps, "mixed", stream=stream, out=hout)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     e2e_steps = 0.0
     for _ in range(args.steps):
-        tracer.trace_host(ctx, med, hrays, wl.dopl, wl.max_steps, "mixed", stream=stream, out=hout,
-                          flags=flags)
+        tracer.trace_host(ctx, med, hrays, wl.dopl, wl.max_steps, "mixed", stream=stream, out=hout)
         e2e_steps += float(hout["steps"].sum().item())
     e2e_s = time.perf_counter() - t0
     h2d = 6 * 4 * hrays.count
@@ -457,7 +429,6 @@ def run_ours(args):
 
     if rank != 0:
         return 0
-    kernel = KERNEL_ONE if args.one_ray else KERNEL_PAIRS
     flops_launch = flops_per_step(4) * steps_per_trace
     achieved = flops_launch / mean_kern / 1e12
     line = {
@@ -471,8 +442,8 @@ def run_ours(args):
                    "l2": "256 MiB buffer zeroed before every step, inside the timed region"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS,
-                     "traffic": profiled_traffic(kernel) if args.rays == N_RAYS and args.workload == "freeform" else None,
-                     "kernel": kernel, "kernel_ms": 1e3 * mean_kern,
+                     "traffic": profiled_traffic() if args.rays == N_RAYS and args.workload == "freeform" else None,
+                     "kernel": KERNEL, "kernel_ms": 1e3 * mean_kern,
                      "flops_per_ray_step": flops_per_step(4),
                      "peak_note": "148 SMs x 128 FP32 lanes x 2 FLOP x 2.032 GHz (derived)"},
         "precision_gate": {
@@ -490,7 +461,6 @@ def run_ours(args):
                 "max_rel_pos": gate_s["pos"], "max_dir": gate_s["dir"], "max_rel_opl": gate_s["opl"],
                 "pass": max(gate_s["pos"], gate_s["dir"], gate_s["opl"]) <= 2e-5}},
         "e2e": {"value": e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "thread_layouts": variants,
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
@@ -517,8 +487,6 @@ def main():
                     help="ray count (profiling of a smaller case; the line then names it)")
     ap.add_argument("--workload", choices=["freeform", "grid", "layered", "luneburg"], default="freeform",
                     help="freeform (the benchmark), or another medium for profiling")
-    ap.add_argument("--one-ray", action="store_true",
-                    help="time the one-ray-per-thread mixed kernel instead of the two-ray packed one")
     ap.add_argument("--profile-only", action="store_true",
                     help="timed steps only: no precision gate, e2e or CPU baseline")
     args = ap.parse_args()

@@ -155,14 +155,8 @@ typedef struct {
  *     index difference n_i - n_{i-1} by the trapezoid rule on grad n (exact to
  *     O(step^3); point values for layered media), an exact step-count optical
  *     path, FP64 for the surface root, the boundary refraction and
- *     near-critical discriminants; persistent ray-pool kernel.  For
- *     polynomial media with n = p inside a box it keeps two rays per thread
- *     and evaluates both with packed FP32 pair instructions (same roundings,
- *     bitwise the same results as one ray per thread).
- * flags: 0, or GRIN_FLAG_ONE_RAY_PER_THREAD (GRIN_PREC_FP32_MIXED only: use
- * the one-ray-per-thread kernel for every medium; ignored by the FP64
- * tracers).  Other bits are GRIN_ERR_INVALID_ARG. */
-#define GRIN_FLAG_ONE_RAY_PER_THREAD 1u
+ *     near-critical discriminants; persistent ray-pool kernel.
+ * flags must be 0. */
 typedef struct {
   double dopl;
   int32_t max_steps;

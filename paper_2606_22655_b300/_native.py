@@ -22,7 +22,6 @@ EXIT_MISS, EXIT_ENTRY_REFLECT, EXIT_MAXSTEPS, EXIT_INVALID = -1, -2, -3, -4
 F32, F64 = 0, 1
 PREC_FP64, PREC_FP32_MIXED, PREC_FP64_FAST = 0, 1, 2
 STATIC_MAX_RAYS = 65536
-FLAG_ONE_RAY_PER_THREAD = 1  # grin_params.flags: one-ray-per-thread mixed kernel
 
 _d3 = ctypes.c_double * 3
 _vp = ctypes.c_void_p

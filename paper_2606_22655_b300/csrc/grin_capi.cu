@@ -260,8 +260,7 @@ static int check_trace_args(grin_ctx ctx, grin_medium medium, const grin_rays* r
   if (medium->ctx != ctx) return GRIN_ERR_INVALID_ARG;
   if (rays->count < 0) return GRIN_ERR_INVALID_ARG;
   if (rays->dtype != GRIN_F32 && rays->dtype != GRIN_F64) return GRIN_ERR_INVALID_ARG;
-  if (!finite_pos(p->dopl) || p->max_steps < 0 || (p->flags & ~GRIN_FLAG_ONE_RAY_PER_THREAD))
-    return GRIN_ERR_INVALID_ARG;
+  if (!finite_pos(p->dopl) || p->max_steps < 0 || p->flags != 0) return GRIN_ERR_INVALID_ARG;
   if (p->precision != GRIN_PREC_FP64 && p->precision != GRIN_PREC_FP32_MIXED &&
       p->precision != GRIN_PREC_FP64_FAST)
     return GRIN_ERR_INVALID_ARG;
@@ -302,7 +301,6 @@ int grin_trace(grin_ctx ctx, grin_medium medium, const grin_rays* rays, const gr
   a.tir_b = out->tir_boundary;
   a.dopl = p->dopl;
   a.max_steps = p->max_steps;
-  a.flags = p->flags;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   int rc;
   if (p->precision == GRIN_PREC_FP64) {
@@ -425,7 +423,6 @@ int grin_trace_adjoint(grin_ctx ctx, grin_medium medium, const grin_rays* rays, 
   a.tir_b = out->tir_boundary;
   a.dopl = p->dopl;
   a.max_steps = p->max_steps;
-  a.flags = p->flags;
   const grin::DevMedium& m = medium->dm;
   int nterms = m.kind == GRIN_MEDIUM_POLY ? grin_poly_terms(m.pclass) : 0;
   int rc = grin::launch_adjoint(m, a, k, ws, gout, grad, nterms, (cudaStream_t)cuda_stream);

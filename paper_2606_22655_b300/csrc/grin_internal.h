@@ -56,7 +56,6 @@ struct TraceArgs {
   int32_t *exit_id, *steps, *tir_i, *tir_b;
   double dopl;
   int32_t max_steps;
-  uint32_t flags = 0;  // grin_params.flags
 };
 
 // Number of kernel launches made; negative grin_status on failure.

@@ -61,7 +61,6 @@ constexpr float kCritBand = 1.0e-5f;  // relative |D| below which FP64 decides
 
 template <int PC, bool GRID, bool LAYERED, int BK, int FORM>
 struct Cfg {
-  static constexpr int kDegree = PC;
   static constexpr int kMinBlocks = GRID ? GRIN_MIXED_MIN_BLOCKS_GRID : GRIN_MIXED_MIN_BLOCKS;
   static __device__ __forceinline__ int bk(const DevMedium& m) { return BK >= 0 ? BK : m.bkind; }
   static __device__ __forceinline__ int form(const DevMedium& m) { return FORM >= 0 ? FORM : m.form; }
@@ -617,10 +616,13 @@ __device__ __forceinline__ bool step_ray(const DevMedium& m, const TraceArgs& a,
   const float D = fmaf(mc, mc, omm);
   const bool tir = D <= 0.0f;
   const float gamma = (c > 0.0f ? omm : -omm) / (sqrtf(fmaxf(D, 0.0f)) + fabsf(mc));
+  // A zero, infinite or undefined gradient, or an undefined index
+  // difference, makes D a NaN (rsqrt(0) = inf and 0 * inf, or inf - inf),
+  // which fails the comparison with the near-critical band; a gradient that
+  // overflows while its components stay finite gives N = 0 and c == 0.
   const bool special =
-      !in || !(n_i > 0.0f) || !isfinite(n_i) || s.steps + 1 >= a.max_steps ||
-      (!homog && (!(gn2 > 0.0f) || !isfinite(gn2) || c == 0.0f || !isfinite(dn) ||
-                  fabsf(D) <= kCritBand * (fabsf(omm) + mc * mc)));
+      !in || !(n_i > 0.0f && n_i < INFINITY) || s.steps + 1 >= a.max_steps ||
+      (!homog && (c == 0.0f || !(fabsf(D) > kCritBand * (fabsf(omm) + mc * mc))));
   if (GRIN_UNLIKELY(special)) {
     // out of line, on a copy: only the copy's address escapes, the live
     // state stays in registers
@@ -691,296 +693,6 @@ __global__ void __launch_bounds__(128, C::kMinBlocks) k_trace_mixed(DevMedium m,
   }
 }
 
-// ------------------------------------------------------- two rays a thread
-//
-// The fast step above is issue-bound: each FP32 add, multiply or fma is one
-// warp instruction, about two thirds of the step.  Blackwell's packed FP32
-// instructions (add/mul/fma .f32x2) do two lanes of that arithmetic in one
-// issue slot, so k_trace_mixed2 keeps two rays per thread, each FP32 field of
-// the state a pair (ray 0 in .x, ray 1 in .y), and runs the step's
-// arithmetic once for both.  Comparisons, reciprocals, square roots and
-// divisions stay per ray, written as in step_ray.  Each packed operation is
-// the same rounding as its scalar twin (a - b is fma(b, -1, a), one rounding
-// of the exact difference), so a ray's result is bitwise that of
-// k_trace_mixed.  When either ray meets a case the fast step does not handle,
-// both take step_slow on unpacked copies, which redoes the same step.
-// Polynomial media with a box boundary and n = p (the common freeform case).
-
-#ifndef GRIN_MIXED2_MIN_BLOCKS
-#define GRIN_MIXED2_MIN_BLOCKS 3
-#endif
-
-struct F2 {
-  float2 v;
-  F2() = default;
-  __device__ __forceinline__ explicit F2(float s) : v(make_float2(s, s)) {}
-  __device__ __forceinline__ F2(float2 w) : v(w) {}
-  __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
-};
-__device__ __forceinline__ F2 fmadd(F2 a, F2 b, F2 c) { return __ffma2_rn(a.v, b.v, c.v); }
-__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return __fadd2_rn(a.v, b.v); }
-__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return __fmul2_rn(a.v, b.v); }
-__device__ __forceinline__ F2 operator-(F2 a, F2 b) {
-  return __ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v);
-}
-
-// Medium constants the packed step reads, each duplicated for both lanes.
-struct PackedMedium {
-  float2 c[kMaxTerms];    // c32 (Horner layout, constant term shifted by base)
-  float2 off[3], isc[3];  // normalisation offset and 1 / scale
-  float2 base;
-};
-
-struct RayP {
-  F2 ph[3], pl[3], d[3], dl[3], gp[3];
-  F2 nu_prev, inv_prev, h;
-};
-
-// The per-ray fields the fast step does not pack.
-struct LaneX {
-  int64_t ray;
-  int steps, full, tir_i, tir_b;
-  float frac;
-  double opl_x;
-  bool active;
-};
-
-template <int J>
-__device__ __forceinline__ float& at(F2& p) {
-  if constexpr (J == 0) return p.v.x;
-  else return p.v.y;
-}
-template <int J>
-__device__ __forceinline__ float at(const F2& p) {
-  if constexpr (J == 0) return p.v.x;
-  else return p.v.y;
-}
-
-template <int J>
-__device__ __forceinline__ void unpack(const RayP& P, const LaneX& l, RayF& s) {
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    s.ph[k] = at<J>(P.ph[k]);
-    s.pl[k] = at<J>(P.pl[k]);
-    s.d[k] = at<J>(P.d[k]);
-    s.dl[k] = at<J>(P.dl[k]);
-    s.gp[k] = at<J>(P.gp[k]);
-  }
-  s.nu_prev = at<J>(P.nu_prev);
-  s.inv_prev = at<J>(P.inv_prev);
-  s.h = at<J>(P.h);
-  s.frac = l.frac;
-  s.lvl_prev = 0;
-  s.steps = l.steps;
-  s.full = l.full;
-  s.tir_i = l.tir_i;
-  s.tir_b = l.tir_b;
-  s.opl_x = l.opl_x;
-}
-
-template <int J>
-__device__ __forceinline__ void pack(const RayF& s, RayP& P, LaneX& l) {
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    at<J>(P.ph[k]) = s.ph[k];
-    at<J>(P.pl[k]) = s.pl[k];
-    at<J>(P.d[k]) = s.d[k];
-    at<J>(P.dl[k]) = s.dl[k];
-    at<J>(P.gp[k]) = s.gp[k];
-  }
-  at<J>(P.nu_prev) = s.nu_prev;
-  at<J>(P.inv_prev) = s.inv_prev;
-  at<J>(P.h) = s.h;
-  l.frac = s.frac;
-  l.steps = s.steps;
-  l.full = s.full;
-  l.tir_i = s.tir_i;
-  l.tir_b = s.tir_b;
-  l.opl_x = s.opl_x;
-}
-
-// add_ff on both lanes.
-__device__ __forceinline__ void add_ff2(F2& hi, F2& lo, F2 x) {
-  x = x + lo;
-  F2 s = hi + x;
-  F2 bp = s - hi;
-  lo = (hi - (s - bp)) + (x - bp);
-  hi = s;
-}
-
-// Lane J of a step the fast path declined: step_slow on a copy (only the
-// copy's address escapes, the packed state stays in registers).
-template <class C, int J>
-__device__ __forceinline__ void slow_lane(const DevMedium& m, const TraceArgs& a, RayP& P,
-                                          LaneX& l, float dopl_f) {
-  if (!l.active) return;
-  RayF t;
-  unpack<J>(P, l, t);
-  l.active = step_slow<C, false>(m, a, l.ray, t, dopl_f);
-  pack<J>(t, P, l);
-}
-
-// The fast-step conditions of step_ray for one lane; inactive lanes never
-// ask for the slow path (their arithmetic runs on stale values and is not
-// used).
-template <class C>
-__device__ __forceinline__ bool special_lane(const DevMedium& m, const TraceArgs& a,
-                                             const LaneX& l, float qx, float qy, float qz,
-                                             float n_i, float gn2, float c, float dn, float D,
-                                             float omm, float mc) {
-  const float q[3] = {qx, qy, qz};
-  return l.active &&
-         (!C::inside(m, q) || !(n_i > 0.0f) || !isfinite(n_i) || l.steps + 1 >= a.max_steps ||
-          !(gn2 > 0.0f) || !isfinite(gn2) || c == 0.0f || !isfinite(dn) ||
-          fabsf(D) <= kCritBand * (fabsf(omm) + mc * mc));
-}
-
-template <class C>
-__device__ __forceinline__ void step_pair(const DevMedium& m, const PackedMedium& pk,
-                                          const TraceArgs& a, RayP& s, LaneX& l0, LaneX& l1,
-                                          float dopl_f) {
-  F2 qh[3], ql[3], dv[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    dv[k] = s.h * s.d[k];
-    F2 y = fmadd(s.h, s.d[k], fmadd(s.h, s.dl[k], s.pl[k]));
-    F2 t = s.ph[k] + y;
-    ql[k] = y - (t - s.ph[k]);
-    qh[k] = t;
-  }
-  // n = p with the constant term shifted by base: nu = q, grad n = grad q
-  const F2 x = (qh[0] - F2(pk.off[0])) * F2(pk.isc[0]);
-  const F2 y = (qh[1] - F2(pk.off[1])) * F2(pk.isc[1]);
-  const F2 z = (qh[2] - F2(pk.off[2])) * F2(pk.isc[2]);
-  F2 nu, g[3];
-  poly_vg<C::kDegree, F2>(reinterpret_cast<const F2*>(pk.c), x, y, z, nu, g[0], g[1], g[2]);
-#pragma unroll
-  for (int k = 0; k < 3; ++k) g[k] = g[k] * F2(pk.isc[k]);
-  const F2 n_i = F2(pk.base) + nu;
-  const F2 inv_n(1.0f / n_i.v.x, 1.0f / n_i.v.y);
-  const F2 gn2 = fmadd(g[0], g[0], fmadd(g[1], g[1], g[2] * g[2]));
-  const F2 ri(rsqrtf(gn2.v.x), rsqrtf(gn2.v.y));
-  const F2 N[3] = {g[0] * ri, g[1] * ri, g[2] * ri};
-  const F2 c = fmadd(N[0], s.d[0], fmadd(N[1], s.d[1], N[2] * s.d[2]));
-  const F2 dn = F2(0.5f) * fmadd(s.gp[0] + g[0], dv[0],
-                                 fmadd(s.gp[1] + g[1], dv[1], (s.gp[2] + g[2]) * dv[2]));
-  const F2 om = dn * inv_n;            // 1 - mu
-  const F2 mu = F2(1.0f) - om;
-  const F2 omm = om * (F2(2.0f) - om);  // 1 - mu^2
-  const F2 mc = mu * c;
-  const F2 D = fmadd(mc, mc, omm);
-  const bool tir0 = D.v.x <= 0.0f, tir1 = D.v.y <= 0.0f;
-  const float gamma0 =
-      (c.v.x > 0.0f ? omm.v.x : -omm.v.x) / (sqrtf(fmaxf(D.v.x, 0.0f)) + fabsf(mc.v.x));
-  const float gamma1 =
-      (c.v.y > 0.0f ? omm.v.y : -omm.v.y) / (sqrtf(fmaxf(D.v.y, 0.0f)) + fabsf(mc.v.y));
-  const bool sp0 = special_lane<C>(m, a, l0, qh[0].v.x, qh[1].v.x, qh[2].v.x, n_i.v.x, gn2.v.x,
-                                   c.v.x, dn.v.x, D.v.x, omm.v.x, mc.v.x);
-  const bool sp1 = special_lane<C>(m, a, l1, qh[0].v.y, qh[1].v.y, qh[2].v.y, n_i.v.y, gn2.v.y,
-                                   c.v.y, dn.v.y, D.v.y, omm.v.y, mc.v.y);
-  if (GRIN_UNLIKELY(sp0 || sp1)) {
-    slow_lane<C, 0>(m, a, s, l0, dopl_f);
-    slow_lane<C, 1>(m, a, s, l1, dopl_f);
-    return;
-  }
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    s.ph[k] = qh[k];
-    s.pl[k] = ql[k];
-  }
-  ++l0.full;
-  ++l0.steps;
-  ++l1.full;
-  ++l1.steps;
-  // Eq. 8, R = I + (gamma N - (1 - mu) I); Sec. II (v), R = I - 2 c N with a
-  // step of dL0 / n_{i-1}
-  const F2 kn(tir0 ? -2.0f * c.v.x : gamma0, tir1 ? -2.0f * c.v.y : gamma1);
-  const F2 kd(tir0 ? 0.0f : -om.v.x, tir1 ? 0.0f : -om.v.y);
-#pragma unroll
-  for (int j = 0; j < 3; ++j) add_ff2(s.d[j], s.dl[j], fmadd(kn, N[j], kd * s.d[j]));
-  s.h = F2(dopl_f) * F2(tir0 ? s.inv_prev.v.x : inv_n.v.x, tir1 ? s.inv_prev.v.y : inv_n.v.y);
-  l0.tir_i += tir0 ? 1 : 0;
-  l1.tir_i += tir1 ? 1 : 0;
-  s.nu_prev = nu;
-  s.inv_prev = inv_n;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) s.gp[k] = g[k];
-}
-
-// Warp-wide claim of new rays for the lanes whose slot J is free (one
-// atomicAdd per warp, ranks from the ballot), as in k_trace_mixed.
-template <class C, int J>
-__device__ __forceinline__ void refill(const DevMedium& m, const TraceArgs& a,
-                                       unsigned long long* queue, unsigned lane, RayP& P,
-                                       LaneX& l, bool& exhausted) {
-  const unsigned need = __ballot_sync(0xffffffffu, !l.active);
-  if (!need || exhausted) return;
-  const int leader = __ffs(need) - 1;
-  const unsigned cnt = __popc(need);
-  unsigned long long base = 0;
-  if ((int)lane == leader) base = atomicAdd(queue, (unsigned long long)cnt);
-  base = __shfl_sync(0xffffffffu, base, leader);
-  exhausted = base + cnt >= (unsigned long long)a.count;
-  if (l.active) return;
-  const unsigned long long rr = base + __popc(need & ((1u << lane) - 1u));
-  if (rr >= (unsigned long long)a.count) return;
-  l.ray = (int64_t)rr;
-  RayF t;
-  l.active = init_ray<C>(m, a, l.ray, t);
-  if (l.active) pack<J>(t, P, l);
-}
-
-template <class C>
-__global__ void __launch_bounds__(128, GRIN_MIXED2_MIN_BLOCKS)
-    k_trace_mixed2(DevMedium m, PackedMedium pk, TraceArgs a, unsigned long long* queue) {
-  const unsigned lane = threadIdx.x & 31u;
-  const float dopl_f = (float)a.dopl;
-  RayP s{};
-  LaneX l0{}, l1{};
-  bool exhausted = false;
-  for (;;) {
-    refill<C, 0>(m, a, queue, lane, s, l0, exhausted);
-    refill<C, 1>(m, a, queue, lane, s, l1, exhausted);
-    if (!__any_sync(0xffffffffu, l0.active || l1.active)) {
-      if (exhausted) break;
-      continue;
-    }
-#pragma unroll 1
-    for (int k = 0; k < kStepQuantum; ++k) {
-      if (l0.active || l1.active) step_pair<C>(m, pk, a, s, l0, l1, dopl_f);
-    }
-  }
-}
-
-template <int PC>
-static int launch_t2(const DevMedium& m, const TraceArgs& a, unsigned long long* queue,
-                     cudaStream_t st, int sm_count) {
-  using C = Cfg<PC, false, false, GRIN_BOUNDARY_BOX, GRIN_FORM_LINEAR>;
-  auto kern = k_trace_mixed2<C>;
-  PackedMedium pk;
-  for (int k = 0; k < kMaxTerms; ++k) pk.c[k] = make_float2(m.c32[k], m.c32[k]);
-  for (int k = 0; k < 3; ++k) {
-    pk.off[k] = make_float2(m.off_f[k], m.off_f[k]);
-    pk.isc[k] = make_float2(m.inv_scale_f[k], m.inv_scale_f[k]);
-  }
-  pk.base = make_float2(m.base_f, m.base_f);
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
-  const int64_t warps_needed = (a.count + 63) / 64;  // 64 rays a warp
-  int block = 128;
-  int64_t blocks = (int64_t)sm_count * per_sm;
-  if (warps_needed <= (int64_t)sm_count * 4) {
-    block = 32;
-    blocks = warps_needed;
-  } else {
-    blocks = blocks < (warps_needed + 3) / 4 ? blocks : (warps_needed + 3) / 4;
-  }
-  if (cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st) != cudaSuccess) return GRIN_ERR_CUDA;
-  return launch_kernel(kern, (unsigned)blocks, block, st, m, pk, a, queue);
-}
-
 template <int PC, bool GRID, bool LAYERED, int BK, int FORM>
 static int launch_t(const DevMedium& m, const TraceArgs& a, unsigned long long* queue,
                     cudaStream_t st, int sm_count) {
@@ -1009,9 +721,6 @@ static int launch_pc(const DevMedium& m, const TraceArgs& a, unsigned long long*
                      cudaStream_t s, int sm) {
   if (m.n_levels > 0) return launch_t<PC, GRID, true, -1, -1>(m, a, q, s, sm);
   const bool fast = m.bkind == GRIN_BOUNDARY_BOX && (GRID || m.form == GRIN_FORM_LINEAR);
-  if constexpr (!GRID) {
-    if (fast && !(a.flags & GRIN_FLAG_ONE_RAY_PER_THREAD)) return launch_t2<PC>(m, a, q, s, sm);
-  }
   return fast ? launch_t<PC, GRID, false, GRIN_BOUNDARY_BOX, GRIN_FORM_LINEAR>(m, a, q, s, sm)
               : launch_t<PC, GRID, false, -1, -1>(m, a, q, s, sm);
 }

@@ -21,7 +21,6 @@ import torch
 from . import _native as N
 
 PRECISION = {"fp64": N.PREC_FP64, "mixed": N.PREC_FP32_MIXED, "fp64-fast": N.PREC_FP64_FAST}
-FLAG_ONE_RAY_PER_THREAD = N.FLAG_ONE_RAY_PER_THREAD
 OUT_FIELDS = ("px", "py", "pz", "dx", "dy", "dz", "opl")
 INT_FIELDS = ("exit_id", "steps", "tir_internal", "tir_boundary")
 
@@ -189,22 +188,22 @@ def _out_struct(out: Dict[str, torch.Tensor]) -> N.Out:
     return s
 
 
-def _params(dopl: float, max_steps: int, precision: str, flags: int = 0) -> N.Params:
+def _params(dopl: float, max_steps: int, precision: str) -> N.Params:
     if precision not in PRECISION:
         raise ValueError(f"precision must be one of {sorted(PRECISION)}")
-    return N.Params(float(dopl), int(max_steps), PRECISION[precision], int(flags))
+    return N.Params(float(dopl), int(max_steps), PRECISION[precision], 0)
 
 
 def trace(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_steps: int,
           precision: str = "mixed", stream: Optional[torch.cuda.Stream] = None,
-          out: Optional[Dict[str, torch.Tensor]] = None, flags: int = 0) -> Dict[str, torch.Tensor]:
+          out: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
     """grin_trace on device tensors; asynchronous on `stream` (default: the
-    current torch stream).  flags: grin_params.flags (FLAG_ONE_RAY_PER_THREAD)."""
+    current torch stream)."""
     if out is None:
         out = empty_result(rays.count, rays.ox.device)
     if stream is None:
         stream = torch.cuda.current_stream(rays.ox.device)
-    rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, precision, flags)
+    rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, precision)
     N.check("grin_trace", ctx.lib.grin_trace(ctx.handle, medium.handle, ctypes.byref(rs), ctypes.byref(ps),
                                              ctypes.byref(os_), ctypes.c_void_p(stream.cuda_stream)))
     return out
@@ -212,14 +211,14 @@ def trace(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_steps: 
 
 def trace_host(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_steps: int,
                precision: str = "mixed", stream: Optional[torch.cuda.Stream] = None,
-               out: Optional[Dict[str, torch.Tensor]] = None, flags: int = 0) -> Dict[str, torch.Tensor]:
+               out: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
     """grin_trace_host: rays and results in host memory (copies and the
     synchronisation happen inside the call)."""
     if out is None:
         out = empty_result(rays.count, "cpu")
     if stream is None:
         stream = torch.cuda.current_stream(ctx.device)
-    rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, precision, flags)
+    rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, precision)
     N.check("grin_trace_host", ctx.lib.grin_trace_host(ctx.handle, medium.handle, ctypes.byref(rs),
                                                        ctypes.byref(ps), ctypes.byref(os_),
                                                        ctypes.c_void_p(stream.cuda_stream)))
