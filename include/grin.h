@@ -200,8 +200,28 @@ int grin_trace(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
 int grin_trace_host(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
                     const grin_params* params, const grin_out* out, void* cuda_stream);
 
-/* Kernel launches made by the last grin_trace / grin_trace_host call on this
- * context (for accounting). */
+/* Trajectory tap: the plain FP64 trace (params->precision must be
+ * GRIN_PREC_FP64) that also records each ray's points, for plots and
+ * debugging of a few rays (one thread per ray).  The paper draws the whole
+ * polyline of each ray (Sec. IV-V); these are its vertices P_i (Eq. 2): the
+ * first point inside the medium (the start point, or the entry point on the
+ * surface), then every step's end point, full steps and steps cut at the
+ * surface (Sec. II (i)) alike.  Exterior segments are not sampled.
+ *   path:     caller-owned device array of rays->count * cap * 3 doubles,
+ *             ray-major: point i of ray r is path[3 (cap r + i) + 0..2];
+ *   cap:      points stored per ray (>= 1); later points are not stored, the
+ *             trace itself runs to its end as in grin_trace;
+ *   path_len: caller-owned device array of rays->count int64: the number of
+ *             points the ray produced, which may exceed cap.
+ * out receives exactly what grin_trace (GRIN_PREC_FP64) writes.  Errors as
+ * grin_trace, and GRIN_ERR_INVALID_ARG for another precision, cap < 1, a
+ * NULL path or path_len, or a path size beyond int64. */
+int grin_trace_path(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
+                    const grin_params* params, const grin_out* out, double* path, int64_t cap,
+                    int64_t* path_len, void* cuda_stream);
+
+/* Kernel launches made by the last grin_trace / grin_trace_host /
+ * grin_trace_path call on this context (for accounting). */
 int grin_ctx_last_launches(grin_ctx ctx, int32_t* launches);
 
 /* ------------------------------------------------------------ adjoint

@@ -99,6 +99,8 @@ def load() -> ctypes.CDLL:
         "grin_medium_device_bytes": (ctypes.c_int, [_vp, P(ctypes.c_size_t)]),
         "grin_trace": (ctypes.c_int, [_vp, _vp, P(Rays), P(Params), P(Out), _vp]),
         "grin_trace_host": (ctypes.c_int, [_vp, _vp, P(Rays), P(Params), P(Out), _vp]),
+        "grin_trace_path": (ctypes.c_int, [_vp, _vp, P(Rays), P(Params), P(Out), _vp, ctypes.c_int64,
+                                           _vp, _vp]),
         "grin_ctx_last_launches": (ctypes.c_int, [_vp, P(ctypes.c_int32)]),
         "grin_trace_host_static": (ctypes.c_int, [P(MediumDesc), P(Rays), P(Params), P(Out), _vp]),
         "grin_trace_adjoint_workspace_size": (ctypes.c_int, [_vp, ctypes.c_int64, P(Params), ctypes.c_int32,

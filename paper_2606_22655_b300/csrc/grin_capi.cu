@@ -4,12 +4,15 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <new>
 #include <vector>
 
 #include "grin_device.cuh"
+#include <cstdint>
+
 #include "grin_internal.h"
 
 using grin::DevMedium;
@@ -270,6 +273,44 @@ static int check_trace_args(grin_ctx ctx, grin_medium medium, const grin_rays* r
   if (!out->px || !out->py || !out->pz || !out->dx || !out->dy || !out->dz || !out->opl ||
       !out->exit_id || !out->steps || !out->tir_internal || !out->tir_boundary)
     return GRIN_ERR_INVALID_ARG;
+  return GRIN_OK;
+}
+
+int grin_trace_path(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
+                    const grin_params* p, const grin_out* out, double* path, int64_t cap,
+                    int64_t* path_len, void* cuda_stream) {
+  int st = check_trace_args(ctx, medium, rays, p, out);
+  if (st != GRIN_OK) return st;
+  if (p->precision != GRIN_PREC_FP64 || cap < 1 || !path || !path_len)
+    return GRIN_ERR_INVALID_ARG;
+  if (rays->count > 0 && cap > INT64_MAX / 3 / rays->count) return GRIN_ERR_INVALID_ARG;
+  ctx->last_launches = 0;
+  if (rays->count == 0) return GRIN_OK;
+  grin::TraceArgs a;
+  a.ox = rays->ox;
+  a.oy = rays->oy;
+  a.oz = rays->oz;
+  a.dx = rays->dx;
+  a.dy = rays->dy;
+  a.dz = rays->dz;
+  a.count = rays->count;
+  a.dtype = rays->dtype;
+  a.px = out->px;
+  a.py = out->py;
+  a.pz = out->pz;
+  a.ux = out->dx;
+  a.uy = out->dy;
+  a.uz = out->dz;
+  a.opl = out->opl;
+  a.exit_id = out->exit_id;
+  a.steps = out->steps;
+  a.tir_i = out->tir_internal;
+  a.tir_b = out->tir_boundary;
+  a.dopl = p->dopl;
+  a.max_steps = p->max_steps;
+  int rc = grin::launch_fp64_path(medium->dm, a, path, cap, path_len, (cudaStream_t)cuda_stream);
+  if (rc < 0) return rc;
+  ctx->last_launches = rc;
   return GRIN_OK;
 }
 

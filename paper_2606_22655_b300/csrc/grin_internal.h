@@ -61,6 +61,9 @@ struct TraceArgs {
 // Number of kernel launches made; negative grin_status on failure.
 int launch_fp64(const DevMedium& m, const TraceArgs& a, cudaStream_t s, int sm_count);
 int launch_fp64_fast(const DevMedium& m, const TraceArgs& a, cudaStream_t s, int sm_count);
+// The plain FP64 trace, recording each ray's points (trace_fp64.cu).
+int launch_fp64_path(const DevMedium& m, const TraceArgs& a, double* path, int64_t cap,
+                     int64_t* plen, cudaStream_t s);
 int launch_mixed(const DevMedium& m, const TraceArgs& a, unsigned long long* queue,
                  cudaStream_t s, int sm_count);
 

@@ -21,8 +21,24 @@
 namespace grin {
 namespace plain {
 
-template <int PC, bool GRID, bool LAYERED>
-__device__ void trace_one(const DevMedium& m, const TraceArgs& a, int64_t r) {
+// Point recorder of grin_trace_path: the first interior point, every full
+// step and every surface cut, at most cap points (ray-major, xyz).
+struct PathTap {
+  double* pts;
+  int64_t cap, n;
+  __device__ __forceinline__ void put(const double* P) {
+    if (n < cap) {
+      pts[3 * n] = P[0];
+      pts[3 * n + 1] = P[1];
+      pts[3 * n + 2] = P[2];
+    }
+    ++n;
+  }
+};
+
+template <int PC, bool GRID, bool LAYERED, bool TAP = false>
+__device__ void trace_one(const DevMedium& m, const TraceArgs& a, int64_t r,
+                          PathTap* tap = nullptr) {
   double P[3] = {ld(a.ox, r, a.dtype), ld(a.oy, r, a.dtype), ld(a.oz, r, a.dtype)};
   double d[3] = {ld(a.dx, r, a.dtype), ld(a.dy, r, a.dtype), ld(a.dz, r, a.dtype)};
   if (!finite3(P) || !finite3(d) || sqrt(dot3(d, d)) == 0.0) {
@@ -55,6 +71,7 @@ __device__ void trace_one(const DevMedium& m, const TraceArgs& a, int64_t r) {
     put(a, r, P, d, opl_ext, GRIN_EXIT_INVALID, 0, 0, 0);
     return;
   }
+  if (TAP) tap->put(P);
   const double dopl = a.dopl;
   double h = dopl / n_prev;
   double Q[3];
@@ -71,6 +88,7 @@ __device__ void trace_one(const DevMedium& m, const TraceArgs& a, int64_t r) {
       P[0] = Pb[0];
       P[1] = Pb[1];
       P[2] = Pb[2];
+      if (TAP) tap->put(P);
       if (snell(d, NB, n_prev / m.n_ext)) {
         ++tb;
         h = dopl / n_prev;
@@ -90,6 +108,7 @@ __device__ void trace_one(const DevMedium& m, const TraceArgs& a, int64_t r) {
     P[2] = Q[2];
     ++full;
     ++steps;
+    if (TAP) tap->put(P);
     double n_i;
     int lvl_i;
     sample<PC, GRID, LAYERED>(m, P, n_i, g, lvl_i);
@@ -137,6 +156,29 @@ __global__ void __launch_bounds__(128) k_trace_fp64(DevMedium m, TraceArgs a) {
     trace_one<PC, GRID, LAYERED>(m, a, r);
 }
 
+// grin_trace_path: the same trace with the point recorder; ray r's points
+// go to path + 3 cap r, its point count (which may exceed cap) to plen[r].
+template <int PC, bool GRID, bool LAYERED>
+__global__ void __launch_bounds__(128) k_trace_fp64_path(DevMedium m, TraceArgs a, double* path,
+                                                         int64_t cap, int64_t* plen) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.count; r += stride) {
+    PathTap tap{path + 3 * cap * r, cap, 0};
+    trace_one<PC, GRID, LAYERED, true>(m, a, r, &tap);
+    plen[r] = tap.n;
+  }
+}
+
+template <int PC, bool GRID, bool LAYERED>
+int launch_path_t(const DevMedium& m, const TraceArgs& a, double* path, int64_t cap,
+                  int64_t* plen, cudaStream_t s) {
+  const int block = 128;
+  int64_t blocks = (a.count + block - 1) / block;
+  if (blocks > (1 << 30)) blocks = 1 << 30;
+  return launch_kernel(k_trace_fp64_path<PC, GRID, LAYERED>, (unsigned)blocks, block, s, m, a,
+                       path, cap, plen);
+}
+
 template <int PC, bool GRID, bool LAYERED>
 int launch_t(const DevMedium& m, const TraceArgs& a, cudaStream_t s) {
   const int block = 128;
@@ -159,6 +201,26 @@ int launch_fp64(const DevMedium& m, const TraceArgs& a, cudaStream_t s, int) {
       return lay ? launch_t<4, false, true>(m, a, s) : launch_t<4, false, false>(m, a, s);
     default:
       return lay ? launch_t<6, false, true>(m, a, s) : launch_t<6, false, false>(m, a, s);
+  }
+}
+
+int launch_fp64_path(const DevMedium& m, const TraceArgs& a, double* path, int64_t cap,
+                     int64_t* plen, cudaStream_t s) {
+  using namespace plain;
+  const bool lay = m.n_levels > 0;
+  if (m.kind == GRIN_MEDIUM_GRID)
+    return lay ? launch_path_t<0, true, true>(m, a, path, cap, plen, s)
+               : launch_path_t<0, true, false>(m, a, path, cap, plen, s);
+  switch (m.pclass) {
+    case kPoly2:
+      return lay ? launch_path_t<2, false, true>(m, a, path, cap, plen, s)
+                 : launch_path_t<2, false, false>(m, a, path, cap, plen, s);
+    case kPoly4:
+      return lay ? launch_path_t<4, false, true>(m, a, path, cap, plen, s)
+                 : launch_path_t<4, false, false>(m, a, path, cap, plen, s);
+    default:
+      return lay ? launch_path_t<6, false, true>(m, a, path, cap, plen, s)
+                 : launch_path_t<6, false, false>(m, a, path, cap, plen, s);
   }
 }
 

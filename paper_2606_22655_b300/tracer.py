@@ -225,6 +225,25 @@ def trace_host(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_st
     return out
 
 
+def trace_path(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_steps: int, cap: int,
+               stream: Optional[torch.cuda.Stream] = None):
+    """grin_trace_path (plain FP64) on device tensors: returns (result dict,
+    points (count, cap, 3) float64, point counts (count,) int64).  Ray r's
+    polyline is points[r, :min(counts[r], cap)]."""
+    dev = rays.ox.device
+    out = empty_result(rays.count, dev)
+    pts = torch.zeros((rays.count, int(cap), 3), dtype=torch.float64, device=dev)
+    cnt = torch.zeros(rays.count, dtype=torch.int64, device=dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, "fp64")
+    N.check("grin_trace_path", ctx.lib.grin_trace_path(
+        ctx.handle, medium.handle, ctypes.byref(rs), ctypes.byref(ps), ctypes.byref(os_),
+        ctypes.c_void_p(pts.data_ptr()), int(cap), ctypes.c_void_p(cnt.data_ptr()),
+        ctypes.c_void_p(stream.cuda_stream)))
+    return out, pts, cnt
+
+
 def to_numpy(res: Dict[str, torch.Tensor]) -> Dict[str, np.ndarray]:
     """Results as numpy with P and d stacked to (n, 3), the oracle's layout."""
     h = {k: v.cpu().numpy() for k, v in res.items()}

@@ -205,6 +205,56 @@ def fiber_medium(nc: float = 1.38, delta: float = 0.2, radius: float = 5.0,
                   n_ext=nc * math.sqrt(1.0 - 2.0 * delta), name="fiber")
 
 
+# Fringe Zernike polynomials Z_m (University of Arizona ordering) as monomials
+# {(i, j): coefficient} of x' = rho cos(theta), y' = rho sin(theta):
+# Z5 = rho^2 cos 2t, Z8 = (3 rho^3 - 2 rho) sin t, Z9 = 6 rho^4 - 6 rho^2 + 1,
+# Z11 = rho^3 sin 3t, Z12 = (4 rho^4 - 3 rho^2) cos 2t, and the rest up to Z13.
+FRINGE_ZERNIKE = {
+    1: {(0, 0): 1.0},
+    2: {(1, 0): 1.0},
+    3: {(0, 1): 1.0},
+    4: {(2, 0): 2.0, (0, 2): 2.0, (0, 0): -1.0},
+    5: {(2, 0): 1.0, (0, 2): -1.0},
+    6: {(1, 1): 2.0},
+    7: {(3, 0): 3.0, (1, 2): 3.0, (1, 0): -2.0},
+    8: {(2, 1): 3.0, (0, 3): 3.0, (0, 1): -2.0},
+    9: {(4, 0): 6.0, (2, 2): 12.0, (0, 4): 6.0, (2, 0): -6.0, (0, 2): -6.0, (0, 0): 1.0},
+    10: {(3, 0): 1.0, (1, 2): -3.0},
+    11: {(2, 1): 3.0, (0, 3): -1.0},
+    12: {(4, 0): 4.0, (0, 4): -4.0, (2, 0): -3.0, (0, 2): 3.0},
+    13: {(3, 1): 8.0, (1, 3): 8.0, (1, 1): -6.0},
+}
+# Legendre polynomials V_n(z') as {power: coefficient}.
+LEGENDRE = {0: {0: 1.0}, 1: {1: 1.0}, 2: {2: 1.5, 0: -0.5}}
+# The corrector's nonzero expansion coefficients c_{m,n} (Sec. V).
+CORRECTOR_COEFFS = {(5, 0): -0.2368, (8, 0): 0.0249, (9, 0): 0.0011, (11, 0): -0.0078,
+                    (12, 0): -0.0013, (8, 1): 0.5548, (11, 1): -0.1731}
+
+
+def corrector_lens_medium(n_lo: float = 1.5148, n_hi: float = 1.5162, rho_max: float = 4.2,
+                          z_max: float = 2.5, coeffs=None, n_ext: float = 1.0) -> Medium:
+    """Freeform cylindrical GRIN corrector (Sec. V, binary linear composition):
+    n = n0 + dn sum c_mn Z_m(x', y') V_n(z') with n0 = (n_hi + n_lo)/2,
+    dn = (n_hi - n_lo)/2, x' = x/rho_max, y' = y/rho_max, z' = 2z/z_max - 1,
+    inside the cylinder rho <= rho_max, 0 <= z <= z_max.  Every Zernike and
+    Legendre term is a polynomial, so the expansion is handed to the tracers
+    as a polynomial medium of the normalised coordinates (degree 4 for the
+    paper's coefficients)."""
+    coeffs = CORRECTOR_COEFFS if coeffs is None else coeffs
+    n0, dn = 0.5 * (n_hi + n_lo), 0.5 * (n_hi - n_lo)
+    terms: Dict[Tuple[int, int, int], float] = {(0, 0, 0): n0}
+    for (m, v), c in coeffs.items():
+        for (i, j), zc in FRINGE_ZERNIKE[m].items():
+            for k, vc in LEGENDRE[v].items():
+                terms[(i, j, k)] = terms.get((i, j, k), 0.0) + dn * c * zc * vc
+    degree = max(sum(e) for e in terms)
+    bk, bp = cylinder(0.0, 0.0, rho_max, 0.0, z_max)
+    return Medium(kind=KIND_POLY, form=FORM_LINEAR, degree=degree,
+                  coeffs=coeffs_from_terms(degree, terms), off=(0.0, 0.0, 0.5 * z_max),
+                  scale=(rho_max, rho_max, 0.5 * z_max), bkind=bk, bparams=bp, n_ext=n_ext,
+                  name="corrector_lens")
+
+
 def homogeneous_box(n: float, lo=(-1.0, -1.0, 0.0), hi=(1.0, 1.0, 1.0), n_ext: float = 1.0) -> Medium:
     bk, bp = box(lo, hi)
     return Medium(kind=KIND_POLY, form=FORM_LINEAR, degree=0, coeffs=np.array([n]),
@@ -316,6 +366,28 @@ def freeform_workload(n_rays: int = 1 << 20, seed: int = BASE_SEED + 1,
     rays = point_source_rays(n_rays, seed if ray_seed is None else ray_seed)
     return Workload(f"freeform_block_{n_rays}", m, rays, 0.01, 20000,
                     math.sqrt(5.0 ** 2 + 5.0 ** 2 + 10.0 ** 2))
+
+
+def corrector_example_ray() -> Rays:
+    """The corrector lens example of Fig. 3(a): P0 = (1, -5, -1.5),
+    theta0 = 80 deg, phi0 = 110 deg."""
+    d = direction(np.radians([80.0]), np.radians([110.0]))
+    return Rays(np.array([[1.0, -5.0, -1.5]]), d)
+
+
+def corrector_workload(n_rays: int = 1 << 16, seed: int = BASE_SEED + 5, **lens) -> Workload:
+    """The corrector lens with a bundle launched from the plane z = -1.5:
+    origins uniform over the disk of radius 4, directions within 20 deg of
+    +z; dL0 = 1e-3 (about 3,800 steps through the 2.5-unit thickness), at
+    most 20000 steps."""
+    m = corrector_lens_medium(**lens)
+    r = 4.0 * np.sqrt(uniform(seed, 1, n_rays))
+    a = uniform(seed, 2, n_rays, 0.0, 2.0 * math.pi)
+    o = np.stack([r * np.cos(a), r * np.sin(a), np.full(n_rays, -1.5)], 1)
+    d = direction(uniform(seed, 3, n_rays, 0.0, math.radians(20.0)),
+                  uniform(seed, 4, n_rays, 0.0, 2.0 * math.pi))
+    return Workload(f"corrector_lens_{n_rays}", m, Rays(o, d), 1e-3, 20000,
+                    math.sqrt(4.2 ** 2 + 1.25 ** 2))
 
 
 def blob_workload(n_rays: int = 1 << 22, res: int = 256, n_levels: int = 0,

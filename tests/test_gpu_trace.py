@@ -193,6 +193,26 @@ def test_fiber_cylinder(ctx):
     check64(g, o, 20.0)
 
 
+def test_corrector_lens_cylinder(ctx):
+    """Sec. V corrector lens (Zernike x Legendre in a cylinder) with a bundle
+    through the aperture, and the paper's example ray of Fig. 3(a), which
+    enters through the side wall and reflects at it once: FP64 against the
+    oracle, mixed against FP64."""
+    wl = W.corrector_workload(2049)
+    g64 = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "fp64")
+    o = orc(wl.medium, wl.rays, wl.dopl, wl.max_steps)
+    check64(g64, o, wl.l_ref)
+    g32 = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "mixed")
+    check32(g32, g64, wl.l_ref, flags32(o), 0.005)
+    r = W.corrector_example_ray()
+    for lo, hi in ((1.5148, 1.5162), (1.5261, 1.5608)):
+        m = W.corrector_lens_medium(n_lo=lo, n_hi=hi)
+        ge = gpu_trace(ctx, m, r, 1e-3, 40000, "fp64")
+        oe = orc(m, r, 1e-3, 40000)
+        check64(ge, oe, wl.l_ref)
+        assert ge["exit_id"][0] == 2 and ge["tir_boundary"][0] == 1
+
+
 # ------------------------------------------------------ gridded and layered
 
 

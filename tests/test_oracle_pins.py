@@ -389,3 +389,49 @@ def test_internal_tir_step_length_uses_previous_index():
     p_k = np.array([0, 0, 1.05]) + k_star * h * d0
     expect = p_k + h * np.array([math.sin(a), 0.0, math.cos(a)])
     np.testing.assert_allclose(r["P"], expect, atol=1e-12)
+
+
+def _fringe_trig(m, rho, t):
+    """Fringe Zernike Z_m from its definition in polar form."""
+    return {1: np.ones_like(rho), 2: rho * np.cos(t), 3: rho * np.sin(t), 4: 2 * rho**2 - 1,
+            5: rho**2 * np.cos(2 * t), 6: rho**2 * np.sin(2 * t),
+            7: (3 * rho**3 - 2 * rho) * np.cos(t), 8: (3 * rho**3 - 2 * rho) * np.sin(t),
+            9: 6 * rho**4 - 6 * rho**2 + 1, 10: rho**3 * np.cos(3 * t), 11: rho**3 * np.sin(3 * t),
+            12: (4 * rho**4 - 3 * rho**2) * np.cos(2 * t),
+            13: (4 * rho**4 - 3 * rho**2) * np.sin(2 * t)}[m]
+
+
+def _corrector_trig(p, coeffs, n_lo, n_hi, rho_max=4.2, z_max=2.5):
+    x, y, z = p[:, 0] / rho_max, p[:, 1] / rho_max, 2 * p[:, 2] / z_max - 1
+    rho, t = np.hypot(x, y), np.arctan2(y, x)
+    legendre = {0: np.ones_like(z), 1: z, 2: 1.5 * z**2 - 0.5}
+    s = sum(c * _fringe_trig(m, rho, t) * legendre[v] for (m, v), c in coeffs.items())
+    return 0.5 * (n_hi + n_lo) + 0.5 * (n_hi - n_lo) * s
+
+
+def test_corrector_lens_zernike_legendre_expansion():
+    """Sec. V corrector lens: the medium handed to the tracers (monomials of
+    the normalised coordinates) against the Zernike x Legendre expansion
+    evaluated in polar form (rho, theta = atan2), for the paper's coefficients
+    and for every Fringe term Z1..Z13 times V0..V2; gradient against central
+    differences of the polar form."""
+    rng = np.random.default_rng(11)
+    k = 40
+    r = 4.2 * np.sqrt(rng.uniform(0, 1, k))
+    a = rng.uniform(0, 2 * np.pi, k)
+    p = np.stack([r * np.cos(a), r * np.sin(a), rng.uniform(0, 2.5, k)], 1)
+    cases = [(W.CORRECTOR_COEFFS, 1.5148, 1.5162), (W.CORRECTOR_COEFFS, 1.5261, 1.5608)]
+    cases += [({(m, v): 1.0}, 1.0, 3.0) for m in range(1, 14) for v in range(3)]
+    for coeffs, lo, hi in cases:
+        med = W.corrector_lens_medium(n_lo=lo, n_hi=hi, coeffs=coeffs)
+        n, g = oracle.medium_eval(med, p)
+        ref = _corrector_trig(p, coeffs, lo, hi)
+        np.testing.assert_allclose(n, ref, rtol=0, atol=1e-14 * max(1.0, np.abs(ref).max()))
+        h = 1e-5
+        for ax in range(3):
+            e = np.zeros(3)
+            e[ax] = h
+            fd = (_corrector_trig(p + e, coeffs, lo, hi) - _corrector_trig(p - e, coeffs, lo, hi)) / (2 * h)
+            np.testing.assert_allclose(g[:, ax], fd, rtol=0, atol=1e-8 * max(1.0, np.abs(fd).max()))
+    # the paper's expansion is a degree-4 polynomial
+    assert W.corrector_lens_medium().degree == 4
