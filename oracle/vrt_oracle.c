@@ -89,6 +89,43 @@ static void poly_eval(const orc_medium* m, const double* P, double* p, double* g
   gp[2] = gz / m->scale[2];
 }
 
+/* Spherical freeform field (Sec. V), in the normalised coordinates:
+ * p = a0 + a1 G1 + a2 G2 + a3 G3 with G1 = 0.3 (r^2 - 1), G2 = r cos(5 theta)
+ * and G3 = r^2 sin^2(theta) cos(2 phi), theta the polar angle from +z' and
+ * phi the azimuth.  Written without angles: cos(theta) = z/r and
+ * cos(5 theta) = 16 c^5 - 20 c^3 + 5 c (Chebyshev T5) give
+ * G2 = z (16 t^2 - 20 t + 5) with t = z^2 / r^2; and
+ * r^2 sin^2(theta) cos(2 phi) = (x^2 + y^2)(cos^2 phi - sin^2 phi) = x^2 - y^2.
+ * The gradient follows by differentiating these forms (dt/dx = -2 x t / r^2,
+ * dt/dy = -2 y t / r^2, dt/dz = 2 z (1 - t) / r^2).  At r = 0 the polar angle
+ * is taken as 0 (t = 1, dt = 0). */
+static void sph_eval(const orc_medium* m, const double* P, double* p, double* gp) {
+  double x = (P[0] - m->off[0]) / m->scale[0];
+  double y = (P[1] - m->off[1]) / m->scale[1];
+  double z = (P[2] - m->off[2]) / m->scale[2];
+  const double* a = m->coeffs;
+  double r2 = x * x + y * y + z * z;
+  double t = 1.0, tx = 0.0, ty = 0.0, tz = 0.0;
+  if (r2 > 0.0) {
+    t = z * z / r2;
+    tx = -2.0 * x * t / r2;
+    ty = -2.0 * y * t / r2;
+    tz = 2.0 * z * (1.0 - t) / r2;
+  }
+  double q = 16.0 * t * t - 20.0 * t + 5.0; /* cos(5 theta) / cos(theta) */
+  double qt = 32.0 * t - 20.0;              /* dq/dt */
+  double g1 = 0.3 * (r2 - 1.0);
+  double g2 = z * q;
+  double g3 = x * x - y * y;
+  *p = a[0] + a[1] * g1 + a[2] * g2 + a[3] * g3;
+  double gx = a[1] * (0.6 * x) + a[2] * (z * qt * tx) + a[3] * (2.0 * x);
+  double gy = a[1] * (0.6 * y) + a[2] * (z * qt * ty) + a[3] * (-2.0 * y);
+  double gz = a[1] * (0.6 * z) + a[2] * (q + z * qt * tz);
+  gp[0] = gx / m->scale[0];
+  gp[1] = gy / m->scale[1];
+  gp[2] = gz / m->scale[2];
+}
+
 /* Catmull-Rom cubic convolution weights (Keys 1981, a = -1/2) for the taps at
  * offsets -1, 0, 1, 2 around the cell containing fraction t, and their
  * derivatives with respect to t. */
@@ -148,7 +185,10 @@ static void field_eval(const orc_medium* m, const double* P, double* f, double* 
     return;
   }
   double p, gp[3];
-  poly_eval(m, P, &p, gp);
+  if (m->kind == 2)
+    sph_eval(m, P, &p, gp);
+  else
+    poly_eval(m, P, &p, gp);
   if (m->form == 0) {
     *f = p;
     g[0] = gp[0];

@@ -25,7 +25,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 BASE_SEED = 20260622
 
 # medium kinds, polynomial forms and boundary kinds (shared vocabulary only)
-KIND_POLY, KIND_GRID = 0, 1
+KIND_POLY, KIND_GRID, KIND_SPHERICAL = 0, 1, 2
 FORM_LINEAR, FORM_SQRT, FORM_RECIP = 0, 1, 2
 BOUNDARY_BOX, BOUNDARY_SPHERE, BOUNDARY_CYLINDER = 0, 1, 2
 
@@ -94,7 +94,9 @@ class Medium:
     kind: KIND_POLY (polynomial p of the normalised coordinates
     x' = (x - off) / scale, with n = p, sqrt(p) or form_c / p) or KIND_GRID
     (float32 samples grid[k, j, i] at origin + (i, j, k) * spacing, read by
-    Catmull-Rom tricubic interpolation).  n_levels > 0 quantises the field into
+    Catmull-Rom tricubic interpolation) or KIND_SPHERICAL (the spherical
+    freeform field of Sec. V, coeffs = a0..a3, normalised by `scale`).
+    n_levels > 0 quantises the field into
     that many isoindicial shells between level_lo and level_hi.  The boundary
     is a box (lo[3], hi[3]), sphere (c[3], R) or z-cylinder (cx, cy, R, z0,
     z1), surrounded by index n_ext."""
@@ -255,6 +257,19 @@ def corrector_lens_medium(n_lo: float = 1.5148, n_hi: float = 1.5162, rho_max: f
                   name="corrector_lens")
 
 
+def spherical_freeform_medium(a=(1.5, 1.0, -0.2, 0.3), radius: float = 1.0, centre=(0.0, 0.0, 0.0),
+                              n_ext: float = 1.0) -> Medium:
+    """Spherical freeform GRIN medium (Sec. V): n = a0 + a1 G1 + a2 G2 + a3 G3
+    with G1 = 0.3 (r^2 - 1), G2 = r cos(5 theta), G3 = r^2 sin^2(theta) cos(2 phi)
+    in coordinates normalised by the sphere's radius; the paper's a = (1.5, 1,
+    -0.2, 0.3) and r_max = 1.  The surround index is not given; 1 is taken."""
+    bk, bp = sphere(centre, radius)
+    return Medium(kind=KIND_SPHERICAL, form=FORM_LINEAR, degree=0,
+                  coeffs=np.asarray(a, dtype=np.float64), off=tuple(centre),
+                  scale=(radius, radius, radius), bkind=bk, bparams=bp, n_ext=n_ext,
+                  name="spherical_freeform")
+
+
 def homogeneous_box(n: float, lo=(-1.0, -1.0, 0.0), hi=(1.0, 1.0, 1.0), n_ext: float = 1.0) -> Medium:
     bk, bp = box(lo, hi)
     return Medium(kind=KIND_POLY, form=FORM_LINEAR, degree=0, coeffs=np.array([n]),
@@ -388,6 +403,29 @@ def corrector_workload(n_rays: int = 1 << 16, seed: int = BASE_SEED + 5, **lens)
                   uniform(seed, 4, n_rays, 0.0, 2.0 * math.pi))
     return Workload(f"corrector_lens_{n_rays}", m, Rays(o, d), 1e-3, 20000,
                     math.sqrt(4.2 ** 2 + 1.25 ** 2))
+
+
+def spherical_example_ray() -> Rays:
+    """The spherical freeform example of Fig. 3(b): P0 = (-1, -1, -1),
+    theta0 = 80 deg, phi0 = 20 deg."""
+    return Rays(np.array([[-1.0, -1.0, -1.0]]), direction(np.radians([80.0]), np.radians([20.0])))
+
+
+def spherical_workload(n_rays: int = 1 << 16, seed: int = BASE_SEED + 6, **medium) -> Workload:
+    """The spherical freeform medium with rays from random points on the
+    sphere of radius 1.5 aimed at random points within 0.7 of the centre;
+    dL0 = 1e-3, at most 20000 steps."""
+    m = spherical_freeform_medium(**medium)
+    def on_sphere(stream):
+        cz = uniform(seed, stream, n_rays, -1.0, 1.0)
+        ph = uniform(seed, stream + 1, n_rays, 0.0, 2.0 * math.pi)
+        s = np.sqrt(1.0 - cz * cz)
+        return np.stack([s * np.cos(ph), s * np.sin(ph), cz], 1)
+    o = 1.5 * on_sphere(1)
+    t = 0.7 * np.cbrt(uniform(seed, 5, n_rays))[:, None] * on_sphere(3)
+    d = t - o
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return Workload(f"spherical_freeform_{n_rays}", m, Rays(o, d), 1e-3, 20000, 1.0)
 
 
 def blob_workload(n_rays: int = 1 << 22, res: int = 256, n_levels: int = 0,

@@ -435,3 +435,73 @@ def test_corrector_lens_zernike_legendre_expansion():
             np.testing.assert_allclose(g[:, ax], fd, rtol=0, atol=1e-8 * max(1.0, np.abs(fd).max()))
     # the paper's expansion is a degree-4 polynomial
     assert W.corrector_lens_medium().degree == 4
+
+
+def _spherical_trig(p, a, radius=1.0):
+    """Sec. V spherical freeform index from its definition in spherical
+    coordinates (theta from +z, phi the azimuth)."""
+    x, y, z = (p / radius).T
+    r = np.sqrt(x * x + y * y + z * z)
+    th = np.arccos(np.clip(z / r, -1.0, 1.0))
+    ph = np.arctan2(y, x)
+    return (a[0] + a[1] * 0.3 * (r**2 - 1) + a[2] * r * np.cos(5 * th)
+            + a[3] * r**2 * np.sin(th)**2 * np.cos(2 * ph))
+
+
+@pytest.mark.parametrize("a", [(1.5, 1.0, -0.2, 0.3), (1.2, -0.7, 0.9, -0.4)])
+def test_spherical_freeform_field_against_definition(a):
+    """The oracle's angle-free form (Chebyshev T5, x^2 - y^2) against the
+    definition with arccos/arctan2 and cosines; the gradient against central
+    differences of the definition; R = 2 exercises the normalisation."""
+    rng = np.random.default_rng(5)
+    R = 2.0
+    v = rng.normal(size=(60, 3))
+    p = R * (0.05 + 0.9 * rng.uniform(size=(60, 1))) * v / np.linalg.norm(v, axis=1, keepdims=True)
+    m = W.spherical_freeform_medium(a=a, radius=R)
+    n, g = oracle.medium_eval(m, p)
+    np.testing.assert_allclose(n, _spherical_trig(p, a, R), rtol=0, atol=2e-15)
+    h = 1e-6
+    for ax in range(3):
+        e = np.zeros(3)
+        e[ax] = h
+        fd = (_spherical_trig(p + e, a, R) - _spherical_trig(p - e, a, R)) / (2 * h)
+        np.testing.assert_allclose(g[:, ax], fd, rtol=0, atol=2e-8)
+
+
+def test_spherical_freeform_reduces_to_polynomial():
+    """With a2 = 0 the field is the quadratic a0 + 0.3 a1 (r^2 - 1) + a3 (x^2 - y^2):
+    rays through both descriptions agree to rounding."""
+    a0, a1, a3 = 1.5, 1.0, 0.3
+    sph = W.spherical_freeform_medium(a=(a0, a1, 0.0, a3))
+    c = W.coeffs_from_terms(2, {(0, 0, 0): a0 - 0.3 * a1, (2, 0, 0): 0.3 * a1 + a3,
+                                (0, 2, 0): 0.3 * a1 - a3, (0, 0, 2): 0.3 * a1})
+    poly = W.Medium(kind=W.KIND_POLY, degree=2, coeffs=c, bkind=sph.bkind, bparams=sph.bparams,
+                    n_ext=1.0)
+    wl = W.spherical_workload(64, a=(a0, a1, 0.0, a3))
+    o1 = oracle.trace(sph, wl.rays.origins, wl.rays.dirs, wl.dopl, wl.max_steps)
+    o2 = oracle.trace(poly, wl.rays.origins, wl.rays.dirs, wl.dopl, wl.max_steps)
+    ok = (o1["margins"][:, 0] > 1e-9) & (o1["margins"][:, 2] > 1e-9)
+    assert ok.mean() > 0.9
+    for k in ("exit_id", "steps", "tir_internal", "tir_boundary"):
+        np.testing.assert_array_equal(o1[k][ok], o2[k][ok])
+    np.testing.assert_allclose(o1["P"][ok], o2["P"][ok], rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_spherical_freeform_axis_ray_closed_form_opl(sign):
+    """On the z axis G3 and its gradient vanish and grad n is axial, so a ray
+    along the axis stays on it exactly; there n = a0 - 0.3 a1 + 0.3 a1 z^2 +
+    a2 z, whose integral over [-1, 1] is 2 a0 - 0.4 a1.  The discrete optical
+    path converges to 1 (the unit exterior segment) + that, at first order."""
+    a = (1.5, 1.0, -0.2, 0.3)
+    m = W.spherical_freeform_medium(a=a)
+    exact = 1.0 + 2 * a[0] - 0.4 * a[1]
+    errs = []
+    for dopl in (1e-3, 5e-4):
+        o = oracle.trace(m, np.array([[0.0, 0.0, -2.0 * sign]]), np.array([[0.0, 0.0, sign]]), dopl, 100000)
+        assert o["exit_id"][0] == 0
+        np.testing.assert_array_equal(o["P"][0, :2], [0.0, 0.0])
+        np.testing.assert_array_equal(o["d"][0], [0.0, 0.0, sign])
+        errs.append(abs(o["opl"][0] - exact))
+    assert errs[0] < 5e-3
+    assert 1.5 < errs[0] / errs[1] < 2.5
