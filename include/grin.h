@@ -66,7 +66,7 @@ enum {
   GRIN_EXIT_INVALID = -4        /* non-finite or zero direction, n <= 0 */
 };
 
-enum { GRIN_MEDIUM_POLY = 0, GRIN_MEDIUM_GRID = 1 };
+enum { GRIN_MEDIUM_POLY = 0, GRIN_MEDIUM_GRID = 1, GRIN_MEDIUM_SPHERICAL = 2 };
 enum { GRIN_FORM_LINEAR = 0, GRIN_FORM_SQRT = 1, GRIN_FORM_RECIP = 2 };
 enum { GRIN_BOUNDARY_BOX = 0, GRIN_BOUNDARY_SPHERE = 1, GRIN_BOUNDARY_CYLINDER = 2 };
 enum { GRIN_F32 = 0, GRIN_F64 = 1 };
@@ -88,7 +88,14 @@ enum { GRIN_PREC_FP64 = 0, GRIN_PREC_FP32_MIXED = 1, GRIN_PREC_FP64_FAST = 2 };
  *   - GRIN_MEDIUM_GRID: float32 samples grid[(k * ny + j) * nx + i] at
  *     origin + (i, j, k) * spacing (host memory, or device memory if
  *     grid_on_device), read by Catmull-Rom tricubic interpolation (Keys 1981)
- *     with edge-clamped taps and its analytic gradient.
+ *     with edge-clamped taps and its analytic gradient;
+ *   - GRIN_MEDIUM_SPHERICAL: the spherical freeform field of Sec. V,
+ *     p = a0 + a1 G1 + a2 G2 + a3 G3 with G1 = 0.3 (r^2 - 1),
+ *     G2 = r cos(5 theta), G3 = r^2 sin^2(theta) cos(2 phi) in the normalised
+ *     coordinates x' (r = |x'|, theta from +z', phi the azimuth), a0..a3 the
+ *     4 host doubles in `coeffs` (degree is ignored); `form` maps p to n as
+ *     for polynomials.  At r = 0 the polar angle is taken as 0.
+ *     grin_trace_adjoint returns GRIN_ERR_NOT_IMPLEMENTED for it.
  * n_levels > 0 turns the field into that many isoindicial shells (the
  * discretised media of Sec. I and the abstract): level
  * k = clamp(floor(n_levels (f - level_lo) / (level_hi - level_lo)), 0,

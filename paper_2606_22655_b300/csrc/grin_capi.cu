@@ -95,7 +95,8 @@ int grin_medium_create(grin_ctx ctx, const grin_medium_desc* d, grin_medium* out
   m.n_ext = d->n_ext;
   m.form_c = d->form_c;
   if (!finite_pos(d->n_ext)) return GRIN_ERR_INVALID_ARG;
-  if (d->kind != GRIN_MEDIUM_POLY && d->kind != GRIN_MEDIUM_GRID) return GRIN_ERR_INVALID_ARG;
+  if (d->kind != GRIN_MEDIUM_POLY && d->kind != GRIN_MEDIUM_GRID && d->kind != GRIN_MEDIUM_SPHERICAL)
+    return GRIN_ERR_INVALID_ARG;
   if (d->n_levels < 0 || d->n_levels > GRIN_MAX_LEVELS) return GRIN_ERR_INVALID_ARG;
   if (d->n_levels > 0 && !(std::isfinite(d->level_lo) && std::isfinite(d->level_hi) &&
                            d->level_hi > d->level_lo))
@@ -119,8 +120,10 @@ int grin_medium_create(grin_ctx ctx, const grin_medium_desc* d, grin_medium* out
   std::memcpy(m.b, b, sizeof(m.b));
 
   std::vector<float> samples;
-  if (d->kind == GRIN_MEDIUM_POLY) {
-    if (d->degree < 0 || d->degree > GRIN_MAX_DEGREE || !d->coeffs) return GRIN_ERR_INVALID_ARG;
+  if (d->kind == GRIN_MEDIUM_POLY || d->kind == GRIN_MEDIUM_SPHERICAL) {
+    const bool sph = d->kind == GRIN_MEDIUM_SPHERICAL;
+    if (!d->coeffs || (!sph && (d->degree < 0 || d->degree > GRIN_MAX_DEGREE)))
+      return GRIN_ERR_INVALID_ARG;
     if (d->form < GRIN_FORM_LINEAR || d->form > GRIN_FORM_RECIP) return GRIN_ERR_INVALID_ARG;
     if (d->form == GRIN_FORM_RECIP && !std::isfinite(d->form_c)) return GRIN_ERR_INVALID_ARG;
     for (int k = 0; k < 3; ++k) {
@@ -130,21 +133,30 @@ int grin_medium_create(grin_ctx ctx, const grin_medium_desc* d, grin_medium* out
       m.off[k] = d->norm_offset[k];
       m.inv_scale[k] = 1.0 / d->norm_scale[k];
     }
-    m.pclass = d->degree <= 2 ? grin::kPoly2 : (d->degree <= 4 ? grin::kPoly4 : grin::kPoly6);
-    const int D = m.pclass;
-    // graded-lex input: kept as is (zero padded to class D) and scattered
-    // into the Horner layout of class D
-    int idx = 0;
-    for (int s = 0; s <= d->degree; ++s)
-      for (int i = s; i >= 0; --i)
-        for (int j = s - i; j >= 0; --j) {
-          double c = d->coeffs[idx];
-          if (!std::isfinite(c)) return GRIN_ERR_INVALID_ARG;
-          m.cglex[idx++] = c;
-          m.c64[grin::hidx(D, i, j, s - i - j)] = c;
-        }
+    if (sph) {
+      // a0..a3 of the spherical freeform field, the same in every layout
+      m.pclass = grin::kSpherical;
+      for (int k = 0; k < 4; ++k) {
+        if (!std::isfinite(d->coeffs[k])) return GRIN_ERR_INVALID_ARG;
+        m.cglex[k] = m.c64[k] = d->coeffs[k];
+      }
+    } else {
+      m.pclass = d->degree <= 2 ? grin::kPoly2 : (d->degree <= 4 ? grin::kPoly4 : grin::kPoly6);
+      const int D = m.pclass;
+      // graded-lex input: kept as is (zero padded to class D) and scattered
+      // into the Horner layout of class D
+      int idx = 0;
+      for (int s = 0; s <= d->degree; ++s)
+        for (int i = s; i >= 0; --i)
+          for (int j = s - i; j >= 0; --j) {
+            double c = d->coeffs[idx];
+            if (!std::isfinite(c)) return GRIN_ERR_INVALID_ARG;
+            m.cglex[idx++] = c;
+            m.c64[grin::hidx(D, i, j, s - i - j)] = c;
+          }
+    }
     for (int k = 0; k < 3; ++k) m.scale[k] = d->norm_scale[k];
-    const double c0 = m.c64[0];  // hidx(D, 0, 0, 0) == 0
+    const double c0 = m.c64[0];  // hidx(D, 0, 0, 0) == 0; a0 of the spherical field
     float base_f = 1.0f;
     if (d->form == GRIN_FORM_LINEAR) base_f = (float)c0;
     else if (d->form == GRIN_FORM_SQRT && c0 > 0.0) base_f = (float)std::sqrt(c0);

@@ -81,6 +81,41 @@ __device__ __forceinline__ void poly_vg(const T* __restrict__ c, T x, T y, T z, 
   pz = PZ;
 }
 
+// Spherical freeform field of Sec. V and its gradient in the normalised
+// coordinates: p = a0 + a1 G1 + a2 G2 + a3 G3 with G1 = 0.3 (r^2 - 1),
+// G2 = r cos(5 theta) = z (16 t^2 - 20 t + 5), t = z^2 / r^2 = cos^2(theta)
+// (Chebyshev T5), and G3 = r^2 sin^2(theta) cos(2 phi) = x^2 - y^2; at r = 0
+// the polar angle is taken as 0 (t = 1).
+template <typename T>
+__device__ __forceinline__ void sph_vg(const T* a, T x, T y, T z, T& p, T& px, T& py, T& pz) {
+  const T r2 = fmadd(x, x, fmadd(y, y, z * z));
+  T t = T(1), tx = T(0), ty = T(0), tz = T(0);
+  if (r2 > T(0)) {
+    const T inv = T(1) / r2;
+    t = z * z * inv;
+    const T k = T(-2) * t * inv;
+    tx = k * x;
+    ty = k * y;
+    tz = T(2) * z * (T(1) - t) * inv;
+  }
+  const T q = fmadd(fmadd(T(16), t, T(-20)), t, T(5));  // cos(5 theta) / cos(theta)
+  const T zq = z * fmadd(T(32), t, T(-20));             // z dq/dt
+  p = fmadd(a[1], T(0.3) * (r2 - T(1)), fmadd(a[2], z * q, fmadd(a[3], fmadd(x, x, -y * y), a[0])));
+  px = fmadd(a[1], T(0.6) * x, fmadd(a[2], zq * tx, a[3] * (T(2) * x)));
+  py = fmadd(a[1], T(0.6) * y, fmadd(a[2], zq * ty, a[3] * (T(-2) * y)));
+  pz = fmadd(a[1], T(0.6) * z, a[2] * fmadd(zq, tz, q));
+}
+
+// The analytic field of class PC: a polynomial, or the spherical freeform
+// field (PC == kSpherical, coefficients a0..a3).
+template <int PC, typename T>
+__device__ __forceinline__ void field_vg(const T* c, T x, T y, T z, T& p, T& px, T& py, T& pz) {
+  if constexpr (PC == kSpherical)
+    sph_vg<T>(c, x, y, z, p, px, py, pz);
+  else
+    poly_vg<PC, T>(c, x, y, z, p, px, py, pz);
+}
+
 // ------------------------------------------------------- tricubic gathers
 
 // Catmull-Rom (Keys cubic convolution, a = -1/2) weights for the taps at -1,

@@ -17,7 +17,9 @@ constexpr int kMaxTerms = 84;
 
 // Polynomial evaluators are instantiated for these total degrees; a medium
 // of lower degree is zero-padded to the next class.
-enum PolyClass : int32_t { kPoly2 = 2, kPoly4 = 4, kPoly6 = 6 };
+// Coefficient layout of an analytic medium, also the template parameter PC of
+// the kernels: polynomial degree classes, or the spherical freeform field.
+enum PolyClass : int32_t { kSpherical = 1, kPoly2 = 2, kPoly4 = 4, kPoly6 = 6 };
 
 // Everything a kernel needs to evaluate n, grad n and the boundary, passed by
 // value as a kernel parameter (it lives in the constant bank, so every lane

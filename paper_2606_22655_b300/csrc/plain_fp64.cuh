@@ -112,6 +112,38 @@ __device__ __forceinline__ void tricubic(const DevMedium& m, const double* P, do
   gf[2] = gz / m.spacing[2];
 }
 
+// Spherical freeform field of Sec. V in the normalised coordinates,
+// p = a0 + a1 G1 + a2 G2 + a3 G3 with G1 = 0.3 (r^2 - 1), G2 = r cos(5 theta)
+// written as z (16 t^2 - 20 t + 5), t = z^2 / r^2 (cos(theta) = z / r and
+// Chebyshev T5), and G3 = r^2 sin^2(theta) cos(2 phi) written as x^2 - y^2;
+// the gradient from those forms.  At r = 0 the polar angle is taken as 0.
+__device__ __forceinline__ void sph(const DevMedium& m, const double* P, double& p, double* gp) {
+  double x = (P[0] - m.off[0]) / m.scale[0];
+  double y = (P[1] - m.off[1]) / m.scale[1];
+  double z = (P[2] - m.off[2]) / m.scale[2];
+  const double* a = m.cglex;
+  double r2 = x * x + y * y + z * z;
+  double t = 1.0, tx = 0.0, ty = 0.0, tz = 0.0;
+  if (r2 > 0.0) {
+    t = z * z / r2;
+    tx = -2.0 * x * t / r2;
+    ty = -2.0 * y * t / r2;
+    tz = 2.0 * z * (1.0 - t) / r2;
+  }
+  double q = 16.0 * t * t - 20.0 * t + 5.0;
+  double qt = 32.0 * t - 20.0;
+  double g1 = 0.3 * (r2 - 1.0);
+  double g2 = z * q;
+  double g3 = x * x - y * y;
+  p = a[0] + a[1] * g1 + a[2] * g2 + a[3] * g3;
+  double gx = a[1] * (0.6 * x) + a[2] * (z * qt * tx) + a[3] * (2.0 * x);
+  double gy = a[1] * (0.6 * y) + a[2] * (z * qt * ty) + a[3] * (-2.0 * y);
+  double gz = a[1] * (0.6 * z) + a[2] * (q + z * qt * tz);
+  gp[0] = gx / m.scale[0];
+  gp[1] = gy / m.scale[1];
+  gp[2] = gz / m.scale[2];
+}
+
 // n (after layering) and the gradient of the smooth field; lvl = level or -1.
 template <int PC, bool GRID, bool LAYERED>
 __device__ __forceinline__ void sample(const DevMedium& m, const double* P, double& n, double* g,
@@ -121,7 +153,10 @@ __device__ __forceinline__ void sample(const DevMedium& m, const double* P, doub
     tricubic(m, P, f, g);
   } else {
     double p, gp[3];
-    poly<PC>(m, P, p, gp);
+    if constexpr (PC == kSpherical)
+      sph(m, P, p, gp);
+    else
+      poly<PC>(m, P, p, gp);
     if (m.form == GRIN_FORM_LINEAR) {
       f = p;
       g[0] = gp[0];

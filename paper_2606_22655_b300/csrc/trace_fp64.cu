@@ -195,6 +195,8 @@ int launch_fp64(const DevMedium& m, const TraceArgs& a, cudaStream_t s, int) {
   if (m.kind == GRIN_MEDIUM_GRID)
     return lay ? launch_t<0, true, true>(m, a, s) : launch_t<0, true, false>(m, a, s);
   switch (m.pclass) {
+    case kSpherical:
+      return lay ? launch_t<1, false, true>(m, a, s) : launch_t<1, false, false>(m, a, s);
     case kPoly2:
       return lay ? launch_t<2, false, true>(m, a, s) : launch_t<2, false, false>(m, a, s);
     case kPoly4:
@@ -212,6 +214,9 @@ int launch_fp64_path(const DevMedium& m, const TraceArgs& a, double* path, int64
     return lay ? launch_path_t<0, true, true>(m, a, path, cap, plen, s)
                : launch_path_t<0, true, false>(m, a, path, cap, plen, s);
   switch (m.pclass) {
+    case kSpherical:
+      return lay ? launch_path_t<1, false, true>(m, a, path, cap, plen, s)
+                 : launch_path_t<1, false, false>(m, a, path, cap, plen, s);
     case kPoly2:
       return lay ? launch_path_t<2, false, true>(m, a, path, cap, plen, s)
                  : launch_path_t<2, false, false>(m, a, path, cap, plen, s);

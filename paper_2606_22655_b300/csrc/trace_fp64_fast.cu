@@ -33,7 +33,7 @@ struct Field64Fast {
       double y = (p.y - m.off[1]) * m.inv_scale[1];
       double z = (p.z - m.off[2]) * m.inv_scale[2];
       double q, qx, qy, qz;
-      poly_vg<PC, double>(m.c64, x, y, z, q, qx, qy, qz);
+      field_vg<PC, double>(m.c64, x, y, z, q, qx, qy, qz);
       V3 gq = mk(qx * m.inv_scale[0], qy * m.inv_scale[1], qz * m.inv_scale[2]);
       if (m.form == GRIN_FORM_LINEAR) {
         f = q;
@@ -183,6 +183,8 @@ int launch_fp64_fast(const DevMedium& m, const TraceArgs& a, cudaStream_t s, int
   if (m.kind == GRIN_MEDIUM_GRID)
     return lay ? launch_t<0, true, true>(m, a, s) : launch_t<0, true, false>(m, a, s);
   switch (m.pclass) {
+    case kSpherical:
+      return lay ? launch_t<1, false, true>(m, a, s) : launch_t<1, false, false>(m, a, s);
     case kPoly2:
       return lay ? launch_t<2, false, true>(m, a, s) : launch_t<2, false, false>(m, a, s);
     case kPoly4:

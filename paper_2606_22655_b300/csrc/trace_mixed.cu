@@ -83,7 +83,7 @@ struct Cfg {
       float y = (py - m.off_f[1]) * m.inv_scale_f[1];
       float z = (pz - m.off_f[2]) * m.inv_scale_f[2];
       float q, qx, qy, qz;
-      poly_vg<PC, float>(m.c32, x, y, z, q, qx, qy, qz);
+      field_vg<PC, float>(m.c32, x, y, z, q, qx, qy, qz);
       qx *= m.inv_scale_f[0];
       qy *= m.inv_scale_f[1];
       qz *= m.inv_scale_f[2];
@@ -729,6 +729,7 @@ int launch_mixed(const DevMedium& m, const TraceArgs& a, unsigned long long* que
                  cudaStream_t s, int sm_count) {
   if (m.kind == GRIN_MEDIUM_GRID) return launch_pc<0, true>(m, a, queue, s, sm_count);
   switch (m.pclass) {
+    case kSpherical: return launch_pc<1, false>(m, a, queue, s, sm_count);
     case kPoly2: return launch_pc<2, false>(m, a, queue, s, sm_count);
     case kPoly4: return launch_pc<4, false>(m, a, queue, s, sm_count);
     default: return launch_pc<6, false>(m, a, queue, s, sm_count);
@@ -827,6 +828,7 @@ int launch_serve_tick(const DevMedium& m, const TraceArgs& a, void* slots, int n
   if (nslots <= 0 || nslots % 128 != 0 || quantum <= 0) return GRIN_ERR_INVALID_ARG;
   if (m.kind == GRIN_MEDIUM_GRID) return tick_pc<0, true>(m, a, slots, nslots, counters, quantum, s);
   switch (m.pclass) {
+    case kSpherical: return tick_pc<1, false>(m, a, slots, nslots, counters, quantum, s);
     case kPoly2: return tick_pc<2, false>(m, a, slots, nslots, counters, quantum, s);
     case kPoly4: return tick_pc<4, false>(m, a, slots, nslots, counters, quantum, s);
     default: return tick_pc<6, false>(m, a, slots, nslots, counters, quantum, s);

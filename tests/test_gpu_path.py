@@ -6,8 +6,8 @@ bitwise the oracle's, since the plain FP64 tracer follows the oracle's
 operations in the same order.  The exit states must be bitwise those of
 grin_trace at GRIN_PREC_FP64.  Media: the freeform block (box), the
 Luneburg lens (sphere, n = sqrt(p)), a homogeneous box whose side walls
-reflect the rays (boundary TIR), a graded fibre (cylinder, internal TIR), a
-blob grid and its layered version."""
+reflect the rays (boundary TIR), a graded fibre (cylinder, internal TIR), the
+spherical freeform medium of Sec. V, a blob grid and its layered version."""
 import math
 
 import numpy as np
@@ -50,6 +50,7 @@ def _cases():
             ("box_tir", box, box_rays, 0.01, 40000),
             ("luneburg", lun.medium, lun_rays, lun.dopl, lun.max_steps),
             ("fiber", W.fiber_medium(length=20.0), _fiber_rays(5), 2e-3, 40000),
+            ("spherical", W.spherical_freeform_medium(), W.spherical_workload(5).rays, 1e-3, 20000),
             ("grid", blob.medium, blob.rays, 0.02, 5000),
             ("layered", lay.medium, lay.rays, 0.02, 5000)]
 

@@ -213,6 +213,32 @@ def test_corrector_lens_cylinder(ctx):
         assert ge["exit_id"][0] == 2 and ge["tir_boundary"][0] == 1
 
 
+def test_spherical_freeform_sphere(ctx):
+    """Sec. V spherical freeform medium (a0..a3 = 1.5, 1, -0.2, 0.3, unit
+    sphere): a bundle (FP64 and FP64 fast against the oracle, mixed against
+    FP64), the paper's example ray of Fig. 3(b), which stays trapped by
+    repeated total reflection at the sphere, and a 16-shell layered version."""
+    import dataclasses
+    wl = W.spherical_workload(2049)
+    g64 = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "fp64")
+    o = orc(wl.medium, wl.rays, wl.dopl, wl.max_steps)
+    check64(g64, o, wl.l_ref)
+    assert (g64["tir_boundary"] > 0).any() and (g64["tir_internal"] > 0).any()
+    gf = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "fp64-fast")
+    rep = compare(gf, o, wl.l_ref, flagged(o["margins"], TAU64))
+    assert rep["int_mismatch_unflagged"] == 0, rep
+    assert max(rep["pos"], rep["dir"], rep["opl"]) <= 1e-8, rep
+    g32 = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "mixed")
+    check32(g32, g64, wl.l_ref, flags32(o), 0.005)
+    r = W.spherical_example_ray()
+    ge = gpu_trace(ctx, wl.medium, r, 1e-3, 40000, "fp64")
+    check64(ge, orc(wl.medium, r, 1e-3, 40000), 1.0)
+    assert ge["exit_id"][0] == tracer.N.EXIT_MAXSTEPS and ge["tir_boundary"][0] > 10
+    lay = dataclasses.replace(wl.medium, n_levels=16, level_lo=1.0, level_hi=2.0)
+    gl = gpu_trace(ctx, lay, wl.rays, wl.dopl, wl.max_steps, "fp64")
+    check64(gl, orc(lay, wl.rays, wl.dopl, wl.max_steps), wl.l_ref)
+
+
 # ------------------------------------------------------ gridded and layered
 
 
