@@ -126,6 +126,24 @@ static void sph_eval(const orc_medium* m, const double* P, double* p, double* gp
   gp[2] = gz / m->scale[2];
 }
 
+/* N2P-GRIN cylindrical lens of Sec. VI: n = [1 + u^beta]^gamma with
+ * u = (R^2 - (rho/2)^2) / F^2, rho the distance from the lens axis (the line
+ * through off[0], off[1] parallel to z); by the chain rule
+ * dn/dx = gamma (1 + u^beta)^(gamma - 1) beta u^(beta - 1) du/dx with
+ * du/dx = -x / (2 F^2), likewise in y, and dn/dz = 0. */
+static void n2p_eval(const orc_medium* m, const double* P, double* p, double* gp) {
+  double R = m->coeffs[0], F = m->coeffs[1], be = m->coeffs[2], ga = m->coeffs[3];
+  double x = P[0] - m->off[0];
+  double y = P[1] - m->off[1];
+  double u = (R * R - (x * x + y * y) / 4.0) / (F * F);
+  double w = 1.0 + pow(u, be);
+  *p = pow(w, ga);
+  double k = ga * pow(w, ga - 1.0) * be * pow(u, be - 1.0) * (-1.0 / (2.0 * F * F));
+  gp[0] = k * x;
+  gp[1] = k * y;
+  gp[2] = 0.0;
+}
+
 /* Catmull-Rom cubic convolution weights (Keys 1981, a = -1/2) for the taps at
  * offsets -1, 0, 1, 2 around the cell containing fraction t, and their
  * derivatives with respect to t. */
@@ -187,6 +205,8 @@ static void field_eval(const orc_medium* m, const double* P, double* f, double* 
   double p, gp[3];
   if (m->kind == 2)
     sph_eval(m, P, &p, gp);
+  else if (m->kind == 3)
+    n2p_eval(m, P, &p, gp);
   else
     poly_eval(m, P, &p, gp);
   if (m->form == 0) {

@@ -26,12 +26,14 @@ extern "C" {
 #endif
 
 typedef struct {
-  int32_t kind;          /* 0 polynomial, 1 grid, 2 spherical freeform (Sec. V) */
+  int32_t kind;          /* 0 polynomial, 1 grid, 2 spherical freeform (Sec. V),
+                            3 N2P cylinder lens (Sec. VI) */
   int32_t form;          /* 0 n=p, 1 n=sqrt(p), 2 n=form_c/p */
   double form_c;
   int32_t degree;        /* polynomial total degree */
   const double* coeffs;  /* graded-lex monomials of the normalised coordinates;
-                            kind 2: a0, a1, a2, a3 */
+                            kind 2: a0, a1, a2, a3; kind 3: R, F, beta, gamma
+                            (axis through off[0], off[1], parallel to z) */
   double off[3];         /* x' = (x - off) / scale */
   double scale[3];
   int32_t nx, ny, nz;    /* grid sizes, x fastest */

@@ -25,7 +25,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 BASE_SEED = 20260622
 
 # medium kinds, polynomial forms and boundary kinds (shared vocabulary only)
-KIND_POLY, KIND_GRID, KIND_SPHERICAL = 0, 1, 2
+KIND_POLY, KIND_GRID, KIND_SPHERICAL, KIND_N2P = 0, 1, 2, 3
 FORM_LINEAR, FORM_SQRT, FORM_RECIP = 0, 1, 2
 BOUNDARY_BOX, BOUNDARY_SPHERE, BOUNDARY_CYLINDER = 0, 1, 2
 
@@ -95,7 +95,9 @@ class Medium:
     x' = (x - off) / scale, with n = p, sqrt(p) or form_c / p) or KIND_GRID
     (float32 samples grid[k, j, i] at origin + (i, j, k) * spacing, read by
     Catmull-Rom tricubic interpolation) or KIND_SPHERICAL (the spherical
-    freeform field of Sec. V, coeffs = a0..a3, normalised by `scale`).
+    freeform field of Sec. V, coeffs = a0..a3, normalised by `scale`) or
+    KIND_N2P (the N2P cylinder lens of Sec. VI, coeffs = R, F, beta, gamma,
+    axis through off[0], off[1]).
     n_levels > 0 quantises the field into
     that many isoindicial shells between level_lo and level_hi.  The boundary
     is a box (lo[3], hi[3]), sphere (c[3], R) or z-cylinder (cx, cy, R, z0,
@@ -268,6 +270,15 @@ def spherical_freeform_medium(a=(1.5, 1.0, -0.2, 0.3), radius: float = 1.0, cent
                   coeffs=np.asarray(a, dtype=np.float64), off=tuple(centre),
                   scale=(radius, radius, radius), bkind=bk, bparams=bp, n_ext=n_ext,
                   name="spherical_freeform")
+
+
+def n2p_lens_medium(beta: float, gamma: float, L: float = 0.3, R: float = 1.0, F: float = 2.0) -> Medium:
+    """Cylindrical N2P-GRIN lens (Sec. VI): n = [1 + ((R^2 - (rho/2)^2)/F^2)^beta]^gamma
+    for z in [-L, 0], rho <= R, in air; axis = z."""
+    bk, bp = cylinder(0.0, 0.0, R, -L, 0.0)
+    return Medium(kind=KIND_N2P, form=FORM_LINEAR, degree=0,
+                  coeffs=np.array([R, F, beta, gamma], dtype=np.float64), bkind=bk, bparams=bp,
+                  n_ext=1.0, name="n2p_lens")
 
 
 def homogeneous_box(n: float, lo=(-1.0, -1.0, 0.0), hi=(1.0, 1.0, 1.0), n_ext: float = 1.0) -> Medium:
