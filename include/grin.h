@@ -66,7 +66,7 @@ enum {
   GRIN_EXIT_INVALID = -4        /* non-finite or zero direction, n <= 0 */
 };
 
-enum { GRIN_MEDIUM_POLY = 0, GRIN_MEDIUM_GRID = 1, GRIN_MEDIUM_SPHERICAL = 2 };
+enum { GRIN_MEDIUM_POLY = 0, GRIN_MEDIUM_GRID = 1, GRIN_MEDIUM_SPHERICAL = 2, GRIN_MEDIUM_N2P = 3 };
 enum { GRIN_FORM_LINEAR = 0, GRIN_FORM_SQRT = 1, GRIN_FORM_RECIP = 2 };
 enum { GRIN_BOUNDARY_BOX = 0, GRIN_BOUNDARY_SPHERE = 1, GRIN_BOUNDARY_CYLINDER = 2 };
 enum { GRIN_F32 = 0, GRIN_F64 = 1 };
@@ -95,6 +95,13 @@ enum { GRIN_PREC_FP64 = 0, GRIN_PREC_FP32_MIXED = 1, GRIN_PREC_FP64_FAST = 2 };
  *     coordinates x' (r = |x'|, theta from +z', phi the azimuth), a0..a3 the
  *     4 host doubles in `coeffs` (degree is ignored); `form` maps p to n as
  *     for polynomials.  At r = 0 the polar angle is taken as 0.
+ *     grin_trace_adjoint returns GRIN_ERR_NOT_IMPLEMENTED for it;
+ *   - GRIN_MEDIUM_N2P: the N2P-GRIN cylinder lens of Sec. VI,
+ *     n = [1 + ((R^2 - (rho/2)^2) / F^2)^beta]^gamma with rho the distance
+ *     from the axis through (norm_offset[0], norm_offset[1]) parallel to z;
+ *     `coeffs` = R > 0, F > 0, beta, gamma (4 host doubles); form must be
+ *     GRIN_FORM_LINEAR; degree and norm_scale are ignored.  The z extent is
+ *     the boundary's (a cylinder, z0 = -L, z1 = 0, in the paper).
  *     grin_trace_adjoint returns GRIN_ERR_NOT_IMPLEMENTED for it.
  * n_levels > 0 turns the field into that many isoindicial shells (the
  * discretised media of Sec. I and the abstract): level

@@ -95,8 +95,7 @@ int grin_medium_create(grin_ctx ctx, const grin_medium_desc* d, grin_medium* out
   m.n_ext = d->n_ext;
   m.form_c = d->form_c;
   if (!finite_pos(d->n_ext)) return GRIN_ERR_INVALID_ARG;
-  if (d->kind != GRIN_MEDIUM_POLY && d->kind != GRIN_MEDIUM_GRID && d->kind != GRIN_MEDIUM_SPHERICAL)
-    return GRIN_ERR_INVALID_ARG;
+  if (d->kind < GRIN_MEDIUM_POLY || d->kind > GRIN_MEDIUM_N2P) return GRIN_ERR_INVALID_ARG;
   if (d->n_levels < 0 || d->n_levels > GRIN_MAX_LEVELS) return GRIN_ERR_INVALID_ARG;
   if (d->n_levels > 0 && !(std::isfinite(d->level_lo) && std::isfinite(d->level_hi) &&
                            d->level_hi > d->level_lo))
@@ -120,7 +119,30 @@ int grin_medium_create(grin_ctx ctx, const grin_medium_desc* d, grin_medium* out
   std::memcpy(m.b, b, sizeof(m.b));
 
   std::vector<float> samples;
-  if (d->kind == GRIN_MEDIUM_POLY || d->kind == GRIN_MEDIUM_SPHERICAL) {
+  if (d->kind == GRIN_MEDIUM_N2P) {
+    // R, F, beta, gamma; the axis through norm_offset[0..1]; no scaling
+    if (!d->coeffs || d->form != GRIN_FORM_LINEAR) return GRIN_ERR_INVALID_ARG;
+    const double* c = d->coeffs;
+    if (!(finite_pos(c[0]) && finite_pos(c[1]) && std::isfinite(c[2]) && std::isfinite(c[3])))
+      return GRIN_ERR_INVALID_ARG;
+    if (!std::isfinite(d->norm_offset[0]) || !std::isfinite(d->norm_offset[1]))
+      return GRIN_ERR_INVALID_ARG;
+    m.pclass = grin::kN2P;
+    for (int k = 0; k < 3; ++k) {
+      m.off[k] = k < 2 ? d->norm_offset[k] : 0.0;
+      m.scale[k] = m.inv_scale[k] = 1.0;
+    }
+    for (int k = 0; k < 4; ++k) m.cglex[k] = m.c64[k] = c[k];
+    m.c64[4] = 0.0;
+    // base = n on the axis; the FP32 copy returns n - base (shift in c32[4])
+    const double n_axis = std::pow(1.0 + std::pow(c[0] * c[0] / (c[1] * c[1]), c[2]), c[3]);
+    float base_f = (float)n_axis;
+    if (!(std::isfinite(base_f) && base_f > 0.0f)) base_f = 1.0f;
+    m.base_f = base_f;
+    m.base = (double)base_f;
+    for (int k = 0; k < 4; ++k) m.c32[k] = (float)c[k];
+    m.c32[4] = base_f;
+  } else if (d->kind == GRIN_MEDIUM_POLY || d->kind == GRIN_MEDIUM_SPHERICAL) {
     const bool sph = d->kind == GRIN_MEDIUM_SPHERICAL;
     if (!d->coeffs || (!sph && (d->degree < 0 || d->degree > GRIN_MAX_DEGREE)))
       return GRIN_ERR_INVALID_ARG;

@@ -106,12 +106,33 @@ __device__ __forceinline__ void sph_vg(const T* a, T x, T y, T z, T& p, T& px, T
   pz = fmadd(a[1], T(0.6) * z, a[2] * fmadd(zq, tz, q));
 }
 
-// The analytic field of class PC: a polynomial, or the spherical freeform
-// field (PC == kSpherical, coefficients a0..a3).
+// N2P-GRIN cylinder lens of Sec. VI at (x, y) from its axis:
+// n = [1 + u^beta]^gamma, u = (R^2 - (rho/2)^2) / F^2, c = (R, F, beta,
+// gamma, shift); returns p = n - shift.  Two powers: w^(gamma - 1) = n / w and
+// u^(beta - 1) = u^beta / u in dn/dx = gamma w^(gamma-1) beta u^(beta-1) (-x / (2 F^2)).
+template <typename T>
+__device__ __forceinline__ void n2p_vg(const T* c, T x, T y, T& p, T& px, T& py, T& pz) {
+  const T R = c[0], F = c[1], be = c[2], ga = c[3];
+  const T inv_f2 = T(1) / (F * F);
+  const T u = fmadd(T(-0.25), fmadd(x, x, y * y), R * R) * inv_f2;
+  const T ub = pow(u, be);
+  const T w = T(1) + ub;
+  const T n = pow(w, ga);
+  const T k = ga * (n / w) * be * (ub / u) * (T(-0.5) * inv_f2);
+  p = n - c[4];
+  px = k * x;
+  py = k * y;
+  pz = T(0);
+}
+
+// The analytic field of class PC: a polynomial, the spherical freeform field
+// (PC == kSpherical, coefficients a0..a3) or the N2P lens (PC == kN2P).
 template <int PC, typename T>
 __device__ __forceinline__ void field_vg(const T* c, T x, T y, T z, T& p, T& px, T& py, T& pz) {
   if constexpr (PC == kSpherical)
     sph_vg<T>(c, x, y, z, p, px, py, pz);
+  else if constexpr (PC == kN2P)
+    n2p_vg<T>(c, x, y, p, px, py, pz);
   else
     poly_vg<PC, T>(c, x, y, z, p, px, py, pz);
 }

@@ -18,8 +18,9 @@ constexpr int kMaxTerms = 84;
 // Polynomial evaluators are instantiated for these total degrees; a medium
 // of lower degree is zero-padded to the next class.
 // Coefficient layout of an analytic medium, also the template parameter PC of
-// the kernels: polynomial degree classes, or the spherical freeform field.
-enum PolyClass : int32_t { kSpherical = 1, kPoly2 = 2, kPoly4 = 4, kPoly6 = 6 };
+// the kernels: polynomial degree classes, the spherical freeform field, or
+// the N2P cylinder lens.
+enum PolyClass : int32_t { kSpherical = 1, kPoly2 = 2, kN2P = 3, kPoly4 = 4, kPoly6 = 6 };
 
 // Everything a kernel needs to evaluate n, grad n and the boundary, passed by
 // value as a kernel parameter (it lives in the constant bank, so every lane

@@ -144,6 +144,23 @@ __device__ __forceinline__ void sph(const DevMedium& m, const double* P, double&
   gp[2] = gz / m.scale[2];
 }
 
+// N2P-GRIN cylinder lens of Sec. VI: n = [1 + u^beta]^gamma with
+// u = (R^2 - (rho/2)^2) / F^2, rho measured from the axis through (off[0],
+// off[1]); dn/dx = gamma (1 + u^beta)^(gamma - 1) beta u^(beta - 1) (-x / (2 F^2)),
+// likewise in y, and dn/dz = 0.
+__device__ __forceinline__ void n2p(const DevMedium& m, const double* P, double& p, double* gp) {
+  double R = m.cglex[0], F = m.cglex[1], be = m.cglex[2], ga = m.cglex[3];
+  double x = P[0] - m.off[0];
+  double y = P[1] - m.off[1];
+  double u = (R * R - (x * x + y * y) / 4.0) / (F * F);
+  double w = 1.0 + pow(u, be);
+  p = pow(w, ga);
+  double k = ga * pow(w, ga - 1.0) * be * pow(u, be - 1.0) * (-1.0 / (2.0 * F * F));
+  gp[0] = k * x;
+  gp[1] = k * y;
+  gp[2] = 0.0;
+}
+
 // n (after layering) and the gradient of the smooth field; lvl = level or -1.
 template <int PC, bool GRID, bool LAYERED>
 __device__ __forceinline__ void sample(const DevMedium& m, const double* P, double& n, double* g,
@@ -155,6 +172,8 @@ __device__ __forceinline__ void sample(const DevMedium& m, const double* P, doub
     double p, gp[3];
     if constexpr (PC == kSpherical)
       sph(m, P, p, gp);
+    else if constexpr (PC == kN2P)
+      n2p(m, P, p, gp);
     else
       poly<PC>(m, P, p, gp);
     if (m.form == GRIN_FORM_LINEAR) {

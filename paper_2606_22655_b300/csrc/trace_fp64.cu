@@ -197,6 +197,8 @@ int launch_fp64(const DevMedium& m, const TraceArgs& a, cudaStream_t s, int) {
   switch (m.pclass) {
     case kSpherical:
       return lay ? launch_t<1, false, true>(m, a, s) : launch_t<1, false, false>(m, a, s);
+    case kN2P:
+      return lay ? launch_t<3, false, true>(m, a, s) : launch_t<3, false, false>(m, a, s);
     case kPoly2:
       return lay ? launch_t<2, false, true>(m, a, s) : launch_t<2, false, false>(m, a, s);
     case kPoly4:
@@ -217,6 +219,9 @@ int launch_fp64_path(const DevMedium& m, const TraceArgs& a, double* path, int64
     case kSpherical:
       return lay ? launch_path_t<1, false, true>(m, a, path, cap, plen, s)
                  : launch_path_t<1, false, false>(m, a, path, cap, plen, s);
+    case kN2P:
+      return lay ? launch_path_t<3, false, true>(m, a, path, cap, plen, s)
+                 : launch_path_t<3, false, false>(m, a, path, cap, plen, s);
     case kPoly2:
       return lay ? launch_path_t<2, false, true>(m, a, path, cap, plen, s)
                  : launch_path_t<2, false, false>(m, a, path, cap, plen, s);

@@ -185,6 +185,8 @@ int launch_fp64_fast(const DevMedium& m, const TraceArgs& a, cudaStream_t s, int
   switch (m.pclass) {
     case kSpherical:
       return lay ? launch_t<1, false, true>(m, a, s) : launch_t<1, false, false>(m, a, s);
+    case kN2P:
+      return lay ? launch_t<3, false, true>(m, a, s) : launch_t<3, false, false>(m, a, s);
     case kPoly2:
       return lay ? launch_t<2, false, true>(m, a, s) : launch_t<2, false, false>(m, a, s);
     case kPoly4:

@@ -730,6 +730,7 @@ int launch_mixed(const DevMedium& m, const TraceArgs& a, unsigned long long* que
   if (m.kind == GRIN_MEDIUM_GRID) return launch_pc<0, true>(m, a, queue, s, sm_count);
   switch (m.pclass) {
     case kSpherical: return launch_pc<1, false>(m, a, queue, s, sm_count);
+    case kN2P: return launch_pc<3, false>(m, a, queue, s, sm_count);
     case kPoly2: return launch_pc<2, false>(m, a, queue, s, sm_count);
     case kPoly4: return launch_pc<4, false>(m, a, queue, s, sm_count);
     default: return launch_pc<6, false>(m, a, queue, s, sm_count);
@@ -829,6 +830,7 @@ int launch_serve_tick(const DevMedium& m, const TraceArgs& a, void* slots, int n
   if (m.kind == GRIN_MEDIUM_GRID) return tick_pc<0, true>(m, a, slots, nslots, counters, quantum, s);
   switch (m.pclass) {
     case kSpherical: return tick_pc<1, false>(m, a, slots, nslots, counters, quantum, s);
+    case kN2P: return tick_pc<3, false>(m, a, slots, nslots, counters, quantum, s);
     case kPoly2: return tick_pc<2, false>(m, a, slots, nslots, counters, quantum, s);
     case kPoly4: return tick_pc<4, false>(m, a, slots, nslots, counters, quantum, s);
     default: return tick_pc<6, false>(m, a, slots, nslots, counters, quantum, s);

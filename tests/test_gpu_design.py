@@ -1,0 +1,66 @@
+"""The N2P-GRIN cylinder lens of Sec. VI on the GPU, and its design by
+successive refinement of (beta, gamma) on the continuous-batching server.
+
+Parity: a fan of parallel rays through the lens, FP64 against the oracle
+(the lens index uses pow, which the CUDA and C libraries round differently
+in the last place, so the plain kernel meets the oracle to 1e-12 rather than
+bitwise), FP64 fast against the oracle, mixed FP32 against FP64.
+Design: the refinement reaches the quasi-stigmatic focus of the paper
+(RMSE_LSA <= 5e-3 R at L = 0.3 R, F = 2 R), and the oracle confirms the RMSE
+at the parameters found."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2606_22655_b300 import n2p_design
+from paper_2606_22655_b300 import tracer
+from paper_2606_22655_b300 import workloads as W
+from tests.compare import compare, flagged
+from tests.test_gpu_trace import TAU64, check32, check64, flags32, gpu_trace, orc
+from tests.test_oracle_pins import n2p_rmse_lsa
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = tracer.Context(0)
+    yield c
+    c.close()
+
+
+def _bundle(n, L):
+    y = W.uniform(W.BASE_SEED + 9, 1, n, 0.0, 0.99)
+    x = W.uniform(W.BASE_SEED + 9, 2, n, -0.1, 0.1)
+    o = np.stack([x, y, np.full(n, -L - 0.5)], 1)
+    return W.Rays(o, np.tile([0.0, 0.0, 1.0], (n, 1)))
+
+
+def test_n2p_lens_parity(ctx):
+    L = 0.3
+    m = W.n2p_lens_medium(0.772, 4.469, L)
+    rays = _bundle(1025, L)
+    dopl, ms = 1e-4, 400000
+    g64 = gpu_trace(ctx, m, rays, dopl, ms, "fp64")
+    o = orc(m, rays, dopl, ms)
+    check64(g64, o, 1.0)
+    assert (g64["exit_id"] == n2p_design.EXIT_FACE).all()
+    gf = gpu_trace(ctx, m, rays, dopl, ms, "fp64-fast")
+    rep = compare(gf, o, 1.0, flagged(o["margins"], TAU64))
+    assert rep["int_mismatch_unflagged"] == 0, rep
+    assert max(rep["pos"], rep["dir"], rep["opl"]) <= 1e-8, rep
+    g32 = gpu_trace(ctx, m, rays, dopl, ms, "mixed")
+    check32(g32, g64, 1.0, flags32(o), 0.005)
+
+
+def test_n2p_design_by_refinement_on_the_server(ctx):
+    res = n2p_design.design(ctx, L=0.3, rounds=5, grid=9, beta=(0.5, 1.2), gamma=(3.0, 6.0))
+    rm = [h["rmse"] for h in res["rounds"]]
+    assert all(b <= a for a, b in zip(rm, rm[1:])), rm  # refinement never loses the best
+    assert res["rmse_lsa"] <= 5e-3, res
+    e_orc, r = n2p_rmse_lsa(res["beta"], res["gamma"], 0.3)
+    assert (r["exit_id"] == n2p_design.EXIT_FACE).all()
+    assert e_orc <= 5e-3
+    assert abs(e_orc - res["rmse_lsa"]) <= 2e-4, (e_orc, res["rmse_lsa"])
