@@ -270,6 +270,18 @@ def adjoint_timing(ctx, dev):
             "precision": "fp64", "gradient_params": int(wl.medium.grid.size)}
 
 
+def design_sweep(ctx):
+    """The N2P lens design of Sec. VI (L = 0.3 R, F = 2 R): successive
+    refinement of (beta, gamma), 8 rounds of 81 concurrent 10-ray jobs on the
+    trace server."""
+    from paper_2606_22655_b300 import n2p_design
+    res = n2p_design.design(ctx, L=0.3, rounds=8, grid=9, beta=(0.2, 4.0), gamma=(1.0, 30.0))
+    return {"workload": "N2P lens L=0.3R F=2R, 10-ray fan, dL0 1e-4 R, 8 rounds x 81 jobs",
+            "wall_s": res["wall_s"], "jobs": res["jobs"], "jobs_per_s": res["jobs"] / res["wall_s"],
+            "round_wall_s": [h["wall_s"] for h in res["rounds"]],
+            "beta": res["beta"], "gamma": res["gamma"], "rmse_lsa_over_R": res["rmse_lsa"]}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -420,6 +432,9 @@ def run_ours(args):
     h2d = 6 * 4 * hrays.count
     d2h = (7 * 8 + 4 * 4) * hrays.count
 
+    design = None
+    if ws == 1 and not args.no_serve:
+        design = design_sweep(ctx)
     adjoint = None
     if ws == 1 and not args.no_serve:
         adjoint = adjoint_timing(ctx, dev)
@@ -466,6 +481,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "serve": serve,
         "adjoint": adjoint,
+        "design_sweep": design,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
