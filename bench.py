@@ -275,7 +275,7 @@ def design_sweep(ctx):
     refinement of (beta, gamma), 8 rounds of 81 concurrent 10-ray jobs on the
     trace server."""
     from paper_2606_22655_b300 import n2p_design
-    res = n2p_design.design(ctx, L=0.3, rounds=8, grid=9, beta=(0.2, 4.0), gamma=(1.0, 30.0))
+    res = n2p_design.design(ctx, L=0.3, rounds=8, grid=9, beta=(0.5, 1.2), gamma=(3.0, 6.0))
     return {"workload": "N2P lens L=0.3R F=2R, 10-ray fan, dL0 1e-4 R, 8 rounds x 81 jobs",
             "wall_s": res["wall_s"], "jobs": res["jobs"], "jobs_per_s": res["jobs"] / res["wall_s"],
             "round_wall_s": [h["wall_s"] for h in res["rounds"]],
