@@ -64,6 +64,24 @@ int grin_ctx_create(int device, grin_ctx* out) {
   return GRIN_OK;
 }
 
+// The context's stream-ordered pool, created on first use with no release
+// threshold, so blocks freed by one call are reused by the next.
+static bool order_pool(grin_ctx ctx) {
+  if (ctx->pool) return true;
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = ctx->device;
+  if (cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->pool = nullptr;
+    return false;
+  }
+  uint64_t keep = UINT64_MAX;
+  cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  return true;
+}
+
 int grin_ctx_destroy(grin_ctx ctx) {
   if (!ctx) return GRIN_ERR_INVALID_ARG;
   if (ctx->children.load() != 0) return GRIN_ERR_BUSY;
@@ -71,6 +89,7 @@ int grin_ctx_destroy(grin_ctx ctx) {
   cudaDeviceSynchronize();
   cudaFree(ctx->queues);
   if (ctx->stage) cudaFree(ctx->stage);
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   delete ctx;
   return GRIN_OK;
 }
@@ -385,7 +404,25 @@ int grin_trace(grin_ctx ctx, grin_medium medium, const grin_rays* rays, const gr
   } else {
     unsigned long long* q = ctx->queues + ctx->next_queue;
     ctx->next_queue = (ctx->next_queue + 1) % kQueueSlots;
+    // large batches: claim rays in the order of where they enter the medium
+    // (ray_order.cu), from scratch allocated and freed on this call's stream
+    void* order = nullptr;
+    int lo = 0;
+    if (a.count >= grin::kOrderMinRays && a.count < (int64_t(1) << 31) && order_pool(ctx) &&
+        cudaMallocFromPoolAsync(&order, grin::order_scratch_bytes(a.count), ctx->pool, s) ==
+            cudaSuccess) {
+      lo = grin::launch_order(medium->dm, a, order, ctx->sm_count, s, &a.perm);
+      if (lo < 0) {
+        a.perm = nullptr;
+        lo = 0;
+      }
+    } else {
+      cudaGetLastError();
+      order = nullptr;
+    }
     rc = grin::launch_mixed(medium->dm, a, q, s, ctx->sm_count);
+    if (order) cudaFreeAsync(order, s);
+    if (rc >= 0) rc += lo;
   }
   if (rc < 0) return rc;
   ctx->last_launches = rc;

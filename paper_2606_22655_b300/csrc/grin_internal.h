@@ -59,6 +59,9 @@ struct TraceArgs {
   int32_t *exit_id, *steps, *tir_i, *tir_b;
   double dopl;
   int32_t max_steps;
+  // mixed tracer: claim order (a permutation of 0..count-1), or nullptr for
+  // index order
+  const uint32_t* perm = nullptr;
 };
 
 // Number of kernel launches made; negative grin_status on failure.
@@ -77,6 +80,15 @@ int launch_serve_tick(const DevMedium& m, const TraceArgs& a, void* slots, int n
                       unsigned long long* counters, int quantum, cudaStream_t s);
 
 constexpr int kQueueSlots = 4096;
+
+// Claim order for the mixed tracer (ray_order.cu): rays bucketed by the cell
+// of the medium's bounding box where they enter it.  Used from this many rays.
+constexpr int64_t kOrderMinRays = 65536;
+size_t order_scratch_bytes(int64_t n);
+// Three launches into `scratch` (order_scratch_bytes(count) bytes, 256-byte
+// aligned); *perm_out points into it.  Returns the launch count or a status.
+int launch_order(const DevMedium& m, const TraceArgs& a, void* scratch, int sm_count,
+                 cudaStream_t s, const uint32_t** perm_out);
 
 // Launches kern<<<grid, block, 0, s>>>(args...) and returns 1, or
 // GRIN_ERR_CUDA if this launch failed.  cudaLaunchKernelEx reports the
@@ -123,6 +135,9 @@ struct grin_ctx_s {
   // device staging for grin_trace_host (grown on demand)
   void* stage = nullptr;
   size_t stage_bytes = 0;
+  // stream-ordered pool for the per-call claim-order scratch of the mixed
+  // tracer (created on first use; keeps freed blocks for reuse)
+  cudaMemPool_t pool = nullptr;
 };
 
 struct grin_medium_s {
