@@ -205,10 +205,11 @@ int grin_medium_device_bytes(grin_medium medium, size_t* bytes);
  * on `cuda_stream`.  count == 0 is a no-op.  Errors: GRIN_ERR_INVALID_ARG
  * for NULL pointers, count < 0, dopl <= 0 or non-finite, max_steps < 0, bad
  * precision or dtype; GRIN_ERR_CUDA if the launch fails.
- * GRIN_PREC_FP32_MIXED with at least 65,536 rays first buckets the rays by
- * the cell of the medium's bounding box where they enter it (three small
- * kernels) and the pool claims them in that order, so neighbouring rays share
- * warps; each ray's result is bitwise the same in any order.  Its scratch
+ * GRIN_PREC_FP32_MIXED on a GRIN_MEDIUM_GRID medium with at least 65,536
+ * rays first buckets the rays by the cell of the medium's bounding box where
+ * they enter it (three small kernels) and the pool claims them in that order,
+ * so neighbouring rays share warps and their interpolation stencils; each
+ * ray's result is bitwise the same in any order.  Its scratch
  * (6 bytes a ray) comes from a stream-ordered memory pool the context owns,
  * allocated and freed on `cuda_stream`; if that allocation fails the rays
  * are claimed in index order. */

@@ -404,11 +404,14 @@ int grin_trace(grin_ctx ctx, grin_medium medium, const grin_rays* rays, const gr
   } else {
     unsigned long long* q = ctx->queues + ctx->next_queue;
     ctx->next_queue = (ctx->next_queue + 1) % kQueueSlots;
-    // large batches: claim rays in the order of where they enter the medium
-    // (ray_order.cu), from scratch allocated and freed on this call's stream
+    // large batches in a gridded medium: claim rays in the order of where
+    // they enter it (ray_order.cu), so a warp's stencils overlap, from scratch
+    // allocated and freed on this call's stream.  Analytic media are ALU-bound
+    // and keep index order, whose ray reads and result writes coalesce.
     void* order = nullptr;
     int lo = 0;
-    if (a.count >= grin::kOrderMinRays && a.count < (int64_t(1) << 31) && order_pool(ctx) &&
+    if (medium->dm.kind == GRIN_MEDIUM_GRID && a.count >= grin::kOrderMinRays &&
+        a.count < (int64_t(1) << 31) && order_pool(ctx) &&
         cudaMallocFromPoolAsync(&order, grin::order_scratch_bytes(a.count), ctx->pool, s) ==
             cudaSuccess) {
       lo = grin::launch_order(medium->dm, a, order, ctx->sm_count, s, &a.perm);

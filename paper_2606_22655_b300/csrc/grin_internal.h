@@ -81,8 +81,9 @@ int launch_serve_tick(const DevMedium& m, const TraceArgs& a, void* slots, int n
 
 constexpr int kQueueSlots = 4096;
 
-// Claim order for the mixed tracer (ray_order.cu): rays bucketed by the cell
-// of the medium's bounding box where they enter it.  Used from this many rays.
+// Claim order for the mixed tracer on gridded media (ray_order.cu): rays
+// bucketed by the cell of the medium's bounding box where they enter it.
+// Used from this many rays.
 constexpr int64_t kOrderMinRays = 65536;
 size_t order_scratch_bytes(int64_t n);
 // Three launches into `scratch` (order_scratch_bytes(count) bytes, 256-byte
