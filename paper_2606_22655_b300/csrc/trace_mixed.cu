@@ -20,11 +20,14 @@
 //     nu = n - base;
 //   - the refraction uses gamma = sgn(c) (1 - mu^2) / (sqrt(D) + mu |c|), an
 //     algebraically equal form of Eq. 9 without the cancellation of
-//     -mu c + sgn(c) sqrt(D); D = (1 - mu^2) + mu^2 c^2; refraction and
-//     reflection are selected without a branch;
+//     -mu c + sgn(c) sqrt(D); D = (1 - mu^2) + mu^2 c^2; steps with D at or
+//     below the near-critical band, total internal reflection included (a
+//     few per ray), take the out-of-line step, so the common step refracts
+//     without a branch;
 //   - when |D| is within a few FP32 roundings of zero (near critical or
 //     grazing incidence) the discriminant and gamma are recomputed in FP64;
-//   - the optical path is exact: dL0 times the count of full steps, plus the
+//   - the optical path is exact: dL0 times the count of full steps (all steps
+//     but those cut at the surface, which are the only ones counted apart), plus the
 //     FP64 exterior segment and the fractions of steps cut at the surface;
 //   - everything at the enclosing surface (the entry intersection and
 //     refraction, the exit root, boundary refraction or TIR) runs in FP64.
@@ -142,7 +145,7 @@ struct RayF {
   float gp[3];                      // grad n at the previous point
   float nu_prev, inv_prev, h;       // n_{i-1} - base, 1 / n_{i-1}, step length
   float frac;                       // sum of the fractions of steps cut at the surface
-  int lvl_prev, steps, full, tir_i, tir_b;
+  int lvl_prev, steps, cut, tir_i, tir_b;  // cut: steps ended early at the surface
   double opl_x;  // exterior segment, in optical length
 };
 
@@ -187,7 +190,8 @@ __device__ __forceinline__ void add_ff(float& hi, float& lo, float x) {
 
 __device__ __forceinline__ void finish(const TraceArgs& a, int64_t r, const RayF& s, V3 p, V3 d,
                                        int exit_id) {
-  double opl = s.opl_x + a.dopl * ((double)s.full + (double)s.frac);
+  // every step but the cut ones adds exactly dL0 (Eq. 3)
+  double opl = s.opl_x + a.dopl * ((double)(s.steps - s.cut) + (double)s.frac);
   store_ray(a, r, p, d, opl, exit_id, s.steps, s.tir_i, s.tir_b);
 }
 
@@ -323,6 +327,7 @@ __device__ __forceinline__ int surface_event_box32(const DevMedium& m, const Tra
   best = fmaxf(best, 0.0f);
   s.frac += best;
   ++s.steps;
+  ++s.cut;
   const int axis = bf >> 1, hi = bf & 1;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -377,7 +382,7 @@ template <class C>
 __device__ bool init_ray(const DevMedium& m, const TraceArgs& a, int64_t r, RayF& s) {
   V3 p = mk(ld(a.ox, r, a.dtype), ld(a.oy, r, a.dtype), ld(a.oz, r, a.dtype));
   V3 d = mk(ld(a.dx, r, a.dtype), ld(a.dy, r, a.dtype), ld(a.dz, r, a.dtype));
-  s.steps = s.full = s.tir_i = s.tir_b = 0;
+  s.steps = s.cut = s.tir_i = s.tir_b = 0;
   s.opl_x = 0.0;
   s.frac = 0.0f;
   if (C::bk(m) == GRIN_BOUNDARY_BOX) return init_ray_box32<C>(m, a, r, s, p, d);
@@ -437,6 +442,7 @@ __device__ __forceinline__ int surface_event(const DevMedium& m, const TraceArgs
   exit64(m, p, q, t, pb, nb, face);
   s.frac += (float)t;
   ++s.steps;
+  ++s.cut;
   double n_prev = (double)m.base_f + (double)s.nu_prev;
   if (refract64(d, nb, n_prev / m.n_ext)) {
     ++s.tir_b;
@@ -500,7 +506,6 @@ __device__ __noinline__ bool step_slow(const DevMedium& m, const TraceArgs& a, i
     s.ph[k] = qh[k];
     s.pl[k] = ql[k];
   }
-  ++s.full;
   ++s.steps;
   float nu_i, g[3];
   int lvl_i;
@@ -577,8 +582,9 @@ __device__ __noinline__ bool step_slow(const DevMedium& m, const TraceArgs& a, i
   return true;
 }
 
-// The common step: the end point is inside, n is usable, and N.I is nonzero
-// and not near critical (or, in a layered medium, the level did not change).
+// The common step: the end point is inside, n is usable, N.I is nonzero and
+// D is above the near-critical band, so the step refracts (or, in a layered
+// medium, the level did not change and it goes straight on).
 // Everything is computed without a branch and one flag routes the rare cases
 // (surface crossing, invalid n, zero or undefined gradient, tangency,
 // near-critical D, the step limit) to step_slow, which redoes the step from
@@ -614,15 +620,14 @@ __device__ __forceinline__ bool step_ray(const DevMedium& m, const TraceArgs& a,
   const float omm = om * (2.0f - om);  // 1 - mu^2
   const float mc = mu * c;
   const float D = fmaf(mc, mc, omm);
-  const bool tir = D <= 0.0f;
-  const float gamma = (c > 0.0f ? omm : -omm) / (sqrtf(fmaxf(D, 0.0f)) + fabsf(mc));
+  const float gamma = (c > 0.0f ? omm : -omm) / (sqrtf(D) + fabsf(mc));
   // A zero, infinite or undefined gradient, or an undefined index
   // difference, makes D a NaN (rsqrt(0) = inf and 0 * inf, or inf - inf),
   // which fails the comparison with the near-critical band; a gradient that
   // overflows while its components stay finite gives N = 0 and c == 0.
   const bool special =
       !in || !(n_i > 0.0f && n_i < INFINITY) || s.steps + 1 >= a.max_steps ||
-      (!homog && (c == 0.0f || !(fabsf(D) > kCritBand * (fabsf(omm) + mc * mc))));
+      (!homog && (c == 0.0f || !(D > kCritBand * (fabsf(omm) + mc * mc))));
   if (GRIN_UNLIKELY(special)) {
     // out of line, on a copy: only the copy's address escapes, the live
     // state stays in registers
@@ -636,17 +641,14 @@ __device__ __forceinline__ bool step_ray(const DevMedium& m, const TraceArgs& a,
     s.ph[k] = qh[k];
     s.pl[k] = ql[k];
   }
-  ++s.full;
   ++s.steps;
   // Eq. 8, R = I + (gamma N - (1 - mu) I); Sec. II (v), R = I - 2 c N with a
   // step of dL0 / n_{i-1}; inside one shell of a layered medium, straight on
-  const bool refl = !homog && tir;
-  const float kn = homog ? 0.0f : (tir ? -2.0f * c : gamma);
-  const float kd = (homog || tir) ? 0.0f : -om;
+  const float kn = homog ? 0.0f : gamma;
+  const float kd = homog ? 0.0f : -om;
 #pragma unroll
   for (int j = 0; j < 3; ++j) add_ff(s.d[j], s.dl[j], fmaf(kn, N[j], kd * s.d[j]));
-  s.h = dopl_f * (refl ? s.inv_prev : inv_n);
-  s.tir_i += refl ? 1 : 0;
+  s.h = dopl_f * inv_n;
   s.nu_prev = nu_i;
   s.inv_prev = inv_n;
   s.lvl_prev = lvl_i;
