@@ -587,8 +587,8 @@ __device__ __noinline__ bool step_slow(const DevMedium& m, const TraceArgs& a, i
 // medium, the level did not change and it goes straight on).
 // Everything is computed without a branch and one flag routes the rare cases
 // (surface crossing, invalid n, zero or undefined gradient, tangency,
-// near-critical D, the step limit) to step_slow, which redoes the step from
-// the unchanged state.
+// D at or below the near-critical band, the step limit) to step_slow, which
+// redoes the step from the unchanged state.
 template <class C, bool LAYERED>
 __device__ __forceinline__ bool step_ray(const DevMedium& m, const TraceArgs& a, int64_t r,
                                          RayF& s, float dopl_f) {
