@@ -188,26 +188,41 @@ __device__ void field_h(const DevMedium& m, const double* P, double& n, double* 
       ddw[a][2] = 4.0 - 9.0 * t;
       ddw[a][3] = 3.0 * t - 1.0;
     }
+    // The tensor-product stencil separates: sums along x of the samples
+    // weighted by w, w', w'' (per row), then along y, then along z, keeping
+    // only the weight combinations of total derivative order <= 2.  Fused
+    // multiply-adds (explicit fma; this file is otherwise built unfused).
     for (int c = 0; c < 4; ++c) {
       int kk = min(max(b0[2] - 1 + c, 0), nn[2] - 1);
+      double y00 = 0.0, y10 = 0.0, y20 = 0.0, y01 = 0.0, y11 = 0.0, y02 = 0.0;
       for (int b = 0; b < 4; ++b) {
         int jj = min(max(b0[1] - 1 + b, 0), nn[1] - 1);
         const float* row = m.grid + (kk * nn[1] + jj) * nn[0];
+        double x0 = 0.0, x1 = 0.0, x2 = 0.0;  // row sums with w, w', w'' in x
         for (int a = 0; a < 4; ++a) {
           int ii = min(max(b0[0] - 1 + a, 0), nn[0] - 1);
-          double s = (double)row[ii];
-          n += w[0][a] * w[1][b] * w[2][c] * s;
-          g[0] += dw[0][a] * w[1][b] * w[2][c] * s;
-          g[1] += w[0][a] * dw[1][b] * w[2][c] * s;
-          g[2] += w[0][a] * w[1][b] * dw[2][c] * s;
-          H[0] += ddw[0][a] * w[1][b] * w[2][c] * s;
-          H[1] += w[0][a] * ddw[1][b] * w[2][c] * s;
-          H[2] += w[0][a] * w[1][b] * ddw[2][c] * s;
-          H[3] += dw[0][a] * dw[1][b] * w[2][c] * s;
-          H[4] += dw[0][a] * w[1][b] * dw[2][c] * s;
-          H[5] += w[0][a] * dw[1][b] * dw[2][c] * s;
+          const double s = (double)row[ii];
+          x0 = fma(w[0][a], s, x0);
+          x1 = fma(dw[0][a], s, x1);
+          x2 = fma(ddw[0][a], s, x2);
         }
+        y00 = fma(w[1][b], x0, y00);
+        y10 = fma(w[1][b], x1, y10);
+        y20 = fma(w[1][b], x2, y20);
+        y01 = fma(dw[1][b], x0, y01);
+        y11 = fma(dw[1][b], x1, y11);
+        y02 = fma(ddw[1][b], x0, y02);
       }
+      n = fma(w[2][c], y00, n);
+      g[0] = fma(w[2][c], y10, g[0]);
+      g[1] = fma(w[2][c], y01, g[1]);
+      g[2] = fma(dw[2][c], y00, g[2]);
+      H[0] = fma(w[2][c], y20, H[0]);
+      H[1] = fma(w[2][c], y02, H[1]);
+      H[2] = fma(ddw[2][c], y00, H[2]);
+      H[3] = fma(w[2][c], y11, H[3]);
+      H[4] = fma(dw[2][c], y10, H[4]);
+      H[5] = fma(dw[2][c], y01, H[5]);
     }
     const double* sp = m.spacing;
     for (int k = 0; k < 3; ++k) g[k] /= sp[k];
@@ -278,14 +293,19 @@ __device__ void param_adj(const DevMedium& m, const double* P, double nb, const 
       plain::keys(u - fl, w[a], dw[a]);
       for (int t = 0; t < 4; ++t) dw[a][t] /= m.spacing[a];
     }
+    // d(n, grad n)/d(sample) = the tap's weight products; factored per row
+    // (b, c): v = w0 A + w0' B with A = w1 (nb w2 + gb2 w2') + gb1 w1' w2 and
+    // B = gb0 w1 w2.
     for (int c = 0; c < 4; ++c) {
       int kk = min(max(b0[2] - 1 + c, 0), nn[2] - 1);
+      const double zc = fma(nb, w[2][c], gb[2] * dw[2][c]);
       for (int b = 0; b < 4; ++b) {
         int jj = min(max(b0[1] - 1 + b, 0), nn[1] - 1);
+        const double A = fma(w[1][b], zc, gb[1] * dw[1][b] * w[2][c]);
+        const double B = gb[0] * w[1][b] * w[2][c];
         for (int a = 0; a < 4; ++a) {
           int ii = min(max(b0[0] - 1 + a, 0), nn[0] - 1);
-          double v = nb * w[0][a] * w[1][b] * w[2][c] + gb[0] * dw[0][a] * w[1][b] * w[2][c] +
-                     gb[1] * w[0][a] * dw[1][b] * w[2][c] + gb[2] * w[0][a] * w[1][b] * dw[2][c];
+          const double v = fma(w[0][a], A, dw[0][a] * B);
           if (v != 0.0) atomicAdd(grad + ((int64_t)kk * nn[1] + jj) * nn[0] + ii, v);
         }
       }
