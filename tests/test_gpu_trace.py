@@ -363,6 +363,34 @@ def test_context_owns_media_and_servers():
     assert c.handle is None and g.handle is None
 
 
+def test_new_media_argument_errors(ctx):
+    """The spherical freeform and N2P kinds reject bad descriptions, an
+    unknown kind is rejected, and the adjoint, which covers polynomial and
+    grid media, answers NOT_IMPLEMENTED for both."""
+    import dataclasses
+    N = tracer.N
+    n2p = W.n2p_lens_medium(0.772, 4.469, 0.3)
+    sph = W.spherical_freeform_medium()
+    bad = [dataclasses.replace(n2p, form=W.FORM_SQRT),
+           dataclasses.replace(n2p, coeffs=np.array([0.0, 2.0, 0.7, 4.4])),
+           dataclasses.replace(n2p, coeffs=np.array([1.0, 0.0, 0.7, 4.4])),
+           dataclasses.replace(n2p, coeffs=np.array([1.0, 2.0, np.nan, 4.4])),
+           dataclasses.replace(sph, coeffs=np.array([1.5, np.inf, 0.0, 0.0])),
+           dataclasses.replace(sph, kind=7)]
+    for spec in bad:
+        with pytest.raises(N.GrinError) as e:
+            tracer.Medium(ctx, spec)
+        assert e.value.status == N.GRIN_ERR_INVALID_ARG, spec
+    rb = tracer.RayBatch.from_numpy(np.array([[0.0, 0.3, -1.0]]), np.array([[0.0, 0.0, 1.0]]),
+                                    dtype=torch.float64)
+    g = {k: torch.zeros(1, dtype=torch.float64, device="cuda") for k in tracer.OUT_FIELDS}
+    for spec in (n2p, sph):
+        med = tracer.Medium(ctx, spec)
+        with pytest.raises(N.GrinError) as e:
+            tracer.trace_adjoint(ctx, med, rb, 1e-3, 100, g, 4, 8)
+        assert e.value.status == N.GRIN_ERR_NOT_IMPLEMENTED
+
+
 def test_trace_host_equals_device(ctx):
     wl = W.freeform_workload(5000)
     med = tracer.Medium(ctx, wl.medium)
