@@ -182,14 +182,18 @@ def oracle_rate(wl, stride: int, threads: int, rays=None):
 def serve_load(ctx, dev_index: int, rates, jobs_per_rate: int, seed: int = 7):
     """Poisson arrivals of trace jobs into one grin_serve server; per rate:
     p50/p99 latency (submit to results in host memory) and ray-steps/s.
-    Jobs draw a medium from {Luneburg lens, freeform block, 128^3 blob grid,
-    its 32-shell layered version} and a ray count log-uniform in
-    [1e3, 1e6]; dL0 is the medium's own."""
+    Jobs draw a medium from {Luneburg lens, freeform block, blob grids at
+    64^3, 128^3, 256^3 and 512^3, the 128^3 grid in 32 shells}, a ray count
+    log-uniform in [1e3, 1e6] and dL0 from {0.02, 0.01, 0.005} (mm, or units
+    of the lens radius); every medium stays resident on the device."""
     import torch
     from paper_2606_22655_b300 import tracer
     from paper_2606_22655_b300 import workloads as W
-    pool = [W.luneburg_workload(), W.freeform_workload(1 << 20),
-            W.blob_workload(n_rays=1 << 20, res=128), W.blob_workload(n_rays=1 << 20, res=128, n_levels=32)]
+    names = ["luneburg", "freeform_block", "grid_64", "grid_128", "grid_256", "grid_512", "layered_128"]
+    pool = [W.luneburg_workload(), W.freeform_workload(1 << 20)]
+    pool += [W.blob_workload(n_rays=1 << 20, res=r) for r in (64, 128, 256, 512)]
+    pool += [W.blob_workload(n_rays=1 << 20, res=128, n_levels=32)]
+    dopls = [0.02, 0.01, 0.005]
     media = [tracer.Medium(ctx, wl.medium) for wl in pool]
     rays = [tracer.RayBatch.from_numpy(wl.rays.origins, wl.rays.dirs, device="cpu", dtype=torch.float32, pin=True)
             for wl in pool]
@@ -200,6 +204,7 @@ def serve_load(ctx, dev_index: int, rates, jobs_per_rate: int, seed: int = 7):
     for ri, rate in enumerate(rates):
         rng = np.random.default_rng(seed + ri)
         kinds = rng.integers(0, len(pool), jobs_per_rate)
+        job_dopl = rng.choice(dopls, jobs_per_rate)
         counts = np.exp(rng.uniform(np.log(1e3), np.log(1e6), jobs_per_rate)).astype(np.int64)
         counts = np.minimum(counts, [pool[k].rays.n for k in kinds])
         gaps = rng.exponential(1.0 / rate, jobs_per_rate)
@@ -224,7 +229,7 @@ def serve_load(ctx, dev_index: int, rates, jobs_per_rate: int, seed: int = 7):
             k = int(kinds[j]); n = int(counts[j]); ob = free.pop()
             sub = tracer.RayBatch(*[t[:n] for t in rays[k].tensors()])
             out = {key: v[:n] for key, v in outs[ob].items()}
-            jid, _ = srv.submit(media[k], sub, pool[k].dopl, pool[k].max_steps, out=out)
+            jid, _ = srv.submit(media[k], sub, float(job_dopl[j]), 20000, out=out)
             inflight.append((jid, ob, n))
         for x in inflight:
             srv.wait(x[0], 600)
@@ -238,7 +243,7 @@ def serve_load(ctx, dev_index: int, rates, jobs_per_rate: int, seed: int = 7):
                         "wall_s": wall})
     st = srv.stats()
     srv.close()
-    return {"media": ["luneburg", "freeform_block", "grid_128", "layered_128"],
+    return {"media": names, "dL0": dopls,
             "ray_count": "log-uniform [1e3, 1e6]", "arrivals": "Poisson", "step_quantum": 1024,
             "sweep": results, "ticks": st["ticks"], "failed": st["failed"]}
 
