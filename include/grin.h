@@ -291,9 +291,11 @@ int grin_trace_adjoint(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
  * rays through one medium (host buffers, like grin_trace_host) traced by the
  * mixed-precision tracer.  A scheduler thread owns the GPU work:
  *   - admission: queued jobs are admitted first come, first served, when
- *     their device footprint (rays in, results out, resident ray state) fits
- *     in what is left of the server's device arena (hbm_budget_bytes, taken
- *     once at creation) and resident ray slots are free;
+ *     their device footprint (rays in, results out, resident ray state and,
+ *     for gridded media with at least 65,536 rays, 6 bytes a ray of claim
+ *     order as in grin_trace) fits in what is left of the server's device
+ *     arena (hbm_budget_bytes, taken once at creation) and resident ray slots
+ *     are free;
  *   - ticks: every tick advances each running job's slots by step_quantum
  *     steps; a slot whose ray ends takes the job's next ray; the ray state
  *     stays on the device between ticks, so a small job submitted while a

@@ -109,19 +109,25 @@ struct Job {
   unsigned long long* host_done = nullptr;  // pinned
 };
 
-// Device layout of a job: counters | rays in | results | slot states.
+// Device layout of a job: counters | rays in | results | slot states |
+// claim order (gridded media with enough rays; see ray_order.cu).
 struct Layout {
-  size_t counters, in, out, slots, total;
+  size_t counters, in, out, slots, order, total;
 };
 
-Layout layout_of(int64_t n, int dtype, int nslots) {
+bool job_ordered(const grin::DevMedium& m, int64_t n) {
+  return m.kind == GRIN_MEDIUM_GRID && n >= grin::kOrderMinRays && n < (int64_t(1) << 31);
+}
+
+Layout layout_of(int64_t n, int dtype, int nslots, bool ordered) {
   Layout L;
   const size_t esz = dtype == GRIN_F64 ? 8 : 4;
   L.counters = 0;
   L.in = kAlign;
   L.out = L.in + round_up(6 * esz * (size_t)n, kAlign);
   L.slots = L.out + round_up((7 * 8 + 4 * 4) * (size_t)n, kAlign);
-  L.total = L.slots + round_up(grin::serve_slot_bytes() * (size_t)nslots, kAlign);
+  L.order = L.slots + round_up(grin::serve_slot_bytes() * (size_t)nslots, kAlign);
+  L.total = L.order + (ordered ? round_up(grin::order_scratch_bytes(n), kAlign) : 0);
   return L;
 }
 
@@ -191,7 +197,8 @@ void admit(grin_server s) {
     }
     const int64_t n = j.rays.count;
     j.nslots = job_slots(s, n);
-    Layout L = layout_of(n, j.rays.dtype, j.nslots);
+    const bool ordered = job_ordered(j.med->dm, n);
+    Layout L = layout_of(n, j.rays.dtype, j.nslots, ordered);
     size_t off;
     if (!s->arena->alloc(L.total, &off)) break;  // first come first served: wait
     s->queue.pop_front();
@@ -248,6 +255,13 @@ void admit(grin_server s) {
     a.tir_b = di[3];
     a.dopl = j.prm.dopl;
     a.max_steps = j.prm.max_steps;
+    a.perm = nullptr;
+    // gridded media: claim the job's rays in entry-cell order (ray_order.cu)
+    if (ordered && grin::launch_order(j.med->dm, a, base + L.order, s->ctx->sm_count, j.stream,
+                                      &a.perm) < 0) {
+      cudaGetLastError();
+      a.perm = nullptr;
+    }
     j.state = GRIN_JOB_RUNNING;
     s->running.push_back(jp);
   }
@@ -404,7 +418,8 @@ int grin_serve_submit(grin_server s, grin_medium med, const grin_rays* rays, con
     if (!out->px || !out->py || !out->pz || !out->dx || !out->dy || !out->dz || !out->opl ||
         !out->exit_id || !out->steps || !out->tir_internal || !out->tir_boundary)
       return GRIN_ERR_INVALID_ARG;
-    Layout L = layout_of(rays->count, rays->dtype, job_slots(s, rays->count));
+    Layout L = layout_of(rays->count, rays->dtype, job_slots(s, rays->count),
+                         job_ordered(med->dm, rays->count));
     if (round_up(L.total, kAlign) > s->arena->capacity()) return GRIN_ERR_BUSY;
   }
   auto j = std::make_shared<Job>();

@@ -781,7 +781,7 @@ __global__ void __launch_bounds__(128, C::kMinBlocks) k_serve_tick(DevMedium m, 
       if (!active) {
         const unsigned long long rr = base + __popc(need & ((1u << lane) - 1u));
         if (rr < (unsigned long long)a.count) {
-          ray = (int64_t)rr;
+          ray = a.perm ? (int64_t)a.perm[rr] : (int64_t)rr;
           active = init_ray<C>(m, a, ray, s);
           if (!active) ++done;
         }
