@@ -577,6 +577,8 @@ struct AdjArgs {
   const double *gpx, *gpy, *gpz, *gdx, *gdy, *gdz, *gopl;  // dL/d(outputs)
   double* grad;      // dL/d(parameters), accumulated
   int nterms;
+  void* order_ws = nullptr;         // scratch of the backward order (or nullptr)
+  const uint32_t* order = nullptr;  // backward sweep: thread t takes ray order[t]
 };
 
 template <int PC, bool GRID>
@@ -611,8 +613,9 @@ __global__ void __launch_bounds__(128) k_adj_forward(DevMedium m, AdjArgs A) {
 
 template <int PC, bool GRID>
 __global__ void __launch_bounds__(128) k_adj_backward(DevMedium m, AdjArgs A) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= A.a.count) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= A.a.count) return;
+  const int64_t r = A.order ? (int64_t)A.order[t] : t;
   const int exit_id = A.meta[2 * r], nsteps = A.meta[2 * r + 1];
   if (exit_id == GRIN_EXIT_INVALID || exit_id == GRIN_EXIT_MISS ||
       exit_id == GRIN_EXIT_ENTRY_REFLECT)
@@ -689,8 +692,23 @@ template <int PC, bool GRID>
 static int run_t(const DevMedium& m, const AdjArgs& A, cudaStream_t st) {
   const unsigned blocks = (unsigned)((A.a.count + 127) / 128);
   if (launch_kernel(k_adj_forward<PC, GRID>, blocks, 128, st, m, A) < 0) return GRIN_ERR_CUDA;
-  if (launch_kernel(k_adj_backward<PC, GRID>, blocks, 128, st, m, A) < 0) return GRIN_ERR_CUDA;
-  return 2;
+  // The backward sweep walks each ray back through all its steps, one
+  // thread a ray: in a gridded medium, where path lengths vary with the exit
+  // face, take the rays longest first, bucketed by step count, so the threads
+  // of a warp have similar amounts of work (measured 6x on the 128^3 blob
+  // grid; on the polynomial block, whose rays have nearly equal lengths, the
+  // permutation only cost locality).
+  AdjArgs B = A;
+  int lo = 0;
+  if (GRID && A.order_ws) {
+    lo = launch_order_by_steps(A.meta, A.a.count, A.order_ws, st, &B.order);
+    if (lo < 0) {
+      B.order = nullptr;
+      lo = 0;
+    }
+  }
+  if (launch_kernel(k_adj_backward<PC, GRID>, blocks, 128, st, m, B) < 0) return GRIN_ERR_CUDA;
+  return 2 + lo;
 }
 
 }  // namespace adj
@@ -700,10 +718,19 @@ bool adjoint_supported(const DevMedium& m) {
   return m.kind == GRIN_MEDIUM_GRID || (m.kind == GRIN_MEDIUM_POLY && m.form == GRIN_FORM_LINEAR);
 }
 
-size_t adjoint_workspace(int64_t rays, int32_t max_steps, int32_t k) {
+// Workspace: checkpoints [ray][segment][kCk] | meta [ray][2] | (256-byte
+// aligned) the backward order's scratch, for fewer than 2^31 rays.
+static size_t adjoint_order_offset(int64_t rays, int32_t max_steps, int32_t k) {
   const int64_t nseg = max_steps / k + 1;
-  return (size_t)rays * (size_t)nseg * adj::kCk * sizeof(double) + (size_t)rays * 2 * sizeof(int32_t) +
-         256;
+  const size_t end = (size_t)rays * (size_t)nseg * adj::kCk * sizeof(double) +
+                     (size_t)rays * 2 * sizeof(int32_t);
+  return (end + 255) & ~size_t(255);
+}
+
+size_t adjoint_workspace(int64_t rays, int32_t max_steps, int32_t k) {
+  size_t bytes = adjoint_order_offset(rays, max_steps, k);
+  if (rays > 0 && rays < (int64_t(1) << 31)) bytes += order_scratch_bytes(rays);
+  return bytes + 256;
 }
 
 int launch_adjoint(const DevMedium& m, const TraceArgs& a, int32_t k, void* ws, const double* const* gout,
@@ -723,6 +750,8 @@ int launch_adjoint(const DevMedium& m, const TraceArgs& a, int32_t k, void* ws, 
   A.gopl = gout[6];
   A.grad = grad;
   A.nterms = nterms;
+  if (a.count < (int64_t(1) << 31))
+    A.order_ws = (char*)ws + adjoint_order_offset(a.count, a.max_steps, k);
   if (m.kind == GRIN_MEDIUM_GRID) return adj::run_t<0, true>(m, A, st);
   switch (m.pclass) {
     case kPoly2: return adj::run_t<2, false>(m, A, st);

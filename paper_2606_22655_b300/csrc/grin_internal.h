@@ -90,6 +90,10 @@ size_t order_scratch_bytes(int64_t n);
 // aligned); *perm_out points into it.  Returns the launch count or a status.
 int launch_order(const DevMedium& m, const TraceArgs& a, void* scratch, int sm_count,
                  cudaStream_t s, const uint32_t** perm_out);
+// The adjoint's backward order: rays by step count (meta[2 r + 1]), longest
+// first; same scratch layout.  Returns the launch count or a status.
+int launch_order_by_steps(const int32_t* meta, int64_t n, void* scratch, cudaStream_t s,
+                          const uint32_t** perm_out);
 
 // Launches kern<<<grid, block, 0, s>>>(args...) and returns 1, or
 // GRIN_ERR_CUDA if this launch failed.  cudaLaunchKernelEx reports the

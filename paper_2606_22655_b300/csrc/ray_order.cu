@@ -117,26 +117,72 @@ size_t order_scratch_bytes(int64_t n) {
   return perm + keys + (size_t)kKeys * sizeof(uint32_t);
 }
 
+// Key of the adjoint's backward sweep: rays by step count, longest first,
+// so a warp's threads walk back through similar numbers of steps.
+__global__ void k_order_steps(int64_t n, const int32_t* meta, uint16_t* keys, uint32_t* hist) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+    const int st = min(max(meta[2 * r + 1], 0), kKeys - 1);
+    const uint32_t key = (uint32_t)(kKeys - 1 - st);
+    keys[r] = (uint16_t)key;
+    atomicAdd(hist + key, 1u);
+  }
+}
+
+struct OrderBufs {
+  uint32_t* perm;
+  uint16_t* keys;
+  uint32_t* hist;
+};
+
+static OrderBufs order_bufs(void* scratch, int64_t n) {
+  char* p = (char*)scratch;
+  OrderBufs b;
+  b.perm = (uint32_t*)p;
+  p += ((size_t)n * sizeof(uint32_t) + 255) & ~size_t(255);
+  b.keys = (uint16_t*)p;
+  p += ((size_t)n * sizeof(uint16_t) + 255) & ~size_t(255);
+  b.hist = (uint32_t*)p;
+  return b;
+}
+
+// The scan and the scatter, after a key kernel has filled keys and hist.
+static int finish_order(const OrderBufs& b, int64_t n, unsigned blocks, cudaStream_t s,
+                        const uint32_t** perm_out) {
+  if (launch_kernel(k_order_scan, 1, kScanThreads, s, b.hist) < 0) return GRIN_ERR_CUDA;
+  if (launch_kernel(k_order_scatter, blocks, 256, s, n, (const uint16_t*)b.keys, b.hist, b.perm) < 0)
+    return GRIN_ERR_CUDA;
+  *perm_out = b.perm;
+  return 2;
+}
+
+static bool clear_hist(const OrderBufs& b, cudaStream_t s) {
+  if (cudaMemsetAsync(b.hist, 0, kKeys * sizeof(uint32_t), s) == cudaSuccess) return true;
+  cudaGetLastError();
+  return false;
+}
+
 int launch_order(const DevMedium& m, const TraceArgs& a, void* scratch, int sm_count,
                  cudaStream_t s, const uint32_t** perm_out) {
   if (a.count <= 0 || a.count >= (int64_t(1) << 31)) return GRIN_ERR_INVALID_ARG;
-  char* p = (char*)scratch;
-  uint32_t* perm = (uint32_t*)p;
-  p += ((size_t)a.count * sizeof(uint32_t) + 255) & ~size_t(255);
-  uint16_t* keys = (uint16_t*)p;
-  p += ((size_t)a.count * sizeof(uint16_t) + 255) & ~size_t(255);
-  uint32_t* hist = (uint32_t*)p;
-  if (cudaMemsetAsync(hist, 0, kKeys * sizeof(uint32_t), s) != cudaSuccess) {
-    cudaGetLastError();
-    return GRIN_ERR_CUDA;
-  }
+  const OrderBufs b = order_bufs(scratch, a.count);
+  if (!clear_hist(b, s)) return GRIN_ERR_CUDA;
   const unsigned blocks = (unsigned)sm_count * 8;
-  if (launch_kernel(k_order_keys, blocks, 256, s, m, a, keys, hist) < 0) return GRIN_ERR_CUDA;
-  if (launch_kernel(k_order_scan, 1, kScanThreads, s, hist) < 0) return GRIN_ERR_CUDA;
-  if (launch_kernel(k_order_scatter, blocks, 256, s, a.count, (const uint16_t*)keys, hist, perm) < 0)
-    return GRIN_ERR_CUDA;
-  *perm_out = perm;
-  return 3;
+  if (launch_kernel(k_order_keys, blocks, 256, s, m, a, b.keys, b.hist) < 0) return GRIN_ERR_CUDA;
+  const int rc = finish_order(b, a.count, blocks, s, perm_out);
+  return rc < 0 ? rc : rc + 1;
+}
+
+int launch_order_by_steps(const int32_t* meta, int64_t n, void* scratch, cudaStream_t s,
+                          const uint32_t** perm_out) {
+  if (n <= 0 || n >= (int64_t(1) << 31)) return GRIN_ERR_INVALID_ARG;
+  const OrderBufs b = order_bufs(scratch, n);
+  if (!clear_hist(b, s)) return GRIN_ERR_CUDA;
+  const int64_t want = (n + 255) / 256;
+  const unsigned blocks = (unsigned)(want < 4096 ? want : 4096);
+  if (launch_kernel(k_order_steps, blocks, 256, s, n, meta, b.keys, b.hist) < 0) return GRIN_ERR_CUDA;
+  const int rc = finish_order(b, n, blocks, s, perm_out);
+  return rc < 0 ? rc : rc + 1;
 }
 
 }  // namespace grin
