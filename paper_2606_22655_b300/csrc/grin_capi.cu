@@ -222,6 +222,7 @@ int grin_medium_create(grin_ctx ctx, const grin_medium_desc* d, grin_medium* out
     m.nx = d->nx;
     m.ny = d->ny;
     m.nz = d->nz;
+    m.rows16 = d->nx % 4 == 0;  // the device copy is cudaMalloc'd (256-byte aligned)
     try {
       samples.resize((size_t)cnt);
     } catch (...) {

@@ -159,6 +159,12 @@ __device__ __forceinline__ void cr_w(T t, T* w, T* dw) {
 // (edge-clamped).  The x sums of each of the 16 rows are taken first, then y,
 // then z: 192 FMAs and 64 cached 4-byte gathers.  Subtracting `sub` (a value
 // near the samples) per tap keeps the FP32 result's low bits.
+// When the grid's rows start on 16-byte boundaries and no x tap is clamped,
+// each row's 4 taps come from the aligned 16-byte block holding the first
+// tap and, when the taps straddle it, the next one: 1 or 2 vector loads a row
+// instead of 4 scalar ones (half the L1 wavefronts of a scattered warp).  The
+// x weights are spread over the 8 loaded positions with zeros around the
+// taps, so each row sums the same products in the same order.
 template <typename T>
 __device__ __forceinline__ void grid_vg(const DevMedium& m, const T* u_in, T sub, T& v, T& gx,
                                         T& gy, T& gz) {
@@ -178,27 +184,66 @@ __device__ __forceinline__ void grid_vg(const DevMedium& m, const T* u_in, T sub
   }
   const float* __restrict__ g = m.grid;
   T V = T(0), GX = T(0), GY = T(0), GZ = T(0);
+  const int x0 = idx[0][0];  // first x tap (unclamped when the window is inside the row)
+  const bool vec = m.rows16 && idx[0][0] == idx[0][1] - 1 && idx[0][3] == idx[0][0] + 3;
+  if (vec) {
+    const int ax = x0 & ~3, o = x0 - ax;  // aligned block start, tap offset in it
+    T wx[8], dwx[8];
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    T sv = T(0), sx = T(0), sy = T(0);
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const float* __restrict__ row = g + (idx[2][c] * n[1] + idx[1][b]) * n[0];
-      T r = T(0), rx = T(0);
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        T s = (T)__ldg(row + idx[0][a]) - sub;
-        r = fmadd(w[0][a], s, r);
-        rx = fmadd(dw[0][a], s, rx);
-      }
-      sv = fmadd(w[1][b], r, sv);
-      sx = fmadd(w[1][b], rx, sx);
-      sy = fmadd(dw[1][b], r, sy);
+    for (int p = 0; p < 8; ++p) {
+      const int t = p - o;
+      wx[p] = t == 0 ? w[0][0] : t == 1 ? w[0][1] : t == 2 ? w[0][2] : t == 3 ? w[0][3] : T(0);
+      dwx[p] = t == 0 ? dw[0][0] : t == 1 ? dw[0][1] : t == 2 ? dw[0][2] : t == 3 ? dw[0][3] : T(0);
     }
-    V = fmadd(w[2][c], sv, V);
-    GX = fmadd(w[2][c], sx, GX);
-    GY = fmadd(w[2][c], sy, GY);
-    GZ = fmadd(dw[2][c], sv, GZ);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      T sv = T(0), sx = T(0), sy = T(0);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const float4* __restrict__ row4 =
+            reinterpret_cast<const float4*>(g + (idx[2][c] * n[1] + idx[1][b]) * n[0] + ax);
+        const float4 A = __ldg(row4);
+        const float4 B = o ? __ldg(row4 + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float q[8] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w};
+        T r = T(0), rx = T(0);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          const T s = (T)q[p] - sub;
+          r = fmadd(wx[p], s, r);
+          rx = fmadd(dwx[p], s, rx);
+        }
+        sv = fmadd(w[1][b], r, sv);
+        sx = fmadd(w[1][b], rx, sx);
+        sy = fmadd(dw[1][b], r, sy);
+      }
+      V = fmadd(w[2][c], sv, V);
+      GX = fmadd(w[2][c], sx, GX);
+      GY = fmadd(w[2][c], sy, GY);
+      GZ = fmadd(dw[2][c], sv, GZ);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      T sv = T(0), sx = T(0), sy = T(0);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const float* __restrict__ row = g + (idx[2][c] * n[1] + idx[1][b]) * n[0];
+        T r = T(0), rx = T(0);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          T s = (T)__ldg(row + idx[0][a]) - sub;
+          r = fmadd(w[0][a], s, r);
+          rx = fmadd(dw[0][a], s, rx);
+        }
+        sv = fmadd(w[1][b], r, sv);
+        sx = fmadd(w[1][b], rx, sx);
+        sy = fmadd(dw[1][b], r, sy);
+      }
+      V = fmadd(w[2][c], sv, V);
+      GX = fmadd(w[2][c], sx, GX);
+      GY = fmadd(w[2][c], sy, GY);
+      GZ = fmadd(dw[2][c], sv, GZ);
+    }
   }
   v = V;
   gx = GX;

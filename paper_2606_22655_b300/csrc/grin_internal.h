@@ -32,6 +32,7 @@ struct DevMedium {
   int32_t n_levels;  // 0: continuous
   int32_t bkind;     // GRIN_BOUNDARY_*
   int32_t nx, ny, nz;
+  int32_t rows16;  // grid rows start on 16-byte boundaries (nx % 4 == 0)
   double form_c, n_ext;
   // Index offset: the FP32 path carries nu = n - base so that the difference
   // of successive indices (which drives each refraction) keeps its bits.
