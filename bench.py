@@ -275,6 +275,37 @@ def adjoint_timing(ctx, dev):
             "precision": "fp64", "gradient_params": int(wl.medium.grid.size)}
 
 
+def media_rates(ctx, dev):
+    """One mixed-precision trace per medium kind (after a warm-up trace):
+    ray-steps/s of each, as grin_trace runs it (claim order included)."""
+    import torch
+    from paper_2606_22655_b300 import tracer
+    from paper_2606_22655_b300 import workloads as W
+    from paper_2606_22655_b300 import n2p_design
+    fan = n2p_design.fan(1 << 16, 0.3)
+    cases = [("luneburg_4096", W.luneburg_workload()),
+             ("corrector_lens_262144", W.corrector_workload(1 << 18)),
+             ("spherical_freeform_262144", W.spherical_workload(1 << 18)),
+             ("n2p_lens_65536", W.Workload("n2p", W.n2p_lens_medium(0.770, 4.462, 0.3), fan, 1e-4, 400000, 1.0)),
+             ("grid_256_1048576", W.blob_workload(n_rays=1 << 20, res=256)),
+             ("layered_256_1048576", W.blob_workload(n_rays=1 << 20, res=256, n_levels=32))]
+    res = {}
+    for name, wl in cases:
+        med = tracer.Medium(ctx, wl.medium)
+        rays = tracer.RayBatch.from_numpy(wl.rays.origins, wl.rays.dirs, device=dev, dtype=torch.float32)
+        out = tracer.empty_result(rays.count, dev)
+        tracer.trace(ctx, med, rays, wl.dopl, wl.max_steps, "mixed", out=out)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        tracer.trace(ctx, med, rays, wl.dopl, wl.max_steps, "mixed", out=out)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        t = e0.elapsed_time(e1) / 1e3
+        res[name] = {"ms": 1e3 * t, "ray_steps_per_s": float(out["steps"].sum()) / t}
+        med.close()
+    return res
+
+
 def design_sweep(ctx):
     """The N2P lens design of Sec. VI (L = 0.3 R, F = 2 R): successive
     refinement of (beta, gamma), 8 rounds of 81 concurrent 10-ray jobs on the
@@ -438,8 +469,10 @@ def run_ours(args):
     d2h = (7 * 8 + 4 * 4) * hrays.count
 
     design = None
+    media = None
     if ws == 1 and not args.no_serve:
         design = design_sweep(ctx)
+        media = media_rates(ctx, dev)
     adjoint = None
     if ws == 1 and not args.no_serve:
         adjoint = adjoint_timing(ctx, dev)
@@ -487,6 +520,7 @@ def run_ours(args):
         "serve": serve,
         "adjoint": adjoint,
         "design_sweep": design,
+        "media_rates": media,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:

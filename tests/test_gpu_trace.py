@@ -265,6 +265,21 @@ def test_grid_fp64_matches_oracle(ctx, blob64):
     check64(g, o, wl.l_ref)
 
 
+@pytest.mark.parametrize("res", [64, 62])
+def test_grid_fp64_fast_matches_oracle(ctx, res):
+    """The FMA tricubic gather against the oracle's 64-term sum, on a grid
+    whose rows start on 16-byte boundaries (64: each stencil row from one or
+    two aligned vector loads) and on one whose rows do not (62: four scalar
+    loads a row).  Same decisions on every unflagged ray, continuous results
+    within the rounding-order bound of the fast kernel (1e-8)."""
+    wl = W.blob_workload(n_rays=1500, res=res)
+    g = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "fp64-fast")
+    o = orc(wl.medium, wl.rays, wl.dopl, wl.max_steps)
+    rep = compare(g, o, wl.l_ref, flagged(o["margins"], TAU64))
+    assert rep["int_mismatch_unflagged"] == 0, rep
+    assert max(rep["pos"], rep["dir"], rep["opl"]) <= 1e-8, rep
+
+
 def test_grid_mixed_error_stated(ctx, blob64):
     wl = blob64
     g64 = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "fp64")
