@@ -44,6 +44,8 @@
 // boundary kind BK and index form FORM, either fixed at compile time (the
 // common box / n = p case, which drops their run-time switches from the step)
 // or -1 for "read from the medium at run time".
+#include <climits>
+
 #include "grin_device.cuh"
 
 namespace grin {
@@ -58,12 +60,17 @@ namespace grin {
 #define GRIN_MIXED_MIN_BLOCKS_GRID 5
 #endif
 constexpr int kStepQuantum = 32;
+// Tap cache of the gridded fast step: 16 rows (one per (z, y) pair of the
+// stencil) of 128 float4 columns, one column per thread; the 4-float pad
+// between rows spreads one column's rows over the banks.
+constexpr int kTapRow = 128 * 4 + 4;
 constexpr float kCritBand = 1.0e-5f;  // relative |D| below which FP64 decides
 
 #define GRIN_UNLIKELY(x) __builtin_expect(!!(x), 0)
 
 template <int PC, bool GRID, bool LAYERED, int BK, int FORM>
 struct Cfg {
+  static constexpr bool kGrid = GRID;
   static constexpr int kMinBlocks = GRID ? GRIN_MIXED_MIN_BLOCKS_GRID : GRIN_MIXED_MIN_BLOCKS;
   static __device__ __forceinline__ int bk(const DevMedium& m) { return BK >= 0 ? BK : m.bkind; }
   static __device__ __forceinline__ int form(const DevMedium& m) { return FORM >= 0 ? FORM : m.form; }
@@ -113,6 +120,12 @@ struct Cfg {
         gz = qz * s;
       }
     }
+    level(m, f, nu, lvl);
+  }
+
+  // f = n - base of the smooth field -> nu = n - base of the medium and its
+  // level (a layered medium takes the centre value of f's shell).
+  static __device__ __forceinline__ void level(const DevMedium& m, float f, float& nu, int& lvl) {
     if (LAYERED) {
       float u = (f - m.lvl_lo_rel_f) * m.lvl_scale_f;
       float fl = floorf(u);
@@ -123,6 +136,62 @@ struct Cfg {
       lvl = 0;
       nu = f;
     }
+  }
+
+  // Gridded media.  The cell of the 64-tap stencil at a point and the
+  // fractions inside it, taken exactly as grid_vg takes them (the grid
+  // coordinate clamped to [-2, n + 1], a NaN to -2).
+  static __device__ __forceinline__ void cell(const DevMedium& m, const float* q, int* i0,
+                                              float* fr) {
+    const int n[3] = {m.nx, m.ny, m.nz};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float u = (q[k] - m.origin_f[k]) * m.inv_spacing_f[k];
+      u = vmax(u, -2.0f);
+      u = vmin(u, (float)(n[k] + 1));
+      const float fl = vfloor(u);
+      i0[k] = (int)fl;
+      fr[k] = u - fl;
+    }
+  }
+
+  // eval for a gridded medium from the cell's 64 taps (sample - base, row
+  // c * 4 + b at col[(c * 4 + b) * kTapRow], x taps in .x .. .w): the same
+  // products summed in the same order as grid_vg's, so the same value and
+  // gradient bit for bit.
+  static __device__ __forceinline__ void eval_taps(const DevMedium& m, const float* fr,
+                                                   const float* col, float& nu, float& gx,
+                                                   float& gy, float& gz, int& lvl) {
+    float w[3][4], dw[3][4];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) cr_w(fr[k], w[k], dw[k]);
+    float V = 0.0f, GX = 0.0f, GY = 0.0f, GZ = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float sv = 0.0f, sx = 0.0f, sy = 0.0f;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const float4 q = *reinterpret_cast<const float4*>(col + (c * 4 + b) * kTapRow);
+        const float t[4] = {q.x, q.y, q.z, q.w};
+        float r = 0.0f, rx = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          r = fmadd(w[0][k], t[k], r);
+          rx = fmadd(dw[0][k], t[k], rx);
+        }
+        sv = fmadd(w[1][b], r, sv);
+        sx = fmadd(w[1][b], rx, sx);
+        sy = fmadd(dw[1][b], r, sy);
+      }
+      V = fmadd(w[2][c], sv, V);
+      GX = fmadd(w[2][c], sx, GX);
+      GY = fmadd(w[2][c], sy, GY);
+      GZ = fmadd(dw[2][c], sv, GZ);
+    }
+    gx = GX * m.inv_spacing_f[0];
+    gy = GY * m.inv_spacing_f[1];
+    gz = GZ * m.inv_spacing_f[2];
+    level(m, V, nu, lvl);
   }
 
   static __device__ __forceinline__ bool inside(const DevMedium& m, const float* q) {
@@ -589,10 +658,10 @@ __device__ __noinline__ bool step_slow(const DevMedium& m, const TraceArgs& a, i
 // (surface crossing, invalid n, zero or undefined gradient, tangency,
 // D at or below the near-critical band, the step limit) to step_slow, which
 // redoes the step from the unchanged state.
-template <class C, bool LAYERED>
-__device__ __forceinline__ bool step_ray(const DevMedium& m, const TraceArgs& a, int64_t r,
-                                         RayF& s, float dopl_f) {
-  float qh[3], ql[3], dv[3];
+//
+// step_point gives the end point Q = P + h I as a hi + lo pair and the step
+// vector h I; step_from finishes the step from n and grad n at Q.
+__device__ __forceinline__ void step_point(const RayF& s, float* qh, float* ql, float* dv) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     dv[k] = s.h * s.d[k];
@@ -601,10 +670,14 @@ __device__ __forceinline__ bool step_ray(const DevMedium& m, const TraceArgs& a,
     ql[k] = y - (t - s.ph[k]);
     qh[k] = t;
   }
+}
+
+template <class C, bool LAYERED>
+__device__ __forceinline__ bool step_from(const DevMedium& m, const TraceArgs& a, int64_t r,
+                                          RayF& s, float dopl_f, const float* qh,
+                                          const float* ql, const float* dv, float nu_i,
+                                          const float* g, int lvl_i) {
   const bool in = C::inside(m, qh);
-  float nu_i, g[3];
-  int lvl_i;
-  C::eval(m, qh[0], qh[1], qh[2], nu_i, g[0], g[1], g[2], lvl_i);
   const float n_i = m.base_f + nu_i;
   const float inv_n = 1.0f / n_i;
   const float gn2 = fmaf(g[0], g[0], fmaf(g[1], g[1], g[2] * g[2]));
@@ -659,10 +732,103 @@ __device__ __forceinline__ bool step_ray(const DevMedium& m, const TraceArgs& a,
 }
 
 template <class C, bool LAYERED>
+__device__ __forceinline__ bool step_ray(const DevMedium& m, const TraceArgs& a, int64_t r,
+                                         RayF& s, float dopl_f) {
+  float qh[3], ql[3], dv[3];
+  step_point(s, qh, ql, dv);
+  float nu_i, g[3];
+  int lvl_i;
+  C::eval(m, qh[0], qh[1], qh[2], nu_i, g[0], g[1], g[2], lvl_i);
+  return step_from<C, LAYERED>(m, a, r, s, dopl_f, qh, ql, dv, nu_i, g, lvl_i);
+}
+
+// Warp-collective: the lanes in `need` get their column of the tap cache
+// refilled for the cell in their key[] (the 64 stencil samples of grid_vg,
+// edge-clamped, minus base).  The whole warp loads one such lane's taps at
+// a time, two x-adjacent taps of one row a lane, so a refill costs the warp
+// two gathers instead of the lane's 64.
+__device__ __forceinline__ void tap_fill(const DevMedium& m, bool need, const int* key,
+                                         float* taps, unsigned lane) {
+  unsigned mask = __ballot_sync(0xffffffffu, need);
+  if (!mask) return;
+  __syncwarp();  // the owners' reads of their old taps come first
+  const int row = (int)(lane >> 1), c = row >> 2, b = row & 3, h = (int)(lane & 1u);
+  const int wbase = (int)(threadIdx.x & ~31u);
+  const float sub = m.base_f;
+  while (mask) {
+    const int src = __ffs(mask) - 1;
+    mask &= mask - 1u;
+    const int kx = __shfl_sync(0xffffffffu, key[0], src);
+    const int ky = __shfl_sync(0xffffffffu, key[1], src);
+    const int kz = __shfl_sync(0xffffffffu, key[2], src);
+    const int iz = min(max(kz - 1 + c, 0), m.nz - 1);
+    const int iy = min(max(ky - 1 + b, 0), m.ny - 1);
+    const int ix0 = min(max(kx - 1 + 2 * h, 0), m.nx - 1);
+    const int ix1 = min(max(kx + 2 * h, 0), m.nx - 1);
+    const float* __restrict__ g = m.grid + (iz * m.ny + iy) * m.nx;
+    const float2 v = make_float2(__ldg(g + ix0) - sub, __ldg(g + ix1) - sub);
+    *reinterpret_cast<float2*>(taps + row * kTapRow + (wbase + src) * 4 + 2 * h) = v;
+  }
+  __syncwarp();
+}
+
+// Up to kStepQuantum steps of the lane's ray; returns how many rays ended.
+// On a gridded medium the fast step reads its taps from the lane's column of
+// the tap cache (key[] = the cell they belong to): a ray stays in one cell
+// for many steps, and a shared-memory row read replaces the gathers.  The
+// out-of-line cases still gather from the grid, with the same result.
+template <class C, bool LAYERED>
+__device__ __forceinline__ unsigned run_quantum(const DevMedium& m, const TraceArgs& a,
+                                                int64_t ray, RayF& s, bool& active,
+                                                float dopl_f, int* key, float* taps,
+                                                unsigned lane) {
+  unsigned ended = 0;
+  if constexpr (!C::kGrid) {
+#pragma unroll 1
+    for (int j = 0; j < kStepQuantum; ++j) {
+      if (active) {
+        active = step_ray<C, LAYERED>(m, a, ray, s, dopl_f);
+        if (!active) ++ended;
+      }
+    }
+  } else {
+    const float* col = taps + threadIdx.x * 4;
+#pragma unroll 1
+    for (int j = 0; j < kStepQuantum; ++j) {
+      float qh[3], ql[3], dv[3], fr[3];
+      bool need = false;
+      if (active) {
+        step_point(s, qh, ql, dv);
+        int i0[3];
+        C::cell(m, qh, i0, fr);
+        need = i0[0] != key[0] || i0[1] != key[1] || i0[2] != key[2];
+        key[0] = i0[0];
+        key[1] = i0[1];
+        key[2] = i0[2];
+      }
+      tap_fill(m, need, key, taps, lane);
+      if (active) {
+        float nu_i, g[3];
+        int lvl_i;
+        C::eval_taps(m, fr, col, nu_i, g[0], g[1], g[2], lvl_i);
+        // the step vector again here, so it is not held across the refill
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dv[k] = s.h * s.d[k];
+        active = step_from<C, LAYERED>(m, a, ray, s, dopl_f, qh, ql, dv, nu_i, g, lvl_i);
+        if (!active) ++ended;
+      }
+    }
+  }
+  return ended;
+}
+
+template <class C, bool LAYERED>
 __global__ void __launch_bounds__(128, C::kMinBlocks) k_trace_mixed(DevMedium m, TraceArgs a,
                                                      unsigned long long* queue) {
   const unsigned lane = threadIdx.x & 31u;
   const float dopl_f = (float)a.dopl;
+  __shared__ __align__(16) float taps[C::kGrid ? 16 * kTapRow : 4];
+  int key[3] = {INT_MIN, INT_MIN, INT_MIN};
   RayF s;
   bool active = false;
   bool exhausted = false;
@@ -688,10 +854,7 @@ __global__ void __launch_bounds__(128, C::kMinBlocks) k_trace_mixed(DevMedium m,
       if (exhausted) break;
       continue;
     }
-#pragma unroll 1
-    for (int k = 0; k < kStepQuantum; ++k) {
-      if (active) active = step_ray<C, LAYERED>(m, a, ray, s, dopl_f);
-    }
+    run_quantum<C, LAYERED>(m, a, ray, s, active, dopl_f, key, taps, lane);
   }
 }
 
@@ -721,7 +884,12 @@ static int launch_t(const DevMedium& m, const TraceArgs& a, unsigned long long* 
 template <int PC, bool GRID>
 static int launch_pc(const DevMedium& m, const TraceArgs& a, unsigned long long* q,
                      cudaStream_t s, int sm) {
-  if (m.n_levels > 0) return launch_t<PC, GRID, true, -1, -1>(m, a, q, s, sm);
+  if (m.n_levels > 0) {
+    if constexpr (GRID)
+      if (m.bkind == GRIN_BOUNDARY_BOX)
+        return launch_t<PC, GRID, true, GRIN_BOUNDARY_BOX, GRIN_FORM_LINEAR>(m, a, q, s, sm);
+    return launch_t<PC, GRID, true, -1, -1>(m, a, q, s, sm);
+  }
   const bool fast = m.bkind == GRIN_BOUNDARY_BOX && (GRID || m.form == GRIN_FORM_LINEAR);
   return fast ? launch_t<PC, GRID, false, GRIN_BOUNDARY_BOX, GRIN_FORM_LINEAR>(m, a, q, s, sm)
               : launch_t<PC, GRID, false, -1, -1>(m, a, q, s, sm);
@@ -764,6 +932,8 @@ __global__ void __launch_bounds__(128, C::kMinBlocks) k_serve_tick(DevMedium m, 
   const unsigned lane = threadIdx.x & 31u;
   const float dopl_f = (float)a.dopl;
   SlotState* me = slots + t;
+  __shared__ __align__(16) float taps[C::kGrid ? 16 * kTapRow : 4];
+  int key[3] = {INT_MIN, INT_MIN, INT_MIN};
   RayF s = me->s;
   bool active = me->active != 0;
   int64_t ray = me->ray;
@@ -791,13 +961,7 @@ __global__ void __launch_bounds__(128, C::kMinBlocks) k_serve_tick(DevMedium m, 
       if (exhausted) break;
       continue;
     }
-#pragma unroll 1
-    for (int j = 0; j < kStepQuantum; ++j) {
-      if (active) {
-        active = step_ray<C, LAYERED>(m, a, ray, s, dopl_f);
-        if (!active) ++done;
-      }
-    }
+    done += run_quantum<C, LAYERED>(m, a, ray, s, active, dopl_f, key, taps, lane);
   }
   me->s = s;
   me->active = active ? 1 : 0;
@@ -819,7 +983,13 @@ static int tick_t(const DevMedium& m, const TraceArgs& a, void* slots, int nslot
 template <int PC, bool GRID>
 static int tick_pc(const DevMedium& m, const TraceArgs& a, void* slots, int nslots,
                    unsigned long long* counters, int quantum, cudaStream_t st) {
-  if (m.n_levels > 0) return tick_t<PC, GRID, true, -1, -1>(m, a, slots, nslots, counters, quantum, st);
+  if (m.n_levels > 0) {
+    if constexpr (GRID)
+      if (m.bkind == GRIN_BOUNDARY_BOX)
+        return tick_t<PC, GRID, true, GRIN_BOUNDARY_BOX, GRIN_FORM_LINEAR>(m, a, slots, nslots,
+                                                                          counters, quantum, st);
+    return tick_t<PC, GRID, true, -1, -1>(m, a, slots, nslots, counters, quantum, st);
+  }
   const bool fast = m.bkind == GRIN_BOUNDARY_BOX && (GRID || m.form == GRIN_FORM_LINEAR);
   return fast ? tick_t<PC, GRID, false, GRIN_BOUNDARY_BOX, GRIN_FORM_LINEAR>(m, a, slots, nslots,
                                                                              counters, quantum, st)
