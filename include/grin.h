@@ -218,7 +218,15 @@ int grin_trace(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
 
 /* Same as grin_trace with rays and out in HOST memory: the library copies the
  * rays to context-owned device buffers, traces, copies the results back and
- * synchronises `cuda_stream` before returning. */
+ * synchronises before returning (no copy is in flight on return).  A batch
+ * of at least 262,144 rays is split into up to 8 chunks of at least 131,072
+ * rays, pipelined on four streams the context owns (created on first use):
+ * the upload of the next chunk and the download of the previous one overlap
+ * the trace of the current one, and the work starts after what is already
+ * queued on `cuda_stream`.  Each ray's result is bitwise the same as one
+ * grin_trace over the whole batch.  Pinned host buffers let the copies run
+ * asynchronously; pageable ones work but serialise them.  Errors: as
+ * grin_trace, plus GRIN_ERR_OOM if the staging buffers cannot grow. */
 int grin_trace_host(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
                     const grin_params* params, const grin_out* out, void* cuda_stream);
 

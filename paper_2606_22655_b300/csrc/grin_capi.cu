@@ -90,6 +90,10 @@ int grin_ctx_destroy(grin_ctx ctx) {
   cudaFree(ctx->queues);
   if (ctx->stage) cudaFree(ctx->stage);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+  for (cudaStream_t h : ctx->hs)
+    if (h) cudaStreamDestroy(h);
+  for (cudaEvent_t e : ctx->hev)
+    if (e) cudaEventDestroy(e);
   delete ctx;
   return GRIN_OK;
 }
@@ -433,6 +437,32 @@ int grin_trace(grin_ctx ctx, grin_medium medium, const grin_rays* rays, const gr
   return GRIN_OK;
 }
 
+// The streams and events of grin_trace_host's pipeline, created once.
+static bool host_pipeline(grin_ctx ctx) {
+  if (ctx->hs[0]) return true;
+  bool ok = true;
+  for (cudaStream_t& h : ctx->hs)
+    ok = ok && cudaStreamCreateWithFlags(&h, cudaStreamNonBlocking) == cudaSuccess;
+  for (cudaEvent_t& e : ctx->hev)
+    ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+  if (ok) return true;
+  cudaGetLastError();
+  for (cudaStream_t& h : ctx->hs)
+    if (h) cudaStreamDestroy(h), h = nullptr;
+  for (cudaEvent_t& e : ctx->hev)
+    if (e) cudaEventDestroy(e), e = nullptr;
+  return false;
+}
+
+static grin_rays rays_at(const grin_rays& r, const void* const* base, int64_t off, int64_t cnt,
+                         size_t esz) {
+  grin_rays c = r;
+  const void** f[6] = {&c.ox, &c.oy, &c.oz, &c.dx, &c.dy, &c.dz};
+  for (int k = 0; k < 6; ++k) *f[k] = (const char*)base[k] + off * esz;
+  c.count = cnt;
+  return c;
+}
+
 int grin_trace_host(grin_ctx ctx, grin_medium medium, const grin_rays* rays, const grin_params* p,
                     const grin_out* out, void* cuda_stream) {
   int st = check_trace_args(ctx, medium, rays, p, out);
@@ -461,37 +491,84 @@ int grin_trace_host(grin_ctx ctx, grin_medium medium, const grin_rays* rays, con
   char* base = (char*)ctx->stage;
   const void* hin[6] = {rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz};
   const void* din[6];
-  for (int k = 0; k < 6; ++k) {
-    din[k] = base + k * esz * (size_t)n;
-    if (cudaMemcpyAsync((void*)din[k], hin[k], esz * (size_t)n, cudaMemcpyHostToDevice, s) !=
-        cudaSuccess)
-      return GRIN_ERR_CUDA;
-  }
+  for (int k = 0; k < 6; ++k) din[k] = base + k * esz * (size_t)n;
   char* ob = base + in_bytes;
   double* dd[7];
   for (int k = 0; k < 7; ++k) dd[k] = (double*)(ob + k * 8 * (size_t)n);
   int32_t* di[4];
   for (int k = 0; k < 4; ++k) di[k] = (int32_t*)(ob + 56 * (size_t)n + k * 4 * (size_t)n);
-  grin_rays dr = *rays;
-  dr.ox = din[0];
-  dr.oy = din[1];
-  dr.oz = din[2];
-  dr.dx = din[3];
-  dr.dy = din[4];
-  dr.dz = din[5];
-  grin_out dout = {dd[0], dd[1], dd[2], dd[3], dd[4], dd[5], dd[6], di[0], di[1], di[2], di[3]};
-  st = grin_trace(ctx, medium, &dr, p, &dout, cuda_stream);
-  if (st != GRIN_OK) return st;
   double* hd[7] = {out->px, out->py, out->pz, out->dx, out->dy, out->dz, out->opl};
   int32_t* hi[4] = {out->exit_id, out->steps, out->tir_internal, out->tir_boundary};
-  for (int k = 0; k < 7; ++k)
-    if (cudaMemcpyAsync(hd[k], dd[k], 8 * (size_t)n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+
+  // Chunks of at least kHostChunkMin rays (a multiple of 1024), at most
+  // kHostChunks of them; a batch below two chunks runs as one.
+  int64_t chunk = n;
+  if (n >= 2 * grin::kHostChunkMin) {
+    chunk = (n + grin::kHostChunks - 1) / grin::kHostChunks;
+    chunk = std::max<int64_t>(grin::kHostChunkMin, (chunk + 1023) / 1024 * 1024);
+  }
+  const int nchunks = (int)((n + chunk - 1) / chunk);
+  const bool piped = nchunks > 1 && host_pipeline(ctx);
+  // Upload, trace, download of chunk i are ordered by events; chunk i + 1's
+  // upload and chunk i - 1's download overlap chunk i's trace, and the traces
+  // alternate between two streams so that the next chunk's kernel takes over
+  // the SMs the previous one frees.  A single chunk runs on the caller's
+  // stream.
+  cudaStream_t up = piped ? ctx->hs[0] : s, down = piped ? ctx->hs[3] : s;
+  if (piped) {
+    cudaEvent_t start = ctx->hev[2 * grin::kHostChunks];
+    bool ok = cudaEventRecord(start, s) == cudaSuccess;
+    for (cudaStream_t h : ctx->hs) ok = ok && cudaStreamWaitEvent(h, start, 0) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
       return GRIN_ERR_CUDA;
-  for (int k = 0; k < 4; ++k)
-    if (cudaMemcpyAsync(hi[k], di[k], 4 * (size_t)n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-      return GRIN_ERR_CUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return GRIN_ERR_CUDA;
-  return GRIN_OK;
+    }
+  }
+  int launches = 0;
+  for (int i = 0; i < (piped ? nchunks : 1) && st == GRIN_OK; ++i) {
+    const int64_t off = piped ? (int64_t)i * chunk : 0;
+    const int64_t cnt = piped ? std::min<int64_t>(chunk, n - off) : n;
+    cudaStream_t ts = piped ? ctx->hs[1 + (i & 1)] : s;
+    for (int k = 0; k < 6 && st == GRIN_OK; ++k)
+      if (cudaMemcpyAsync((char*)din[k] + off * esz, (const char*)hin[k] + off * esz,
+                          esz * (size_t)cnt, cudaMemcpyHostToDevice, up) != cudaSuccess)
+        st = GRIN_ERR_CUDA;
+    if (st == GRIN_OK && piped &&
+        (cudaEventRecord(ctx->hev[2 * i], up) != cudaSuccess ||
+         cudaStreamWaitEvent(ts, ctx->hev[2 * i], 0) != cudaSuccess))
+      st = GRIN_ERR_CUDA;
+    if (st != GRIN_OK) break;
+    grin_rays dr = rays_at(*rays, din, off, cnt, esz);
+    grin_out dout = {dd[0] + off, dd[1] + off, dd[2] + off, dd[3] + off, dd[4] + off, dd[5] + off,
+                     dd[6] + off, di[0] + off, di[1] + off, di[2] + off, di[3] + off};
+    st = grin_trace(ctx, medium, &dr, p, &dout, ts);
+    if (st != GRIN_OK) break;
+    launches += ctx->last_launches;
+    if (piped && (cudaEventRecord(ctx->hev[2 * i + 1], ts) != cudaSuccess ||
+                  cudaStreamWaitEvent(down, ctx->hev[2 * i + 1], 0) != cudaSuccess)) {
+      st = GRIN_ERR_CUDA;
+      break;
+    }
+    for (int k = 0; k < 7 && st == GRIN_OK; ++k)
+      if (cudaMemcpyAsync(hd[k] + off, dd[k] + off, 8 * (size_t)cnt, cudaMemcpyDeviceToHost,
+                          down) != cudaSuccess)
+        st = GRIN_ERR_CUDA;
+    for (int k = 0; k < 4 && st == GRIN_OK; ++k)
+      if (cudaMemcpyAsync(hi[k] + off, di[k] + off, 4 * (size_t)cnt, cudaMemcpyDeviceToHost,
+                          down) != cudaSuccess)
+        st = GRIN_ERR_CUDA;
+  }
+  // Nothing may still read or write the caller's buffers when this returns.
+  bool synced = true;
+  if (piped)
+    for (cudaStream_t h : ctx->hs) synced = cudaStreamSynchronize(h) == cudaSuccess && synced;
+  synced = cudaStreamSynchronize(s) == cudaSuccess && synced;
+  if (st != GRIN_OK) {
+    cudaGetLastError();
+    return st;
+  }
+  ctx->last_launches = launches;
+  return synced ? GRIN_OK : GRIN_ERR_CUDA;
 }
 
 int grin_trace_adjoint_workspace_size(grin_medium medium, int64_t ray_count, const grin_params* p,

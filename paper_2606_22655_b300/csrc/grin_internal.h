@@ -82,6 +82,11 @@ int launch_serve_tick(const DevMedium& m, const TraceArgs& a, void* slots, int n
 
 constexpr int kQueueSlots = 4096;
 
+// grin_trace_host pipelines batches of at least 2 * kHostChunkMin rays in up
+// to kHostChunks chunks (each at least kHostChunkMin rays).
+constexpr int kHostChunks = 8;
+constexpr int64_t kHostChunkMin = 131072;
+
 // Claim order for the mixed tracer on gridded media (ray_order.cu): rays
 // bucketed by the cell of the medium's bounding box where they enter it.
 // Used from this many rays.
@@ -144,6 +149,11 @@ struct grin_ctx_s {
   // stream-ordered pool for the per-call claim-order scratch of the mixed
   // tracer (created on first use; keeps freed blocks for reuse)
   cudaMemPool_t pool = nullptr;
+  // grin_trace_host's pipeline (created on first use): upload stream, two
+  // trace streams, download stream; per chunk an upload and a trace event;
+  // and an event marking the caller's stream
+  cudaStream_t hs[4] = {};
+  cudaEvent_t hev[2 * grin::kHostChunks + 1] = {};
 };
 
 struct grin_medium_s {

@@ -288,6 +288,19 @@ def test_grid_mixed_error_stated(ctx, blob64):
     stated32(g32, g64, wl.l_ref, flags32(o), 0.97, 2e-3)
 
 
+@pytest.mark.parametrize("res", [7, 8])
+def test_small_grid_mixed_error_stated(ctx, res):
+    """Coarse grids, where a large share of the stencils reach past a face
+    and are edge-clamped: the mixed tracer's tap cache is refilled with the
+    clamped taps (nx = 8: rows on 16-byte boundaries; nx = 7: not)."""
+    wl = W.blob_workload(n_rays=2000, res=res)
+    g64 = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "fp64")
+    g32 = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "mixed")
+    o = orc(wl.medium, wl.rays, wl.dopl, wl.max_steps)
+    check64(g64, o, wl.l_ref)
+    stated32(g32, g64, wl.l_ref, flags32(o), 0.97, 2e-3)
+
+
 def test_layered_fp64_matches_oracle(ctx):
     wl = W.blob_workload(n_rays=2000, res=64, n_levels=32)
     g = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "fp64")
@@ -414,6 +427,25 @@ def test_trace_host_equals_device(ctx):
     host = tracer.to_numpy(tracer.trace_host(ctx, med, rb, wl.dopl, wl.max_steps, "mixed"))
     for k in dev:
         np.testing.assert_array_equal(dev[k], host[k])
+
+
+@pytest.mark.parametrize("kind", ["freeform", "grid"])
+def test_trace_host_pipelined_equals_device(ctx, kind):
+    """A host batch of at least 262,144 rays is traced in chunks whose copies
+    overlap the traces (here 131,072 + 131,072 + 37,856 rays).  Every result
+    must be bitwise that of one device trace of the whole batch, and the call
+    reports each chunk's launches (a grid chunk of at least 65,536 rays adds
+    its three ordering kernels)."""
+    n = 300000
+    wl = W.freeform_workload(n) if kind == "freeform" else W.blob_workload(n_rays=n, res=64)
+    med = tracer.Medium(ctx, wl.medium)
+    dev = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "mixed", med=med)
+    rb = tracer.RayBatch.from_numpy(wl.rays.origins, wl.rays.dirs, device="cpu", dtype=torch.float64,
+                                    pin=True)
+    host = tracer.to_numpy(tracer.trace_host(ctx, med, rb, wl.dopl, wl.max_steps, "mixed"))
+    assert ctx.last_launches() == (3 if kind == "freeform" else 4 + 4 + 1)
+    for k in dev:
+        np.testing.assert_array_equal(dev[k], host[k], err_msg=k)
 
 
 @pytest.mark.parametrize("levels", [0, 32])
