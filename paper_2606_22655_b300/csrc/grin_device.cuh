@@ -140,19 +140,20 @@ __device__ __forceinline__ void field_vg(const T* c, T x, T y, T z, T& p, T& px,
 // ------------------------------------------------------- tricubic gathers
 
 // Catmull-Rom (Keys cubic convolution, a = -1/2) weights for the taps at -1,
-// 0, 1, 2 of the cell containing fraction t, and their t-derivatives.
+// 0, 1, 2 of the cell containing fraction t, and their t-derivatives, in
+// Horner form with the halves folded into the coefficients (18 operations).
 template <typename T>
 __device__ __forceinline__ void cr_w(T t, T* w, T* dw) {
-  const T h = T(0.5);
-  T t2 = t * t;
-  w[0] = h * t * fmadd(t, T(2) - t, T(-1));           // (-t^3 + 2t^2 - t) / 2
-  w[1] = h * fmadd(t2, fmadd(T(3), t, T(-5)), T(2));    // (3t^3 - 5t^2 + 2) / 2
-  w[2] = h * t * fmadd(t, fmadd(T(-3), t, T(4)), T(1));  // (-3t^3 + 4t^2 + t) / 2
-  w[3] = h * t2 * (t - T(1));                        // (t^3 - t^2) / 2
-  dw[0] = h * fmadd(t, fmadd(T(-3), t, T(4)), T(-1));    // (-3t^2 + 4t - 1) / 2
-  dw[1] = h * t * fmadd(T(9), t, T(-10));              // (9t^2 - 10t) / 2
-  dw[2] = h * fmadd(t, fmadd(T(-9), t, T(8)), T(1));     // (-9t^2 + 8t + 1) / 2
-  dw[3] = h * t * fmadd(T(3), t, T(-2));               // (3t^2 - 2t) / 2
+  const T t2 = t * t;
+  const T b = fmadd(T(-1.5), t, T(2));
+  w[0] = t * fmadd(fmadd(T(-0.5), t, T(1)), t, T(-0.5));  // (-t^3 + 2t^2 - t) / 2
+  w[1] = fmadd(t2, fmadd(T(1.5), t, T(-2.5)), T(1));       // (3t^3 - 5t^2 + 2) / 2
+  w[2] = t * fmadd(b, t, T(0.5));                         // (-3t^3 + 4t^2 + t) / 2
+  w[3] = t2 * fmadd(T(0.5), t, T(-0.5));                  // (t^3 - t^2) / 2
+  dw[0] = fmadd(b, t, T(-0.5));                           // (-3t^2 + 4t - 1) / 2
+  dw[1] = t * fmadd(T(4.5), t, T(-5));                    // (9t^2 - 10t) / 2
+  dw[2] = fmadd(fmadd(T(-4.5), t, T(4)), t, T(0.5));      // (-9t^2 + 8t + 1) / 2
+  dw[3] = t * fmadd(T(1.5), t, T(-1));                    // (3t^2 - 2t) / 2
 }
 
 // Interpolated (sample - sub) and its gradient in grid units, from 64 taps
