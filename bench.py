@@ -248,15 +248,16 @@ def serve_load(ctx, dev_index: int, rates, jobs_per_rate: int, seed: int = 7):
             "sweep": results, "ticks": st["ticks"], "failed": st["failed"]}
 
 
-def adjoint_timing(ctx, dev):
+def adjoint_timing(ctx, dev, n_rays=1 << 18):
     """One gradient of the image-plane design loss (16 target spots on
-    z = 30 mm) with respect to the 128^3 blob grid: 262,144 collimated rays,
-    dL0 = 0.02 mm (up to 2000 steps), checkpoints every 64 steps; the
-    FP64 forward sweep with checkpoints plus the backward sweep."""
+    z = 30 mm) with respect to the 128^3 blob grid: 262,144 collimated rays
+    (or n_rays, to profile a smaller case), dL0 = 0.02 mm (up to 2000 steps),
+    checkpoints every 64 steps; the FP64 forward sweep with checkpoints plus
+    the backward sweep."""
     import torch
     from paper_2606_22655_b300 import tracer
     from paper_2606_22655_b300 import workloads as W
-    wl = W.blob_workload(n_rays=1 << 18, res=128)
+    wl = W.blob_workload(n_rays=n_rays, res=128)
     med = tracer.Medium(ctx, wl.medium)
     rays = tracer.RayBatch.from_numpy(wl.rays.origins, wl.rays.dirs, device=dev, dtype=torch.float64)
     n = rays.count
@@ -270,7 +271,7 @@ def adjoint_timing(ctx, dev):
     torch.cuda.synchronize(dev)
     t = e0.elapsed_time(e1) / 1e3
     steps = float(out["steps"].sum())
-    return {"workload": "grid_128 adjoint, 262144 rays, dL0 0.02 mm, K=64", "seconds": t,
+    return {"workload": f"grid_128 adjoint, {n} rays, dL0 0.02 mm, K=64", "seconds": t,
             "forward_ray_steps": steps, "ray_steps_per_s_fwd_plus_bwd": steps / t,
             "precision": "fp64", "gradient_params": int(wl.medium.grid.size)}
 
@@ -544,10 +545,25 @@ def main():
                     help="freeform (the benchmark), or another medium for profiling")
     ap.add_argument("--profile-only", action="store_true",
                     help="timed steps only: no precision gate, e2e or CPU baseline")
+    ap.add_argument("--adjoint-only", type=int, default=0, metavar="RAYS",
+                    help="only the adjoint timing, on RAYS rays (to profile its kernels)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.adjoint_only:
+        return run_adjoint_only(args.adjoint_only)
     return run_ours(args)
+
+
+def run_adjoint_only(n_rays: int) -> int:
+    """The adjoint timing alone (one warm-up call, one timed call) on one GPU."""
+    import torch
+    from paper_2606_22655_b300 import tracer
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ctx = tracer.Context(0)
+    print(json.dumps(dict(adjoint_only=True, **adjoint_timing(ctx, dev, n_rays))), flush=True)
+    return 0
 
 
 if __name__ == "__main__":
