@@ -21,6 +21,9 @@ Parity status per function (pins live in tests/test_oracle_pins.py):
     of the samples at nodes;
   - layered shells: pinned by Snell's law at a planar level crossing;
   - tangent incidence (case iv): pinned by its closed-form first arc;
+  - forward-mode tangents (trace_tangent, polynomial n = p in a box): values
+    and decisions bitwise those of trace; derivatives pinned against central
+    differences of trace, inside the medium and through the exit;
   - freeform and blob media as a whole: parity unpinned beyond the
     invariants above (no closed form exists).
 """
@@ -84,6 +87,9 @@ def _load():
         lib.orc_trace_path.argtypes = [ctypes.POINTER(_Medium), ctypes.POINTER(_Params), dp, dp,
                                        dp, dp, dp, ip, ip, ip, ip, dp, dp, ctypes.c_int64,
                                        ctypes.POINTER(ctypes.c_int64)]
+        lib.orc_trace_tangent.argtypes = [ctypes.POINTER(_Medium), ctypes.POINTER(_Params),
+                                          ctypes.c_int64, dp, dp, dp, dp, dp, ip, ip, dp, dp, dp,
+                                          ip, ctypes.c_int32]
         _lib = lib
     return _lib
 
@@ -175,3 +181,31 @@ def trace_path(medium, origin, direction, dopl: float, max_steps: int, cap: Opti
                        ip(out["tir_internal"]), ip(out["tir_boundary"]), _ptr(out["margins"]),
                        _ptr(path), cap, ctypes.byref(plen))
     return out, path[: plen.value]
+
+
+def trace_tangent(medium, origins, dirs, dopl: float, max_steps: int,
+                  threads: Optional[int] = None) -> Dict[str, np.ndarray]:
+    """Exit state of every ray (as `trace`) and its forward-mode derivative
+    with respect to each polynomial coefficient: tP, td (n, nc, 3), topl
+    (n, nc); flag (n,) marks rays whose tangents are not followed
+    (tangential incidence, clamped crossing fraction).  Polynomial media with
+    n = p in a box only."""
+    lib = _load()
+    b = _Bound(medium)
+    o = np.ascontiguousarray(origins, dtype=np.float64).reshape(-1, 3)
+    d = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+    n = o.shape[0]
+    nc = (medium.degree + 1) * (medium.degree + 2) * (medium.degree + 3) // 6
+    out = dict(P=np.zeros((n, 3)), d=np.zeros((n, 3)), opl=np.zeros(n),
+               exit_id=np.zeros(n, np.int32), steps=np.zeros(n, np.int32),
+               tP=np.zeros((n, nc, 3)), td=np.zeros((n, nc, 3)), topl=np.zeros((n, nc)),
+               flag=np.zeros(n, np.int32))
+    prm = _Params(float(dopl), int(max_steps))
+    ip = lambda a: _ptr(a, ctypes.c_int32)
+    rc = lib.orc_trace_tangent(ctypes.byref(b.s), ctypes.byref(prm), n, _ptr(o), _ptr(d),
+                               _ptr(out["P"]), _ptr(out["d"]), _ptr(out["opl"]), ip(out["exit_id"]),
+                               ip(out["steps"]), _ptr(out["tP"]), _ptr(out["td"]), _ptr(out["topl"]),
+                               ip(out["flag"]), int(threads or os.cpu_count() or 1))
+    if rc != 0:
+        raise ValueError("trace_tangent: polynomial media with n = p in a box only")
+    return out

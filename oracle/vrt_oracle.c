@@ -783,3 +783,352 @@ int orc_trace_path(const orc_medium* m, const orc_params* p, const double* o, co
   store(&j, 0, &r);
   return 0;
 }
+
+/* ------------------------------------------------- forward-mode tangents */
+
+/* Hessian of p in physical coordinates and, per monomial, its value phi and
+ * gradient gphi at P (the derivatives of n = p and grad n with respect to
+ * each coefficient); p and grad p themselves come from poly_eval. */
+static void poly_second(const orc_medium* m, const double* P, double H[3][3], double* phi,
+                        double (*gphi)[3]) {
+  double x[3];
+  for (int a = 0; a < 3; ++a) x[a] = (P[a] - m->off[a]) / m->scale[a];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) H[a][b] = 0.0;
+  int idx = 0;
+  for (int s = 0; s <= m->degree; ++s) {
+    for (int i = s; i >= 0; --i) {
+      for (int j = s - i; j >= 0; --j) {
+        int e[3] = {i, j, s - i - j};
+        double v[3], d1[3], d2[3]; /* x_a^e, its first and second derivatives */
+        for (int a = 0; a < 3; ++a) {
+          v[a] = ipow(x[a], e[a]);
+          d1[a] = e[a] > 0 ? (double)e[a] * ipow(x[a], e[a] - 1) : 0.0;
+          d2[a] = e[a] > 1 ? (double)(e[a] * (e[a] - 1)) * ipow(x[a], e[a] - 2) : 0.0;
+        }
+        phi[idx] = v[0] * v[1] * v[2];
+        gphi[idx][0] = d1[0] * v[1] * v[2] / m->scale[0];
+        gphi[idx][1] = v[0] * d1[1] * v[2] / m->scale[1];
+        gphi[idx][2] = v[0] * v[1] * d1[2] / m->scale[2];
+        double c = m->coeffs[idx];
+        for (int a = 0; a < 3; ++a) {
+          for (int b = 0; b < 3; ++b) {
+            double t = 1.0;
+            for (int q = 0; q < 3; ++q) {
+              if (a == b && q == a) t = t * d2[q];
+              else if (q == a || q == b) t = t * d1[q];
+              else t = t * v[q];
+            }
+            H[a][b] += c * t / (m->scale[a] * m->scale[b]);
+          }
+        }
+        ++idx;
+      }
+    }
+  }
+}
+
+/* Tangent of refract_or_reflect's unit result R for tangents dI, dN, dmu of
+ * its arguments, in the case (refraction, or reflection when tir) that the
+ * value took: the chain rule through c = N.I, D, gamma (Eq. 9), R = mu I +
+ * gamma N (Eq. 8) or I - 2 c N, and the renormalisation. */
+static void refract_tangent(const double* I, const double* N, double mu, int tir,
+                            const double* dI, const double* dN, double dmu, double* dR) {
+  double c = dot3(N, I);
+  double dc = dot3(dN, I) + dot3(N, dI);
+  double Rr[3], dRr[3];
+  if (tir) {
+    for (int a = 0; a < 3; ++a) {
+      Rr[a] = I[a] - 2.0 * c * N[a];
+      dRr[a] = dI[a] - 2.0 * (dc * N[a] + c * dN[a]);
+    }
+  } else {
+    double D = 1.0 - mu * mu * (1.0 - c * c);
+    double dD = -2.0 * mu * dmu * (1.0 - c * c) + 2.0 * mu * mu * c * dc;
+    double s = c > 0.0 ? 1.0 : (c < 0.0 ? -1.0 : 0.0);
+    double sq = sqrt(D);
+    double gamma = -mu * c + s * sq;
+    double dgamma = -dmu * c - mu * dc + s * dD / (2.0 * sq);
+    for (int a = 0; a < 3; ++a) {
+      Rr[a] = mu * I[a] + gamma * N[a];
+      dRr[a] = dmu * I[a] + mu * dI[a] + dgamma * N[a] + gamma * dN[a];
+    }
+  }
+  double L = norm3(Rr);
+  double R[3] = {Rr[0] / L, Rr[1] / L, Rr[2] / L};
+  double p = dot3(R, dRr);
+  for (int a = 0; a < 3; ++a) dR[a] = (dRr[a] - R[a] * p) / L;
+}
+
+/* Per coefficient j the tangents carried along a ray. */
+typedef struct {
+  double P[3], d[3], Q[3], n_prev, h, opl;
+} tangent;
+
+/* One ray of a polynomial medium with n = p in a box: trace_one's values and
+ * decisions (the same operations, in the same order), with every continuous
+ * quantity also carrying its derivative with respect to each of the nc
+ * coefficients.  The entry point does not depend on the coefficients; at the
+ * exit the crossing fraction t = (b - P_a) / (Q_a - P_a) carries one.
+ * Returns 1 when the ray met a case the tangents do not follow (tangential
+ * incidence N.I == 0, or a crossing fraction clamped to [0, 1]). */
+static int tangent_one(const orc_medium* m, const orc_params* prm, const double* o,
+                       const double* d0, ray_out* out, int nc, tangent* T, double* phi,
+                       double (*gphi)[3]) {
+  double P[3] = {o[0], o[1], o[2]}, d[3] = {d0[0], d0[1], d0[2]};
+  nsum opl = {0.0, 0.0};
+  int flag = 0;
+  memset(out, 0, sizeof(*out));
+  memset(T, 0, (size_t)nc * sizeof(tangent));
+  out->exit_id = EXIT_INVALID;
+  for (int a = 0; a < 3; ++a) {
+    out->P[a] = o[a];
+    out->d[a] = d0[a];
+  }
+  if (!finite3(P) || !finite3(d) || norm3(d) == 0.0) return 0;
+  normalize3(d);
+  const double zero[3] = {0.0, 0.0, 0.0};
+
+  double n_prev, g[3], H[3][3];
+  if (inside(m, P)) {
+    poly_eval(m, P, &n_prev, g);
+    poly_second(m, P, H, phi, gphi);
+    for (int j = 0; j < nc; ++j) T[j].n_prev = phi[j];
+  } else {
+    double t, Pb[3], NB[3], Dm;
+    int face;
+    if (!enter(m, P, d, &t, Pb, NB, &face)) {
+      out->exit_id = EXIT_MISS;
+      for (int a = 0; a < 3; ++a) out->d[a] = d[a];
+      return 0;
+    }
+    nsum_add(&opl, m->n_ext * t);
+    for (int a = 0; a < 3; ++a) P[a] = Pb[a];
+    double n_b;
+    poly_eval(m, P, &n_b, g);
+    poly_second(m, P, H, phi, gphi);
+    double R[3];
+    double mu = m->n_ext / n_b;
+    int tir = refract_or_reflect(d, NB, mu, R, &Dm);
+    for (int j = 0; j < nc; ++j) {
+      double dmu = -m->n_ext * phi[j] / (n_b * n_b);
+      refract_tangent(d, NB, mu, tir, zero, zero, dmu, T[j].d);
+      T[j].n_prev = phi[j];
+    }
+    for (int a = 0; a < 3; ++a) d[a] = R[a];
+    if (tir) {
+      out->exit_id = EXIT_ENTRY_REFLECT;
+      goto done;
+    }
+    n_prev = n_b;
+  }
+  if (!(isfinite(n_prev) && n_prev > 0.0)) {
+    out->exit_id = EXIT_INVALID;
+    goto done;
+  }
+
+  double dopl = prm->dopl;
+  double h = dopl / n_prev;
+  double Q[3];
+  for (int a = 0; a < 3; ++a) Q[a] = P[a] + h * d[a];
+  for (int j = 0; j < nc; ++j) {
+    T[j].h = -dopl * T[j].n_prev / (n_prev * n_prev);
+    for (int a = 0; a < 3; ++a) T[j].Q[a] = T[j].P[a] + T[j].h * d[a] + h * T[j].d[a];
+  }
+  int steps = 0;
+  out->exit_id = EXIT_MAXSTEPS;
+  while (steps < prm->max_steps) {
+    if (!inside(m, Q)) {
+      double t, Pb[3], NB[3], R[3], Dm;
+      int face;
+      exit_root(m, P, Q, &t, Pb, NB, &face);
+      int ax = face / 2;
+      double bv = (face & 1) ? m->b[3 + ax] : m->b[ax];
+      double Da = Q[ax] - P[ax];
+      double traw = (bv - P[ax]) / Da;
+      int clamped = !(traw > 0.0) || traw > 1.0;
+      if (clamped) flag = 1;
+      for (int j = 0; j < nc; ++j) {
+        double dDa = T[j].Q[ax] - T[j].P[ax];
+        double dt = clamped ? 0.0 : (-T[j].P[ax] * Da - (bv - P[ax]) * dDa) / (Da * Da);
+        double dPb[3];
+        for (int a = 0; a < 3; ++a)
+          dPb[a] = T[j].P[a] + dt * (Q[a] - P[a]) + t * (T[j].Q[a] - T[j].P[a]);
+        dPb[ax] = 0.0;
+        for (int a = 0; a < 3; ++a) T[j].P[a] = dPb[a];
+        T[j].opl += dt * dopl;
+      }
+      nsum_add(&opl, t * dopl);
+      ++steps;
+      for (int a = 0; a < 3; ++a) P[a] = Pb[a];
+      double mu = n_prev / m->n_ext;
+      int tir = refract_or_reflect(d, NB, mu, R, &Dm);
+      for (int j = 0; j < nc; ++j) {
+        double dd[3];
+        refract_tangent(d, NB, mu, tir, T[j].d, zero, T[j].n_prev / m->n_ext, dd);
+        for (int a = 0; a < 3; ++a) T[j].d[a] = dd[a];
+      }
+      for (int a = 0; a < 3; ++a) d[a] = R[a];
+      if (tir) {
+        ++out->tir_bnd;
+        h = dopl / n_prev;
+        for (int j = 0; j < nc; ++j) T[j].h = -dopl * T[j].n_prev / (n_prev * n_prev);
+        poly_eval(m, P, &n_prev, g);
+        poly_second(m, P, H, phi, gphi);
+        if (!(isfinite(n_prev) && n_prev > 0.0)) {
+          out->exit_id = EXIT_INVALID;
+          break;
+        }
+        for (int a = 0; a < 3; ++a) Q[a] = P[a] + h * d[a];
+        for (int j = 0; j < nc; ++j) {
+          T[j].n_prev = phi[j] + dot3(g, T[j].P);
+          for (int a = 0; a < 3; ++a) T[j].Q[a] = T[j].P[a] + T[j].h * d[a] + h * T[j].d[a];
+        }
+        continue;
+      }
+      out->exit_id = face;
+      break;
+    }
+    for (int a = 0; a < 3; ++a) P[a] = Q[a];
+    for (int j = 0; j < nc; ++j)
+      for (int a = 0; a < 3; ++a) T[j].P[a] = T[j].Q[a];
+    nsum_add(&opl, dopl);
+    ++steps;
+
+    double n_i;
+    poly_eval(m, P, &n_i, g);
+    poly_second(m, P, H, phi, gphi);
+    if (!(isfinite(n_i) && n_i > 0.0)) {
+      out->exit_id = EXIT_INVALID;
+      break;
+    }
+    double gn = norm3(g);
+    if (gn == 0.0 || !isfinite(gn)) {
+      for (int j = 0; j < nc; ++j) {
+        double dn_i = phi[j] + dot3(g, T[j].P);
+        T[j].n_prev = dn_i;
+        T[j].h = -dopl * dn_i / (n_i * n_i);
+      }
+      n_prev = n_i;
+      h = dopl / n_i;
+    } else {
+      double N[3] = {g[0] / gn, g[1] / gn, g[2] / gn};
+      double c = dot3(N, d);
+      double mu = n_prev / n_i;
+      if (c == 0.0) {
+        /* tangential incidence: trace_one's arc, value only */
+        flag = 1;
+        double hi = dopl / n_i;
+        double Pn[3] = {P[0] + hi * N[0], P[1] + hi * N[1], P[2] + hi * N[2]};
+        double n2, g2[3];
+        poly_eval(m, Pn, &n2, g2);
+        double k = (n2 - n_i) / (2.0 * n_i);
+        double w = 1.0 - k * k;
+        double a0 = w > 0.0 ? sqrt(w) : 0.0;
+        for (int a = 0; a < 3; ++a) d[a] = a0 * d[a] + k * N[a];
+        normalize3(d);
+        n_prev = n_i;
+        h = hi;
+      } else {
+        double R[3], Dm;
+        int tir = refract_or_reflect(d, N, mu, R, &Dm);
+        for (int j = 0; j < nc; ++j) {
+          double dn_i = phi[j] + dot3(g, T[j].P);
+          double dg[3], dN[3], dd[3];
+          for (int a = 0; a < 3; ++a)
+            dg[a] = gphi[j][a] + H[a][0] * T[j].P[0] + H[a][1] * T[j].P[1] + H[a][2] * T[j].P[2];
+          double Ndg = dot3(N, dg);
+          for (int a = 0; a < 3; ++a) dN[a] = (dg[a] - N[a] * Ndg) / gn;
+          double dmu = T[j].n_prev / n_i - n_prev * dn_i / (n_i * n_i);
+          refract_tangent(d, N, mu, tir, T[j].d, dN, dmu, dd);
+          for (int a = 0; a < 3; ++a) T[j].d[a] = dd[a];
+          T[j].h = tir ? -dopl * T[j].n_prev / (n_prev * n_prev) : -dopl * dn_i / (n_i * n_i);
+          T[j].n_prev = dn_i;
+        }
+        for (int a = 0; a < 3; ++a) d[a] = R[a];
+        if (tir) {
+          ++out->tir_int;
+          h = dopl / n_prev;
+        } else {
+          h = dopl / n_i;
+        }
+        n_prev = n_i;
+      }
+    }
+    for (int a = 0; a < 3; ++a) Q[a] = P[a] + h * d[a];
+    for (int j = 0; j < nc; ++j)
+      for (int a = 0; a < 3; ++a) T[j].Q[a] = T[j].P[a] + T[j].h * d[a] + h * T[j].d[a];
+  }
+  out->steps = steps;
+done:
+  for (int a = 0; a < 3; ++a) {
+    out->P[a] = P[a];
+    out->d[a] = d[a];
+  }
+  out->opl = opl.s + opl.c;
+  return flag;
+}
+
+typedef struct {
+  const orc_medium* m;
+  const orc_params* p;
+  int64_t n;
+  const double *o, *d;
+  double *P_out, *d_out, *opl, *tP, *td, *topl;
+  int32_t *exit_id, *steps, *flag;
+  int nc, tid, nt;
+} tjob;
+
+static void* tangent_worker(void* arg) {
+  tjob* j = (tjob*)arg;
+  tangent* T = (tangent*)malloc((size_t)j->nc * sizeof(tangent));
+  double* phi = (double*)malloc((size_t)j->nc * sizeof(double));
+  double(*gphi)[3] = (double(*)[3])malloc((size_t)j->nc * sizeof(*gphi));
+  ray_out r;
+  for (int64_t i = j->tid; i < j->n; i += j->nt) {
+    j->flag[i] = tangent_one(j->m, j->p, j->o + 3 * i, j->d + 3 * i, &r, j->nc, T, phi, gphi);
+    for (int a = 0; a < 3; ++a) {
+      j->P_out[3 * i + a] = r.P[a];
+      j->d_out[3 * i + a] = r.d[a];
+    }
+    j->opl[i] = r.opl;
+    j->exit_id[i] = r.exit_id;
+    j->steps[i] = r.steps;
+    for (int c = 0; c < j->nc; ++c) {
+      for (int a = 0; a < 3; ++a) {
+        j->tP[(i * j->nc + c) * 3 + a] = T[c].P[a];
+        j->td[(i * j->nc + c) * 3 + a] = T[c].d[a];
+      }
+      j->topl[i * j->nc + c] = T[c].opl;
+    }
+  }
+  free(T);
+  free(phi);
+  free(gphi);
+  return NULL;
+}
+
+int orc_trace_tangent(const orc_medium* m, const orc_params* p, int64_t n, const double* o,
+                      const double* d, double* P_out, double* d_out, double* opl,
+                      int32_t* exit_id, int32_t* steps, double* tP, double* td, double* topl,
+                      int32_t* flag, int32_t nthreads) {
+  if (m->kind != 0 || m->form != 0 || m->bkind != 0 || m->n_levels != 0 || m->degree < 0)
+    return -1;
+  int nc = (m->degree + 1) * (m->degree + 2) * (m->degree + 3) / 6;
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > 256) nthreads = 256;
+  tjob jobs[256];
+  pthread_t th[256];
+  for (int t = 0; t < nthreads; ++t) {
+    tjob j = {m, p, n, o, d, P_out, d_out, opl, tP, td, topl, exit_id, steps, flag, nc, t,
+              nthreads};
+    jobs[t] = j;
+  }
+  if (nthreads == 1) {
+    tangent_worker(&jobs[0]);
+    return 0;
+  }
+  for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, tangent_worker, &jobs[t]);
+  for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+  return 0;
+}

@@ -78,6 +78,22 @@ int orc_trace_path(const orc_medium* m, const orc_params* p, const double* o,
                    int32_t* tir_bnd, double* margins, double* path,
                    int64_t cap, int64_t* path_len);
 
+/* Forward-mode derivatives (tangents) of each ray's exit point, direction
+ * and optical path with respect to every coefficient of a polynomial medium
+ * with n = p in a box, without layering: the values and decisions of
+ * orc_trace_batch, each continuous quantity carrying its derivative through
+ * the step (Eq. 2-9), the exit crossing and the boundary refraction.  nc =
+ * (degree + 1)(degree + 2)(degree + 3) / 6; tP[3 nc n] and td[3 nc n] are
+ * laid out ray, then coefficient, then component; topl[nc n].  flag[i] = 1
+ * when ray i met tangential incidence (N.I == 0) or a crossing fraction
+ * clamped to [0, 1], which the tangents do not follow.  Returns -1 for any
+ * other medium, else 0. */
+int orc_trace_tangent(const orc_medium* m, const orc_params* p, int64_t n,
+                      const double* o, const double* d, double* P_out,
+                      double* d_out, double* opl, int32_t* exit_id,
+                      int32_t* steps, double* tP, double* td, double* topl,
+                      int32_t* flag, int32_t nthreads);
+
 #ifdef __cplusplus
 }
 #endif

@@ -565,3 +565,61 @@ def test_n2p_lens_reaches_the_paper_design_quality():
     assert e <= 5e-3
     e_off, _ = n2p_rmse_lsa(0.74, 4.3, 0.3)
     assert e_off > 10 * e
+
+
+# ------------------------------------------------- forward-mode tangents
+
+
+def _tangent_vs_fd(dopl, max_steps, coords, h=1e-6):
+    """Per coefficient: the oracle's tangent of (P, d) against the central
+    difference of oracle traces with the coefficient moved by +-h, on the
+    rays whose integer outcomes do not change and whose differences at h and
+    h / 2 agree to 1e-6 (there the differences' own error, truncation plus
+    rounding noise / h, is below that).  Returns the relative errors."""
+    m = W.freeform_block_medium()
+    rays = W.point_source_rays(64, W.BASE_SEED + 4)
+    t = oracle.trace_tangent(m, rays.origins, rays.dirs, dopl, max_steps)
+    base = oracle.trace(m, rays.origins, rays.dirs, dopl, max_steps)
+    for k in ("P", "d", "opl", "exit_id", "steps"):
+        np.testing.assert_array_equal(t[k], base[k], err_msg=k)  # same values, same decisions
+    errs = []
+    for i in coords:
+        keep = (t["flag"] == 0) & (base["exit_id"] != oracle.EXIT_MISS)
+        fds = []
+        for hh in (h, h / 2):
+            res = []
+            for s in (+hh, -hh):
+                mm = W.Medium(**{**m.__dict__})
+                c = m.coeffs.copy()
+                c[i] += s
+                mm.coeffs = c
+                res.append((oracle.trace(mm, rays.origins, rays.dirs, dopl, max_steps), c[i]))
+            (rp, vp), (rm, vm) = res
+            for k in ("exit_id", "steps", "tir_internal", "tir_boundary"):
+                keep &= (rp[k] == base[k]) & (rm[k] == base[k])
+            fds.append(np.concatenate([rp["P"] - rm["P"], rp["d"] - rm["d"]], 1) / (vp - vm))
+        a, b = fds
+        scale = np.abs(a).max(1) + 1e-300
+        keep &= np.abs(a - b).max(1) / scale <= 1e-6
+        tan = np.concatenate([t["tP"][:, i], t["td"][:, i]], 1)
+        errs.append((np.abs(tan - a).max(1) / scale)[keep])
+    return errs
+
+
+def test_tangents_match_central_differences_inside():
+    """Forward-mode derivatives of the ray state after 800 steps (no exit)
+    with respect to six of the 35 coefficients: within 5e-5 of the central
+    differences on every ray where those are accurate, with the median ray
+    within 1e-6.  A dropped term (the Hessian of n, the derivative of mu or
+    of the step length) gives O(1) errors on most rays."""
+    for e in _tangent_vs_fd(0.02, 800, (0, 1, 5, 12, 20, 34)):
+        assert e.size >= 20
+        assert e.max() <= 5e-5 and np.median(e) <= 1e-6, (e.max(), np.median(e))
+
+
+def test_tangents_match_central_differences_through_the_exit():
+    """The same through the exit crossing and the exit refraction: dL0 =
+    0.2 mm, so every ray leaves the block within about 160 steps."""
+    for e in _tangent_vs_fd(0.2, 20000, (0, 5, 20)):
+        assert e.size >= 20
+        assert e.max() <= 5e-5 and np.median(e) <= 1e-6, (e.max(), np.median(e))
