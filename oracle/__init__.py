@@ -21,9 +21,10 @@ Parity status per function (pins live in tests/test_oracle_pins.py):
     of the samples at nodes;
   - layered shells: pinned by Snell's law at a planar level crossing;
   - tangent incidence (case iv): pinned by its closed-form first arc;
-  - forward-mode tangents (trace_tangent, polynomial n = p in a box): values
-    and decisions bitwise those of trace; derivatives pinned against central
-    differences of trace, inside the medium and through the exit;
+  - forward-mode tangents (trace_tangent; polynomial coefficients with
+    n = p, or grid samples, in a box): values and decisions bitwise those of
+    trace; derivatives pinned against central differences of trace, inside
+    the medium, through the exit and at edge-clamped samples;
   - freeform and blob media as a whole: parity unpinned beyond the
     invariants above (no closed form exists).
 """
@@ -88,8 +89,9 @@ def _load():
                                        dp, dp, dp, ip, ip, ip, ip, dp, dp, ctypes.c_int64,
                                        ctypes.POINTER(ctypes.c_int64)]
         lib.orc_trace_tangent.argtypes = [ctypes.POINTER(_Medium), ctypes.POINTER(_Params),
-                                          ctypes.c_int64, dp, dp, dp, dp, dp, ip, ip, dp, dp, dp,
-                                          ip, ctypes.c_int32]
+                                          ctypes.c_int64, dp, dp, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_int64), dp, dp, dp, ip, ip, dp,
+                                          dp, dp, ip, ctypes.c_int32]
         _lib = lib
     return _lib
 
@@ -183,19 +185,25 @@ def trace_path(medium, origin, direction, dopl: float, max_steps: int, cap: Opti
     return out, path[: plen.value]
 
 
-def trace_tangent(medium, origins, dirs, dopl: float, max_steps: int,
+def trace_tangent(medium, origins, dirs, dopl: float, max_steps: int, samples=None,
                   threads: Optional[int] = None) -> Dict[str, np.ndarray]:
     """Exit state of every ray (as `trace`) and its forward-mode derivative
-    with respect to each polynomial coefficient: tP, td (n, nc, 3), topl
-    (n, nc); flag (n,) marks rays whose tangents are not followed
-    (tangential incidence, clamped crossing fraction).  Polynomial media with
-    n = p in a box only."""
+    with respect to each polynomial coefficient (polynomial media with n = p)
+    or to each grid sample in `samples` (flat indices, x fastest; grid
+    media): tP, td (n, nc, 3), topl (n, nc); flag (n,) marks rays whose
+    tangents are not followed (tangential incidence, clamped crossing
+    fraction).  Box boundaries, no layering."""
     lib = _load()
     b = _Bound(medium)
     o = np.ascontiguousarray(origins, dtype=np.float64).reshape(-1, 3)
     d = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
     n = o.shape[0]
-    nc = (medium.degree + 1) * (medium.degree + 2) * (medium.degree + 3) // 6
+    if samples is None:
+        nc = (medium.degree + 1) * (medium.degree + 2) * (medium.degree + 3) // 6
+        par = np.zeros(1, np.int64)
+    else:
+        par = np.ascontiguousarray(samples, dtype=np.int64).ravel()
+        nc = par.size
     out = dict(P=np.zeros((n, 3)), d=np.zeros((n, 3)), opl=np.zeros(n),
                exit_id=np.zeros(n, np.int32), steps=np.zeros(n, np.int32),
                tP=np.zeros((n, nc, 3)), td=np.zeros((n, nc, 3)), topl=np.zeros((n, nc)),
@@ -203,9 +211,10 @@ def trace_tangent(medium, origins, dirs, dopl: float, max_steps: int,
     prm = _Params(float(dopl), int(max_steps))
     ip = lambda a: _ptr(a, ctypes.c_int32)
     rc = lib.orc_trace_tangent(ctypes.byref(b.s), ctypes.byref(prm), n, _ptr(o), _ptr(d),
+                               0 if samples is None else nc, _ptr(par, ctypes.c_int64),
                                _ptr(out["P"]), _ptr(out["d"]), _ptr(out["opl"]), ip(out["exit_id"]),
                                ip(out["steps"]), _ptr(out["tP"]), _ptr(out["td"]), _ptr(out["topl"]),
                                ip(out["flag"]), int(threads or os.cpu_count() or 1))
     if rc != 0:
-        raise ValueError("trace_tangent: polynomial media with n = p in a box only")
+        raise ValueError("trace_tangent: polynomial (n = p) or grid media in a box, samples in range")
     return out

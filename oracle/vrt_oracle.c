@@ -860,21 +860,103 @@ static void refract_tangent(const double* I, const double* N, double mu, int tir
   for (int a = 0; a < 3; ++a) dR[a] = (dRr[a] - R[a] * p) / L;
 }
 
-/* Per coefficient j the tangents carried along a ray. */
+/* Tricubic interpolant: its Hessian in physical coordinates and, for each
+ * of the np samples params[] (flat index, x fastest), the derivative of f and
+ * grad f with respect to that sample at P.  A sample's weight is the product
+ * of its per-axis weights, each summed over the stencil taps that the edge
+ * clamp maps onto it. */
+static void grid_second(const orc_medium* m, const double* P, int np, const int64_t* params,
+                        double H[3][3], double* phi, double (*gphi)[3]) {
+  int n[3] = {m->nx, m->ny, m->nz};
+  int base[3];
+  double w[3][4], dw[3][4], ddw[3][4];
+  for (int a = 0; a < 3; ++a) {
+    double u = (P[a] - m->origin[a]) / m->spacing[a];
+    if (!(u > -2.0)) u = -2.0;
+    if (u > (double)n[a] + 1.0) u = (double)n[a] + 1.0;
+    double fl = floor(u), t = u - fl;
+    base[a] = (int)fl;
+    cr_weights(t, w[a], dw[a]);
+    ddw[a][0] = -3.0 * t + 2.0; /* second derivatives of the Keys weights */
+    ddw[a][1] = 9.0 * t - 5.0;
+    ddw[a][2] = -9.0 * t + 4.0;
+    ddw[a][3] = 3.0 * t - 1.0;
+  }
+  double hxx = 0.0, hyy = 0.0, hzz = 0.0, hxy = 0.0, hxz = 0.0, hyz = 0.0;
+  for (int c = 0; c < 4; ++c) {
+    int kk = clampi(base[2] - 1 + c, 0, n[2] - 1);
+    for (int b = 0; b < 4; ++b) {
+      int jj = clampi(base[1] - 1 + b, 0, n[1] - 1);
+      for (int a = 0; a < 4; ++a) {
+        int ii = clampi(base[0] - 1 + a, 0, n[0] - 1);
+        double s = (double)m->grid[((int64_t)kk * n[1] + jj) * n[0] + ii];
+        hxx += ddw[0][a] * w[1][b] * w[2][c] * s;
+        hyy += w[0][a] * ddw[1][b] * w[2][c] * s;
+        hzz += w[0][a] * w[1][b] * ddw[2][c] * s;
+        hxy += dw[0][a] * dw[1][b] * w[2][c] * s;
+        hxz += dw[0][a] * w[1][b] * dw[2][c] * s;
+        hyz += w[0][a] * dw[1][b] * dw[2][c] * s;
+      }
+    }
+  }
+  const double* sp = m->spacing;
+  H[0][0] = hxx / (sp[0] * sp[0]);
+  H[1][1] = hyy / (sp[1] * sp[1]);
+  H[2][2] = hzz / (sp[2] * sp[2]);
+  H[0][1] = H[1][0] = hxy / (sp[0] * sp[1]);
+  H[0][2] = H[2][0] = hxz / (sp[0] * sp[2]);
+  H[1][2] = H[2][1] = hyz / (sp[1] * sp[2]);
+  for (int q = 0; q < np; ++q) {
+    int64_t idx = params[q];
+    int want[3] = {(int)(idx % n[0]), (int)((idx / n[0]) % n[1]),
+                   (int)(idx / ((int64_t)n[0] * n[1]))};
+    double W[3], dW[3];
+    for (int a = 0; a < 3; ++a) {
+      W[a] = 0.0;
+      dW[a] = 0.0;
+      for (int t = 0; t < 4; ++t) {
+        if (clampi(base[a] - 1 + t, 0, n[a] - 1) == want[a]) {
+          W[a] += w[a][t];
+          dW[a] += dw[a][t];
+        }
+      }
+    }
+    phi[q] = W[0] * W[1] * W[2];
+    gphi[q][0] = dW[0] * W[1] * W[2] / sp[0];
+    gphi[q][1] = W[0] * dW[1] * W[2] / sp[1];
+    gphi[q][2] = W[0] * W[1] * dW[2] / sp[2];
+  }
+}
+
+/* n and grad n as trace_one samples them, and the second-order data of the
+ * tangents: polynomial coefficients (all of them) or grid samples params[]. */
+static void ref_eval(const orc_medium* m, const double* P, double* n, double* g) {
+  if (m->kind == 1) grid_eval(m, P, n, g);
+  else poly_eval(m, P, n, g);
+}
+
+static void ref_second(const orc_medium* m, const double* P, int np, const int64_t* params,
+                       double H[3][3], double* phi, double (*gphi)[3]) {
+  if (m->kind == 1) grid_second(m, P, np, params, H, phi, gphi);
+  else poly_second(m, P, H, phi, gphi);
+}
+
+/* Per parameter j the tangents carried along a ray. */
 typedef struct {
   double P[3], d[3], Q[3], n_prev, h, opl;
 } tangent;
 
-/* One ray of a polynomial medium with n = p in a box: trace_one's values and
- * decisions (the same operations, in the same order), with every continuous
- * quantity also carrying its derivative with respect to each of the nc
- * coefficients.  The entry point does not depend on the coefficients; at the
+/* One ray of a polynomial medium with n = p, or of a grid medium, in a box:
+ * trace_one's values and decisions (the same operations, in the same order),
+ * with every continuous quantity also carrying its derivative with respect to
+ * each of the nc parameters (all polynomial coefficients, or the grid samples
+ * params[]).  The entry point does not depend on the coefficients; at the
  * exit the crossing fraction t = (b - P_a) / (Q_a - P_a) carries one.
  * Returns 1 when the ray met a case the tangents do not follow (tangential
  * incidence N.I == 0, or a crossing fraction clamped to [0, 1]). */
 static int tangent_one(const orc_medium* m, const orc_params* prm, const double* o,
-                       const double* d0, ray_out* out, int nc, tangent* T, double* phi,
-                       double (*gphi)[3]) {
+                       const double* d0, ray_out* out, int nc, const int64_t* params, tangent* T,
+                       double* phi, double (*gphi)[3]) {
   double P[3] = {o[0], o[1], o[2]}, d[3] = {d0[0], d0[1], d0[2]};
   nsum opl = {0.0, 0.0};
   int flag = 0;
@@ -891,8 +973,8 @@ static int tangent_one(const orc_medium* m, const orc_params* prm, const double*
 
   double n_prev, g[3], H[3][3];
   if (inside(m, P)) {
-    poly_eval(m, P, &n_prev, g);
-    poly_second(m, P, H, phi, gphi);
+    ref_eval(m, P, &n_prev, g);
+    ref_second(m, P, nc, params, H, phi, gphi);
     for (int j = 0; j < nc; ++j) T[j].n_prev = phi[j];
   } else {
     double t, Pb[3], NB[3], Dm;
@@ -905,8 +987,8 @@ static int tangent_one(const orc_medium* m, const orc_params* prm, const double*
     nsum_add(&opl, m->n_ext * t);
     for (int a = 0; a < 3; ++a) P[a] = Pb[a];
     double n_b;
-    poly_eval(m, P, &n_b, g);
-    poly_second(m, P, H, phi, gphi);
+    ref_eval(m, P, &n_b, g);
+    ref_second(m, P, nc, params, H, phi, gphi);
     double R[3];
     double mu = m->n_ext / n_b;
     int tir = refract_or_reflect(d, NB, mu, R, &Dm);
@@ -973,8 +1055,8 @@ static int tangent_one(const orc_medium* m, const orc_params* prm, const double*
         ++out->tir_bnd;
         h = dopl / n_prev;
         for (int j = 0; j < nc; ++j) T[j].h = -dopl * T[j].n_prev / (n_prev * n_prev);
-        poly_eval(m, P, &n_prev, g);
-        poly_second(m, P, H, phi, gphi);
+        ref_eval(m, P, &n_prev, g);
+        ref_second(m, P, nc, params, H, phi, gphi);
         if (!(isfinite(n_prev) && n_prev > 0.0)) {
           out->exit_id = EXIT_INVALID;
           break;
@@ -996,8 +1078,8 @@ static int tangent_one(const orc_medium* m, const orc_params* prm, const double*
     ++steps;
 
     double n_i;
-    poly_eval(m, P, &n_i, g);
-    poly_second(m, P, H, phi, gphi);
+    ref_eval(m, P, &n_i, g);
+    ref_second(m, P, nc, params, H, phi, gphi);
     if (!(isfinite(n_i) && n_i > 0.0)) {
       out->exit_id = EXIT_INVALID;
       break;
@@ -1021,7 +1103,7 @@ static int tangent_one(const orc_medium* m, const orc_params* prm, const double*
         double hi = dopl / n_i;
         double Pn[3] = {P[0] + hi * N[0], P[1] + hi * N[1], P[2] + hi * N[2]};
         double n2, g2[3];
-        poly_eval(m, Pn, &n2, g2);
+        ref_eval(m, Pn, &n2, g2);
         double k = (n2 - n_i) / (2.0 * n_i);
         double w = 1.0 - k * k;
         double a0 = w > 0.0 ? sqrt(w) : 0.0;
@@ -1076,6 +1158,7 @@ typedef struct {
   const double *o, *d;
   double *P_out, *d_out, *opl, *tP, *td, *topl;
   int32_t *exit_id, *steps, *flag;
+  const int64_t* params;
   int nc, tid, nt;
 } tjob;
 
@@ -1086,7 +1169,8 @@ static void* tangent_worker(void* arg) {
   double(*gphi)[3] = (double(*)[3])malloc((size_t)j->nc * sizeof(*gphi));
   ray_out r;
   for (int64_t i = j->tid; i < j->n; i += j->nt) {
-    j->flag[i] = tangent_one(j->m, j->p, j->o + 3 * i, j->d + 3 * i, &r, j->nc, T, phi, gphi);
+    j->flag[i] = tangent_one(j->m, j->p, j->o + 3 * i, j->d + 3 * i, &r, j->nc, j->params, T,
+                             phi, gphi);
     for (int a = 0; a < 3; ++a) {
       j->P_out[3 * i + a] = r.P[a];
       j->d_out[3 * i + a] = r.d[a];
@@ -1109,19 +1193,28 @@ static void* tangent_worker(void* arg) {
 }
 
 int orc_trace_tangent(const orc_medium* m, const orc_params* p, int64_t n, const double* o,
-                      const double* d, double* P_out, double* d_out, double* opl,
-                      int32_t* exit_id, int32_t* steps, double* tP, double* td, double* topl,
-                      int32_t* flag, int32_t nthreads) {
-  if (m->kind != 0 || m->form != 0 || m->bkind != 0 || m->n_levels != 0 || m->degree < 0)
+                      const double* d, int32_t nparams, const int64_t* params, double* P_out,
+                      double* d_out, double* opl, int32_t* exit_id, int32_t* steps, double* tP,
+                      double* td, double* topl, int32_t* flag, int32_t nthreads) {
+  if (m->bkind != 0 || m->n_levels != 0) return -1;
+  int nc;
+  if (m->kind == 0 && m->form == 0 && m->degree >= 0) {
+    nc = (m->degree + 1) * (m->degree + 2) * (m->degree + 3) / 6;
+  } else if (m->kind == 1 && nparams > 0 && params) {
+    int64_t total = (int64_t)m->nx * m->ny * m->nz;
+    for (int q = 0; q < nparams; ++q)
+      if (params[q] < 0 || params[q] >= total) return -1;
+    nc = nparams;
+  } else {
     return -1;
-  int nc = (m->degree + 1) * (m->degree + 2) * (m->degree + 3) / 6;
+  }
   if (nthreads < 1) nthreads = 1;
   if (nthreads > 256) nthreads = 256;
   tjob jobs[256];
   pthread_t th[256];
   for (int t = 0; t < nthreads; ++t) {
-    tjob j = {m, p, n, o, d, P_out, d_out, opl, tP, td, topl, exit_id, steps, flag, nc, t,
-              nthreads};
+    tjob j = {m, p, n, o, d, P_out, d_out, opl, tP, td, topl, exit_id, steps, flag,
+              m->kind == 1 ? params : NULL, nc, t, nthreads};
     jobs[t] = j;
   }
   if (nthreads == 1) {

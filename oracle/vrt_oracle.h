@@ -79,20 +79,22 @@ int orc_trace_path(const orc_medium* m, const orc_params* p, const double* o,
                    int64_t cap, int64_t* path_len);
 
 /* Forward-mode derivatives (tangents) of each ray's exit point, direction
- * and optical path with respect to every coefficient of a polynomial medium
- * with n = p in a box, without layering: the values and decisions of
- * orc_trace_batch, each continuous quantity carrying its derivative through
- * the step (Eq. 2-9), the exit crossing and the boundary refraction.  nc =
- * (degree + 1)(degree + 2)(degree + 3) / 6; tP[3 nc n] and td[3 nc n] are
- * laid out ray, then coefficient, then component; topl[nc n].  flag[i] = 1
+ * and optical path with respect to nc parameters, in a box without layering:
+ * every coefficient of a polynomial medium with n = p (nc = (degree + 1)
+ * (degree + 2)(degree + 3) / 6; nparams and params unused), or the nparams
+ * grid samples params[] (flat index, x fastest) of a grid medium (nc =
+ * nparams).  The values and decisions are those of orc_trace_batch, each
+ * continuous quantity carrying its derivative through the step (Eq. 2-9), the
+ * exit crossing and the boundary refraction.  tP[3 nc n] and td[3 nc n] are
+ * laid out ray, then parameter, then component; topl[nc n].  flag[i] = 1
  * when ray i met tangential incidence (N.I == 0) or a crossing fraction
  * clamped to [0, 1], which the tangents do not follow.  Returns -1 for any
- * other medium, else 0. */
+ * other medium or an out-of-range sample, else 0. */
 int orc_trace_tangent(const orc_medium* m, const orc_params* p, int64_t n,
-                      const double* o, const double* d, double* P_out,
-                      double* d_out, double* opl, int32_t* exit_id,
-                      int32_t* steps, double* tP, double* td, double* topl,
-                      int32_t* flag, int32_t nthreads);
+                      const double* o, const double* d, int32_t nparams,
+                      const int64_t* params, double* P_out, double* d_out,
+                      double* opl, int32_t* exit_id, int32_t* steps, double* tP,
+                      double* td, double* topl, int32_t* flag, int32_t nthreads);
 
 #ifdef __cplusplus
 }

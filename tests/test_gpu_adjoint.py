@@ -148,21 +148,53 @@ def test_polynomial_coefficients_against_oracle_tangents(ctx):
     targets = W.design_targets(rays.n)
     t = oracle.trace_tangent(m, rays.origins, rays.dirs, dopl, max_steps)
     keep = t["flag"] == 0
-    P, d = t["P"], t["d"]
-    sig = (Z_IMG - P[:, 2]) / d[:, 2]
-    ex = 2.0 * (P[:, 0] + sig * d[:, 0] - targets[:, 0])  # de/dX
-    ey = 2.0 * (P[:, 1] + sig * d[:, 1] - targets[:, 1])  # de/dY
-    w = np.where((t["exit_id"] >= 0) & keep, 1.0 / rays.n, 0.0)
-    lat = ex * d[:, 0] + ey * d[:, 1]
-    gP = np.stack([ex, ey, -lat / d[:, 2]], 1) * w[:, None]
-    gd = np.stack([ex * sig, ey * sig, -sig * lat / d[:, 2]], 1) * w[:, None]
-    terms = np.einsum("rk,rjk->rj", gP, t["tP"]) + np.einsum("rk,rjk->rj", gd, t["td"])
-    ref, mag = terms.sum(0), np.abs(terms).sum(0)
+    ref, mag = tangent_gradient(t, targets, keep)
     _, g = adjoint_grad(ctx, m, m.coeffs, rays, targets, dopl, max_steps, 64, keep)
     err = np.abs(g - ref) / np.maximum(mag, 1e-300)
     print("worst coefficient", int(err.argmax()), "error", float(err.max()), "kept", float(keep.mean()))
     assert keep.mean() > 0.95
     assert err.max() <= 1e-10, (float(err.max()), int(err.argmax()))
+
+
+def tangent_gradient(t, targets, keep):
+    """dL/dtheta_j of the image-plane loss from the oracle's tangents:
+    sum over kept exiting rays of dL/d(P, d) . d(P, d)/dtheta_j, with
+    X = P_x + s d_x, Y = P_y + s d_y, s = (Z - P_z) / d_z.  Returns the
+    gradient and sum_r |per-ray term| per parameter."""
+    P, d = t["P"], t["d"]
+    n = P.shape[0]
+    sig = (Z_IMG - P[:, 2]) / d[:, 2]
+    ex = 2.0 * (P[:, 0] + sig * d[:, 0] - targets[:, 0])  # de/dX
+    ey = 2.0 * (P[:, 1] + sig * d[:, 1] - targets[:, 1])  # de/dY
+    w = np.where((t["exit_id"] >= 0) & keep, 1.0 / n, 0.0)
+    lat = ex * d[:, 0] + ey * d[:, 1]
+    gP = np.stack([ex, ey, -lat / d[:, 2]], 1) * w[:, None]
+    gd = np.stack([ex * sig, ey * sig, -sig * lat / d[:, 2]], 1) * w[:, None]
+    terms = np.einsum("rk,rjk->rj", gP, t["tP"]) + np.einsum("rk,rjk->rj", gd, t["td"])
+    return terms.sum(0), np.abs(terms).sum(0)
+
+
+def test_grid_samples_against_oracle_tangents(ctx):
+    """The same FP64 reference for the gridded medium: the adjoint's gradient
+    at 64 samples of the 64^3 blob grid (among those with a gradient above
+    1e-2 of the largest) against the oracle's tangents with respect to those
+    samples, within 1e-10 of sum_r |per-ray term|."""
+    wl = W.blob_workload(n_rays=384, res=64)
+    m = wl.medium
+    dopl, max_steps = 0.02, 20000
+    targets = W.design_targets(wl.rays.n) + 10.0  # spots around the cube's axis
+    theta0 = m.grid.astype(np.float64).ravel()
+    _, g_all = adjoint_grad(ctx, m, theta0, wl.rays, targets, dopl, max_steps, 64)
+    cand = np.flatnonzero(np.abs(g_all) > 1e-2 * np.abs(g_all).max())
+    coords = np.random.default_rng(3).choice(cand, size=min(64, cand.size), replace=False)
+    t = oracle.trace_tangent(m, wl.rays.origins, wl.rays.dirs, dopl, max_steps, samples=coords)
+    keep = t["flag"] == 0
+    ref, mag = tangent_gradient(t, targets, keep)
+    _, g = adjoint_grad(ctx, m, theta0, wl.rays, targets, dopl, max_steps, 64, keep)
+    err = np.abs(g[coords] - ref) / np.maximum(mag, 1e-300)
+    print("worst sample", int(coords[err.argmax()]), "error", float(err.max()), "kept", float(keep.mean()))
+    assert keep.mean() > 0.95
+    assert err.max() <= 1e-10, (float(err.max()), int(coords[err.argmax()]))
 
 
 def test_grid_samples_against_oracle_fd(ctx):

@@ -623,3 +623,59 @@ def test_tangents_match_central_differences_through_the_exit():
     for e in _tangent_vs_fd(0.2, 20000, (0, 5, 20)):
         assert e.size >= 20
         assert e.max() <= 5e-5 and np.median(e) <= 1e-6, (e.max(), np.median(e))
+
+
+def test_grid_sample_tangents_match_central_differences():
+    """Tangents with respect to grid samples (the weight of a sample at P is
+    the product of its per-axis Catmull-Rom weights, summed over the taps the
+    edge clamp maps onto it, plus the interpolant's Hessian for the moved
+    points): against central differences of oracle traces with the float32
+    sample moved by 8 units in the last place, on each ray the sample
+    influences: the tangent lies within four times the gap between the
+    differences at 16 and 8 units (their own error, a few 1e-6 relative) plus
+    1e-6, where a dropped term would miss by orders of magnitude.  The
+    samples are the cells that eight rays cross at step 400 and, on the
+    entry face, where the edge clamp sums several taps onto one sample, the
+    cells they cross at step 2."""
+    wl = W.blob_workload(n_rays=256, res=64)
+    m, rays = wl.medium, wl.rays
+    nz, ny, nx = m.grid.shape
+    pts = np.concatenate([oracle.trace(m, rays.origins[:8], rays.dirs[:8], 0.02, k)["P"]
+                          for k in (400, 2)])
+    cell = np.floor((pts - np.array(m.origin)) / np.array(m.spacing)).astype(np.int64)
+    cell = np.clip(cell, 0, [nx - 1, ny - 1, nz - 1])
+    samples = (cell[:, 2] * ny + cell[:, 1]) * nx + cell[:, 0]
+    t = oracle.trace_tangent(m, rays.origins, rays.dirs, 0.02, 800, samples=samples)
+    base = oracle.trace(m, rays.origins, rays.dirs, 0.02, 800)
+    for k in ("P", "d", "opl", "exit_id", "steps"):
+        np.testing.assert_array_equal(t[k], base[k], err_msg=k)
+    flat = m.grid.ravel()
+    ulp = float(np.spacing(np.float32(1.5)))
+    errs = []
+    for q, i in enumerate(samples):
+        keep = t["flag"] == 0
+        fds = []
+        for k in (16, 8):
+            res = []
+            for s in (+1, -1):
+                g = flat.copy()
+                g[i] = np.float32(np.float64(g[i]) + s * k * ulp)
+                mm = W.Medium(**{**m.__dict__})
+                mm.grid = g.reshape(m.grid.shape)
+                res.append((oracle.trace(mm, rays.origins, rays.dirs, 0.02, 800), float(g[i])))
+            (rp, vp), (rm, vm) = res
+            for key in ("exit_id", "steps", "tir_internal", "tir_boundary"):
+                keep &= (rp[key] == base[key]) & (rm[key] == base[key])
+            fds.append(np.concatenate([rp["P"] - rm["P"], rp["d"] - rm["d"]], 1) / (vp - vm))
+        a, b = fds
+        scale = np.abs(b).max(1)
+        keep &= scale > 0
+        tan = np.concatenate([t["tP"][:, q], t["td"][:, q]], 1)
+        gap = np.abs(a - b).max(1)
+        errs.append((np.abs(tan - b).max(1) / (4.0 * gap + 1e-6 * scale + 1e-300))[keep])
+        # a ray the sample cannot reach has a zero tangent
+        far = np.abs(a).max(1) == 0
+        assert np.abs(tan[far & (t["flag"] == 0)]).max(initial=0.0) == 0.0
+    e = np.concatenate(errs)
+    assert e.size >= 8
+    assert e.max() <= 1.0, e.max()
