@@ -32,7 +32,9 @@ namespace grin {
 namespace adj {
 
 constexpr int kMaxK = 64;
-constexpr int kCk = 8;  // checkpoint words: P[3], I[3], n_{i-1}, h
+// checkpoint words: P[3], I[3], n_{i-1}, h at the start of a step; with a
+// checkpoint every step (K = 1) also the step's case and face, kind + 4 face
+constexpr int kCk = 9;
 enum Kind : int { kNormal = 0, kCrossReflect = 1, kExit = 2 };
 
 struct St {
@@ -593,8 +595,9 @@ __global__ void __launch_bounds__(128) k_adj_forward(DevMedium m, AdjArgs A) {
   if (live) {
     int face = 0;
     while (!s.done && s.steps < A.a.max_steps) {
+      double* c = nullptr;
       if (s.steps % A.k == 0) {
-        double* c = ck + (size_t)(s.steps / A.k) * kCk;
+        c = ck + (size_t)(s.steps / A.k) * kCk;
         for (int q = 0; q < 3; ++q) {
           c[q] = s.P[q];
           c[3 + q] = s.d[q];
@@ -602,7 +605,8 @@ __global__ void __launch_bounds__(128) k_adj_forward(DevMedium m, AdjArgs A) {
         c[6] = s.n_prev;
         c[7] = s.h;
       }
-      advance<PC, GRID>(m, A.a.dopl, s, face);
+      const int kind = advance<PC, GRID>(m, A.a.dopl, s, face);
+      if (A.k == 1) c[8] = (double)(kind + 4 * face);
     }
   }
   double opl = s.opl_ext + A.a.dopl * (double)s.full + A.a.dopl * s.frac;
@@ -636,7 +640,19 @@ __global__ void __launch_bounds__(128) k_adj_backward(DevMedium m, AdjArgs A) {
   const double* ck = A.ckpt + (size_t)r * A.nseg * kCk;
   double rec[kMaxK][kCk];
   int kind[kMaxK], fc[kMaxK];
-  if (nsteps > 0) {
+  if (nsteps > 0 && A.k == 1) {
+    // every step's start state, case and face were stored: no recompute
+    for (int i = nsteps - 1; i >= 0; --i) {
+      const double* c = ck + (size_t)i * kCk;
+      const int code = (int)c[8], kd = code & 3, face = code >> 2;
+      if (i == nsteps - 1 && exit_id >= 0)
+        exit_back(m, c, face, Pob, dob, fb, lam);
+      else if (kd == kCrossReflect)
+        reflect_back<PC, GRID>(m, dopl, c, face, fb, lam, acc, A.grad);
+      else
+        normal_back<PC, GRID>(m, dopl, c, lam, acc, A.grad);
+    }
+  } else if (nsteps > 0) {
     const int last = (nsteps - 1) / A.k;
     for (int seg = last; seg >= 0; --seg) {
       const int s0 = seg * A.k, s1 = min(s0 + A.k, nsteps);

@@ -230,4 +230,18 @@ def test_checkpoint_interval_does_not_change_the_gradient(ctx):
     targets = W.design_targets(rays.n)
     _, g64 = adjoint_grad(ctx, m, m.coeffs, rays, targets, 0.02, 20000, 64)
     _, g7 = adjoint_grad(ctx, m, m.coeffs, rays, targets, 0.02, 20000, 7)
+    _, g1 = adjoint_grad(ctx, m, m.coeffs, rays, targets, 0.02, 20000, 1)  # every step stored
     np.testing.assert_allclose(g7, g64, rtol=1e-12, atol=1e-15 * np.abs(g64).max())
+    np.testing.assert_allclose(g1, g64, rtol=1e-12, atol=1e-15 * np.abs(g64).max())
+
+
+def test_stored_steps_grid_gradient_equals_recomputed(ctx):
+    """On the blob grid, checkpoint_every = 1 (every step stored with its
+    case, no recompute) gives the gradient of checkpoint_every = 64."""
+    wl = W.blob_workload(n_rays=384, res=64)
+    m = wl.medium
+    targets = W.design_targets(wl.rays.n) + 10.0
+    theta0 = m.grid.astype(np.float64).ravel()
+    _, g64 = adjoint_grad(ctx, m, theta0, wl.rays, targets, 0.02, 20000, 64)
+    _, g1 = adjoint_grad(ctx, m, theta0, wl.rays, targets, 0.02, 20000, 1)
+    np.testing.assert_allclose(g1, g64, rtol=1e-12, atol=1e-15 * np.abs(g64).max())
