@@ -226,14 +226,16 @@ __device__ void field_h(const DevMedium& m, const double* P, double& n, double* 
       H[4] = fma(dw[2][c], y10, H[4]);
       H[5] = fma(dw[2][c], y01, H[5]);
     }
-    const double* sp = m.spacing;
-    for (int k = 0; k < 3; ++k) g[k] /= sp[k];
-    H[0] /= sp[0] * sp[0];
-    H[1] /= sp[1] * sp[1];
-    H[2] /= sp[2] * sp[2];
-    H[3] /= sp[0] * sp[1];
-    H[4] /= sp[0] * sp[2];
-    H[5] /= sp[1] * sp[2];
+    // to physical units by the stored reciprocals: nothing here feeds a
+    // decision, so products replace the divisions
+    const double* is = m.inv_spacing;
+    for (int k = 0; k < 3; ++k) g[k] *= is[k];
+    H[0] *= is[0] * is[0];
+    H[1] *= is[1] * is[1];
+    H[2] *= is[2] * is[2];
+    H[3] *= is[0] * is[1];
+    H[4] *= is[0] * is[2];
+    H[5] *= is[1] * is[2];
   } else {
     double x[3];
     for (int k = 0; k < 3; ++k) x[k] = (P[k] - m.off[k]) / m.scale[k];
@@ -266,14 +268,14 @@ __device__ void field_h(const DevMedium& m, const double* P, double& n, double* 
           H[4] += c * dX * Y * dZ;
           H[5] += c * X * dY * dZ;
         }
-    const double* sc = m.scale;
-    for (int k = 0; k < 3; ++k) g[k] /= sc[k];
-    H[0] /= sc[0] * sc[0];
-    H[1] /= sc[1] * sc[1];
-    H[2] /= sc[2] * sc[2];
-    H[3] /= sc[0] * sc[1];
-    H[4] /= sc[0] * sc[2];
-    H[5] /= sc[1] * sc[2];
+    const double* is = m.inv_scale;
+    for (int k = 0; k < 3; ++k) g[k] *= is[k];
+    H[0] *= is[0] * is[0];
+    H[1] *= is[1] * is[1];
+    H[2] *= is[2] * is[2];
+    H[3] *= is[0] * is[1];
+    H[4] *= is[0] * is[2];
+    H[5] *= is[1] * is[2];
   }
 }
 
@@ -293,7 +295,7 @@ __device__ void param_adj(const DevMedium& m, const double* P, double nb, const 
       double fl = floor(u);
       b0[a] = (int)fl;
       plain::keys(u - fl, w[a], dw[a]);
-      for (int t = 0; t < 4; ++t) dw[a][t] /= m.spacing[a];
+      for (int t = 0; t < 4; ++t) dw[a][t] *= m.inv_spacing[a];
     }
     // d(n, grad n)/d(sample) = the tap's weight products; factored per row
     // (b, c): v = w0 A + w0' B with A = w1 (nb w2 + gb2 w2') + gb1 w1' w2 and
@@ -320,7 +322,8 @@ __device__ void param_adj(const DevMedium& m, const double* P, double nb, const 
       pw[k][0] = 1.0;
       for (int e = 1; e <= PC; ++e) pw[k][e] = pw[k][e - 1] * x[k];
     }
-    const double gx = gb[0] / m.scale[0], gy = gb[1] / m.scale[1], gz = gb[2] / m.scale[2];
+    const double gx = gb[0] * m.inv_scale[0], gy = gb[1] * m.inv_scale[1],
+                 gz = gb[2] * m.inv_scale[2];
     int idx = 0;
     for (int s = 0; s <= PC; ++s)
       for (int i = s; i >= 0; --i)
