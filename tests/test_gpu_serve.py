@@ -137,3 +137,33 @@ def test_submit_argument_errors(ctx, jobs):
     srv.close()
     foreign.close()
     other.close()
+
+
+def test_submit_and_wait_from_several_threads(ctx, jobs):
+    """The serve API is thread-safe: four host threads submit every job and
+    wait on their own ids at once (ctypes releases the GIL inside each call,
+    so the calls overlap in the library).  Every result is bitwise the
+    direct trace's, and the server counts all twenty jobs."""
+    import threading
+    srv = tracer.Server(ctx, 1 << 30, step_quantum=256)
+    failures = []
+
+    def worker():
+        try:
+            mine = [(srv.submit(med, rays, wl.dopl, wl.max_steps), ref) for wl, med, rays, ref in jobs]
+            for (jid, res), ref in mine:
+                assert srv.wait(jid, 120) == N.JOB_DONE
+                same(res, ref)
+        except Exception as e:  # reported on the main thread
+            failures.append(e)
+
+    threads = [threading.Thread(target=worker) for _ in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(300)
+    assert not any(t.is_alive() for t in threads)
+    assert not failures, failures
+    st = srv.stats()
+    assert st["done"] == 4 * len(jobs) and st["failed"] == 0
+    srv.close()
