@@ -70,9 +70,9 @@ KERNEL = "k_trace_mixed<Cfg<4,false,false,box,linear>,false>"
 PROFILE = "profiles/k_trace_mixed_freeform_block_1048576.md"
 
 
-def profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, or None if the
-    kernel sources changed since that capture."""
+def profiled_value(key: str):
+    """A figure `key: value` from the committed ncu summary of the kernel, or
+    None if the kernel sources changed since that capture."""
     import hashlib
     import re
     try:
@@ -83,10 +83,33 @@ def profiled_traffic():
     except OSError:
         return None
     sha = re.search(r"kernel_source_sha: ([0-9a-f]+)", text)
-    tb = re.search(r"traffic_bytes_per_launch: (\d+)", text)
-    if not sha or not tb or sha.group(1) != h.hexdigest()[:16]:
+    v = re.search(re.escape(key) + r": ([0-9.]+)", text)
+    if not sha or not v or sha.group(1) != h.hexdigest()[:16]:
         return None
-    return int(tb.group(1))
+    return float(v.group(1))
+
+
+def profiled_traffic():
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)."""
+    v = profiled_value("traffic_bytes_per_launch")
+    return None if v is None else int(v)
+
+
+# CUDA-core issue peak: 148 SMs x 128 FP32 lanes x 2.032 GHz, lane operations a second
+FP32_ISSUE_PEAK = 148 * 128 * 2.032e9
+
+
+def fp32_issue(rate: float):
+    """FP32 issue rate against the CUDA-core peak: the executed FFMA + FADD +
+    FMUL lane operations per ray-step that ncu counted for this kernel
+    (committed summary) times the measured ray-steps/s."""
+    ops = profiled_value("fp32_lane_ops_per_ray_step")
+    if ops is None:
+        return None
+    achieved = ops * rate
+    return {"achieved": achieved / 1e12, "peak": FP32_ISSUE_PEAK / 1e12, "unit": "T lane-ops/s",
+            "frac": achieved / FP32_ISSUE_PEAK, "fp32_lane_ops_per_ray_step": ops,
+            "source": "ncu sass op counts (FFMA + FADD + FMUL) of " + PROFILE}
 
 
 def rank_ray_seed(rank: int) -> int:
@@ -512,7 +535,9 @@ def run_ours(args):
                      "traffic": profiled_traffic() if args.rays == N_RAYS and args.workload == "freeform" else None,
                      "kernel": KERNEL, "kernel_ms": 1e3 * mean_kern,
                      "flops_per_ray_step": flops_per_step(4),
-                     "peak_note": "148 SMs x 128 FP32 lanes x 2 FLOP x 2.032 GHz (derived)"},
+                     "peak_note": "148 SMs x 128 FP32 lanes x 2 FLOP x 2.032 GHz (derived)",
+                     "fp32_issue": fp32_issue(steps_per_trace / mean_kern)
+                     if args.rays == N_RAYS and args.workload == "freeform" else None},
         "precision_gate": {
             "vs": "plain FP64 GPU tracer on the same float32 input rays",
             "fp64_ms": 1e3 * fp64_s, "fp64_ray_steps_per_s": float(res64["steps"].sum()) / fp64_s,
