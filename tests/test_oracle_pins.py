@@ -571,11 +571,11 @@ def test_n2p_lens_reaches_the_paper_design_quality():
 
 
 def _tangent_vs_fd(dopl, max_steps, coords, h=1e-6):
-    """Per coefficient: the oracle's tangent of (P, d) against the central
-    difference of oracle traces with the coefficient moved by +-h, on the
-    rays whose integer outcomes do not change and whose differences at h and
-    h / 2 agree to 1e-6 (there the differences' own error, truncation plus
-    rounding noise / h, is below that).  Returns the relative errors."""
+    """Per coefficient: the oracle's tangent of (P, d, OPL) against the
+    central difference of oracle traces with the coefficient moved by +-h,
+    on the rays whose integer outcomes do not change and whose differences at
+    h and h / 2 agree to 1e-6 (there the differences' own error, truncation
+    plus rounding noise / h, is below that).  Returns the relative errors."""
     m = W.freeform_block_medium()
     rays = W.point_source_rays(64, W.BASE_SEED + 4)
     t = oracle.trace_tangent(m, rays.origins, rays.dirs, dopl, max_steps)
@@ -597,11 +597,12 @@ def _tangent_vs_fd(dopl, max_steps, coords, h=1e-6):
             (rp, vp), (rm, vm) = res
             for k in ("exit_id", "steps", "tir_internal", "tir_boundary"):
                 keep &= (rp[k] == base[k]) & (rm[k] == base[k])
-            fds.append(np.concatenate([rp["P"] - rm["P"], rp["d"] - rm["d"]], 1) / (vp - vm))
+            fds.append(np.concatenate([rp["P"] - rm["P"], rp["d"] - rm["d"],
+                                       (rp["opl"] - rm["opl"])[:, None]], 1) / (vp - vm))
         a, b = fds
         scale = np.abs(a).max(1) + 1e-300
         keep &= np.abs(a - b).max(1) / scale <= 1e-6
-        tan = np.concatenate([t["tP"][:, i], t["td"][:, i]], 1)
+        tan = np.concatenate([t["tP"][:, i], t["td"][:, i], t["topl"][:, i][:, None]], 1)
         errs.append((np.abs(tan - a).max(1) / scale)[keep])
     return errs
 
