@@ -21,6 +21,13 @@ Parity status per function (pins live in tests/test_oracle_pins.py):
     of the samples at nodes;
   - layered shells: pinned by Snell's law at a planar level crossing;
   - tangent incidence (case iv): pinned by its closed-form first arc;
+  - cylinder side wall (entry and exit roots, radial normal, critical-angle
+    split): pinned by the half-chord geometry and vector Snell;
+  - decision margins (boundary, critical, tangent, level): pinned by rays
+    built with known distances, cosines and level coordinates;
+  - edge-clamped tricubic taps: pinned against Keys' piecewise kernel;
+  - the inner index at the exit face (n at the last interior point): pinned
+    by the conserved transverse momentum of a z-stratified medium;
   - forward-mode tangents (trace_tangent; polynomial coefficients with
     n = p, or grid samples, in a box): values and decisions bitwise those of
     trace; derivatives pinned against central differences of trace, inside

@@ -680,3 +680,243 @@ def test_grid_sample_tangents_match_central_differences():
     e = np.concatenate(errs)
     assert e.size >= 8
     assert e.max() <= 1.0, e.max()
+
+
+# ------------------------------------------------- cylinder side wall (Sec. II (i))
+
+
+def _homogeneous_cylinder(n, radius=1.0, z0=0.0, z1=10.0, n_ext=1.0):
+    bk, bp = W.cylinder(0.0, 0.0, radius, z0, z1)
+    return W.Medium(kind=W.KIND_POLY, form=W.FORM_LINEAR, degree=0, coeffs=np.array([n]),
+                    bkind=bk, bparams=bp, n_ext=n_ext)
+
+
+def _circle_hits(o, d, radius):
+    """Both crossings of the line o + s d with the circle x^2 + y^2 = R^2 in the
+    xy plane, by geometry: the foot of the perpendicular from the axis and
+    the half chord."""
+    dxy = np.array([d[0], d[1]])
+    u = dxy / np.linalg.norm(dxy)
+    s_foot = -np.dot(o[:2], u)                      # along the projected line
+    miss = np.linalg.norm(o[:2] + s_foot * u)       # distance of the line from the axis
+    half = math.sqrt(radius * radius - miss * miss)
+    scale = np.linalg.norm(dxy)                     # projected length per unit s
+    return (s_foot - half) / scale, (s_foot + half) / scale
+
+
+def test_cylinder_side_wall_entry_and_exit():
+    """A homogeneous cylinder (n = 1.5 in air) entered and left through its
+    side wall: the entry point is the nearer circle crossing, the outward
+    normal there is (x, y, 0)/R, vector Snell (Eq. 1) holds at both walls,
+    the ray crosses the chord in ceil(n L / dL0) steps (the last one cut at
+    the wall), and OPL = n_ext |E - o| + n L."""
+    n, dopl, R = 1.5, 1e-3, 2.0
+    m = _homogeneous_cylinder(n, radius=R)
+    o = np.array([-5.0, 0.6, 2.0])
+    d0 = np.array([1.0, 0.2, 0.14])
+    d0 /= np.linalg.norm(d0)
+    r = _one(m, o, d0, dopl, 100000)
+    s_in, _ = _circle_hits(o, d0, R)
+    E = o + s_in * d0
+    NE = np.array([E[0], E[1], 0.0]) / R           # outward unit normal
+    # direction inside: tangential part of n d conserved, normal part inward
+    ti = (1.0 / n) * (d0 - np.dot(d0, NE) * NE)
+    Rin = ti - math.sqrt(1.0 - np.dot(ti, ti)) * NE
+    np.testing.assert_allclose(1.0 * np.cross(NE, d0), n * np.cross(NE, Rin), atol=1e-15)
+    # the far crossing of the chord from E (E lies on the circle)
+    rxy = Rin[:2]
+    L = -2.0 * np.dot(E[:2], rxy) / np.dot(rxy, rxy)
+    X = E + L * Rin
+    NX = np.array([X[0], X[1], 0.0]) / R
+    assert r["exit_id"] == 0 and r["tir_boundary"] == 0
+    assert r["steps"] == math.ceil(n * L / dopl)
+    assert 0.05 < (n * L / dopl) % 1 < 0.95  # no rounding ambiguity in the count
+    np.testing.assert_allclose(r["P"], X, atol=1e-12)
+    assert r["opl"] == pytest.approx(s_in + n * L, rel=1e-13)
+    # Snell at the exit wall with the outward normal at X
+    np.testing.assert_allclose(n * np.cross(NX, Rin), 1.0 * np.cross(NX, r["d"]), atol=1e-12)
+    assert np.dot(r["d"], NX) > 0
+
+
+@pytest.mark.parametrize("sign", [+1, -1])
+def test_cylinder_side_wall_critical_angle_split(sign):
+    """Sec. II (v) at the curved wall: a meridional ray from the axis meets
+    the side wall where the normal is x; 1e-6 rad beyond the critical angle
+    it is reflected, 1e-6 rad short of it it leaves through the side with
+    the tangential (z) component of n d conserved."""
+    n = 1.5
+    m = _homogeneous_cylinder(n, radius=0.7, z0=-50.0, z1=50.0)
+    inc = math.asin(1.0 / n) + sign * 1e-6   # angle to the wall normal
+    alpha = math.pi / 2 - inc                # angle to the axis
+    d0 = np.array([math.sin(alpha), 0.0, math.cos(alpha)])
+    r = _one(m, (0, 0, 0), d0, 1e-3, 20000)
+    if sign > 0:
+        assert r["tir_boundary"] >= 1 and r["exit_id"] != 0
+    else:
+        assert r["exit_id"] == 0 and r["tir_boundary"] == 0
+        assert r["P"][0] == pytest.approx(0.7, abs=1e-12)
+        assert r["d"][2] == pytest.approx(n * math.sin(inc), rel=1e-12)
+
+
+# ------------------------------------------ decision margins (flagging of rays)
+
+
+def test_boundary_margin_is_distance_in_steps():
+    """A ray that runs parallel to the box face x = 1 at distance d keeps every
+    step end d from it; the end face z = L sits half a step past the last
+    full step, so the boundary margin is d / h with h = dL0 / n."""
+    n, dopl, dist = 1.5, 0.01, 1e-4
+    h = dopl / n
+    z0, k = 0.1, 57
+    m = W.homogeneous_box(n, lo=(-1, -1, 0), hi=(1, 1, z0 + (k + 0.5) * h))
+    r = _one(m, (1.0 - dist, 0.0, z0), (0, 0, 1), dopl, 1000)
+    assert r["exit_id"] == 5 and r["steps"] == k + 1
+    assert r["margins"][oracle.M_BND] == pytest.approx(dist / h, rel=1e-9)
+
+
+@pytest.mark.parametrize("kind", ["sphere", "cylinder"])
+def test_curved_boundary_margin_is_distance_in_steps(kind):
+    """For a sphere or a cylinder side wall the boundary margin measures the
+    distance of a step end to the surface, in steps, to first order: a ray
+    from the centre along x whose last interior step end lies half a step
+    inside the wall (radius (k + 1/2) h) has margin 1/2 - O(h / R)."""
+    n, dopl, k = 1.5, 0.01, 140
+    h = dopl / n
+    R = (k + 0.5) * h
+    if kind == "sphere":
+        bk, bp = W.sphere((0.0, 0.0, 0.0), R)
+    else:
+        bk, bp = W.cylinder(0.0, 0.0, R, -1.0, 1.0)
+    m = W.Medium(kind=W.KIND_POLY, form=W.FORM_LINEAR, degree=0, coeffs=np.array([n]),
+                 bkind=bk, bparams=bp, n_ext=1.0)
+    r = _one(m, (0, 0, 0), (1, 0, 0), dopl, 1000)
+    assert r["exit_id"] == 0 and r["steps"] == k + 1
+    assert r["margins"][oracle.M_BND] == pytest.approx(0.5, abs=h / R)
+
+
+@pytest.mark.parametrize("deg", [50.0, 20.0])
+def test_critical_margin_is_cosine_distance(deg):
+    """The critical margin is the distance of |N.I| from its critical value
+    cos(theta_c) = sqrt(1 - (n_ext / n)^2): for a ray inside a homogeneous
+    box (n = 1.5, air outside) meeting the +x wall at incidence theta it is
+    |cos(theta) - cos(theta_c)|, whether the ray leaves (20 deg) or is
+    reflected (50 deg); entry refractions (mu < 1) have no critical angle."""
+    n = 1.5
+    th = math.radians(deg)
+    m = W.homogeneous_box(n, lo=(-1, -1, -20), hi=(1, 1, 20))
+    # 6000 steps reach both x walls, not the z faces
+    r = _one(m, (0, 0, 0), (math.cos(th), 0.0, math.sin(th)), 1e-3, 6000)
+    cc = math.cos(math.asin(1.0 / n))
+    expect = abs(math.cos(th) - cc)
+    if deg < 40:
+        assert r["exit_id"] == 1
+        assert r["margins"][oracle.M_CRIT] == pytest.approx(expect, rel=1e-12)
+    else:
+        assert r["tir_boundary"] >= 1
+        assert r["margins"][oracle.M_CRIT] == pytest.approx(expect, rel=1e-12)
+
+
+def test_tangent_margin_is_smallest_normal_cosine():
+    """In n = 1.5 + 0.1 x the normal is x at every point; a ray launched at
+    angle b off the y axis towards +x bends towards +x, so the smallest
+    |N.I| over its refractions is the first one, sin(b)."""
+    c = W.coeffs_from_terms(1, {(0, 0, 0): 1.5, (1, 0, 0): 0.1})
+    m = W.Medium(kind=W.KIND_POLY, form=W.FORM_LINEAR, degree=1, coeffs=c, bkind=W.BOUNDARY_BOX,
+                 bparams=(-1, -1, -1, 1, 1, 1, 0, 0), n_ext=1.0)
+    b = math.radians(3.0)
+    r = _one(m, (0, -0.5, 0), (math.sin(b), math.cos(b), 0.0), 1e-3, 5000)
+    assert r["margins"][oracle.M_TAN] == pytest.approx(math.sin(b), rel=1e-14)
+
+
+@pytest.mark.parametrize("z0", [0.3, 0.9])
+def test_level_margin_is_distance_to_next_shell(z0):
+    """With f = 1.5 + 0.2 (z - 1) in two shells on [1.3, 1.7] the level
+    coordinate L (f - lo) / (hi - lo) equals z; a ray along x at height z0
+    stays at level coordinate z0, whose distance to the nearest shell
+    boundary (an integer) is min(z0, 1 - z0)."""
+    c = W.coeffs_from_terms(1, {(0, 0, 0): 1.5, (0, 0, 1): 0.2})
+    m = W.Medium(kind=W.KIND_POLY, form=W.FORM_LINEAR, degree=1, coeffs=c, off=(0, 0, 1),
+                 n_levels=2, level_lo=1.3, level_hi=1.7, bkind=W.BOUNDARY_BOX,
+                 bparams=(-1, -1, 0, 1, 1, 2, 0, 0), n_ext=1.0)
+    r = _one(m, (-0.5, 0, z0), (1, 0, 0), 1e-3, 5000)
+    assert r["exit_id"] == 1
+    assert r["margins"][oracle.M_LEVEL] == pytest.approx(min(z0, 1 - z0), rel=1e-12)
+
+
+# --------------------------------------------- edge-clamped tricubic (Keys 1981)
+
+
+def _keys(s):
+    """Keys' cubic convolution kernel with a = -1/2 and its derivative, in the
+    piecewise form of the 1981 paper."""
+    a = abs(s)
+    if a <= 1.0:
+        return 1.5 * a ** 3 - 2.5 * a ** 2 + 1.0, math.copysign(1.0, s) * (4.5 * a * a - 5.0 * a)
+    if a < 2.0:
+        return (-0.5 * a ** 3 + 2.5 * a ** 2 - 4.0 * a + 2.0,
+                math.copysign(1.0, s) * (-1.5 * a * a + 5.0 * a - 4.0))
+    return 0.0, 0.0
+
+
+def _clamped_tricubic(grid, h, p):
+    nz, ny, nx = grid.shape
+    u = [p[a] / h for a in range(3)]
+    base = [math.floor(x) for x in u]
+    v, g = 0.0, [0.0, 0.0, 0.0]
+    for k in range(base[2] - 1, base[2] + 3):
+        for j in range(base[1] - 1, base[1] + 3):
+            for i in range(base[0] - 1, base[0] + 3):
+                s = float(grid[min(max(k, 0), nz - 1), min(max(j, 0), ny - 1), min(max(i, 0), nx - 1)])
+                (wx, dx), (wy, dy), (wz, dz) = _keys(u[0] - i), _keys(u[1] - j), _keys(u[2] - k)
+                v += wx * wy * wz * s
+                g[0] += dx * wy * wz * s / h
+                g[1] += wx * dy * wz * s / h
+                g[2] += wx * wy * dz * s / h
+    return v, g
+
+
+def test_tricubic_edge_clamp_against_keys_kernel():
+    """Near and beyond the grid's faces the stencil reaches past the samples;
+    taps there repeat the edge sample (R17).  The oracle's value and gradient
+    match a sum of Keys-kernel weights over the clamped taps, in the first
+    and last cells and half a cell outside, on every axis."""
+    res, h = 5, 0.5
+    grid = (1.5 + 0.05 * W.uniform(17, 1, res ** 3, -1.0, 1.0)).reshape(res, res, res).astype(np.float32)
+    m = W.grid_medium(grid, h, size=h * (res - 1))
+    bands = [(-0.5 * h, 0.0), (0.0, h), ((res - 2) * h, (res - 1) * h), ((res - 1) * h, (res - 0.5) * h)]
+    pts = []
+    for s in range(24):
+        lo, hi = bands[s % 4]
+        p = W.uniform(18, s, 3, 0.0, 1.0)
+        axis = s % 3
+        q = [lo + p[0] * (hi - lo) if a == axis else (0.2 + 3.6 * p[a]) * h for a in range(3)]
+        pts.append(q)
+    pts = np.array(pts)
+    n, g = oracle.medium_eval(m, pts)
+    for i, p in enumerate(pts):
+        v, gg = _clamped_tricubic(grid, h, p)
+        assert n[i] == pytest.approx(v, abs=1e-14)
+        np.testing.assert_allclose(g[i], gg, atol=1e-13)
+
+
+# ------------------------------------------ index on the inner side at the exit (R10)
+
+
+def test_exit_uses_previous_point_index():
+    """At the exit face the inner index of Eq. 1 is n_{i-1}, the index at the
+    last interior point (the previous point of the step that crossed).  In
+    n = 1.5 + 0.1 z' the normals of every refraction are along z, so n_{i-1}
+    times the transverse direction is carried unchanged from the entry face
+    (where n_ext times it is the input's) to the exit face: the ray leaves
+    along its input direction.  Taking n at the surface point instead would
+    scale the exit's transverse part by n(P_b) / n_{i-1}, about 1 + 3e-5
+    here."""
+    c = W.coeffs_from_terms(1, {(0, 0, 0): 1.5, (0, 0, 1): 0.1})
+    m = W.Medium(kind=W.KIND_POLY, form=W.FORM_LINEAR, degree=1, coeffs=c, off=(0, 0, 1),
+                 bkind=W.BOUNDARY_BOX, bparams=(-10, -10, 0, 10, 10, 2, 0, 0), n_ext=1.0)
+    th = math.radians(40.0)
+    d0 = np.array([math.sin(th) * 0.8, math.sin(th) * 0.6, math.cos(th)])
+    for dopl in (1e-3, 7e-4):
+        r = _one(m, (0, 0, -1), d0, dopl, 100000)
+        assert r["exit_id"] == 5 and r["tir_internal"] == 0
+        np.testing.assert_allclose(r["d"], d0, atol=1e-13)
