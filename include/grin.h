@@ -374,11 +374,14 @@ int grin_serve_stats(grin_server server, grin_serve_counters* stats);
  *     stream before each launch).  It is shared by all calls and keeps the
  *     last call's contents: calls whose GPU work overlaps (other streams or
  *     threads) race on it and must be serialised by the caller.
- *   - Runs on the calling thread's current device.  The first call on each
- *     device looks the array's address up (cudaGetSymbolAddress); make that
- *     first call before any stream capture.
- *   - Synchronises `cuda_stream` before returning; same statuses as
- *     grin_trace_host. */
+ *   - Runs on the calling thread's current device and context; every call
+ *     looks the array's address up there (cudaGetSymbolAddress, which
+ *     allocates nothing once the library's module is loaded), so a device
+ *     reset or a different current context between calls is safe.
+ *   - Copies into the caller's host buffers and synchronises `cuda_stream`
+ *     before returning, which a stream being captured into a CUDA graph does
+ *     not allow: on such a stream it returns GRIN_ERR_INVALID_ARG and queues
+ *     nothing.  Otherwise the same statuses as grin_trace_host. */
 int grin_trace_host_static(const grin_medium_desc* desc, const grin_rays* rays,
                            const grin_params* params, const grin_out* out, void* cuda_stream);
 

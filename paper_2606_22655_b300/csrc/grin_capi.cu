@@ -19,6 +19,181 @@ using grin::DevMedium;
 
 using grin::kQueueSlots;
 
+static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+// The device record of a medium description (validated), as every trace
+// kernel takes it by value; for a grid medium the samples are copied into
+// *samples (the caller uploads them and sets m->grid).  A grid medium with
+// samples == nullptr is refused.
+int grin::describe_medium(const grin_medium_desc* d, DevMedium* mp, std::vector<float>* samples) {
+  if (!d || !mp) return GRIN_ERR_INVALID_ARG;
+  DevMedium& m = *mp;
+  std::memset(&m, 0, sizeof(m));
+  m.kind = d->kind;
+  m.form = d->form;
+  m.n_levels = d->n_levels;
+  m.bkind = d->boundary_kind;
+  m.n_ext = d->n_ext;
+  m.form_c = d->form_c;
+  if (!finite_pos(d->n_ext)) return GRIN_ERR_INVALID_ARG;
+  if (d->kind < GRIN_MEDIUM_POLY || d->kind > GRIN_MEDIUM_N2P) return GRIN_ERR_INVALID_ARG;
+  if (d->n_levels < 0 || d->n_levels > GRIN_MAX_LEVELS) return GRIN_ERR_INVALID_ARG;
+  if (d->n_levels > 0 && !(std::isfinite(d->level_lo) && std::isfinite(d->level_hi) &&
+                           d->level_hi > d->level_lo))
+    return GRIN_ERR_INVALID_ARG;
+  for (int k = 0; k < 8; ++k)
+    if (!std::isfinite(d->boundary[k])) return GRIN_ERR_INVALID_ARG;
+  const double* b = d->boundary;
+  switch (d->boundary_kind) {
+    case GRIN_BOUNDARY_BOX:
+      if (!(b[0] < b[3] && b[1] < b[4] && b[2] < b[5])) return GRIN_ERR_INVALID_ARG;
+      break;
+    case GRIN_BOUNDARY_SPHERE:
+      if (!(b[3] > 0.0)) return GRIN_ERR_INVALID_ARG;
+      break;
+    case GRIN_BOUNDARY_CYLINDER:
+      if (!(b[2] > 0.0 && b[3] < b[4])) return GRIN_ERR_INVALID_ARG;
+      break;
+    default:
+      return GRIN_ERR_INVALID_ARG;
+  }
+  std::memcpy(m.b, b, sizeof(m.b));
+
+  if (d->kind == GRIN_MEDIUM_N2P) {
+    // R, F, beta, gamma; the axis through norm_offset[0..1]; no scaling
+    if (!d->coeffs || d->form != GRIN_FORM_LINEAR) return GRIN_ERR_INVALID_ARG;
+    const double* c = d->coeffs;
+    if (!(finite_pos(c[0]) && finite_pos(c[1]) && std::isfinite(c[2]) && std::isfinite(c[3])))
+      return GRIN_ERR_INVALID_ARG;
+    if (!std::isfinite(d->norm_offset[0]) || !std::isfinite(d->norm_offset[1]))
+      return GRIN_ERR_INVALID_ARG;
+    m.pclass = grin::kN2P;
+    for (int k = 0; k < 3; ++k) {
+      m.off[k] = k < 2 ? d->norm_offset[k] : 0.0;
+      m.scale[k] = m.inv_scale[k] = 1.0;
+    }
+    for (int k = 0; k < 4; ++k) m.cglex[k] = m.c64[k] = c[k];
+    m.c64[4] = 0.0;
+    // base = n on the axis; the FP32 copy returns n - base (shift in c32[4])
+    const double n_axis = std::pow(1.0 + std::pow(c[0] * c[0] / (c[1] * c[1]), c[2]), c[3]);
+    float base_f = (float)n_axis;
+    if (!(std::isfinite(base_f) && base_f > 0.0f)) base_f = 1.0f;
+    m.base_f = base_f;
+    m.base = (double)base_f;
+    for (int k = 0; k < 4; ++k) m.c32[k] = (float)c[k];
+    m.c32[4] = base_f;
+  } else if (d->kind == GRIN_MEDIUM_POLY || d->kind == GRIN_MEDIUM_SPHERICAL) {
+    const bool sph = d->kind == GRIN_MEDIUM_SPHERICAL;
+    if (!d->coeffs || (!sph && (d->degree < 0 || d->degree > GRIN_MAX_DEGREE)))
+      return GRIN_ERR_INVALID_ARG;
+    if (d->form < GRIN_FORM_LINEAR || d->form > GRIN_FORM_RECIP) return GRIN_ERR_INVALID_ARG;
+    if (d->form == GRIN_FORM_RECIP && !std::isfinite(d->form_c)) return GRIN_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; ++k) {
+      if (!std::isfinite(d->norm_offset[k]) || !std::isfinite(d->norm_scale[k]) ||
+          d->norm_scale[k] == 0.0)
+        return GRIN_ERR_INVALID_ARG;
+      m.off[k] = d->norm_offset[k];
+      m.inv_scale[k] = 1.0 / d->norm_scale[k];
+    }
+    if (sph) {
+      // a0..a3 of the spherical freeform field, the same in every layout
+      m.pclass = grin::kSpherical;
+      for (int k = 0; k < 4; ++k) {
+        if (!std::isfinite(d->coeffs[k])) return GRIN_ERR_INVALID_ARG;
+        m.cglex[k] = m.c64[k] = d->coeffs[k];
+      }
+    } else {
+      m.pclass = d->degree <= 2 ? grin::kPoly2 : (d->degree <= 4 ? grin::kPoly4 : grin::kPoly6);
+      const int D = m.pclass;
+      // graded-lex input: kept as is (zero padded to class D) and scattered
+      // into the Horner layout of class D
+      int idx = 0;
+      for (int s = 0; s <= d->degree; ++s)
+        for (int i = s; i >= 0; --i)
+          for (int j = s - i; j >= 0; --j) {
+            double c = d->coeffs[idx];
+            if (!std::isfinite(c)) return GRIN_ERR_INVALID_ARG;
+            m.cglex[idx++] = c;
+            m.c64[grin::hidx(D, i, j, s - i - j)] = c;
+          }
+    }
+    for (int k = 0; k < 3; ++k) m.scale[k] = d->norm_scale[k];
+    const double c0 = m.c64[0];  // hidx(D, 0, 0, 0) == 0; a0 of the spherical field
+    float base_f = 1.0f;
+    if (d->form == GRIN_FORM_LINEAR) base_f = (float)c0;
+    else if (d->form == GRIN_FORM_SQRT && c0 > 0.0) base_f = (float)std::sqrt(c0);
+    else if (d->form == GRIN_FORM_RECIP && c0 != 0.0 && std::isfinite(d->form_c / c0))
+      base_f = (float)(d->form_c / c0);
+    if (!(std::isfinite(base_f) && base_f > 0.0f)) base_f = 1.0f;
+    m.base_f = base_f;
+    m.base = (double)base_f;
+    for (int k = 0; k < grin::kMaxTerms; ++k) m.c32[k] = (float)m.c64[k];
+    if (d->form == GRIN_FORM_LINEAR) m.c32[0] = (float)(c0 - m.base);
+    else if (d->form == GRIN_FORM_SQRT) m.c32[0] = (float)(c0 - m.base * m.base);
+  } else {
+    if (!samples) return GRIN_ERR_INVALID_ARG;
+    if (!d->grid || d->nx < 1 || d->ny < 1 || d->nz < 1) return GRIN_ERR_INVALID_ARG;
+    const int64_t cnt = (int64_t)d->nx * d->ny * d->nz;
+    if (cnt >= (int64_t(1) << 31)) return GRIN_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; ++k) {
+      if (!finite_pos(d->spacing[k]) || !std::isfinite(d->origin[k])) return GRIN_ERR_INVALID_ARG;
+      m.origin[k] = d->origin[k];
+      m.spacing[k] = d->spacing[k];
+      m.inv_spacing[k] = 1.0 / d->spacing[k];
+    }
+    m.nx = d->nx;
+    m.ny = d->ny;
+    m.nz = d->nz;
+    m.rows16 = d->nx % 4 == 0;  // the device copy is cudaMalloc'd (256-byte aligned)
+    try {
+      samples->resize((size_t)cnt);
+    } catch (...) {
+      return GRIN_ERR_OOM;
+    }
+    if (d->grid_on_device) {
+      if (cudaMemcpy(samples->data(), d->grid, (size_t)cnt * sizeof(float), cudaMemcpyDeviceToHost) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        return GRIN_ERR_INVALID_ARG;
+      }
+    } else {
+      std::memcpy(samples->data(), d->grid, (size_t)cnt * sizeof(float));
+    }
+    float lo = INFINITY, hi = -INFINITY;
+    for (float v : *samples) {
+      if (!std::isfinite(v)) return GRIN_ERR_INVALID_ARG;
+      lo = std::min(lo, v);
+      hi = std::max(hi, v);
+    }
+    // FP32 interpolation subtracts this value from every tap (exact for
+    // samples within a factor two of it), the samples stay as given
+    float base_f = (float)(0.5 * ((double)lo + (double)hi));
+    if (!(std::isfinite(base_f) && base_f != 0.0f)) base_f = 1.0f;
+    m.base_f = base_f;
+    m.base = (double)base_f;
+  }
+  if (d->n_levels > 0) {
+    m.lvl_lo = d->level_lo;
+    m.lvl_hi = d->level_hi;
+    m.lvl_span = d->level_hi - d->level_lo;
+    m.lvl_lo_rel_f = (float)(d->level_lo - m.base);
+    m.lvl_scale_f = (float)((double)d->n_levels / m.lvl_span);
+    m.lvl_step_f = (float)(m.lvl_span / (double)d->n_levels);
+  }
+  m.form_c_f = (float)m.form_c;
+  m.n_ext_f = (float)m.n_ext;
+  for (int k = 0; k < 3; ++k) {
+    m.off_f[k] = (float)m.off[k];
+    m.inv_scale_f[k] = (float)m.inv_scale[k];
+    m.origin_f[k] = (float)m.origin[k];
+    m.inv_spacing_f[k] = (float)m.inv_spacing[k];
+    m.origin_lo_f[k] = (float)(m.origin[k] - (double)m.origin_f[k]);
+    m.inv_spacing_lo_f[k] = (float)(m.inv_spacing[k] - (double)m.inv_spacing_f[k]);
+  }
+  for (int k = 0; k < 8; ++k) m.b_f[k] = (float)m.b[k];
+  return GRIN_OK;
+}
+
 extern "C" {
 
 const char* grin_status_string(int status) {
@@ -104,173 +279,13 @@ int grin_ctx_last_launches(grin_ctx ctx, int32_t* launches) {
   return GRIN_OK;
 }
 
-static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
-
 int grin_medium_create(grin_ctx ctx, const grin_medium_desc* d, grin_medium* out) {
   if (!ctx || !d || !out) return GRIN_ERR_INVALID_ARG;
   *out = nullptr;
   DevMedium m;
-  std::memset(&m, 0, sizeof(m));
-  m.kind = d->kind;
-  m.form = d->form;
-  m.n_levels = d->n_levels;
-  m.bkind = d->boundary_kind;
-  m.n_ext = d->n_ext;
-  m.form_c = d->form_c;
-  if (!finite_pos(d->n_ext)) return GRIN_ERR_INVALID_ARG;
-  if (d->kind < GRIN_MEDIUM_POLY || d->kind > GRIN_MEDIUM_N2P) return GRIN_ERR_INVALID_ARG;
-  if (d->n_levels < 0 || d->n_levels > GRIN_MAX_LEVELS) return GRIN_ERR_INVALID_ARG;
-  if (d->n_levels > 0 && !(std::isfinite(d->level_lo) && std::isfinite(d->level_hi) &&
-                           d->level_hi > d->level_lo))
-    return GRIN_ERR_INVALID_ARG;
-  for (int k = 0; k < 8; ++k)
-    if (!std::isfinite(d->boundary[k])) return GRIN_ERR_INVALID_ARG;
-  const double* b = d->boundary;
-  switch (d->boundary_kind) {
-    case GRIN_BOUNDARY_BOX:
-      if (!(b[0] < b[3] && b[1] < b[4] && b[2] < b[5])) return GRIN_ERR_INVALID_ARG;
-      break;
-    case GRIN_BOUNDARY_SPHERE:
-      if (!(b[3] > 0.0)) return GRIN_ERR_INVALID_ARG;
-      break;
-    case GRIN_BOUNDARY_CYLINDER:
-      if (!(b[2] > 0.0 && b[3] < b[4])) return GRIN_ERR_INVALID_ARG;
-      break;
-    default:
-      return GRIN_ERR_INVALID_ARG;
-  }
-  std::memcpy(m.b, b, sizeof(m.b));
-
   std::vector<float> samples;
-  if (d->kind == GRIN_MEDIUM_N2P) {
-    // R, F, beta, gamma; the axis through norm_offset[0..1]; no scaling
-    if (!d->coeffs || d->form != GRIN_FORM_LINEAR) return GRIN_ERR_INVALID_ARG;
-    const double* c = d->coeffs;
-    if (!(finite_pos(c[0]) && finite_pos(c[1]) && std::isfinite(c[2]) && std::isfinite(c[3])))
-      return GRIN_ERR_INVALID_ARG;
-    if (!std::isfinite(d->norm_offset[0]) || !std::isfinite(d->norm_offset[1]))
-      return GRIN_ERR_INVALID_ARG;
-    m.pclass = grin::kN2P;
-    for (int k = 0; k < 3; ++k) {
-      m.off[k] = k < 2 ? d->norm_offset[k] : 0.0;
-      m.scale[k] = m.inv_scale[k] = 1.0;
-    }
-    for (int k = 0; k < 4; ++k) m.cglex[k] = m.c64[k] = c[k];
-    m.c64[4] = 0.0;
-    // base = n on the axis; the FP32 copy returns n - base (shift in c32[4])
-    const double n_axis = std::pow(1.0 + std::pow(c[0] * c[0] / (c[1] * c[1]), c[2]), c[3]);
-    float base_f = (float)n_axis;
-    if (!(std::isfinite(base_f) && base_f > 0.0f)) base_f = 1.0f;
-    m.base_f = base_f;
-    m.base = (double)base_f;
-    for (int k = 0; k < 4; ++k) m.c32[k] = (float)c[k];
-    m.c32[4] = base_f;
-  } else if (d->kind == GRIN_MEDIUM_POLY || d->kind == GRIN_MEDIUM_SPHERICAL) {
-    const bool sph = d->kind == GRIN_MEDIUM_SPHERICAL;
-    if (!d->coeffs || (!sph && (d->degree < 0 || d->degree > GRIN_MAX_DEGREE)))
-      return GRIN_ERR_INVALID_ARG;
-    if (d->form < GRIN_FORM_LINEAR || d->form > GRIN_FORM_RECIP) return GRIN_ERR_INVALID_ARG;
-    if (d->form == GRIN_FORM_RECIP && !std::isfinite(d->form_c)) return GRIN_ERR_INVALID_ARG;
-    for (int k = 0; k < 3; ++k) {
-      if (!std::isfinite(d->norm_offset[k]) || !std::isfinite(d->norm_scale[k]) ||
-          d->norm_scale[k] == 0.0)
-        return GRIN_ERR_INVALID_ARG;
-      m.off[k] = d->norm_offset[k];
-      m.inv_scale[k] = 1.0 / d->norm_scale[k];
-    }
-    if (sph) {
-      // a0..a3 of the spherical freeform field, the same in every layout
-      m.pclass = grin::kSpherical;
-      for (int k = 0; k < 4; ++k) {
-        if (!std::isfinite(d->coeffs[k])) return GRIN_ERR_INVALID_ARG;
-        m.cglex[k] = m.c64[k] = d->coeffs[k];
-      }
-    } else {
-      m.pclass = d->degree <= 2 ? grin::kPoly2 : (d->degree <= 4 ? grin::kPoly4 : grin::kPoly6);
-      const int D = m.pclass;
-      // graded-lex input: kept as is (zero padded to class D) and scattered
-      // into the Horner layout of class D
-      int idx = 0;
-      for (int s = 0; s <= d->degree; ++s)
-        for (int i = s; i >= 0; --i)
-          for (int j = s - i; j >= 0; --j) {
-            double c = d->coeffs[idx];
-            if (!std::isfinite(c)) return GRIN_ERR_INVALID_ARG;
-            m.cglex[idx++] = c;
-            m.c64[grin::hidx(D, i, j, s - i - j)] = c;
-          }
-    }
-    for (int k = 0; k < 3; ++k) m.scale[k] = d->norm_scale[k];
-    const double c0 = m.c64[0];  // hidx(D, 0, 0, 0) == 0; a0 of the spherical field
-    float base_f = 1.0f;
-    if (d->form == GRIN_FORM_LINEAR) base_f = (float)c0;
-    else if (d->form == GRIN_FORM_SQRT && c0 > 0.0) base_f = (float)std::sqrt(c0);
-    else if (d->form == GRIN_FORM_RECIP && c0 != 0.0 && std::isfinite(d->form_c / c0))
-      base_f = (float)(d->form_c / c0);
-    if (!(std::isfinite(base_f) && base_f > 0.0f)) base_f = 1.0f;
-    m.base_f = base_f;
-    m.base = (double)base_f;
-    for (int k = 0; k < grin::kMaxTerms; ++k) m.c32[k] = (float)m.c64[k];
-    if (d->form == GRIN_FORM_LINEAR) m.c32[0] = (float)(c0 - m.base);
-    else if (d->form == GRIN_FORM_SQRT) m.c32[0] = (float)(c0 - m.base * m.base);
-  } else {
-    if (!d->grid || d->nx < 1 || d->ny < 1 || d->nz < 1) return GRIN_ERR_INVALID_ARG;
-    const int64_t cnt = (int64_t)d->nx * d->ny * d->nz;
-    if (cnt >= (int64_t(1) << 31)) return GRIN_ERR_INVALID_ARG;
-    for (int k = 0; k < 3; ++k) {
-      if (!finite_pos(d->spacing[k]) || !std::isfinite(d->origin[k])) return GRIN_ERR_INVALID_ARG;
-      m.origin[k] = d->origin[k];
-      m.spacing[k] = d->spacing[k];
-      m.inv_spacing[k] = 1.0 / d->spacing[k];
-    }
-    m.nx = d->nx;
-    m.ny = d->ny;
-    m.nz = d->nz;
-    m.rows16 = d->nx % 4 == 0;  // the device copy is cudaMalloc'd (256-byte aligned)
-    try {
-      samples.resize((size_t)cnt);
-    } catch (...) {
-      return GRIN_ERR_OOM;
-    }
-    if (d->grid_on_device) {
-      if (cudaMemcpy(samples.data(), d->grid, (size_t)cnt * sizeof(float), cudaMemcpyDeviceToHost) !=
-          cudaSuccess) {
-        cudaGetLastError();
-        return GRIN_ERR_INVALID_ARG;
-      }
-    } else {
-      std::memcpy(samples.data(), d->grid, (size_t)cnt * sizeof(float));
-    }
-    float lo = INFINITY, hi = -INFINITY;
-    for (float v : samples) {
-      if (!std::isfinite(v)) return GRIN_ERR_INVALID_ARG;
-      lo = std::min(lo, v);
-      hi = std::max(hi, v);
-    }
-    // FP32 interpolation subtracts this value from every tap (exact for
-    // samples within a factor two of it), the samples stay as given
-    float base_f = (float)(0.5 * ((double)lo + (double)hi));
-    if (!(std::isfinite(base_f) && base_f != 0.0f)) base_f = 1.0f;
-    m.base_f = base_f;
-    m.base = (double)base_f;
-  }
-  if (d->n_levels > 0) {
-    m.lvl_lo = d->level_lo;
-    m.lvl_hi = d->level_hi;
-    m.lvl_span = d->level_hi - d->level_lo;
-    m.lvl_lo_rel_f = (float)(d->level_lo - m.base);
-    m.lvl_scale_f = (float)((double)d->n_levels / m.lvl_span);
-    m.lvl_step_f = (float)(m.lvl_span / (double)d->n_levels);
-  }
-  m.form_c_f = (float)m.form_c;
-  m.n_ext_f = (float)m.n_ext;
-  for (int k = 0; k < 3; ++k) {
-    m.off_f[k] = (float)m.off[k];
-    m.inv_scale_f[k] = (float)m.inv_scale[k];
-    m.origin_f[k] = (float)m.origin[k];
-    m.inv_spacing_f[k] = (float)m.inv_spacing[k];
-  }
-  for (int k = 0; k < 8; ++k) m.b_f[k] = (float)m.b[k];
+  const int st = grin::describe_medium(d, &m, &samples);
+  if (st != GRIN_OK) return st;
 
   grin_medium med = new (std::nothrow) grin_medium_s;
   if (!med) return GRIN_ERR_OOM;

@@ -7,6 +7,7 @@
 
 #include <atomic>
 #include <utility>
+#include <vector>
 
 #include "grin.h"
 
@@ -48,6 +49,9 @@ struct DevMedium {
   float c32[kMaxTerms];           // same, constant term shifted for nu
   float base_f, form_c_f, n_ext_f;
   float off_f[3], inv_scale_f[3], origin_f[3], inv_spacing_f[3];
+  // residuals of origin_f and inv_spacing_f: origin = origin_f + origin_lo_f and
+  // 1 / spacing = inv_spacing_f + inv_spacing_lo_f to about 2^-48 relative
+  float origin_lo_f[3], inv_spacing_lo_f[3];
   float lvl_lo_rel_f, lvl_scale_f, lvl_step_f;  // lo - base, L / span, span / L
   float b_f[8];
 };
@@ -64,6 +68,10 @@ struct TraceArgs {
   // index order
   const uint32_t* perm = nullptr;
 };
+
+// Validated device record of a medium description (grin_capi.cu); a grid's
+// samples go to *samples for the caller to upload (nullptr refuses grids).
+int describe_medium(const grin_medium_desc* d, DevMedium* m, std::vector<float>* samples);
 
 // Number of kernel launches made; negative grin_status on failure.
 int launch_fp64(const DevMedium& m, const TraceArgs& a, cudaStream_t s, int sm_count);

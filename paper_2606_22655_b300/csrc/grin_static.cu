@@ -21,7 +21,6 @@
 
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "grin_device.cuh"
 #include "grin_internal.h"
@@ -37,115 +36,26 @@ constexpr size_t kScratchBytes = kHeader + kPerRay * (size_t)kMaxRays;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// Device addresses of g_scratch, looked up once per device.
-constexpr int kMaxDevices = 64;
-unsigned char* g_scratch_dev[kMaxDevices] = {};
-int g_sm_count[kMaxDevices] = {};
-std::mutex g_setup_mutex;
-
+// The device address of g_scratch in the current context, looked up on every
+// call: cudaGetSymbolAddress allocates nothing once the module is loaded, and
+// an address cached per device could name a module instance that a later
+// cudaDeviceReset, or another context made current by the caller, no longer
+// holds.
 int scratch_for_current_device(unsigned char** ptr, int* sms) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return GRIN_ERR_CUDA;
-  if (dev < 0 || dev >= kMaxDevices) return GRIN_ERR_INVALID_ARG;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_dev[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return GRIN_ERR_CUDA;
-    }
-    int n = 0;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-      cudaGetLastError();
-      return GRIN_ERR_CUDA;
-    }
-    g_sm_count[dev] = n;
-    g_scratch_dev[dev] = (unsigned char*)p;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();
+    return GRIN_ERR_CUDA;
   }
-  *ptr = g_scratch_dev[dev];
-  *sms = g_sm_count[dev];
-  return GRIN_OK;
-}
-
-// The polynomial medium as grin_medium_create would hold it, built on the
-// stack (the polynomial lives entirely in the kernel parameter block).
-int poly_medium(const grin_medium_desc* d, grin::DevMedium* out) {
-  grin::DevMedium& m = *out;
-  std::memset(&m, 0, sizeof(m));
-  if (d->kind != GRIN_MEDIUM_POLY || !d->coeffs) return GRIN_ERR_INVALID_ARG;
-  if (d->degree < 0 || d->degree > GRIN_MAX_DEGREE) return GRIN_ERR_INVALID_ARG;
-  if (d->form < GRIN_FORM_LINEAR || d->form > GRIN_FORM_RECIP) return GRIN_ERR_INVALID_ARG;
-  if (d->form == GRIN_FORM_RECIP && !std::isfinite(d->form_c)) return GRIN_ERR_INVALID_ARG;
-  if (!(std::isfinite(d->n_ext) && d->n_ext > 0.0)) return GRIN_ERR_INVALID_ARG;
-  if (d->n_levels < 0 || d->n_levels > GRIN_MAX_LEVELS) return GRIN_ERR_INVALID_ARG;
-  if (d->n_levels > 0 &&
-      !(std::isfinite(d->level_lo) && std::isfinite(d->level_hi) && d->level_hi > d->level_lo))
-    return GRIN_ERR_INVALID_ARG;
-  const double* b = d->boundary;
-  for (int k = 0; k < 8; ++k)
-    if (!std::isfinite(b[k])) return GRIN_ERR_INVALID_ARG;
-  if (d->boundary_kind == GRIN_BOUNDARY_BOX) {
-    if (!(b[0] < b[3] && b[1] < b[4] && b[2] < b[5])) return GRIN_ERR_INVALID_ARG;
-  } else if (d->boundary_kind == GRIN_BOUNDARY_SPHERE) {
-    if (!(b[3] > 0.0)) return GRIN_ERR_INVALID_ARG;
-  } else if (d->boundary_kind == GRIN_BOUNDARY_CYLINDER) {
-    if (!(b[2] > 0.0 && b[3] < b[4])) return GRIN_ERR_INVALID_ARG;
-  } else {
-    return GRIN_ERR_INVALID_ARG;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return GRIN_ERR_CUDA;
   }
-  m.kind = GRIN_MEDIUM_POLY;
-  m.form = d->form;
-  m.form_c = d->form_c;
-  m.n_levels = d->n_levels;
-  m.bkind = d->boundary_kind;
-  m.n_ext = d->n_ext;
-  std::memcpy(m.b, b, sizeof(m.b));
-  for (int k = 0; k < 3; ++k) {
-    if (!std::isfinite(d->norm_offset[k]) || !std::isfinite(d->norm_scale[k]) ||
-        d->norm_scale[k] == 0.0)
-      return GRIN_ERR_INVALID_ARG;
-    m.off[k] = d->norm_offset[k];
-    m.scale[k] = d->norm_scale[k];
-    m.inv_scale[k] = 1.0 / d->norm_scale[k];
-  }
-  m.pclass = d->degree <= 2 ? grin::kPoly2 : (d->degree <= 4 ? grin::kPoly4 : grin::kPoly6);
-  const int D = m.pclass;
-  int idx = 0;
-  for (int s = 0; s <= d->degree; ++s)
-    for (int i = s; i >= 0; --i)
-      for (int j = s - i; j >= 0; --j) {
-        double c = d->coeffs[idx];
-        if (!std::isfinite(c)) return GRIN_ERR_INVALID_ARG;
-        m.cglex[idx++] = c;
-        m.c64[grin::hidx(D, i, j, s - i - j)] = c;
-      }
-  const double c0 = m.c64[0];
-  float base_f = 1.0f;
-  if (d->form == GRIN_FORM_LINEAR) base_f = (float)c0;
-  else if (d->form == GRIN_FORM_SQRT && c0 > 0.0) base_f = (float)std::sqrt(c0);
-  else if (d->form == GRIN_FORM_RECIP && c0 != 0.0 && std::isfinite(d->form_c / c0))
-    base_f = (float)(d->form_c / c0);
-  if (!(std::isfinite(base_f) && base_f > 0.0f)) base_f = 1.0f;
-  m.base_f = base_f;
-  m.base = (double)base_f;
-  for (int k = 0; k < grin::kMaxTerms; ++k) m.c32[k] = (float)m.c64[k];
-  if (d->form == GRIN_FORM_LINEAR) m.c32[0] = (float)(c0 - m.base);
-  else if (d->form == GRIN_FORM_SQRT) m.c32[0] = (float)(c0 - m.base * m.base);
-  if (d->n_levels > 0) {
-    m.lvl_lo = d->level_lo;
-    m.lvl_hi = d->level_hi;
-    m.lvl_span = d->level_hi - d->level_lo;
-    m.lvl_lo_rel_f = (float)(d->level_lo - m.base);
-    m.lvl_scale_f = (float)((double)d->n_levels / m.lvl_span);
-    m.lvl_step_f = (float)(m.lvl_span / (double)d->n_levels);
-  }
-  m.form_c_f = (float)m.form_c;
-  m.n_ext_f = (float)m.n_ext;
-  for (int k = 0; k < 3; ++k) {
-    m.off_f[k] = (float)m.off[k];
-    m.inv_scale_f[k] = (float)m.inv_scale[k];
-  }
-  for (int k = 0; k < 8; ++k) m.b_f[k] = (float)m.b[k];
+  *ptr = (unsigned char*)p;
+  *sms = n;
   return GRIN_OK;
 }
 
@@ -162,8 +72,11 @@ extern "C" int grin_trace_host_static(const grin_medium_desc* desc, const grin_r
   if (p->precision != GRIN_PREC_FP64 && p->precision != GRIN_PREC_FP32_MIXED &&
       p->precision != GRIN_PREC_FP64_FAST)
     return GRIN_ERR_INVALID_ARG;
+  // polynomial media only (they live entirely in the kernel's parameter
+  // block); built exactly as grin_medium_create builds them
+  if (desc->kind != GRIN_MEDIUM_POLY) return GRIN_ERR_INVALID_ARG;
   grin::DevMedium m;
-  int st = poly_medium(desc, &m);
+  int st = grin::describe_medium(desc, &m, nullptr);
   if (st != GRIN_OK) return st;
   const int64_t n = rays->count;
   if (n == 0) return GRIN_OK;
@@ -173,11 +86,19 @@ extern "C" int grin_trace_host_static(const grin_medium_desc* desc, const grin_r
       !out->exit_id || !out->steps || !out->tir_internal || !out->tir_boundary)
     return GRIN_ERR_INVALID_ARG;
 
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // the copies into pageable host memory and the final synchronisation are
+  // not allowed while the stream is being captured into a graph
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return GRIN_ERR_CUDA;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return GRIN_ERR_INVALID_ARG;
   unsigned char* base = nullptr;
   int sms = 0;
   st = scratch_for_current_device(&base, &sms);
   if (st != GRIN_OK) return st;
-  cudaStream_t s = (cudaStream_t)cuda_stream;
   const size_t esz = rays->dtype == GRIN_F64 ? 8 : 4;
   unsigned long long* queue = (unsigned long long*)base;
   unsigned char* in = base + kHeader;
