@@ -79,7 +79,8 @@ class _Medium(ctypes.Structure):
 
 
 class _Params(ctypes.Structure):
-    _fields_ = [("dopl", ctypes.c_double), ("max_steps", ctypes.c_int32)]
+    _fields_ = [("dopl", ctypes.c_double), ("max_steps", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("index_rule", ctypes.c_int32), ("perturb", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
 def _load():
@@ -146,9 +147,12 @@ def medium_eval(medium, points) -> (np.ndarray, np.ndarray):
 
 
 def trace(medium, origins, dirs, dopl: float, max_steps: int,
-          threads: Optional[int] = None) -> Dict[str, np.ndarray]:
+          threads: Optional[int] = None, flags: int = 0, index_rule: int = 0,
+          perturb: float = 0.0, seed: int = 0) -> Dict[str, np.ndarray]:
     """Trace every ray; returns exit point P, direction d, optical path opl,
-    exit_id, steps, tir_internal, tir_boundary and margins (n, 4)."""
+    exit_id, steps, tir_internal, tir_boundary and margins (n, 4).
+    index_rule, perturb and seed select the conditioning probe (see
+    vrt_oracle.h); the defaults trace the method itself."""
     lib = _load()
     b = _Bound(medium)
     o = np.ascontiguousarray(origins, dtype=np.float64).reshape(-1, 3)
@@ -158,7 +162,7 @@ def trace(medium, origins, dirs, dopl: float, max_steps: int,
                exit_id=np.zeros(n, np.int32), steps=np.zeros(n, np.int32),
                tir_internal=np.zeros(n, np.int32), tir_boundary=np.zeros(n, np.int32),
                margins=np.zeros((n, 4)))
-    prm = _Params(float(dopl), int(max_steps))
+    prm = _Params(float(dopl), int(max_steps), int(flags), int(index_rule), float(perturb), int(seed))
     if threads is None:
         threads = os.cpu_count() or 1
     if n:
@@ -184,7 +188,7 @@ def trace_path(medium, origin, direction, dopl: float, max_steps: int, cap: Opti
                tir_boundary=np.zeros(1, np.int32), margins=np.zeros(4))
     plen = ctypes.c_int64()
     ip = lambda a: _ptr(a, ctypes.c_int32)
-    prm = _Params(float(dopl), int(max_steps))
+    prm = _Params(float(dopl), int(max_steps), 0, 0, 0.0, 0)
     lib.orc_trace_path(ctypes.byref(b.s), ctypes.byref(prm), _ptr(o), _ptr(d), _ptr(out["P"]),
                        _ptr(out["d"]), _ptr(out["opl"]), ip(out["exit_id"]), ip(out["steps"]),
                        ip(out["tir_internal"]), ip(out["tir_boundary"]), _ptr(out["margins"]),
@@ -215,7 +219,7 @@ def trace_tangent(medium, origins, dirs, dopl: float, max_steps: int, samples=No
                exit_id=np.zeros(n, np.int32), steps=np.zeros(n, np.int32),
                tP=np.zeros((n, nc, 3)), td=np.zeros((n, nc, 3)), topl=np.zeros((n, nc)),
                flag=np.zeros(n, np.int32))
-    prm = _Params(float(dopl), int(max_steps))
+    prm = _Params(float(dopl), int(max_steps), 0, 0, 0.0, 0)
     ip = lambda a: _ptr(a, ctypes.c_int32)
     rc = lib.orc_trace_tangent(ctypes.byref(b.s), ctypes.byref(prm), n, _ptr(o), _ptr(d),
                                0 if samples is None else nc, _ptr(par, ctypes.c_int64),

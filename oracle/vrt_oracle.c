@@ -552,7 +552,18 @@ static void sample(const orc_medium* m, const double* P, double* n, double* g, i
   }
 }
 
-static void trace_one(const orc_medium* m, const orc_params* prm, const double* o,
+/* Conditioning probe: a deterministic value in [-1, 1) for (seed, ray,
+ * step, axis) from the SplitMix64 finaliser (Steele, Lea and Flood 2014). */
+static double probe_uniform(uint64_t seed, int64_t ray, int steps, int axis) {
+  uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(4 * ((uint64_t)ray * 1000003ull +
+                                                              (uint64_t)steps) + (uint64_t)axis + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+static void trace_one(const orc_medium* m, const orc_params* prm, int64_t ray, const double* o,
                       const double* d0, ray_out* out, double* path, int64_t cap,
                       int64_t* plen) {
   double P[3] = {o[0], o[1], o[2]}, d[3] = {d0[0], d0[1], d0[2]};
@@ -642,7 +653,12 @@ static void trace_one(const orc_medium* m, const orc_params* prm, const double* 
       out->exit_id = face;
       break;
     }
-    for (int a = 0; a < 3; ++a) P[a] = Q[a];
+    double step_v[3], g_prev[3];
+    for (int a = 0; a < 3; ++a) {
+      step_v[a] = Q[a] - P[a];
+      g_prev[a] = g[a];
+      P[a] = Q[a];
+    }
     nsum_add(&opl, dopl);
     ++steps;
     if (path && np < cap) {
@@ -653,6 +669,10 @@ static void trace_one(const orc_medium* m, const orc_params* prm, const double* 
     double n_i;
     int lvl_i;
     sample(m, P, &n_i, g, &lvl_i, &u);
+    if (prm->perturb > 0.0) {
+      double gl = norm3(g);
+      for (int a = 0; a < 3; ++a) g[a] += prm->perturb * gl * probe_uniform(prm->seed, ray, steps, a);
+    }
     if (lvl_i >= 0) out->mg[ORC_M_LEVEL] = minf(out->mg[ORC_M_LEVEL], fabs(u - floor(u + 0.5)));
     if (!(isfinite(n_i) && n_i > 0.0)) {
       out->exit_id = EXIT_INVALID;
@@ -669,6 +689,12 @@ static void trace_one(const orc_medium* m, const orc_params* prm, const double* 
       double N[3] = {g[0] / gn, g[1] / gn, g[2] / gn}; /* Eq. 5 */
       double c = dot3(N, d);
       double mu = n_prev / n_i;
+      if (prm->index_rule == 1 && lvl_i < 0) {
+        /* probe: n_i - n_{i-1} by the trapezoid rule on grad n */
+        double dn = 0.5 * ((g_prev[0] + g[0]) * step_v[0] + (g_prev[1] + g[1]) * step_v[1] +
+                           (g_prev[2] + g[2]) * step_v[2]);
+        mu = 1.0 - dn / n_i;
+      }
       out->mg[ORC_M_TAN] = minf(out->mg[ORC_M_TAN], fabs(c));
       if (c == 0.0) {
         /* Sec. II (iv): tangential incidence, circular arc of curvature
@@ -744,7 +770,7 @@ static void* worker(void* arg) {
   job* j = (job*)arg;
   ray_out r;
   for (int64_t i = j->tid; i < j->n; i += j->nt) {
-    trace_one(j->m, j->p, j->o + 3 * i, j->d + 3 * i, &r, NULL, 0, NULL);
+    trace_one(j->m, j->p, i, j->o + 3 * i, j->d + 3 * i, &r, NULL, 0, NULL);
     store(j, i, &r);
   }
   return NULL;
@@ -778,7 +804,7 @@ int orc_trace_path(const orc_medium* m, const orc_params* p, const double* o, co
                    double* path, int64_t cap, int64_t* path_len) {
   ray_out r;
   *path_len = 0;
-  trace_one(m, p, o, d, &r, path, cap, path_len);
+  trace_one(m, p, 0, o, d, &r, path, cap, path_len);
   job j = {m, p, 1, o, d, P_out, d_out, opl, margins, exit_id, steps, tir_int, tir_bnd, 0, 1};
   store(&j, 0, &r);
   return 0;

@@ -50,6 +50,17 @@ typedef struct {
 typedef struct {
   double dopl;           /* Delta L_0: optical path per step */
   int32_t max_steps;
+  int32_t flags;         /* 0 (ORC_LEVEL_ROOT below for layered media) */
+  /* Conditioning probe, for judging which rays a less precise tracer can be
+   * held to (0, 0.0 for the method itself): index_rule 1 takes the index
+   * difference n_i - n_{i-1} of a refraction (continuous media) by the
+   * trapezoid rule on grad n along the step instead of from the two point
+   * values; perturb > 0 adds to every sampled gradient a pseudo-random
+   * vector of at most perturb |grad n| per component (SplitMix64 of seed,
+   * ray index, step and axis). */
+  int32_t index_rule;
+  double perturb;
+  uint64_t seed;
 } orc_params;
 
 /* Per-ray decision margins: min distance of |N.I| from its critical value

@@ -75,19 +75,19 @@ struct Cfg {
   static __device__ __forceinline__ int bk(const DevMedium& m) { return BK >= 0 ? BK : m.bkind; }
   static __device__ __forceinline__ int form(const DevMedium& m) { return FORM >= 0 ? FORM : m.form; }
 
-  // nu = n - base (after layering), the gradient of the smooth field, level.
+  // nu = n - base (after layering), the gradient of the smooth field, level,
+  // at the point (px + lx, py + ly, pz + lz) (a hi + lo pair; polynomial
+  // media read the hi part).
   static __device__ __forceinline__ void eval(const DevMedium& m, float px, float py, float pz,
-                                              float& nu, float& gx, float& gy, float& gz,
-                                              int& lvl) {
+                                              float lx, float ly, float lz, float& nu,
+                                              float& gx, float& gy, float& gz, int& lvl) {
     float f;
     if (GRID) {
-      float u[3] = {(px - m.origin_f[0]) * m.inv_spacing_f[0],
-                    (py - m.origin_f[1]) * m.inv_spacing_f[1],
-                    (pz - m.origin_f[2]) * m.inv_spacing_f[2]};
-      grid_vg<float>(m, u, m.base_f, f, gx, gy, gz);
-      gx *= m.inv_spacing_f[0];
-      gy *= m.inv_spacing_f[1];
-      gz *= m.inv_spacing_f[2];
+      const float ph[3] = {px, py, pz}, pl[3] = {lx, ly, lz};
+      int i0[3];
+      float fr[3];
+      cell(m, ph, pl, i0, fr);
+      grid_gather(m, i0, fr, f, gx, gy, gz);
     } else {
       float x = (px - m.off_f[0]) * m.inv_scale_f[0];
       float y = (py - m.off_f[1]) * m.inv_scale_f[1];
@@ -138,30 +138,106 @@ struct Cfg {
     }
   }
 
-  // Gridded media.  The cell of the 64-tap stencil at a point and the
-  // fractions inside it, taken exactly as grid_vg takes them (the grid
-  // coordinate clamped to [-2, n + 1], a NaN to -2).
-  static __device__ __forceinline__ void cell(const DevMedium& m, const float* q, int* i0,
-                                              float* fr) {
+  // Gridded media.  The cell of the 64-tap stencil at the point ph + pl and
+  // the fractions inside it.  The grid coordinate u = (p - origin) / spacing
+  // is formed as u_h + corr: u_h = fl(fl(ph - origin_f) * inv_spacing_f) picks
+  // the cell (clamped to [-2, n + 1], a NaN to -2) and corr collects, by
+  // TwoSum and a fused product residual, every part that u_h drops (the
+  // subtraction's and the product's rounding, the point's low part and the
+  // residuals of origin_f and inv_spacing_f).  An FP32 point near 10 mm is
+  // only good to about 1e-6 mm, 1e-5 of a 256^3 cell; with corr the fraction
+  // is good to FP32 resolution within the cell, which keeps grad n and hence
+  // N.I at about 1e-7 (near turning points of n, where Eq. 9 is steep in
+  // N.I, that error is what the path accumulates).  The fraction may leave
+  // [0, 1) by corr; the cell's polynomial is then taken a hair outside it.
+  static __device__ __forceinline__ void cell(const DevMedium& m, const float* ph, const float* pl,
+                                              int* i0, float* fr) {
     const int n[3] = {m.nx, m.ny, m.nz};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      float u = (q[k] - m.origin_f[k]) * m.inv_spacing_f[k];
-      u = vmax(u, -2.0f);
-      u = vmin(u, (float)(n[k] + 1));
-      const float fl = vfloor(u);
+      const float s = m.inv_spacing_f[k];
+      const float a = ph[k] - m.origin_f[k];
+      const float bp = a - ph[k];
+      const float ea = (ph[k] - (a - bp)) + (-m.origin_f[k] - bp);  // a + ea = ph - origin_f
+      float u = a * s;
+      const float eu = fmaf(a, s, -u);                              // u + eu = a s
+      float corr = fmaf(a, m.inv_spacing_lo_f[k], fmaf((ea + pl[k]) - m.origin_lo_f[k], s, eu));
+      if (!(u > -2.0f)) {
+        u = -2.0f;
+        corr = 0.0f;
+      }
+      if (u > (float)(n[k] + 1)) {
+        u = (float)(n[k] + 1);
+        corr = 0.0f;
+      }
+      const float fl = floorf(u);
       i0[k] = (int)fl;
-      fr[k] = u - fl;
+      fr[k] = (u - fl) + corr;
     }
   }
 
-  // eval for a gridded medium from the cell's 64 taps (sample - base, row
-  // c * 4 + b at col[(c * 4 + b) * kTapRow], x taps in .x .. .w): the same
-  // products summed in the same order as grid_vg's, so the same value and
-  // gradient bit for bit.
+  // The sample at the stencil's centre tap (cell corner i0, edge-clamped):
+  // every tap is taken relative to it, so the sums of the interpolant and
+  // its gradient carry the local variation of the samples (a few 1e-3 on a
+  // 256^3 blob field) instead of their offset from a global base (5e-2),
+  // with ten times fewer rounding errors in grad n.
+  static __device__ __forceinline__ float centre_tap(const DevMedium& m, const int* i0) {
+    const int ix = min(max(i0[0], 0), m.nx - 1), iy = min(max(i0[1], 0), m.ny - 1),
+              iz = min(max(i0[2], 0), m.nz - 1);
+    return __ldg(m.grid + ((int64_t)iz * m.ny + iy) * m.nx + ix);
+  }
+
+  // Catmull-Rom value (f = n - base) and gradient (physical units) at cell
+  // i0 and fractions fr, gathering the 64 edge-clamped taps from the grid:
+  // the same products summed in the same order as eval_taps from the tap
+  // cache, so both give the same bits.
+  static __device__ __forceinline__ void grid_gather(const DevMedium& m, const int* i0,
+                                                     const float* fr, float& f, float& gx,
+                                                     float& gy, float& gz) {
+    float w[3][4], dw[3][4];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) cr_w(fr[k], w[k], dw[k]);
+    const float lb = centre_tap(m, i0);
+    const int ix[4] = {min(max(i0[0] - 1, 0), m.nx - 1), min(max(i0[0], 0), m.nx - 1),
+                       min(max(i0[0] + 1, 0), m.nx - 1), min(max(i0[0] + 2, 0), m.nx - 1)};
+    float V = 0.0f, GX = 0.0f, GY = 0.0f, GZ = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int iz = min(max(i0[2] - 1 + c, 0), m.nz - 1);
+      float sv = 0.0f, sx = 0.0f, sy = 0.0f;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int iy = min(max(i0[1] - 1 + b, 0), m.ny - 1);
+        const float* __restrict__ row = m.grid + ((int64_t)iz * m.ny + iy) * m.nx;
+        float r = 0.0f, rx = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float t = __ldg(row + ix[k]) - lb;
+          r = fmadd(w[0][k], t, r);
+          rx = fmadd(dw[0][k], t, rx);
+        }
+        sv = fmadd(w[1][b], r, sv);
+        sx = fmadd(w[1][b], rx, sx);
+        sy = fmadd(dw[1][b], r, sy);
+      }
+      V = fmadd(w[2][c], sv, V);
+      GX = fmadd(w[2][c], sx, GX);
+      GY = fmadd(w[2][c], sy, GY);
+      GZ = fmadd(dw[2][c], sv, GZ);
+    }
+    f = V + (lb - m.base_f);
+    gx = GX * m.inv_spacing_f[0];
+    gy = GY * m.inv_spacing_f[1];
+    gz = GZ * m.inv_spacing_f[2];
+  }
+
+  // eval for a gridded medium from the cell's 64 taps (sample - lb, lb the
+  // centre tap; row c * 4 + b at col[(c * 4 + b) * kTapRow], x taps in
+  // .x .. .w): the same products summed in the same order as grid_gather's,
+  // so the same value and gradient bit for bit.
   static __device__ __forceinline__ void eval_taps(const DevMedium& m, const float* fr,
-                                                   const float* col, float& nu, float& gx,
-                                                   float& gy, float& gz, int& lvl) {
+                                                   const float* col, float lb, float& nu,
+                                                   float& gx, float& gy, float& gz, int& lvl) {
     float w[3][4], dw[3][4];
 #pragma unroll
     for (int k = 0; k < 3; ++k) cr_w(fr[k], w[k], dw[k]);
@@ -191,7 +267,7 @@ struct Cfg {
     gx = GX * m.inv_spacing_f[0];
     gy = GY * m.inv_spacing_f[1];
     gz = GZ * m.inv_spacing_f[2];
-    level(m, V, nu, lvl);
+    level(m, V + (lb - m.base_f), nu, lvl);
   }
 
   static __device__ __forceinline__ bool inside(const DevMedium& m, const float* q) {
@@ -281,6 +357,14 @@ __device__ __forceinline__ void renorm(float* v) {
 
 __device__ __forceinline__ V3 v3f(const float* v) { return mk((double)v[0], (double)v[1], (double)v[2]); }
 
+// eval at an FP64 point, split into a hi + lo float pair.
+template <class C>
+__device__ __forceinline__ void eval64(const DevMedium& m, V3 p, float& nu, float* g, int& lvl) {
+  const float hx = (float)p.x, hy = (float)p.y, hz = (float)p.z;
+  C::eval(m, hx, hy, hz, (float)(p.x - (double)hx), (float)(p.y - (double)hy),
+          (float)(p.z - (double)hz), nu, g[0], g[1], g[2], lvl);
+}
+
 // Box entry in FP32.  With an axis-aligned face the incidence cosine is one
 // direction component, the crossing a slab parameter and the reflection a
 // sign flip, so FP32 carries them to its own rounding; the entry point is
@@ -326,7 +410,7 @@ __device__ bool init_ray_box32(const DevMedium& m, const TraceArgs& a, int64_t r
     for (int k = 0; k < 3; ++k) o[k] = fmaf(tn, d[k], o[k]);
     o[axis] = hi ? b[3 + axis] : b[axis];
     s.opl_x = m.n_ext * (double)tn;
-    C::eval(m, o[0], o[1], o[2], nu, s.gp[0], s.gp[1], s.gp[2], s.lvl_prev);
+    C::eval(m, o[0], o[1], o[2], 0.0f, 0.0f, 0.0f, nu, s.gp[0], s.gp[1], s.gp[2], s.lvl_prev);
     // Snell at the face: N = outward axis, c = N.I, mu = n_ext / n(P_b)
     const float mu = m.n_ext_f / (m.base_f + nu);
     const float c = hi ? d[axis] : -d[axis];
@@ -342,7 +426,7 @@ __device__ bool init_ray_box32(const DevMedium& m, const TraceArgs& a, int64_t r
     d[axis] += hi ? gamma : -gamma;
     renorm(d);
   } else {
-    C::eval(m, o[0], o[1], o[2], nu, s.gp[0], s.gp[1], s.gp[2], s.lvl_prev);
+    C::eval(m, o[0], o[1], o[2], 0.0f, 0.0f, 0.0f, nu, s.gp[0], s.gp[1], s.gp[2], s.lvl_prev);
   }
   if (!set_index(m, s, nu)) {
     finish(a, r, s, v3f(o), v3f(d), GRIN_EXIT_INVALID);
@@ -424,7 +508,8 @@ __device__ __forceinline__ int surface_event_box32(const DevMedium& m, const Tra
     ++s.tir_b;
     s.h = dopl_f * s.inv_prev;
     float nu;
-    C::eval(m, s.ph[0], s.ph[1], s.ph[2], nu, s.gp[0], s.gp[1], s.gp[2], s.lvl_prev);
+    C::eval(m, s.ph[0], s.ph[1], s.ph[2], s.pl[0], s.pl[1], s.pl[2], nu, s.gp[0], s.gp[1], s.gp[2],
+            s.lvl_prev);
     if (!set_index(m, s, nu)) {
       finish(a, r, s, pos64(s), dir64(s), GRIN_EXIT_INVALID);
       return 2;
@@ -471,14 +556,14 @@ __device__ bool init_ray(const DevMedium& m, const TraceArgs& a, int64_t r, RayF
     }
     s.opl_x = m.n_ext * t;
     p = pb;
-    C::eval(m, (float)p.x, (float)p.y, (float)p.z, nu, s.gp[0], s.gp[1], s.gp[2], s.lvl_prev);
+    eval64<C>(m, p, nu, s.gp, s.lvl_prev);
     double nb_in = (double)m.base_f + (double)nu;
     if (refract64(d, nb, m.n_ext / nb_in)) {
       finish(a, r, s, p, d, GRIN_EXIT_ENTRY_REFLECT);
       return false;
     }
   } else {
-    C::eval(m, (float)p.x, (float)p.y, (float)p.z, nu, s.gp[0], s.gp[1], s.gp[2], s.lvl_prev);
+    eval64<C>(m, p, nu, s.gp, s.lvl_prev);
   }
   if (!set_index(m, s, nu)) {
     finish(a, r, s, p, d, GRIN_EXIT_INVALID);
@@ -517,7 +602,7 @@ __device__ __forceinline__ int surface_event(const DevMedium& m, const TraceArgs
     ++s.tir_b;
     s.h = dopl_f * s.inv_prev;
     float nu;
-    C::eval(m, (float)pb.x, (float)pb.y, (float)pb.z, nu, s.gp[0], s.gp[1], s.gp[2], s.lvl_prev);
+    eval64<C>(m, pb, nu, s.gp, s.lvl_prev);
     bool ok = set_index(m, s, nu);
     set_pos(s, pb);
     set_dir(s, d);
@@ -533,6 +618,12 @@ __device__ __forceinline__ int surface_event(const DevMedium& m, const TraceArgs
   }
   finish(a, r, s, pb, d, face);
   return 2;
+}
+
+// The index difference n_i - n_{i-1} of a step dv by the trapezoid rule on
+// grad n at its ends (gp, g).
+__device__ __forceinline__ float trapezoid(const float* gp, const float* g, const float* dv) {
+  return 0.5f * fmaf(gp[0] + g[0], dv[0], fmaf(gp[1] + g[1], dv[1], (gp[2] + g[2]) * dv[2]));
 }
 
 // Near critical or grazing incidence: D and gamma from the same FP32 inputs
@@ -578,7 +669,7 @@ __device__ __noinline__ bool step_slow(const DevMedium& m, const TraceArgs& a, i
   ++s.steps;
   float nu_i, g[3];
   int lvl_i;
-  C::eval(m, qh[0], qh[1], qh[2], nu_i, g[0], g[1], g[2], lvl_i);
+  C::eval(m, qh[0], qh[1], qh[2], ql[0], ql[1], ql[2], nu_i, g[0], g[1], g[2], lvl_i);
   const float n_i = m.base_f + nu_i;
   if (GRIN_UNLIKELY(!(isfinite(n_i) && n_i > 0.0f))) {
     finish(a, r, s, pos64(s), dir64(s), GRIN_EXIT_INVALID);
@@ -597,8 +688,8 @@ __device__ __noinline__ bool step_slow(const DevMedium& m, const TraceArgs& a, i
       float hi = dopl_f * inv_n;
       float nu2, g2x, g2y, g2z;
       int l2;
-      C::eval(m, fmaf(hi, N[0], qh[0]), fmaf(hi, N[1], qh[1]), fmaf(hi, N[2], qh[2]), nu2, g2x,
-              g2y, g2z, l2);
+      C::eval(m, fmaf(hi, N[0], qh[0]), fmaf(hi, N[1], qh[1]), fmaf(hi, N[2], qh[2]), ql[0], ql[1],
+              ql[2], nu2, g2x, g2y, g2z, l2);
       float k = (nu2 - nu_i) * 0.5f * inv_n;
       float w = fmaf(-k, k, 1.0f);
       float a0 = w > 0.0f ? sqrtf(w) : 0.0f;
@@ -615,8 +706,7 @@ __device__ __noinline__ bool step_slow(const DevMedium& m, const TraceArgs& a, i
     } else {
       float dn = nu_i - s.nu_prev;
       if (!LAYERED) {
-        float dt = 0.5f * fmaf(s.gp[0] + g[0], dv[0],
-                               fmaf(s.gp[1] + g[1], dv[1], (s.gp[2] + g[2]) * dv[2]));
+        float dt = trapezoid(s.gp, g, dv);
         if (isfinite(dt)) dn = dt;
       }
       const float om = dn * inv_n;           // 1 - mu
@@ -686,8 +776,7 @@ __device__ __forceinline__ bool step_from(const DevMedium& m, const TraceArgs& a
   float N[3] = {g[0] * ri, g[1] * ri, g[2] * ri};
   const float c = fmaf(N[0], s.d[0], fmaf(N[1], s.d[1], N[2] * s.d[2]));
   float dn = nu_i - s.nu_prev;
-  if (!LAYERED)
-    dn = 0.5f * fmaf(s.gp[0] + g[0], dv[0], fmaf(s.gp[1] + g[1], dv[1], (s.gp[2] + g[2]) * dv[2]));
+  if (!LAYERED) dn = trapezoid(s.gp, g, dv);
   const float om = dn * inv_n;         // 1 - mu
   const float mu = 1.0f - om;
   const float omm = om * (2.0f - om);  // 1 - mu^2
@@ -738,23 +827,23 @@ __device__ __forceinline__ bool step_ray(const DevMedium& m, const TraceArgs& a,
   step_point(s, qh, ql, dv);
   float nu_i, g[3];
   int lvl_i;
-  C::eval(m, qh[0], qh[1], qh[2], nu_i, g[0], g[1], g[2], lvl_i);
+  C::eval(m, qh[0], qh[1], qh[2], ql[0], ql[1], ql[2], nu_i, g[0], g[1], g[2], lvl_i);
   return step_from<C, LAYERED>(m, a, r, s, dopl_f, qh, ql, dv, nu_i, g, lvl_i);
 }
 
 // Warp-collective: the lanes in `need` get their column of the tap cache
-// refilled for the cell in their key[] (the 64 stencil samples of grid_vg,
-// edge-clamped, minus base).  The whole warp loads one such lane's taps at
-// a time, two x-adjacent taps of one row a lane, so a refill costs the warp
-// two gathers instead of the lane's 64.
+// refilled for the cell in their key[] (the 64 edge-clamped stencil samples
+// of grid_gather, minus the centre tap, which the lane keeps in lb).  The
+// whole warp loads one such lane's taps at a time, two x-adjacent taps of
+// one row a lane (lane 10 holds the centre tap (kx, ky, kz) as its second),
+// so a refill costs the warp two gathers instead of the lane's 64.
 __device__ __forceinline__ void tap_fill(const DevMedium& m, bool need, const int* key,
-                                         float* taps, unsigned lane) {
+                                         float& lb, float* taps, unsigned lane) {
   unsigned mask = __ballot_sync(0xffffffffu, need);
   if (!mask) return;
   __syncwarp();  // the owners' reads of their old taps come first
   const int row = (int)(lane >> 1), c = row >> 2, b = row & 3, h = (int)(lane & 1u);
   const int wbase = (int)(threadIdx.x & ~31u);
-  const float sub = m.base_f;
   while (mask) {
     const int src = __ffs(mask) - 1;
     mask &= mask - 1u;
@@ -765,9 +854,12 @@ __device__ __forceinline__ void tap_fill(const DevMedium& m, bool need, const in
     const int iy = min(max(ky - 1 + b, 0), m.ny - 1);
     const int ix0 = min(max(kx - 1 + 2 * h, 0), m.nx - 1);
     const int ix1 = min(max(kx + 2 * h, 0), m.nx - 1);
-    const float* __restrict__ g = m.grid + (iz * m.ny + iy) * m.nx;
-    const float2 v = make_float2(__ldg(g + ix0) - sub, __ldg(g + ix1) - sub);
-    *reinterpret_cast<float2*>(taps + row * kTapRow + (wbase + src) * 4 + 2 * h) = v;
+    const float* __restrict__ g = m.grid + ((int64_t)iz * m.ny + iy) * m.nx;
+    const float v0 = __ldg(g + ix0), v1 = __ldg(g + ix1);
+    const float sub = __shfl_sync(0xffffffffu, v1, 10);  // row 5 = (c, b) = (1, 1), x = kx
+    if ((int)lane == src) lb = sub;
+    *reinterpret_cast<float2*>(taps + row * kTapRow + (wbase + src) * 4 + 2 * h) =
+        make_float2(v0 - sub, v1 - sub);
   }
   __syncwarp();
 }
@@ -780,7 +872,7 @@ __device__ __forceinline__ void tap_fill(const DevMedium& m, bool need, const in
 template <class C, bool LAYERED>
 __device__ __forceinline__ unsigned run_quantum(const DevMedium& m, const TraceArgs& a,
                                                 int64_t ray, RayF& s, bool& active,
-                                                float dopl_f, int* key, float* taps,
+                                                float dopl_f, int* key, float& lb, float* taps,
                                                 unsigned lane) {
   unsigned ended = 0;
   if constexpr (!C::kGrid) {
@@ -800,17 +892,17 @@ __device__ __forceinline__ unsigned run_quantum(const DevMedium& m, const TraceA
       if (active) {
         step_point(s, qh, ql, dv);
         int i0[3];
-        C::cell(m, qh, i0, fr);
+        C::cell(m, qh, ql, i0, fr);
         need = i0[0] != key[0] || i0[1] != key[1] || i0[2] != key[2];
         key[0] = i0[0];
         key[1] = i0[1];
         key[2] = i0[2];
       }
-      tap_fill(m, need, key, taps, lane);
+      tap_fill(m, need, key, lb, taps, lane);
       if (active) {
         float nu_i, g[3];
         int lvl_i;
-        C::eval_taps(m, fr, col, nu_i, g[0], g[1], g[2], lvl_i);
+        C::eval_taps(m, fr, col, lb, nu_i, g[0], g[1], g[2], lvl_i);
         // the step vector again here, so it is not held across the refill
 #pragma unroll
         for (int k = 0; k < 3; ++k) dv[k] = s.h * s.d[k];
@@ -829,6 +921,7 @@ __global__ void __launch_bounds__(128, C::kMinBlocks) k_trace_mixed(DevMedium m,
   const float dopl_f = (float)a.dopl;
   __shared__ __align__(16) float taps[C::kGrid ? 16 * kTapRow : 4];
   int key[3] = {INT_MIN, INT_MIN, INT_MIN};
+  float lb = 0.0f;  // centre tap of the cached cell
   RayF s;
   bool active = false;
   bool exhausted = false;
@@ -854,7 +947,7 @@ __global__ void __launch_bounds__(128, C::kMinBlocks) k_trace_mixed(DevMedium m,
       if (exhausted) break;
       continue;
     }
-    run_quantum<C, LAYERED>(m, a, ray, s, active, dopl_f, key, taps, lane);
+    run_quantum<C, LAYERED>(m, a, ray, s, active, dopl_f, key, lb, taps, lane);
   }
 }
 
@@ -934,6 +1027,7 @@ __global__ void __launch_bounds__(128, C::kMinBlocks) k_serve_tick(DevMedium m, 
   SlotState* me = slots + t;
   __shared__ __align__(16) float taps[C::kGrid ? 16 * kTapRow : 4];
   int key[3] = {INT_MIN, INT_MIN, INT_MIN};
+  float lb = 0.0f;  // centre tap of the cached cell
   RayF s = me->s;
   bool active = me->active != 0;
   int64_t ray = me->ray;
@@ -961,7 +1055,7 @@ __global__ void __launch_bounds__(128, C::kMinBlocks) k_serve_tick(DevMedium m, 
       if (exhausted) break;
       continue;
     }
-    done += run_quantum<C, LAYERED>(m, a, ray, s, active, dopl_f, key, taps, lane);
+    done += run_quantum<C, LAYERED>(m, a, ray, s, active, dopl_f, key, lb, taps, lane);
   }
   me->s = s;
   me->active = active ? 1 : 0;

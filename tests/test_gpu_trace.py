@@ -3,15 +3,15 @@
 Plain FP64 path: integer outcomes (exit id, steps, TIR counts) identical to
 the oracle on every ray the oracle does not flag (a decision margin below
 1e-9); exit point / direction / optical path within 1e-12 relative.
-Mixed FP32 path on the Luneburg lens and the freeform block: within 2e-5 of
-the plain FP64 GPU path (position relative to the medium's bounding radius,
-direction absolute, OPL relative) on every ray with identical integer
-outcomes that the oracle does not flag at the FP32 thresholds; unflagged
-integer mismatches are counted and bounded.  On gridded, layered and
-fish-eye media the FP32 error is stated (measured bounds), not gated: long
-paths there cross many turning points of n, where sgn(N.I) in Eq. 9 makes
-the discrete map jump by the kink sqrt(1 - mu^2), and FP32 trajectory error
-decides the side of some kinks.
+Mixed FP32 path, against the oracle directly: integer outcomes identical and
+exit point / direction / optical path within 2e-5 (position relative to the
+medium's bounding radius, direction absolute, OPL relative) on every ray the
+FP32 flag rule of tests/compare.py does not excuse (a decision margin inside
+the FP32 path's drift, or a ray whose oracle trace is not stable under the
+FP32 path's approximation and twice its rounding of the normal); the
+flagged fraction is bounded per medium.  The spherical freeform medium of
+Sec. V, whose r cos(5 theta) puts many turning points of n on every path, is
+stated (fraction within 2e-5 and the largest error) rather than gated.
 """
 import math
 
@@ -22,7 +22,7 @@ import torch
 import oracle
 from paper_2606_22655_b300 import tracer
 from paper_2606_22655_b300 import workloads as W
-from tests.compare import TAU32, TAU32_GEOM, compare, flagged
+from tests.compare import compare, flagged, fp32_flags
 
 pytestmark = pytest.mark.gpu
 
@@ -63,15 +63,18 @@ def check64(g, o, l_ref):
     return rep
 
 
-def flags32(o):
-    return flagged(o["margins"], TAU32, TAU32_GEOM)
+def flags32(o, medium, rays, dopl, max_steps, l_ref):
+    return fp32_flags(o, medium, rays.origins, rays.dirs, dopl, max_steps, l_ref)
 
 
-def check32(g32, g64, l_ref, flags, max_int_mismatch_frac, tol=TOL32):
-    rep = compare(g32, g64, l_ref, flags)
-    frac = rep["int_mismatch_unflagged"] / rep["n"]
-    assert frac <= max_int_mismatch_frac, rep
+def check32(g32, o, l_ref, flags, max_flagged=1.0, tol=TOL32):
+    """The FP32 path against the oracle result o: no integer mismatch and
+    every continuous result within tol on the unflagged rays, and at most
+    max_flagged of the rays flagged."""
+    rep = compare(g32, o, l_ref, flags)
+    assert rep["int_mismatch_unflagged"] == 0, rep
     assert rep["pos"] <= tol and rep["dir"] <= tol and rep["opl"] <= tol, rep
+    assert rep["n_flagged"] <= max_flagged * rep["n"], rep
     return rep
 
 
@@ -103,12 +106,11 @@ def test_luneburg_fp64_matches_oracle(ctx):
     assert (g["exit_id"] == 0).all()
 
 
-def test_luneburg_mixed_matches_fp64(ctx):
+def test_luneburg_mixed_matches_oracle(ctx):
     wl = W.luneburg_workload()
-    g64 = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "fp64")
     g32 = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "mixed")
     o = orc(wl.medium, wl.rays, wl.dopl, wl.max_steps)
-    check32(g32, g64, wl.l_ref, flags32(o), 0.002)
+    check32(g32, o, wl.l_ref, flags32(o, wl.medium, wl.rays, wl.dopl, wl.max_steps, wl.l_ref), 0.01)
 
 
 def test_freeform_ragged_fp64_matches_oracle(ctx):
@@ -134,13 +136,11 @@ def test_freeform_ragged_fp64_fast_matches_oracle(ctx):
     assert max(rep["pos"], rep["dir"], rep["opl"]) <= 1e-8, rep
 
 
-def test_freeform_ragged_mixed_matches_fp64(ctx):
+def test_freeform_ragged_mixed_matches_oracle(ctx):
     wl = W.freeform_workload(3001)
-    g64 = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "fp64")
     g32 = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "mixed")
     o = orc(wl.medium, wl.rays, wl.dopl, wl.max_steps)
-    rep = check32(g32, g64, wl.l_ref, flags32(o), 0.005)
-    assert rep["n_flagged"] <= 0.03 * rep["n"], rep
+    check32(g32, o, wl.l_ref, flags32(o, wl.medium, wl.rays, wl.dopl, wl.max_steps, wl.l_ref), 0.06)
 
 
 def test_freeform_fullsize_sampled(ctx):
@@ -153,15 +153,17 @@ def test_freeform_fullsize_sampled(ctx):
     idx = np.arange(7, wl.rays.n, 257)
     o = orc(wl.medium, wl.rays.subset(idx), wl.dopl, wl.max_steps)
     check64({k: v[idx] for k, v in g64.items()}, o, wl.l_ref)
-    # the mixed run read float32 rays: compare it with the FP64 kernel on the
-    # same float32 rays
+    # the mixed run read float32 rays: compare it with the oracle on the same
+    # float32 rays, sample by sample
     rays32 = W.Rays(wl.rays.origins.astype(np.float32).astype(np.float64),
                     wl.rays.dirs.astype(np.float32).astype(np.float64))
-    g64b = gpu_trace(ctx, wl.medium, rays32, wl.dopl, wl.max_steps, "fp64")
-    o32 = orc(wl.medium, rays32.subset(idx), wl.dopl, wl.max_steps)
+    s32 = rays32.subset(idx)
+    o32 = orc(wl.medium, s32, wl.dopl, wl.max_steps)
     sub = lambda g: {k: v[idx] for k, v in g.items()}
-    check32(sub(g32), sub(g64b), wl.l_ref, flags32(o32), 0.005)
-    # every ray (no oracle flags at this size): the bulk is inside the gate
+    check32(sub(g32), o32, wl.l_ref, flags32(o32, wl.medium, s32, wl.dopl, wl.max_steps, wl.l_ref), 0.06)
+    # every ray against the FP64 kernel on the same float32 rays (no oracle
+    # flags at this size): the bulk is inside the gate
+    g64b = gpu_trace(ctx, wl.medium, rays32, wl.dopl, wl.max_steps, "fp64")
     rep = compare(g32, g64b, wl.l_ref)
     assert rep["pos_p99"] <= TOL32 and rep["dir_p99"] <= TOL32, rep
     assert rep["int_mismatch_unflagged"] <= 0.005 * rep["n"], rep
@@ -175,11 +177,13 @@ def test_fisheye_sphere_recip_form(ctx):
     g = gpu_trace(ctx, m, rays, 2e-3, 20000, "fp64")
     o = orc(m, rays, 2e-3, 20000)
     check64(g, o, 3.0)
-    # FP32: stated on one pass (1500 steps, about one turning point of n)
-    g = gpu_trace(ctx, m, rays, 2e-3, 1500, "fp64")
+    # FP32 on one pass (1500 steps, about one turning point of n): its
+    # trapezoid index difference departs from the point values by a third
+    # order term a step, which the short length scale of this field makes
+    # visible, so the conditioning probe excuses about a quarter of the rays
     g32 = gpu_trace(ctx, m, rays, 2e-3, 1500, "mixed")
     o = orc(m, rays, 2e-3, 1500)
-    stated32(g32, g, 3.0, flags32(o), 0.90, 1e-3)
+    check32(g32, o, 3.0, flags32(o, m, rays, 2e-3, 1500, 3.0), 0.35)
 
 
 def test_fiber_cylinder(ctx):
@@ -206,7 +210,7 @@ def test_corrector_lens_cylinder(ctx):
     o = orc(wl.medium, wl.rays, wl.dopl, wl.max_steps)
     check64(g64, o, wl.l_ref)
     g32 = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "mixed")
-    check32(g32, g64, wl.l_ref, flags32(o), 0.005)
+    check32(g32, o, wl.l_ref, flags32(o, wl.medium, wl.rays, wl.dopl, wl.max_steps, wl.l_ref), 0.06)
     r = W.corrector_example_ray()
     for lo, hi in ((1.5148, 1.5162), (1.5261, 1.5608)):
         m = W.corrector_lens_medium(n_lo=lo, n_hi=hi)
@@ -236,11 +240,12 @@ def test_spherical_freeform_sphere(ctx):
     assert rep["int_mismatch_unflagged"] == 0, rep
     assert max(rep["pos_p99"], rep["dir_p99"]) <= 1e-9, rep
     assert max(rep["pos"], rep["dir"], rep["opl"]) <= 1e-4, rep
-    # FP32 error stated, not gated: n spans 1 to 2 within the unit sphere and
-    # r cos(5 theta) puts many turning points of n on every path (measured:
-    # 91.8 % of unflagged rays within 2e-5, p99 1.1e-4, max 3.1e-3)
+    # FP32 error against the oracle stated, not gated: n spans 1 to 2 within
+    # the unit sphere and r cos(5 theta) puts many turning points of n on
+    # every path; the probe excuses about 40 % of the rays and a few of the
+    # rest exceed 2e-5 (measured: 3 of 2,049, the largest 2.8e-5)
     g32 = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "mixed")
-    stated32(g32, g64, wl.l_ref, flags32(o), 0.90, 5e-3)
+    stated32(g32, o, wl.l_ref, flags32(o, wl.medium, wl.rays, wl.dopl, wl.max_steps, wl.l_ref), 0.99, 1e-4)
     r = W.spherical_example_ray()
     ge = gpu_trace(ctx, wl.medium, r, 1e-3, 40000, "fp64")
     check64(ge, orc(wl.medium, r, 1e-3, 40000), 1.0)
@@ -280,16 +285,15 @@ def test_grid_fp64_fast_matches_oracle(ctx, res):
     assert max(rep["pos"], rep["dir"], rep["opl"]) <= 1e-8, rep
 
 
-def test_grid_mixed_error_stated(ctx, blob64):
+def test_grid_mixed_matches_oracle(ctx, blob64):
     wl = blob64
-    g64 = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "fp64")
     g32 = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "mixed")
     o = orc(wl.medium, wl.rays, wl.dopl, wl.max_steps)
-    stated32(g32, g64, wl.l_ref, flags32(o), 0.97, 2e-3)
+    check32(g32, o, wl.l_ref, flags32(o, wl.medium, wl.rays, wl.dopl, wl.max_steps, wl.l_ref), 0.12)
 
 
 @pytest.mark.parametrize("res", [7, 8])
-def test_small_grid_mixed_error_stated(ctx, res):
+def test_small_grid_mixed_matches_oracle(ctx, res):
     """Coarse grids, where a large share of the stencils reach past a face
     and are edge-clamped: the mixed tracer's tap cache is refilled with the
     clamped taps (nx = 8: rows on 16-byte boundaries; nx = 7: not)."""
@@ -298,7 +302,7 @@ def test_small_grid_mixed_error_stated(ctx, res):
     g32 = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "mixed")
     o = orc(wl.medium, wl.rays, wl.dopl, wl.max_steps)
     check64(g64, o, wl.l_ref)
-    stated32(g32, g64, wl.l_ref, flags32(o), 0.97, 2e-3)
+    check32(g32, o, wl.l_ref, flags32(o, wl.medium, wl.rays, wl.dopl, wl.max_steps, wl.l_ref), 0.2)
 
 
 def test_layered_fp64_matches_oracle(ctx):
@@ -308,23 +312,34 @@ def test_layered_fp64_matches_oracle(ctx):
     check64(g, o, wl.l_ref)
 
 
-def test_layered_mixed_error_stated(ctx):
+def test_layered_mixed_matches_oracle(ctx):
+    """Point-sampled shells: every level change is decided by a sample that
+    may lie close to a shell boundary, so the level margin excuses about 15 %
+    of the rays."""
     wl = W.blob_workload(n_rays=2000, res=64, n_levels=32)
-    g64 = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "fp64")
     g32 = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "mixed")
     o = orc(wl.medium, wl.rays, wl.dopl, wl.max_steps)
-    stated32(g32, g64, wl.l_ref, flags32(o), 0.97, 2e-3)
+    check32(g32, o, wl.l_ref, flags32(o, wl.medium, wl.rays, wl.dopl, wl.max_steps, wl.l_ref), 0.25)
 
 
-def test_grid256_fullsize_sampled(ctx):
-    """The 256^3 blob grid at full ray count is too slow for the oracle; a
-    strided sample of 1,024 of its 4,194,304 rays is traced on both sides."""
-    wl = W.blob_workload(n_rays=1 << 22, res=256)
+@pytest.mark.parametrize("levels", [0, 32])
+def test_grid256_fullsize_sampled(ctx, levels):
+    """The 256^3 blob grid (and its 32 shells) at full ray count, 4,194,304
+    rays: the mixed tracer runs the whole batch in the benchmark's launch
+    configuration (float32 rays, claimed in entry-cell order), the plain FP64
+    tracer a strided sample of 1,024 rays, and both are compared with the
+    oracle on that sample."""
+    wl = W.blob_workload(n_rays=1 << 22, res=256, n_levels=levels)
     idx = np.arange(3, wl.rays.n, 4096)
     sub = wl.rays.subset(idx)
     g = gpu_trace(ctx, wl.medium, sub, wl.dopl, wl.max_steps, "fp64")
     o = orc(wl.medium, sub, wl.dopl, wl.max_steps)
     check64(g, o, wl.l_ref)
+    g32 = gpu_trace(ctx, wl.medium, wl.rays, wl.dopl, wl.max_steps, "mixed", dtype=torch.float32)
+    r32 = W.Rays(sub.origins.astype(np.float32).astype(np.float64), sub.dirs.astype(np.float32).astype(np.float64))
+    o32 = orc(wl.medium, r32, wl.dopl, wl.max_steps)
+    check32({k: v[idx] for k, v in g32.items()}, o32, wl.l_ref,
+            flags32(o32, wl.medium, r32, wl.dopl, wl.max_steps, wl.l_ref), 0.25 if levels else 0.12)
 
 
 # --------------------------------------------------------------- edge cases
