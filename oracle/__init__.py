@@ -51,6 +51,7 @@ _lib = None
 
 EXIT_MISS, EXIT_ENTRY_REFLECT, EXIT_MAXSTEPS, EXIT_INVALID = -1, -2, -3, -4
 M_CRIT, M_TAN, M_BND, M_LEVEL = 0, 1, 2, 3
+LEVEL_ROOT = 1  # trace flag: shell crossings solved on the step (layered media)
 
 
 def build(force: bool = False) -> str:
@@ -174,7 +175,8 @@ def trace(medium, origins, dirs, dopl: float, max_steps: int,
     return out
 
 
-def trace_path(medium, origin, direction, dopl: float, max_steps: int, cap: Optional[int] = None):
+def trace_path(medium, origin, direction, dopl: float, max_steps: int, cap: Optional[int] = None,
+               flags: int = 0):
     """One ray with its full list of points inside the medium; returns
     (result dict, path (m, 3))."""
     lib = _load()
@@ -188,7 +190,7 @@ def trace_path(medium, origin, direction, dopl: float, max_steps: int, cap: Opti
                tir_boundary=np.zeros(1, np.int32), margins=np.zeros(4))
     plen = ctypes.c_int64()
     ip = lambda a: _ptr(a, ctypes.c_int32)
-    prm = _Params(float(dopl), int(max_steps), 0, 0, 0.0, 0)
+    prm = _Params(float(dopl), int(max_steps), int(flags), 0, 0.0, 0)
     lib.orc_trace_path(ctypes.byref(b.s), ctypes.byref(prm), _ptr(o), _ptr(d), _ptr(out["P"]),
                        _ptr(out["d"]), _ptr(out["opl"]), ip(out["exit_id"]), ip(out["steps"]),
                        ip(out["tir_internal"]), ip(out["tir_boundary"]), _ptr(out["margins"]),

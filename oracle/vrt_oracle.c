@@ -620,7 +620,92 @@ static void trace_one(const orc_medium* m, const orc_params* prm, int64_t ray, c
   for (int a = 0; a < 3; ++a) Q[a] = P[a] + h * d[a]; /* Eq. 2 */
   int steps = 0;
   out->exit_id = EXIT_MAXSTEPS;
+  const int level_root = (prm->flags & ORC_LEVEL_ROOT) && m->n_levels > 0;
   while (steps < prm->max_steps) {
+    if (level_root) {
+      /* Layered shells with their crossings solved (the discretised media
+       * of Sec. I as a stack of isoindicial surfaces).  n is constant inside
+       * a shell, so a step runs straight (Sec. II (iii)) unless it meets a
+       * shell boundary or the enclosing surface first.  At the first point
+       * of the step outside the current shell, found by bisection on the
+       * segment, the ray refracts by Eq. 8-9 with the normal of the
+       * isoindicial surface, grad f / |grad f| of the smooth field, and
+       * mu = n_k / n_k' of the two shells, or is totally reflected
+       * (Sec. II (v)); as at the enclosing surface (Sec. II (i)) the step
+       * ends there and counts as a step, adding its fraction of dL0. */
+      out->mg[ORC_M_BND] = minf(out->mg[ORC_M_BND], boundary_margin(m, Q, h));
+      double E[3], tb = 1.0, Pb[3], NB[3];
+      int face = 0, leaves = !inside(m, Q);
+      if (leaves) {
+        exit_root(m, P, Q, &tb, Pb, NB, &face);
+        for (int a = 0; a < 3; ++a) E[a] = Pb[a];
+      } else {
+        for (int a = 0; a < 3; ++a) E[a] = Q[a];
+      }
+      double nE, gE[3], uE;
+      int lE;
+      sample(m, E, &nE, gE, &lE, &uE);
+      out->mg[ORC_M_LEVEL] = minf(out->mg[ORC_M_LEVEL], fabs(uE - floor(uE + 0.5)));
+      if (lE != lvl_prev) {
+        double lo = 0.0, hi = 1.0, X[3], nX, gX[3], uX;
+        int lX;
+        for (int it = 0; it < 128; ++it) {
+          double mid = 0.5 * (lo + hi);
+          if (!(mid > lo && mid < hi)) break;
+          for (int a = 0; a < 3; ++a) X[a] = P[a] + mid * (E[a] - P[a]);
+          sample(m, X, &nX, gX, &lX, &uX);
+          if (lX == lvl_prev) lo = mid;
+          else hi = mid;
+        }
+        for (int a = 0; a < 3; ++a) X[a] = P[a] + hi * (E[a] - P[a]);
+        sample(m, X, &nX, gX, &lX, &uX);
+        nsum_add(&opl, hi * tb * dopl);
+        ++steps;
+        for (int a = 0; a < 3; ++a) P[a] = X[a];
+        if (path && np < cap) {
+          for (int a = 0; a < 3; ++a) path[3 * np + a] = P[a];
+          ++np;
+        }
+        if (!(isfinite(nX) && nX > 0.0)) {
+          out->exit_id = EXIT_INVALID;
+          break;
+        }
+        double gn = norm3(gX);
+        if (gn == 0.0 || !isfinite(gn)) {
+          /* Sec. II (ii): no normal; straight on into the new shell */
+          n_prev = nX;
+          lvl_prev = lX;
+        } else {
+          double N[3] = {gX[0] / gn, gX[1] / gn, gX[2] / gn}, R[3];
+          out->mg[ORC_M_TAN] = minf(out->mg[ORC_M_TAN], fabs(dot3(N, d)));
+          int tir = refract_or_reflect(d, N, n_prev / nX, R, &Dm);
+          out->mg[ORC_M_CRIT] = minf(out->mg[ORC_M_CRIT], fabs(Dm));
+          for (int a = 0; a < 3; ++a) d[a] = R[a];
+          if (tir) {
+            ++out->tir_int;
+          } else {
+            n_prev = nX;
+            lvl_prev = lX;
+          }
+        }
+        h = dopl / n_prev;
+        for (int a = 0; a < 3; ++a) Q[a] = P[a] + h * d[a];
+        continue;
+      }
+      if (!leaves) {
+        for (int a = 0; a < 3; ++a) P[a] = Q[a];
+        nsum_add(&opl, dopl);
+        ++steps;
+        if (path && np < cap) {
+          for (int a = 0; a < 3; ++a) path[3 * np + a] = P[a];
+          ++np;
+        }
+        for (int a = 0; a < 3; ++a) Q[a] = P[a] + h * d[a];
+        continue;
+      }
+      /* the step meets the enclosing surface inside the shell: the boundary
+       * event below */
+    }
     out->mg[ORC_M_BND] = minf(out->mg[ORC_M_BND], boundary_margin(m, Q, h));
     if (!inside(m, Q)) {
       /* Sec. II (i): the step ends on the enclosing surface, where the

@@ -50,7 +50,7 @@ typedef struct {
 typedef struct {
   double dopl;           /* Delta L_0: optical path per step */
   int32_t max_steps;
-  int32_t flags;         /* 0 (ORC_LEVEL_ROOT below for layered media) */
+  int32_t flags;         /* 0, or ORC_LEVEL_ROOT (below) */
   /* Conditioning probe, for judging which rays a less precise tracer can be
    * held to (0, 0.0 for the method itself): index_rule 1 takes the index
    * difference n_i - n_{i-1} of a refraction (continuous media) by the
@@ -68,6 +68,11 @@ typedef struct {
  * endpoint to the boundary in units of the step, min distance of the quantised
  * level coordinate to an integer. */
 enum { ORC_M_CRIT = 0, ORC_M_TAN = 1, ORC_M_BND = 2, ORC_M_LEVEL = 3, ORC_NM = 4 };
+
+/* orc_params.flags: for layered media, refract where a step meets a shell
+ * boundary (found by bisection on the step) instead of at the first sampled
+ * point beyond it. */
+enum { ORC_LEVEL_ROOT = 1 };
 
 /* Index and its gradient at a point.  Returns 0. */
 int orc_medium_eval(const orc_medium* m, const double* P, double* n, double* g);

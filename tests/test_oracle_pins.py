@@ -4,6 +4,7 @@ Each test checks the oracle against something other than itself: a closed
 form, exact rational arithmetic, a value printed in the paper, an invariant
 or a convergence order.  No GPU is used.
 """
+import dataclasses
 import json
 import math
 import os
@@ -920,3 +921,88 @@ def test_exit_uses_previous_point_index():
         r = _one(m, (0, 0, -1), d0, dopl, 100000)
         assert r["exit_id"] == 5 and r["tir_internal"] == 0
         np.testing.assert_allclose(r["d"], d0, atol=1e-13)
+
+
+# --------------------------------------- shells with exact crossings (flag LEVEL_ROOT)
+
+
+def _planar_shells(levels):
+    """f = 1.3 + 0.2 z on z in [0, 2] in L shells on [1.3, 1.7]: shell k is
+    the slab 2k/L <= z < 2(k+1)/L with index 1.3 + (k + 1/2) 0.4 / L."""
+    c = W.coeffs_from_terms(1, {(0, 0, 0): 1.5, (0, 0, 1): 0.2})
+    return W.Medium(kind=W.KIND_POLY, form=W.FORM_LINEAR, degree=1, coeffs=c, off=(0, 0, 1),
+                    n_levels=levels, level_lo=1.3, level_hi=1.7, bkind=W.BOUNDARY_BOX,
+                    bparams=(-50, -50, 0, 50, 50, 2, 0, 0), n_ext=1.0)
+
+
+@pytest.mark.parametrize("levels", [4, 32])
+def test_level_root_planar_stack_closed_form(levels):
+    """With crossings solved, a ray through a stack of planar shells is the
+    textbook one: in shell k (thickness T = 2/L, index n_k) it runs straight
+    at sin(theta_k) = sin(theta_0) / n_k (Snell at every interface), so it
+    leaves at the lateral offset tan(theta_0) + sum T tan(theta_k) along its
+    input direction, with OPL 1/cos(theta_0) + sum n_k T / cos(theta_k), in
+    sum ceil(n_k l_k / dL0) steps (each shell's last step cut at its upper
+    plane)."""
+    dopl = 1e-3
+    m = _planar_shells(levels)
+    th0 = math.radians(35.0)
+    u = np.array([0.6, 0.8, 0.0])
+    d0 = math.sin(th0) * u + np.array([0.0, 0.0, math.cos(th0)])
+    res = oracle.trace(m, np.array([[0.0, 0.0, -1.0]]), d0[None], dopl, 1_000_000, threads=1,
+                       flags=oracle.LEVEL_ROOT)
+    r = {k: v[0] for k, v in res.items()}
+    T = 2.0 / levels
+    lat, opl, steps = math.tan(th0), 1.0 / math.cos(th0), 0
+    for k in range(levels):
+        nk = 1.3 + (k + 0.5) * 0.4 / levels
+        tk = math.asin(math.sin(th0) / nk)
+        lk = T / math.cos(tk)
+        lat += T * math.tan(tk)
+        opl += nk * lk
+        q = nk * lk / dopl
+        assert 1e-6 < q % 1 < 1 - 1e-6  # no rounding ambiguity in the count
+        steps += math.ceil(q)
+    assert r["exit_id"] == 5 and r["tir_internal"] == 0 and r["tir_boundary"] == 0
+    np.testing.assert_allclose(r["P"], lat * u + np.array([0, 0, 2.0]), atol=1e-12)
+    np.testing.assert_allclose(r["d"], d0, atol=1e-13)
+    assert r["opl"] == pytest.approx(opl, rel=1e-13)
+    assert r["steps"] == steps
+
+
+def test_level_root_total_reflection_on_the_shell_plane():
+    """Sec. II (v) at an isoindicial surface: in n = 1.6 (z > 1) over n = 1.4
+    (z < 1) a ray at 80 deg to the normal (critical angle 61 deg) is
+    reflected exactly where it meets the plane z = 1, at x = 0.05 tan(80),
+    and leaves it mirrored."""
+    m = _planar_shells(2)
+    a = math.radians(80.0)
+    d0 = np.array([math.sin(a), 0.0, -math.cos(a)])
+    h = 1e-3 / 1.6
+    n_before = math.floor(0.05 / (h * math.cos(a)))
+    res, path = oracle.trace_path(m, (0, 0, 1.05), d0, 1e-3, n_before + 5, flags=oracle.LEVEL_ROOT)
+    assert res["tir_internal"][0] == 1
+    hit = path[n_before + 1]  # entry point, n_before full steps, then the cut at the plane
+    np.testing.assert_allclose(hit, [0.05 * math.tan(a), 0.0, 1.0], atol=1e-13)
+    np.testing.assert_allclose(res["d"], [math.sin(a), 0.0, math.cos(a)], atol=1e-14)
+    assert np.all(path[: len(path), 2] >= 1.0 - 1e-15)
+
+
+def test_level_root_spherical_shells():
+    """The Luneburg lens in 8 shells on [1, sqrt 2]: every level boundary is a
+    sphere r_k = sqrt(2 - b_k^2), so each crossing point lies on one, and with
+    the radial normal of Eq. 5 the Bouguer invariant n |r x d| of every
+    segment equals the entry value (the impact parameter 0.5)."""
+    m = dataclasses.replace(W.luneburg_medium(), n_levels=8, level_lo=1.0, level_hi=math.sqrt(2.0))
+    res, path = oracle.trace_path(m, (0.3, 0.4, -1.5), (0, 0, 1), 2e-3, 100000, flags=oracle.LEVEL_ROOT)
+    assert res["exit_id"][0] == 0
+    radii = np.sqrt(2.0 - (1.0 + np.arange(1, 8) * (math.sqrt(2.0) - 1.0) / 8) ** 2)
+    seg = np.diff(path, axis=0)
+    dirs = seg / np.linalg.norm(seg, axis=1, keepdims=True)
+    n_seg, _ = oracle.medium_eval(m, 0.5 * (path[:-1] + path[1:]))
+    inv = n_seg * np.linalg.norm(np.cross(path[:-1], dirs), axis=1)
+    assert np.abs(inv - 0.5).max() < 1e-12
+    changes = np.nonzero(np.diff(n_seg))[0] + 1  # vertices where the shell changes
+    assert len(changes) >= 8
+    r = np.linalg.norm(path[changes], axis=1)
+    assert np.abs(r[:, None] - radii[None, :]).min(axis=1).max() < 1e-13
