@@ -53,7 +53,9 @@ typedef enum {
   GRIN_ERR_TIMEOUT = -5,       /* a bounded wait ran out */
   GRIN_ERR_BUSY = -6,          /* admission refused (serving); context still owns objects */
   GRIN_ERR_NOT_FOUND = -7,     /* unknown job id (serving) */
-  GRIN_ERR_CANCELLED = -8      /* job cancelled (serving) */
+  GRIN_ERR_CANCELLED = -8,     /* job cancelled (serving) */
+  GRIN_ERR_CHECKED_BOUNDS = -9 /* the bounds-checked build caught an out-of-range
+                                  index in a kernel (see grin_checked_status) */
 } grin_status;
 
 /* Exit ids written per ray.  Non-negative ids name the face the ray left by:
@@ -147,7 +149,25 @@ typedef struct {
  * surround for a ray that left), the accumulated optical path length (the
  * exterior approach segment included), the exit id, the number of interior
  * steps (a step cut short at the surface counts as one), and the numbers of
- * internal and boundary total internal reflections. */
+ * internal and boundary total internal reflections.
+ *
+ * margin (optional, NULL to skip): 4 doubles a ray, ray-major
+ * (margin[4 r + k]), the decision margins of the trace, each the minimum
+ * over the ray's steps of a quantity whose sign decides an integer outcome,
+ * so that a caller can tell which exit states are ill-conditioned:
+ *   k = 0: distance of |N.I| from its critical value sqrt(1 - 1/mu^2) at a
+ *          refraction test with mu > 1 (D / (mu^2 (|N.I| + critical)),
+ *          Eq. 9 and Sec. II (v)); INFINITY if no test had mu > 1;
+ *   k = 1: |N.I| at the gradient steps (the sign in Eq. 9; the tangential
+ *          case Sec. II (iv) at zero);
+ *   k = 2: distance of a step's end point to the enclosing surface, in
+ *          steps (first order for curved surfaces; Sec. II (i));
+ *   k = 3: distance of the level coordinate of a layered medium to the
+ *          nearest shell boundary, in levels; INFINITY for continuous media.
+ * GRIN_PREC_FP64 computes them in FP64 exactly as the plain tracer steps;
+ * GRIN_PREC_FP32_MIXED computes them in FP32 on its own trajectory;
+ * GRIN_PREC_FP64_FAST and the serving and allocation-free entry points do
+ * not (GRIN_ERR_NOT_IMPLEMENTED when margin is not NULL). */
 typedef struct {
   double *px, *py, *pz;
   double *dx, *dy, *dz;
@@ -156,7 +176,26 @@ typedef struct {
   int32_t* steps;
   int32_t* tir_internal;
   int32_t* tir_boundary;
+  double* margin;
 } grin_out;
+
+/* grin_params.flags.
+ * GRIN_TRACE_LEVEL_ROOT: for a layered medium, refract where a step meets a
+ *   shell boundary instead of at the first sampled point beyond it.  The
+ *   layered media are the discretised media of Sec. I, stacks of isoindicial
+ *   surfaces; with this flag the first point of a step outside the current
+ *   shell (found on the step, by bisection in FP64 or by safeguarded Newton
+ *   iterations in the mixed tracer) ends the step (it counts as a step and
+ *   adds its fraction of Delta L_0, like a crossing of the enclosing
+ *   surface, Sec. II (i)), and the ray refracts there by Eq. 8-9 with the
+ *   isoindicial normal grad f / |grad f| of the smooth field and
+ *   mu = n_k / n_k' of the two shells, or is totally reflected (Sec. II
+ *   (v)) and stays in its shell.  Inside a shell the steps are straight
+ *   (Sec. II (iii)).  No effect on continuous media.  GRIN_PREC_FP64 and
+ *   GRIN_PREC_FP32_MIXED (and the serving loop) support it;
+ *   GRIN_PREC_FP64_FAST and grin_trace_adjoint return
+ *   GRIN_ERR_NOT_IMPLEMENTED. */
+enum { GRIN_TRACE_LEVEL_ROOT = 1u };
 
 /* dopl = Delta L_0 > 0 (Eq. 3); max_steps >= 0 interior steps per ray;
  * precision:
@@ -170,7 +209,8 @@ typedef struct {
  *     O(step^3); point values for layered media), an exact step-count optical
  *     path, FP64 for the surface root, the boundary refraction and
  *     near-critical discriminants; persistent ray-pool kernel.
- * flags must be 0. */
+ * flags: 0 or GRIN_TRACE_LEVEL_ROOT (above); other bits give
+ * GRIN_ERR_INVALID_ARG. */
 typedef struct {
   double dopl;
   int32_t max_steps;

@@ -531,6 +531,16 @@ static void nsum_add(nsum* a, double x) {
 
 static double minf(double a, double b) { return a < b ? a : b; }
 
+/* Distance of the level coordinate u to the nearest shell boundary: the
+ * integers 1 .. L-1 (the levels clamp below 0 and above L-1, so u = 0 and
+ * u = L decide nothing). */
+static double level_margin(const orc_medium* m, double u) {
+  double k = floor(u + 0.5);
+  if (k < 1.0) k = 1.0;
+  if (k > (double)m->n_levels - 1.0) k = (double)m->n_levels - 1.0;
+  return m->n_levels > 1 ? fabs(u - k) : INFINITY;
+}
+
 typedef struct {
   double P[3], d[3], opl;
   int exit_id, steps, tir_int, tir_bnd;
@@ -621,18 +631,21 @@ static void trace_one(const orc_medium* m, const orc_params* prm, int64_t ray, c
   int steps = 0;
   out->exit_id = EXIT_MAXSTEPS;
   const int level_root = (prm->flags & ORC_LEVEL_ROOT) && m->n_levels > 0;
+  double rem = 1.0; /* fraction of the current step's dL0 still to go */
+  int crossings = 0; /* shell crossings in the current step */
   while (steps < prm->max_steps) {
     if (level_root) {
       /* Layered shells with their crossings solved (the discretised media
        * of Sec. I as a stack of isoindicial surfaces).  n is constant inside
-       * a shell, so a step runs straight (Sec. II (iii)) unless it meets a
-       * shell boundary or the enclosing surface first.  At the first point
-       * of the step outside the current shell, found by bisection on the
-       * segment, the ray refracts by Eq. 8-9 with the normal of the
-       * isoindicial surface, grad f / |grad f| of the smooth field, and
-       * mu = n_k / n_k' of the two shells, or is totally reflected
-       * (Sec. II (v)); as at the enclosing surface (Sec. II (i)) the step
-       * ends there and counts as a step, adding its fraction of dL0. */
+       * a shell, so the ray runs straight (Sec. II (iii)) until it meets a
+       * shell boundary or the enclosing surface.  At the first point of the
+       * segment outside the current shell, found by bisection, it refracts
+       * by Eq. 8-9 with the normal of the isoindicial surface, grad f /
+       * |grad f| of the smooth field, and mu = n_k / n_k' of the two shells,
+       * or is totally reflected (Sec. II (v)), and goes on with the rest of
+       * the step's optical path dL0 (rem, a fraction of it) in its new
+       * direction.  A step therefore still adds dL0 (Eq. 3); the enclosing
+       * surface ends a step as in Sec. II (i).  Q = P + rem h d here. */
       out->mg[ORC_M_BND] = minf(out->mg[ORC_M_BND], boundary_margin(m, Q, h));
       double E[3], tb = 1.0, Pb[3], NB[3];
       int face = 0, leaves = !inside(m, Q);
@@ -645,8 +658,16 @@ static void trace_one(const orc_medium* m, const orc_params* prm, int64_t ray, c
       double nE, gE[3], uE;
       int lE;
       sample(m, E, &nE, gE, &lE, &uE);
-      out->mg[ORC_M_LEVEL] = minf(out->mg[ORC_M_LEVEL], fabs(uE - floor(uE + 0.5)));
+      if (lE != lvl_prev && crossings == ORC_MAX_CROSSINGS) {
+        /* a ray grazing a curved shell boundary can cross it back and forth
+         * at ever shorter intervals: after ORC_MAX_CROSSINGS crossings in
+         * one step the rest of the step runs straight and the ray takes the
+         * shell it ends in */
+        lvl_prev = lE;
+        n_prev = nE;
+      }
       if (lE != lvl_prev) {
+        ++crossings;
         double lo = 0.0, hi = 1.0, X[3], nX, gX[3], uX;
         int lX;
         for (int it = 0; it < 128; ++it) {
@@ -659,8 +680,14 @@ static void trace_one(const orc_medium* m, const orc_params* prm, int64_t ray, c
         }
         for (int a = 0; a < 3; ++a) X[a] = P[a] + hi * (E[a] - P[a]);
         sample(m, X, &nX, gX, &lX, &uX);
-        nsum_add(&opl, hi * tb * dopl);
-        ++steps;
+        if (prm->perturb > 0.0) {
+          double gl = norm3(gX);
+          for (int a = 0; a < 3; ++a)
+            gX[a] += prm->perturb * gl * probe_uniform(prm->seed, ray, steps + 1000000 * crossings, a);
+        }
+        double used = hi * tb * rem; /* fraction of dL0 up to the crossing */
+        nsum_add(&opl, used * dopl);
+        rem = rem - used;
         for (int a = 0; a < 3; ++a) P[a] = X[a];
         if (path && np < cap) {
           for (int a = 0; a < 3; ++a) path[3 * np + a] = P[a];
@@ -689,22 +716,25 @@ static void trace_one(const orc_medium* m, const orc_params* prm, int64_t ray, c
           }
         }
         h = dopl / n_prev;
-        for (int a = 0; a < 3; ++a) Q[a] = P[a] + h * d[a];
+        for (int a = 0; a < 3; ++a) Q[a] = P[a] + rem * h * d[a];
         continue;
       }
+      crossings = 0;
       if (!leaves) {
         for (int a = 0; a < 3; ++a) P[a] = Q[a];
-        nsum_add(&opl, dopl);
+        nsum_add(&opl, rem * dopl);
         ++steps;
+        rem = 1.0;
         if (path && np < cap) {
           for (int a = 0; a < 3; ++a) path[3 * np + a] = P[a];
           ++np;
         }
+        h = dopl / n_prev;
         for (int a = 0; a < 3; ++a) Q[a] = P[a] + h * d[a];
         continue;
       }
-      /* the step meets the enclosing surface inside the shell: the boundary
-       * event below */
+      /* the rest of the step meets the enclosing surface inside the shell:
+       * the boundary event below */
     }
     out->mg[ORC_M_BND] = minf(out->mg[ORC_M_BND], boundary_margin(m, Q, h));
     if (!inside(m, Q)) {
@@ -713,8 +743,9 @@ static void trace_one(const orc_medium* m, const orc_params* prm, int64_t ray, c
       double t, Pb[3], NB[3], R[3];
       int face;
       exit_root(m, P, Q, &t, Pb, NB, &face);
-      nsum_add(&opl, t * dopl);
+      nsum_add(&opl, t * rem * dopl);
       ++steps;
+      rem = 1.0;
       for (int a = 0; a < 3; ++a) P[a] = Pb[a];
       if (path && np < cap) {
         for (int a = 0; a < 3; ++a) path[3 * np + a] = P[a];
@@ -758,7 +789,7 @@ static void trace_one(const orc_medium* m, const orc_params* prm, int64_t ray, c
       double gl = norm3(g);
       for (int a = 0; a < 3; ++a) g[a] += prm->perturb * gl * probe_uniform(prm->seed, ray, steps, a);
     }
-    if (lvl_i >= 0) out->mg[ORC_M_LEVEL] = minf(out->mg[ORC_M_LEVEL], fabs(u - floor(u + 0.5)));
+    if (lvl_i >= 0) out->mg[ORC_M_LEVEL] = minf(out->mg[ORC_M_LEVEL], level_margin(m, u));
     if (!(isfinite(n_i) && n_i > 0.0)) {
       out->exit_id = EXIT_INVALID;
       break;

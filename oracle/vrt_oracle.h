@@ -65,14 +65,17 @@ typedef struct {
 
 /* Per-ray decision margins: min distance of |N.I| from its critical value
  * over refraction tests, min |N.I| over gradient steps, min distance of a step
- * endpoint to the boundary in units of the step, min distance of the quantised
- * level coordinate to an integer. */
+ * endpoint to the boundary in units of the step, min distance of the level
+ * coordinate to a shell boundary (the integers 1 .. n_levels - 1). */
 enum { ORC_M_CRIT = 0, ORC_M_TAN = 1, ORC_M_BND = 2, ORC_M_LEVEL = 3, ORC_NM = 4 };
 
-/* orc_params.flags: for layered media, refract where a step meets a shell
+/* orc_params.flags: for layered media, refract where the ray meets a shell
  * boundary (found by bisection on the step) instead of at the first sampled
- * point beyond it. */
+ * point beyond it, and go on with the rest of the step's optical path. */
 enum { ORC_LEVEL_ROOT = 1 };
+/* Shell crossings within one step, at most (then the rest of the step runs
+ * straight and the ray takes the shell it ends in). */
+enum { ORC_MAX_CROSSINGS = 16 };
 
 /* Index and its gradient at a point.  Returns 0. */
 int orc_medium_eval(const orc_medium* m, const double* P, double* n, double* g);

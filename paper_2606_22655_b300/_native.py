@@ -15,9 +15,11 @@ LIB_PATH = os.environ.get("GRIN_LIB") or os.path.join(HERE, "lib", "libgrin_vrt.
 
 GRIN_OK = 0
 (GRIN_ERR_INVALID_ARG, GRIN_ERR_OOM, GRIN_ERR_CUDA, GRIN_ERR_NOT_IMPLEMENTED, GRIN_ERR_TIMEOUT,
- GRIN_ERR_BUSY, GRIN_ERR_NOT_FOUND, GRIN_ERR_CANCELLED) = range(-1, -9, -1)
+ GRIN_ERR_BUSY, GRIN_ERR_NOT_FOUND, GRIN_ERR_CANCELLED, GRIN_ERR_CHECKED_BOUNDS) = range(-1, -10, -1)
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA runtime error",
-          -4: "not implemented", -5: "timed out", -6: "busy", -7: "not found", -8: "cancelled"}
+          -4: "not implemented", -5: "timed out", -6: "busy", -7: "not found", -8: "cancelled",
+          -9: "index out of bounds (checked build)"}
+TRACE_LEVEL_ROOT = 1
 EXIT_MISS, EXIT_ENTRY_REFLECT, EXIT_MAXSTEPS, EXIT_INVALID = -1, -2, -3, -4
 F32, F64 = 0, 1
 PREC_FP64, PREC_FP32_MIXED, PREC_FP64_FAST = 0, 1, 2
@@ -49,7 +51,7 @@ class Rays(ctypes.Structure):
 class Out(ctypes.Structure):
     _fields_ = [("px", _vp), ("py", _vp), ("pz", _vp), ("dx", _vp), ("dy", _vp), ("dz", _vp),
                 ("opl", _vp), ("exit_id", _vp), ("steps", _vp), ("tir_internal", _vp),
-                ("tir_boundary", _vp)]
+                ("tir_boundary", _vp), ("margin", _vp)]
 
 
 class Params(ctypes.Structure):

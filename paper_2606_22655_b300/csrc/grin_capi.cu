@@ -207,6 +207,7 @@ const char* grin_status_string(int status) {
     case GRIN_ERR_BUSY: return "busy";
     case GRIN_ERR_NOT_FOUND: return "not found";
     case GRIN_ERR_CANCELLED: return "cancelled";
+    case GRIN_ERR_CHECKED_BOUNDS: return "index out of bounds (checked build)";
     default: return "unknown status";
   }
 }
@@ -336,10 +337,14 @@ static int check_trace_args(grin_ctx ctx, grin_medium medium, const grin_rays* r
   if (medium->ctx != ctx) return GRIN_ERR_INVALID_ARG;
   if (rays->count < 0) return GRIN_ERR_INVALID_ARG;
   if (rays->dtype != GRIN_F32 && rays->dtype != GRIN_F64) return GRIN_ERR_INVALID_ARG;
-  if (!finite_pos(p->dopl) || p->max_steps < 0 || p->flags != 0) return GRIN_ERR_INVALID_ARG;
+  if (!finite_pos(p->dopl) || p->max_steps < 0 || (p->flags & ~(uint32_t)GRIN_TRACE_LEVEL_ROOT))
+    return GRIN_ERR_INVALID_ARG;
   if (p->precision != GRIN_PREC_FP64 && p->precision != GRIN_PREC_FP32_MIXED &&
       p->precision != GRIN_PREC_FP64_FAST)
     return GRIN_ERR_INVALID_ARG;
+  // the fast FP64 tracer keeps neither margins nor the shell-crossing variant
+  if (p->precision == GRIN_PREC_FP64_FAST && (p->flags || out->margin))
+    return GRIN_ERR_NOT_IMPLEMENTED;
   if (rays->count == 0) return GRIN_OK;
   if (!rays->ox || !rays->oy || !rays->oz || !rays->dx || !rays->dy || !rays->dz)
     return GRIN_ERR_INVALID_ARG;
@@ -381,6 +386,8 @@ int grin_trace_path(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
   a.tir_b = out->tir_boundary;
   a.dopl = p->dopl;
   a.max_steps = p->max_steps;
+  a.flags = p->flags;
+  a.margin = out->margin;
   int rc = grin::launch_fp64_path(medium->dm, a, path, cap, path_len, (cudaStream_t)cuda_stream);
   if (rc < 0) return rc;
   ctx->last_launches = rc;
@@ -415,6 +422,8 @@ int grin_trace(grin_ctx ctx, grin_medium medium, const grin_rays* rays, const gr
   a.tir_b = out->tir_boundary;
   a.dopl = p->dopl;
   a.max_steps = p->max_steps;
+  a.flags = p->flags;
+  a.margin = out->margin;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   int rc;
   if (p->precision == GRIN_PREC_FP64) {
@@ -487,7 +496,8 @@ int grin_trace_host(grin_ctx ctx, grin_medium medium, const grin_rays* rays, con
   if (n == 0) return GRIN_OK;
   const size_t esz = rays->dtype == GRIN_F64 ? 8 : 4;
   const size_t in_bytes = 6 * esz * (size_t)n;
-  const size_t out_bytes = (7 * 8 + 4 * 4) * (size_t)n;
+  const bool with_margin = out->margin != nullptr;
+  const size_t out_bytes = (7 * 8 + 4 * 4 + (with_margin ? 32 : 0)) * (size_t)n;
   const size_t need = in_bytes + out_bytes + 256;
   if (ctx->stage_bytes < need) {
     if (ctx->stage) {
@@ -512,6 +522,7 @@ int grin_trace_host(grin_ctx ctx, grin_medium medium, const grin_rays* rays, con
   for (int k = 0; k < 7; ++k) dd[k] = (double*)(ob + k * 8 * (size_t)n);
   int32_t* di[4];
   for (int k = 0; k < 4; ++k) di[k] = (int32_t*)(ob + 56 * (size_t)n + k * 4 * (size_t)n);
+  double* dm = with_margin ? (double*)(ob + 72 * (size_t)n) : nullptr;  // 4 a ray
   double* hd[7] = {out->px, out->py, out->pz, out->dx, out->dy, out->dz, out->opl};
   int32_t* hi[4] = {out->exit_id, out->steps, out->tir_internal, out->tir_boundary};
 
@@ -555,7 +566,8 @@ int grin_trace_host(grin_ctx ctx, grin_medium medium, const grin_rays* rays, con
     if (st != GRIN_OK) break;
     grin_rays dr = rays_at(*rays, din, off, cnt, esz);
     grin_out dout = {dd[0] + off, dd[1] + off, dd[2] + off, dd[3] + off, dd[4] + off, dd[5] + off,
-                     dd[6] + off, di[0] + off, di[1] + off, di[2] + off, di[3] + off};
+                     dd[6] + off, di[0] + off, di[1] + off, di[2] + off, di[3] + off,
+                     with_margin ? dm + 4 * off : nullptr};
     st = grin_trace(ctx, medium, &dr, p, &dout, ts);
     if (st != GRIN_OK) break;
     launches += ctx->last_launches;
@@ -572,6 +584,10 @@ int grin_trace_host(grin_ctx ctx, grin_medium medium, const grin_rays* rays, con
       if (cudaMemcpyAsync(hi[k] + off, di[k] + off, 4 * (size_t)cnt, cudaMemcpyDeviceToHost,
                           down) != cudaSuccess)
         st = GRIN_ERR_CUDA;
+    if (with_margin && st == GRIN_OK &&
+        cudaMemcpyAsync(out->margin + 4 * off, dm + 4 * off, 32 * (size_t)cnt,
+                        cudaMemcpyDeviceToHost, down) != cudaSuccess)
+      st = GRIN_ERR_CUDA;
   }
   // Nothing may still read or write the caller's buffers when this returns.
   bool synced = true;
@@ -602,6 +618,7 @@ int grin_trace_adjoint(grin_ctx ctx, grin_medium medium, const grin_rays* rays, 
   if (st != GRIN_OK) return st;
   if (!g || !grad || !ws || k < 1 || k > 64 || p->precision != GRIN_PREC_FP64)
     return GRIN_ERR_INVALID_ARG;
+  if (p->flags || out->margin) return GRIN_ERR_NOT_IMPLEMENTED;
   if (!grin::adjoint_supported(medium->dm)) return GRIN_ERR_NOT_IMPLEMENTED;
   ctx->last_launches = 0;
   if (rays->count == 0) return GRIN_OK;
@@ -631,6 +648,8 @@ int grin_trace_adjoint(grin_ctx ctx, grin_medium medium, const grin_rays* rays, 
   a.tir_b = out->tir_boundary;
   a.dopl = p->dopl;
   a.max_steps = p->max_steps;
+  a.flags = p->flags;
+  a.margin = out->margin;
   const grin::DevMedium& m = medium->dm;
   int nterms = m.kind == GRIN_MEDIUM_POLY ? grin_poly_terms(m.pclass) : 0;
   int rc = grin::launch_adjoint(m, a, k, ws, gout, grad, nterms, (cudaStream_t)cuda_stream);

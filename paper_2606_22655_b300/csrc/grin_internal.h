@@ -67,6 +67,10 @@ struct TraceArgs {
   // mixed tracer: claim order (a permutation of 0..count-1), or nullptr for
   // index order
   const uint32_t* perm = nullptr;
+  // grin_params.flags (GRIN_TRACE_LEVEL_ROOT) and the optional per-ray decision
+  // margins (grin_out.margin: 4 doubles a ray, or nullptr)
+  uint32_t flags = 0;
+  double* margin = nullptr;
 };
 
 // Validated device record of a medium description (grin_capi.cu); a grid's

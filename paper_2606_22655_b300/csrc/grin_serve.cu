@@ -255,6 +255,7 @@ void admit(grin_server s) {
     a.tir_b = di[3];
     a.dopl = j.prm.dopl;
     a.max_steps = j.prm.max_steps;
+    a.flags = j.prm.flags;
     a.perm = nullptr;
     // gridded media: claim the job's rays in entry-cell order (ray_order.cu)
     if (ordered && grin::launch_order(j.med->dm, a, base + L.order, s->ctx->sm_count, j.stream,
@@ -410,8 +411,10 @@ int grin_serve_submit(grin_server s, grin_medium med, const grin_rays* rays, con
   if (!s || !med || !rays || !p || !out || !job_id) return GRIN_ERR_INVALID_ARG;
   if (med->ctx != s->ctx || rays->count < 0) return GRIN_ERR_INVALID_ARG;
   if (rays->dtype != GRIN_F32 && rays->dtype != GRIN_F64) return GRIN_ERR_INVALID_ARG;
-  if (p->precision != GRIN_PREC_FP32_MIXED || !(p->dopl > 0.0) || p->max_steps < 0 || p->flags)
+  if (p->precision != GRIN_PREC_FP32_MIXED || !(p->dopl > 0.0) || p->max_steps < 0 ||
+      (p->flags & ~(uint32_t)GRIN_TRACE_LEVEL_ROOT))
     return GRIN_ERR_INVALID_ARG;
+  if (out->margin) return GRIN_ERR_NOT_IMPLEMENTED;
   if (rays->count > 0) {
     if (!rays->ox || !rays->oy || !rays->oz || !rays->dx || !rays->dy || !rays->dz)
       return GRIN_ERR_INVALID_ARG;

@@ -67,8 +67,11 @@ extern "C" int grin_trace_host_static(const grin_medium_desc* desc, const grin_r
   if (!desc || !rays || !p || !out) return GRIN_ERR_INVALID_ARG;
   if (rays->count < 0 || rays->count > kMaxRays) return GRIN_ERR_INVALID_ARG;
   if (rays->dtype != GRIN_F32 && rays->dtype != GRIN_F64) return GRIN_ERR_INVALID_ARG;
-  if (!(std::isfinite(p->dopl) && p->dopl > 0.0) || p->max_steps < 0 || p->flags != 0)
+  if (!(std::isfinite(p->dopl) && p->dopl > 0.0) || p->max_steps < 0 ||
+      (p->flags & ~(uint32_t)GRIN_TRACE_LEVEL_ROOT))
     return GRIN_ERR_INVALID_ARG;
+  if (out->margin || (p->precision == GRIN_PREC_FP64_FAST && p->flags))
+    return GRIN_ERR_NOT_IMPLEMENTED;
   if (p->precision != GRIN_PREC_FP64 && p->precision != GRIN_PREC_FP32_MIXED &&
       p->precision != GRIN_PREC_FP64_FAST)
     return GRIN_ERR_INVALID_ARG;
@@ -137,6 +140,7 @@ extern "C" int grin_trace_host_static(const grin_medium_desc* desc, const grin_r
   a.tir_b = di[3];
   a.dopl = p->dopl;
   a.max_steps = p->max_steps;
+  a.flags = p->flags;
   int rc;
   if (p->precision == GRIN_PREC_FP64) rc = grin::launch_fp64(m, a, s, sms);
   else if (p->precision == GRIN_PREC_FP64_FAST) rc = grin::launch_fp64_fast(m, a, s, sms);

@@ -164,7 +164,7 @@ __device__ __forceinline__ void n2p(const DevMedium& m, const double* P, double&
 // n (after layering) and the gradient of the smooth field; lvl = level or -1.
 template <int PC, bool GRID, bool LAYERED>
 __device__ __forceinline__ void sample(const DevMedium& m, const double* P, double& n, double* g,
-                                       int& lvl) {
+                                       int& lvl, double* ucoord = nullptr) {
   double f;
   if (GRID) {
     tricubic(m, P, f, g);
@@ -206,10 +206,57 @@ __device__ __forceinline__ void sample(const DevMedium& m, const double* P, doub
     else k = (int)fl;
     lvl = k;
     n = m.lvl_lo + ((double)k + 0.5) * (hi - m.lvl_lo) / L;
+    if (ucoord) *ucoord = uu;
   } else {
     lvl = -1;
     n = f;
+    if (ucoord) *ucoord = 0.5;
   }
+}
+
+// Decision margins of a ray (the quantities whose sign decides an integer
+// outcome), each the minimum over the trace: [0] distance of |N.I| from its
+// critical value at a refraction with mu > 1, [1] |N.I| at gradient steps,
+// [2] distance of a step end point to the enclosing surface in steps, [3]
+// distance of the level coordinate to the nearest shell boundary.
+struct Margins {
+  double v[4];
+  __device__ __forceinline__ void init() { v[0] = v[1] = v[2] = v[3] = INFINITY; }
+  __device__ __forceinline__ void take(int k, double x) { v[k] = x < v[k] ? x : v[k]; }
+};
+
+// Distance of the level coordinate u to the nearest shell boundary, the
+// integers 1 .. L-1 (u = 0 and u = L decide nothing: the levels clamp).
+__device__ __forceinline__ double lmargin(const DevMedium& m, double u) {
+  double k = floor(u + 0.5);
+  if (k < 1.0) k = 1.0;
+  if (k > (double)m.n_levels - 1.0) k = (double)m.n_levels - 1.0;
+  return m.n_levels > 1 ? fabs(u - k) : INFINITY;
+}
+
+// Distance of a point to the enclosing surface in units of the step h, to
+// first order for the curved surfaces.
+__device__ __forceinline__ double bmargin(const DevMedium& m, const double* P, double h) {
+  const double* b = m.b;
+  if (m.bkind == GRIN_BOUNDARY_BOX) {
+    double r = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+      double d1 = fabs(P[a] - b[a]), d2 = fabs(b[3 + a] - P[a]);
+      if (d1 < r) r = d1;
+      if (d2 < r) r = d2;
+    }
+    return r / h;
+  }
+  if (m.bkind == GRIN_BOUNDARY_SPHERE) {
+    double r[3] = {P[0] - b[0], P[1] - b[1], P[2] - b[2]};
+    return fabs(dot3(r, r) - b[3] * b[3]) / (2.0 * b[3] * h);
+  }
+  double x = P[0] - b[0], y = P[1] - b[1];
+  double r = fabs(x * x + y * y - b[2] * b[2]) / (2.0 * b[2] * h);
+  double d1 = fabs(P[2] - b[3]) / h, d2 = fabs(b[4] - P[2]) / h;
+  if (d1 < r) r = d1;
+  if (d2 < r) r = d2;
+  return r;
 }
 
 __device__ __forceinline__ bool inside(const DevMedium& m, const double* P) {
@@ -399,10 +446,20 @@ __device__ inline void leave(const DevMedium& m, const double* P, const double* 
 
 // Eq. 8-9 (positive root) or, for D <= 0, the Sec. II (v) reflection;
 // d is replaced by the unit result; returns true on reflection.
-__device__ __forceinline__ bool snell(double* d, const double* N, double mu) {
+__device__ __forceinline__ bool snell(double* d, const double* N, double mu,
+                                      double* margin = nullptr) {
   double c = dot3(N, d);
   double D = 1.0 - mu * mu * (1.0 - c * c);
   double R[3];
+  if (margin) {
+    // |N.I| minus its critical value sqrt(1 - 1/mu^2), as D / (mu^2 (|c| + c_crit))
+    if (mu > 1.0) {
+      double cc = sqrt(1.0 - 1.0 / (mu * mu));
+      *margin = fabs(D) / (mu * mu * (fabs(c) + cc));
+    } else {
+      *margin = INFINITY;
+    }
+  }
   if (D <= 0.0) {
     for (int a = 0; a < 3; ++a) R[a] = d[a] - 2.0 * c * N[a];
     normalize3(R);

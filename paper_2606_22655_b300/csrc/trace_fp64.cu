@@ -21,6 +21,11 @@
 namespace grin {
 namespace plain {
 
+// Shell crossings within one step, at most (GRIN_TRACE_LEVEL_ROOT): a ray
+// grazing a curved shell boundary can cross it back and forth at ever shorter
+// intervals; after this many the rest of the step runs straight.
+constexpr int kMaxCrossings = 16;
+
 // Point recorder of grin_trace_path: the first interior point, every full
 // step and every surface cut, at most cap points (ray-major, xyz).
 struct PathTap {
@@ -39,14 +44,25 @@ struct PathTap {
 template <int PC, bool GRID, bool LAYERED, bool TAP = false>
 __device__ void trace_one(const DevMedium& m, const TraceArgs& a, int64_t r,
                           PathTap* tap = nullptr) {
+  // decision margins are kept only when the caller asked for them
+  const bool keep = a.margin != nullptr;
+  Margins mg;
+  mg.init();
+  double dm = INFINITY;
+  auto finish = [&](const double* P, const double* d, double opl, int exit_id, int steps, int ti,
+                    int tb) {
+    put(a, r, P, d, opl, exit_id, steps, ti, tb);
+    if (keep)
+      for (int k = 0; k < 4; ++k) a.margin[4 * r + k] = mg.v[k];
+  };
   double P[3] = {ld(a.ox, r, a.dtype), ld(a.oy, r, a.dtype), ld(a.oz, r, a.dtype)};
   double d[3] = {ld(a.dx, r, a.dtype), ld(a.dy, r, a.dtype), ld(a.dz, r, a.dtype)};
   if (!finite3(P) || !finite3(d) || sqrt(dot3(d, d)) == 0.0) {
-    put(a, r, P, d, 0.0, GRIN_EXIT_INVALID, 0, 0, 0);
+    finish(P, d, 0.0, GRIN_EXIT_INVALID, 0, 0, 0);
     return;
   }
   normalize3(d);
-  double n_prev, g[3], opl_ext = 0.0;
+  double n_prev, g[3], opl_ext = 0.0, u;
   int lvl_prev;
   if (inside(m, P)) {
     sample<PC, GRID, LAYERED>(m, P, n_prev, g, lvl_prev);
@@ -54,7 +70,7 @@ __device__ void trace_one(const DevMedium& m, const TraceArgs& a, int64_t r,
     double t, Pb[3], NB[3];
     int face;
     if (!enter(m, P, d, t, Pb, NB, face)) {
-      put(a, r, P, d, 0.0, GRIN_EXIT_MISS, 0, 0, 0);
+      finish(P, d, 0.0, GRIN_EXIT_MISS, 0, 0, 0);
       return;
     }
     opl_ext = m.n_ext * t;
@@ -62,13 +78,15 @@ __device__ void trace_one(const DevMedium& m, const TraceArgs& a, int64_t r,
     P[1] = Pb[1];
     P[2] = Pb[2];
     sample<PC, GRID, LAYERED>(m, P, n_prev, g, lvl_prev);
-    if (snell(d, NB, m.n_ext / n_prev)) {
-      put(a, r, P, d, opl_ext, GRIN_EXIT_ENTRY_REFLECT, 0, 0, 0);
+    const bool refl = snell(d, NB, m.n_ext / n_prev, keep ? &dm : nullptr);
+    if (keep) mg.take(0, fabs(dm));
+    if (refl) {
+      finish(P, d, opl_ext, GRIN_EXIT_ENTRY_REFLECT, 0, 0, 0);
       return;
     }
   }
   if (!(isfinite(n_prev) && n_prev > 0.0)) {
-    put(a, r, P, d, opl_ext, GRIN_EXIT_INVALID, 0, 0, 0);
+    finish(P, d, opl_ext, GRIN_EXIT_INVALID, 0, 0, 0);
     return;
   }
   if (TAP) tap->put(P);
@@ -78,18 +96,117 @@ __device__ void trace_one(const DevMedium& m, const TraceArgs& a, int64_t r,
   for (int k = 0; k < 3; ++k) Q[k] = P[k] + h * d[k];
   int steps = 0, full = 0, ti = 0, tb = 0, exit_id = GRIN_EXIT_MAXSTEPS;
   double frac = 0.0;
+  const bool level_root = LAYERED && (a.flags & GRIN_TRACE_LEVEL_ROOT);
+  double rem = 1.0;   // fraction of the current step's dL0 still to go
+  int crossings = 0;  // shell crossings in the current step
   while (steps < a.max_steps) {
+    if (LAYERED && level_root) {
+      // Shells with their crossings solved: straight inside a shell (Sec. II
+      // (iii)); where the ray leaves its shell, the first point outside it
+      // (bisection on the segment) is where it refracts (Eq. 8-9) with the
+      // isoindicial normal grad f / |grad f| and mu = n_k / n_k', or is
+      // totally reflected (Sec. II (v)), and it goes on with the rest of the
+      // step's optical path (rem, a fraction of dL0; Q = P + rem h d).  At
+      // most kMaxCrossings crossings a step; then the rest of the step runs
+      // straight into the shell it ends in.
+      if (keep) mg.take(2, bmargin(m, Q, h));
+      double E[3], tq = 1.0, Pb[3], NB[3];
+      int face = 0;
+      const bool leaves = !inside(m, Q);
+      if (leaves) {
+        leave(m, P, Q, tq, Pb, NB, face);
+        E[0] = Pb[0];
+        E[1] = Pb[1];
+        E[2] = Pb[2];
+      } else {
+        E[0] = Q[0];
+        E[1] = Q[1];
+        E[2] = Q[2];
+      }
+      double nE, gE[3];
+      int lE;
+      sample<PC, GRID, LAYERED>(m, E, nE, gE, lE);
+      if (lE != lvl_prev && crossings == kMaxCrossings) {
+        lvl_prev = lE;
+        n_prev = nE;
+      }
+      if (lE != lvl_prev) {
+        ++crossings;
+        double lo = 0.0, hi = 1.0, X[3], nX, gX[3];
+        int lX;
+        for (int it = 0; it < 128; ++it) {
+          double mid = 0.5 * (lo + hi);
+          if (!(mid > lo && mid < hi)) break;
+          for (int k = 0; k < 3; ++k) X[k] = P[k] + mid * (E[k] - P[k]);
+          sample<PC, GRID, LAYERED>(m, X, nX, gX, lX);
+          if (lX == lvl_prev) lo = mid;
+          else hi = mid;
+        }
+        for (int k = 0; k < 3; ++k) X[k] = P[k] + hi * (E[k] - P[k]);
+        sample<PC, GRID, LAYERED>(m, X, nX, gX, lX);
+        const double used = hi * tq * rem;
+        frac += used;
+        rem = rem - used;
+        P[0] = X[0];
+        P[1] = X[1];
+        P[2] = X[2];
+        if (TAP) tap->put(P);
+        if (!(isfinite(nX) && nX > 0.0)) {
+          exit_id = GRIN_EXIT_INVALID;
+          break;
+        }
+        double gn = sqrt(dot3(gX, gX));
+        if (gn == 0.0 || !isfinite(gn)) {
+          n_prev = nX;
+          lvl_prev = lX;
+        } else {
+          double N[3] = {gX[0] / gn, gX[1] / gn, gX[2] / gn};
+          if (keep) mg.take(1, fabs(dot3(N, d)));
+          const bool refl = snell(d, N, n_prev / nX, keep ? &dm : nullptr);
+          if (keep) mg.take(0, fabs(dm));
+          if (refl) {
+            ++ti;
+          } else {
+            n_prev = nX;
+            lvl_prev = lX;
+          }
+        }
+        h = dopl / n_prev;
+        for (int k = 0; k < 3; ++k) Q[k] = P[k] + rem * h * d[k];
+        continue;
+      }
+      crossings = 0;
+      if (!leaves) {
+        P[0] = Q[0];
+        P[1] = Q[1];
+        P[2] = Q[2];
+        if (rem == 1.0) ++full;
+        else frac += rem;
+        ++steps;
+        rem = 1.0;
+        if (TAP) tap->put(P);
+        h = dopl / n_prev;
+        for (int k = 0; k < 3; ++k) Q[k] = P[k] + h * d[k];
+        continue;
+      }
+      // the rest of the step meets the enclosing surface inside the shell:
+      // below
+    }
+    if (keep) mg.take(2, bmargin(m, Q, h));
     if (!inside(m, Q)) {
       double t, Pb[3], NB[3];
       int face;
       leave(m, P, Q, t, Pb, NB, face);
-      frac += t;
+      frac += t * rem;
+      rem = 1.0;
       ++steps;
       P[0] = Pb[0];
       P[1] = Pb[1];
       P[2] = Pb[2];
       if (TAP) tap->put(P);
-      if (snell(d, NB, n_prev / m.n_ext)) {
+      const bool refl = snell(d, NB, n_prev / m.n_ext, keep ? &dm : nullptr);
+      if (keep) mg.take(0, fabs(dm));
+      if (refl) {
         ++tb;
         h = dopl / n_prev;
         sample<PC, GRID, LAYERED>(m, P, n_prev, g, lvl_prev);
@@ -111,7 +228,8 @@ __device__ void trace_one(const DevMedium& m, const TraceArgs& a, int64_t r,
     if (TAP) tap->put(P);
     double n_i;
     int lvl_i;
-    sample<PC, GRID, LAYERED>(m, P, n_i, g, lvl_i);
+    sample<PC, GRID, LAYERED>(m, P, n_i, g, lvl_i, &u);
+    if (keep && LAYERED) mg.take(3, lmargin(m, u));
     if (!(isfinite(n_i) && n_i > 0.0)) {
       exit_id = GRIN_EXIT_INVALID;
       break;
@@ -122,6 +240,7 @@ __device__ void trace_one(const DevMedium& m, const TraceArgs& a, int64_t r,
     } else {
       double N[3] = {g[0] / gn, g[1] / gn, g[2] / gn};
       double c = dot3(N, d);
+      if (keep) mg.take(1, fabs(c));
       if (c == 0.0) {
         double hi = dopl / n_i;
         double Pn[3] = {P[0] + hi * N[0], P[1] + hi * N[1], P[2] + hi * N[2]};
@@ -134,11 +253,15 @@ __device__ void trace_one(const DevMedium& m, const TraceArgs& a, int64_t r,
         for (int q = 0; q < 3; ++q) d[q] = a0 * d[q] + k * N[q];
         normalize3(d);
         h = hi;
-      } else if (snell(d, N, n_prev / n_i)) {
-        ++ti;
-        h = dopl / n_prev;
       } else {
-        h = dopl / n_i;
+        const bool refl = snell(d, N, n_prev / n_i, keep ? &dm : nullptr);
+        if (keep) mg.take(0, fabs(dm));
+        if (refl) {
+          ++ti;
+          h = dopl / n_prev;
+        } else {
+          h = dopl / n_i;
+        }
       }
     }
     n_prev = n_i;
@@ -146,7 +269,7 @@ __device__ void trace_one(const DevMedium& m, const TraceArgs& a, int64_t r,
     for (int k = 0; k < 3; ++k) Q[k] = P[k] + h * d[k];
   }
   double opl = opl_ext + dopl * (double)full + dopl * frac;
-  put(a, r, P, d, opl, exit_id, steps, ti, tb);
+  finish(P, d, opl, exit_id, steps, ti, tb);
 }
 
 template <int PC, bool GRID, bool LAYERED>

@@ -15,49 +15,6 @@
 
 namespace grin {
 
-template <int PC, bool GRID, bool LAYERED>
-struct Field64Fast {
-  // n (after layering) and grad of the smooth field at p; lvl = level (or 0).
-  static __device__ __forceinline__ void eval(const DevMedium& m, V3 p, double& n, V3& g,
-                                              int& lvl) {
-    double f;
-    if (GRID) {
-      double u[3] = {(p.x - m.origin[0]) * m.inv_spacing[0], (p.y - m.origin[1]) * m.inv_spacing[1],
-                     (p.z - m.origin[2]) * m.inv_spacing[2]};
-      double v, gx, gy, gz;
-      grid_vg<double>(m, u, 0.0, v, gx, gy, gz);
-      f = v;
-      g = mk(gx * m.inv_spacing[0], gy * m.inv_spacing[1], gz * m.inv_spacing[2]);
-    } else {
-      double x = (p.x - m.off[0]) * m.inv_scale[0];
-      double y = (p.y - m.off[1]) * m.inv_scale[1];
-      double z = (p.z - m.off[2]) * m.inv_scale[2];
-      double q, qx, qy, qz;
-      field_vg<PC, double>(m.c64, x, y, z, q, qx, qy, qz);
-      V3 gq = mk(qx * m.inv_scale[0], qy * m.inv_scale[1], qz * m.inv_scale[2]);
-      if (m.form == GRIN_FORM_LINEAR) {
-        f = q;
-        g = gq;
-      } else if (m.form == GRIN_FORM_SQRT) {
-        f = sqrt(q);
-        g = scale(0.5 / f, gq);
-      } else {
-        f = m.form_c / q;
-        g = scale(-f / q, gq);
-      }
-    }
-    if (LAYERED) {
-      double u = (f - m.lvl_lo) * (double)m.n_levels / m.lvl_span;
-      double fl = floor(u);
-      int k = fl >= 0.0 ? (fl > (double)(m.n_levels - 1) ? m.n_levels - 1 : (int)fl) : 0;
-      lvl = k;
-      n = m.lvl_lo + ((double)k + 0.5) * m.lvl_span / (double)m.n_levels;
-    } else {
-      lvl = 0;
-      n = f;
-    }
-  }
-};
 
 template <int PC, bool GRID, bool LAYERED>
 __device__ void trace_one_fp64_fast(const DevMedium& m, const TraceArgs& a, int64_t r) {

@@ -45,6 +45,7 @@
 // common box / n = p case, which drops their run-time switches from the step)
 // or -1 for "read from the medium at run time".
 #include <climits>
+#include <type_traits>
 
 #include "grin_device.cuh"
 
@@ -68,9 +69,18 @@ constexpr float kCritBand = 1.0e-5f;  // relative |D| below which FP64 decides
 
 #define GRIN_UNLIKELY(x) __builtin_expect(!!(x), 0)
 
-template <int PC, bool GRID, bool LAYERED, int BK, int FORM>
+struct RayF;
+struct RayFM;
+
+// MG: the kernel also keeps each ray's decision margins (grin_out.margin),
+// in the state type RayFM.
+template <int PC, bool GRID, bool LAYERED, int BK, int FORM, bool MG = false>
 struct Cfg {
   static constexpr bool kGrid = GRID;
+  static constexpr int kPC = PC;
+  static constexpr bool kLayered = LAYERED;
+  static constexpr bool kMG = MG;
+  using State = typename std::conditional<MG, RayFM, RayF>::type;
   static constexpr int kMinBlocks = GRID ? GRIN_MIXED_MIN_BLOCKS_GRID : GRIN_MIXED_MIN_BLOCKS;
   static __device__ __forceinline__ int bk(const DevMedium& m) { return BK >= 0 ? BK : m.bkind; }
   static __device__ __forceinline__ int form(const DevMedium& m) { return FORM >= 0 ? FORM : m.form; }
@@ -80,8 +90,17 @@ struct Cfg {
   // media read the hi part).
   static __device__ __forceinline__ void eval(const DevMedium& m, float px, float py, float pz,
                                               float lx, float ly, float lz, float& nu,
-                                              float& gx, float& gy, float& gz, int& lvl) {
+                                              float& gx, float& gy, float& gz, int& lvl,
+                                              float* uo = nullptr) {
     float f;
+    field(m, px, py, pz, lx, ly, lz, f, gx, gy, gz);
+    level(m, f, nu, lvl, uo);
+  }
+
+  // The smooth field f = n - base (before any layering) and its gradient.
+  static __device__ __forceinline__ void field(const DevMedium& m, float px, float py, float pz,
+                                               float lx, float ly, float lz, float& f,
+                                               float& gx, float& gy, float& gz) {
     if (GRID) {
       const float ph[3] = {px, py, pz}, pl[3] = {lx, ly, lz};
       int i0[3];
@@ -120,22 +139,30 @@ struct Cfg {
         gz = qz * s;
       }
     }
-    level(m, f, nu, lvl);
   }
 
   // f = n - base of the smooth field -> nu = n - base of the medium and its
   // level (a layered medium takes the centre value of f's shell).
-  static __device__ __forceinline__ void level(const DevMedium& m, float f, float& nu, int& lvl) {
+  // (uo: the level coordinate, for the level margin)
+  static __device__ __forceinline__ void level(const DevMedium& m, float f, float& nu, int& lvl,
+                                               float* uo = nullptr) {
     if (LAYERED) {
       float u = (f - m.lvl_lo_rel_f) * m.lvl_scale_f;
       float fl = floorf(u);
       int k = fl >= 0.0f ? (fl > (float)(m.n_levels - 1) ? m.n_levels - 1 : (int)fl) : 0;
       lvl = k;
-      nu = fmaf((float)k + 0.5f, m.lvl_step_f, m.lvl_lo_rel_f);
+      nu = shell_nu(m, k);
+      if (uo) *uo = u;
     } else {
       lvl = 0;
       nu = f;
+      if (uo) *uo = 0.5f;
     }
+  }
+
+  // n - base of shell k of a layered medium.
+  static __device__ __forceinline__ float shell_nu(const DevMedium& m, int k) {
+    return fmaf((float)k + 0.5f, m.lvl_step_f, m.lvl_lo_rel_f);
   }
 
   // Gridded media.  The cell of the 64-tap stencil at the point ph + pl and
@@ -237,7 +264,8 @@ struct Cfg {
   // so the same value and gradient bit for bit.
   static __device__ __forceinline__ void eval_taps(const DevMedium& m, const float* fr,
                                                    const float* col, float lb, float& nu,
-                                                   float& gx, float& gy, float& gz, int& lvl) {
+                                                   float& gx, float& gy, float& gz, int& lvl,
+                                                   float* uo = nullptr) {
     float w[3][4], dw[3][4];
 #pragma unroll
     for (int k = 0; k < 3; ++k) cr_w(fr[k], w[k], dw[k]);
@@ -267,7 +295,7 @@ struct Cfg {
     gx = GX * m.inv_spacing_f[0];
     gy = GY * m.inv_spacing_f[1];
     gz = GZ * m.inv_spacing_f[2];
-    level(m, V + (lb - m.base_f), nu, lvl);
+    level(m, V + (lb - m.base_f), nu, lvl, uo);
   }
 
   static __device__ __forceinline__ bool inside(const DevMedium& m, const float* q) {
@@ -292,7 +320,70 @@ struct RayF {
   float frac;                       // sum of the fractions of steps cut at the surface
   int lvl_prev, steps, cut, tir_i, tir_b;  // cut: steps ended early at the surface
   double opl_x;  // exterior segment, in optical length
+  // layered media with GRIN_TRACE_LEVEL_ROOT: the fraction of the current
+  // step's dL0 spent before its shell crossings, and their number
+  float used;
+  int xc;
 };
+
+// The state with the ray's decision margins (grin_out.margin, in FP32 on this
+// path's own trajectory): the minimum over the trace of [0] |N.I| minus its
+// critical value at refractions with mu > 1, [1] |N.I| at gradient steps,
+// [2] the distance of a step end to the surface in steps, [3] the distance
+// of the level coordinate to the nearest shell boundary.
+struct RayFM : RayF {
+  float mg[4];
+};
+
+template <class C>
+__device__ __forceinline__ void mg_init(RayF& s) {
+  if constexpr (C::kMG)
+    for (int k = 0; k < 4; ++k) static_cast<RayFM&>(s).mg[k] = INFINITY;
+}
+
+template <class C>
+__device__ __forceinline__ void mg_take(RayF& s, int k, float v) {
+  if constexpr (C::kMG) {
+    float& x = static_cast<RayFM&>(s).mg[k];
+    x = fminf(x, v);
+  }
+}
+
+// |N.I| minus its critical value for a refraction test with
+// c = N.I, mu = 1 - om, omm = 1 - mu^2 and discriminant D = mu^2 c^2 + omm:
+// D / (mu^2 (|c| + c_crit)) with c_crit = sqrt(-omm) / mu when mu > 1.
+__device__ __forceinline__ float crit_margin(float c, float mu, float omm, float D) {
+  return omm < 0.0f ? fabsf(D) / (mu * fmaf(mu, fabsf(c), sqrtf(-omm))) : INFINITY;
+}
+
+// Distance of the level coordinate u to the nearest shell boundary, the
+// integers 1 .. L-1 (the levels clamp below 0 and above L-1).
+__device__ __forceinline__ float lvl_margin(const DevMedium& m, float u) {
+  const float k = fminf(fmaxf(rintf(u), 1.0f), (float)(m.n_levels - 1));
+  return m.n_levels > 1 ? fabsf(u - k) : INFINITY;
+}
+
+// Distance of a point to the enclosing surface, in steps of length h (first
+// order for the curved surfaces).
+template <class C>
+__device__ __forceinline__ float bnd_margin(const DevMedium& m, const float* q, float h) {
+  const float* b = m.b_f;
+  const int k = C::bk(m);
+  float r;
+  if (k == GRIN_BOUNDARY_BOX) {
+    r = fminf(fminf(fminf(fabsf(q[0] - b[0]), fabsf(b[3] - q[0])),
+                    fminf(fabsf(q[1] - b[1]), fabsf(b[4] - q[1]))),
+              fminf(fabsf(q[2] - b[2]), fabsf(b[5] - q[2])));
+  } else if (k == GRIN_BOUNDARY_SPHERE) {
+    float x = q[0] - b[0], y = q[1] - b[1], z = q[2] - b[2];
+    r = fabsf(fmaf(x, x, fmaf(y, y, z * z)) - b[3] * b[3]) / (2.0f * b[3]);
+  } else {
+    float x = q[0] - b[0], y = q[1] - b[1];
+    r = fminf(fabsf(fmaf(x, x, y * y) - b[2] * b[2]) / (2.0f * b[2]),
+              fminf(fabsf(q[2] - b[3]), fabsf(b[4] - q[2])));
+  }
+  return r / h;
+}
 
 __device__ __forceinline__ V3 pos64(const RayF& s) {
   return mk((double)s.ph[0] + (double)s.pl[0], (double)s.ph[1] + (double)s.pl[1],
@@ -340,6 +431,16 @@ __device__ __forceinline__ void finish(const TraceArgs& a, int64_t r, const RayF
   store_ray(a, r, p, d, opl, exit_id, s.steps, s.tir_i, s.tir_b);
 }
 
+// finish, and the margins when the kernel keeps them and the caller asked.
+template <class C>
+__device__ __forceinline__ void fin(const TraceArgs& a, int64_t r, const RayF& s, V3 p, V3 d,
+                                    int exit_id) {
+  finish(a, r, s, p, d, exit_id);
+  if constexpr (C::kMG)
+    if (a.margin)
+      for (int k = 0; k < 4; ++k) a.margin[4 * r + k] = (double)static_cast<const RayFM&>(s).mg[k];
+}
+
 // (n_{i-1} - base) -> the state's index fields; false if n is not usable.
 __device__ __forceinline__ bool set_index(const DevMedium& m, RayF& s, float nu) {
   s.nu_prev = nu;
@@ -377,7 +478,7 @@ __device__ bool init_ray_box32(const DevMedium& m, const TraceArgs& a, int64_t r
   float d[3] = {(float)d64.x, (float)d64.y, (float)d64.z};
   float dd = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
   if (!finite3(p64) || !finite3(d64) || !(dd > 0.0f) || !isfinite(dd)) {
-    finish(a, r, s, p64, d64, GRIN_EXIT_INVALID);
+    fin<C>(a, r, s, p64, d64, GRIN_EXIT_INVALID);
     return false;
   }
   renorm(d);
@@ -403,7 +504,7 @@ __device__ bool init_ray_box32(const DevMedium& m, const TraceArgs& a, int64_t r
       tf = fminf(tf, up);
     }
     if (axis < 0 || !(tn >= 0.0f && tn < tf)) {
-      finish(a, r, s, p64, v3f(d), GRIN_EXIT_MISS);
+      fin<C>(a, r, s, p64, v3f(d), GRIN_EXIT_MISS);
       return false;
     }
 #pragma unroll
@@ -415,9 +516,10 @@ __device__ bool init_ray_box32(const DevMedium& m, const TraceArgs& a, int64_t r
     const float mu = m.n_ext_f / (m.base_f + nu);
     const float c = hi ? d[axis] : -d[axis];
     const float D = 1.0f - mu * mu * fmaf(-c, c, 1.0f);
+    mg_take<C>(s, 0, crit_margin(c, mu, fmaf(-mu, mu, 1.0f), D));
     if (D <= 0.0f) {
       d[axis] = -d[axis];
-      finish(a, r, s, v3f(o), v3f(d), GRIN_EXIT_ENTRY_REFLECT);
+      fin<C>(a, r, s, v3f(o), v3f(d), GRIN_EXIT_ENTRY_REFLECT);
       return false;
     }
     const float gamma = fmaf(-mu, c, copysignf(sqrtf(D), c));
@@ -429,11 +531,11 @@ __device__ bool init_ray_box32(const DevMedium& m, const TraceArgs& a, int64_t r
     C::eval(m, o[0], o[1], o[2], 0.0f, 0.0f, 0.0f, nu, s.gp[0], s.gp[1], s.gp[2], s.lvl_prev);
   }
   if (!set_index(m, s, nu)) {
-    finish(a, r, s, v3f(o), v3f(d), GRIN_EXIT_INVALID);
+    fin<C>(a, r, s, v3f(o), v3f(d), GRIN_EXIT_INVALID);
     return false;
   }
   if (a.max_steps <= 0) {
-    finish(a, r, s, v3f(o), v3f(d), GRIN_EXIT_MAXSTEPS);
+    fin<C>(a, r, s, v3f(o), v3f(d), GRIN_EXIT_MAXSTEPS);
     return false;
   }
 #pragma unroll
@@ -445,6 +547,22 @@ __device__ bool init_ray_box32(const DevMedium& m, const TraceArgs& a, int64_t r
   }
   s.h = (float)a.dopl * s.inv_prev;
   return true;
+}
+
+// A step ends on the enclosing surface a fraction t of the way along what was
+// left of it: it counts as a step and adds that part of dL0 (plus, in a
+// layered medium with its crossings solved, what the step spent before them).
+template <class C>
+__device__ __forceinline__ void cut_step(RayF& s, float t) {
+  if constexpr (C::kLayered) {
+    s.frac += fmaf(t, 1.0f - s.used, s.used);
+    s.used = 0.0f;
+    s.xc = 0;
+  } else {
+    s.frac += t;
+  }
+  ++s.steps;
+  ++s.cut;
 }
 
 // Box crossing in FP32 (see init_ray_box32): the fraction of the step to
@@ -478,9 +596,7 @@ __device__ __forceinline__ int surface_event_box32(const DevMedium& m, const Tra
   }
   if (bf < 0 || best > 1.0f) return 0;  // the compensated end point is inside
   best = fmaxf(best, 0.0f);
-  s.frac += best;
-  ++s.steps;
-  ++s.cut;
+  cut_step<C>(s, best);
   const int axis = bf >> 1, hi = bf & 1;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -495,6 +611,7 @@ __device__ __forceinline__ int surface_event_box32(const DevMedium& m, const Tra
   const float mu = (m.base_f + s.nu_prev) / m.n_ext_f;
   const float c = hi ? s.d[axis] : -s.d[axis];
   const float D = 1.0f - mu * mu * fmaf(-c, c, 1.0f);
+  mg_take<C>(s, 0, crit_margin(c, mu, fmaf(-mu, mu, 1.0f), D));
   bool tir = D <= 0.0f;
   if (GRIN_UNLIKELY(fabsf(D) <= kCritBand)) {
     double mu64 = ((double)m.base_f + (double)s.nu_prev) / m.n_ext;
@@ -511,11 +628,11 @@ __device__ __forceinline__ int surface_event_box32(const DevMedium& m, const Tra
     C::eval(m, s.ph[0], s.ph[1], s.ph[2], s.pl[0], s.pl[1], s.pl[2], nu, s.gp[0], s.gp[1], s.gp[2],
             s.lvl_prev);
     if (!set_index(m, s, nu)) {
-      finish(a, r, s, pos64(s), dir64(s), GRIN_EXIT_INVALID);
+      fin<C>(a, r, s, pos64(s), dir64(s), GRIN_EXIT_INVALID);
       return 2;
     }
     if (s.steps >= a.max_steps) {
-      finish(a, r, s, pos64(s), dir64(s), GRIN_EXIT_MAXSTEPS);
+      fin<C>(a, r, s, pos64(s), dir64(s), GRIN_EXIT_MAXSTEPS);
       return 2;
     }
     return 1;
@@ -526,7 +643,7 @@ __device__ __forceinline__ int surface_event_box32(const DevMedium& m, const Tra
   for (int k = 0; k < 3; ++k) R[k] = mu * (s.d[k] + s.dl[k]);
   R[axis] += hi ? gamma : -gamma;
   renorm(R);
-  finish(a, r, s, pos64(s), v3f(R), bf);
+  fin<C>(a, r, s, pos64(s), v3f(R), bf);
   return 2;
 }
 
@@ -539,9 +656,14 @@ __device__ bool init_ray(const DevMedium& m, const TraceArgs& a, int64_t r, RayF
   s.steps = s.cut = s.tir_i = s.tir_b = 0;
   s.opl_x = 0.0;
   s.frac = 0.0f;
+  if constexpr (C::kLayered) {
+    s.used = 0.0f;
+    s.xc = 0;
+  }
+  mg_init<C>(s);
   if (C::bk(m) == GRIN_BOUNDARY_BOX) return init_ray_box32<C>(m, a, r, s, p, d);
   if (!finite3(p) || !finite3(d) || dot(d, d) == 0.0) {
-    finish(a, r, s, p, d, GRIN_EXIT_INVALID);
+    fin<C>(a, r, s, p, d, GRIN_EXIT_INVALID);
     return false;
   }
   d = unit(d);
@@ -551,26 +673,29 @@ __device__ bool init_ray(const DevMedium& m, const TraceArgs& a, int64_t r, RayF
     V3 pb, nb;
     int face;
     if (!enter64(m, p, d, t, pb, nb, face)) {
-      finish(a, r, s, p, d, GRIN_EXIT_MISS);
+      fin<C>(a, r, s, p, d, GRIN_EXIT_MISS);
       return false;
     }
     s.opl_x = m.n_ext * t;
     p = pb;
     eval64<C>(m, p, nu, s.gp, s.lvl_prev);
     double nb_in = (double)m.base_f + (double)nu;
-    if (refract64(d, nb, m.n_ext / nb_in)) {
-      finish(a, r, s, p, d, GRIN_EXIT_ENTRY_REFLECT);
+    double cm = INFINITY;
+    const bool refl = refract64(d, nb, m.n_ext / nb_in, C::kMG ? &cm : nullptr);
+    mg_take<C>(s, 0, (float)cm);
+    if (refl) {
+      fin<C>(a, r, s, p, d, GRIN_EXIT_ENTRY_REFLECT);
       return false;
     }
   } else {
     eval64<C>(m, p, nu, s.gp, s.lvl_prev);
   }
   if (!set_index(m, s, nu)) {
-    finish(a, r, s, p, d, GRIN_EXIT_INVALID);
+    fin<C>(a, r, s, p, d, GRIN_EXIT_INVALID);
     return false;
   }
   if (a.max_steps <= 0) {
-    finish(a, r, s, p, d, GRIN_EXIT_MAXSTEPS);
+    fin<C>(a, r, s, p, d, GRIN_EXIT_MAXSTEPS);
     return false;
   }
   set_pos(s, p);
@@ -594,11 +719,12 @@ __device__ __forceinline__ int surface_event(const DevMedium& m, const TraceArgs
   V3 pb, nb;
   int face;
   exit64(m, p, q, t, pb, nb, face);
-  s.frac += (float)t;
-  ++s.steps;
-  ++s.cut;
+  cut_step<C>(s, (float)t);
   double n_prev = (double)m.base_f + (double)s.nu_prev;
-  if (refract64(d, nb, n_prev / m.n_ext)) {
+  double cm = INFINITY;
+  const bool refl = refract64(d, nb, n_prev / m.n_ext, C::kMG ? &cm : nullptr);
+  mg_take<C>(s, 0, (float)cm);
+  if (refl) {
     ++s.tir_b;
     s.h = dopl_f * s.inv_prev;
     float nu;
@@ -607,16 +733,16 @@ __device__ __forceinline__ int surface_event(const DevMedium& m, const TraceArgs
     set_pos(s, pb);
     set_dir(s, d);
     if (!ok) {
-      finish(a, r, s, pb, d, GRIN_EXIT_INVALID);
+      fin<C>(a, r, s, pb, d, GRIN_EXIT_INVALID);
       return 2;
     }
     if (s.steps >= a.max_steps) {
-      finish(a, r, s, pb, d, GRIN_EXIT_MAXSTEPS);
+      fin<C>(a, r, s, pb, d, GRIN_EXIT_MAXSTEPS);
       return 2;
     }
     return 1;
   }
-  finish(a, r, s, pb, d, face);
+  fin<C>(a, r, s, pb, d, face);
   return 2;
 }
 
@@ -641,6 +767,161 @@ __device__ __forceinline__ bool crit64(const float* N, const float* d, float dn,
   return false;
 }
 
+// The smooth field f = n - base and its gradient at an FP64 point.
+template <class C>
+__device__ __forceinline__ void field64(const DevMedium& m, V3 p, float& f, float* g) {
+  const float hx = (float)p.x, hy = (float)p.y, hz = (float)p.z;
+  C::field(m, hx, hy, hz, (float)(p.x - (double)hx), (float)(p.y - (double)hy),
+           (float)(p.z - (double)hz), f, g[0], g[1], g[2]);
+}
+
+// Shell crossings within one step, at most (GRIN_TRACE_LEVEL_ROOT): a ray
+// grazing a curved shell boundary can cross it back and forth at ever shorter
+// intervals; after this many the rest of the step runs straight into the
+// shell it ends in.
+constexpr int kMaxCrossings = 16;
+
+// The rest of a step in a layered medium with its shell crossings solved
+// (GRIN_TRACE_LEVEL_ROOT; Q = P + h I is what is left of the step, h =
+// (1 - used) dL0 / n_k).  Inside the shell the ray runs straight (Sec. II
+// (iii)).  If Q (or the point where the segment meets the enclosing surface)
+// lies in another shell, the segment first meets the boundary f = f_b of
+// the ray's shell where safeguarded Newton iterations on the segment put it
+// (regula falsi start; a bracket kept by the sign of f - f_b; bisection when
+// a Newton step leaves it); the ray refracts there in FP64 by Eq. 8-9 with
+// the isoindicial normal grad f / |grad f| and mu = n_k / n_k', or is
+// totally reflected and stays in its shell (Sec. II (v)), and goes on with
+// the rest of the step's optical path.  Returns false when the ray finished.
+template <class C>
+__device__ __forceinline__ bool level_root_step(const DevMedium& m, const TraceArgs& a, int64_t r,
+                                                RayF& s, float dopl_f, const float* qh,
+                                                const float* ql) {
+  const V3 p = pos64(s);
+  const V3 q = mk((double)qh[0] + (double)ql[0], (double)qh[1] + (double)ql[1],
+                  (double)qh[2] + (double)ql[2]);
+  mg_take<C>(s, 2, bnd_margin<C>(m, qh, s.h));
+  double tb = 1.0;
+  V3 e = q, pb, nb;
+  int face = 0;
+  const bool leaves = !inside64(m, q);
+  if (leaves) {
+    exit64(m, p, q, tb, pb, nb, face);
+    e = pb;
+  }
+  float fE, gE[3], nuE;
+  int lE;
+  field64<C>(m, e, fE, gE);
+  C::level(m, fE, nuE, lE);
+  if (lE != s.lvl_prev && s.xc == kMaxCrossings) {
+    s.lvl_prev = lE;
+    if (!set_index(m, s, nuE)) {
+      fin<C>(a, r, s, pos64(s), dir64(s), GRIN_EXIT_INVALID);
+      return false;
+    }
+  }
+  const int k = s.lvl_prev;
+  if (lE == k) {
+    s.xc = 0;
+    if (leaves) {
+      const int rc = surface_event<C>(m, a, r, s, dopl_f, qh);
+      if (rc == 2) return false;
+      if (rc == 1) return true;
+    }
+    // straight on to the end of the step inside the shell
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      s.ph[j] = qh[j];
+      s.pl[j] = ql[j];
+    }
+    ++s.steps;
+    s.used = 0.0f;
+    s.h = dopl_f * s.inv_prev;
+    if (s.steps >= a.max_steps) {
+      fin<C>(a, r, s, pos64(s), dir64(s), GRIN_EXIT_MAXSTEPS);
+      return false;
+    }
+    return true;
+  }
+  ++s.xc;
+  // the boundary of shell k towards the end's shell: f_b; inside shell k
+  // means f < f_b going up, f >= f_b going down
+  const bool up = lE > k;
+  const int k2 = up ? k + 1 : k - 1;
+  // in FP64, as the level values below: lo + k span / L, less base
+  const double L = (double)m.n_levels;
+  const double fb = (m.lvl_lo - m.base) + (double)(up ? k + 1 : k) * m.lvl_span / L;
+  float fP, gX[3];
+  field64<C>(m, p, fP, gX);
+  const V3 seg = mk(e.x - p.x, e.y - p.y, e.z - p.z);
+  double lo = 0.0, hi = 1.0;
+  const double a0 = (double)fP - fb, a1 = (double)fE - fb;
+  double t = (a0 != a1) ? a0 / (a0 - a1) : 0.5;
+  if (!(t > lo && t < hi)) t = 0.5;
+  V3 x = axpy(t, seg, p), gx64;
+  for (int it = 0; it < 10; ++it) {
+    float fX;
+    field64<C>(m, x, fX, gX);
+    const double phi = (double)fX - fb;
+    if (up ? phi < 0.0 : phi >= 0.0) lo = t;
+    else hi = t;
+    const double dphi = (double)gX[0] * seg.x + (double)gX[1] * seg.y + (double)gX[2] * seg.z;
+    double tn = t - phi / dphi;
+    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+    const bool done = fabs(tn - t) <= 1e-7 * fabs(t) + 1e-12;
+    t = tn;
+    x = axpy(t, seg, p);
+    if (done) break;
+  }
+  // One Newton step on the field evaluated in FP64 (f rounded to FP32 moves
+  // the boundary by ~4e-9 in n, which at a curved isosurface and a
+  // near-critical crossing is felt in the refracted direction), which also
+  // gives the normal.
+  {
+    double fn;
+    V3 g64;
+    int l64;
+    Field64Fast<C::kPC, C::kGrid, false>::eval(m, x, fn, g64, l64);
+    const double dphi = dot(g64, seg);
+    const double tn = t - (fn - (fb + m.base)) / dphi;
+    if (tn > lo && tn < hi && isfinite(tn)) {
+      t = tn;
+      x = axpy(t, seg, p);
+    }
+    gX[0] = (float)g64.x;  // (kept in FP64 below)
+    gX[1] = (float)g64.y;
+    gX[2] = (float)g64.z;
+    gx64 = g64;
+  }
+  // the ray is at x, a fraction t tb of what was left of the step further on
+  set_pos(s, x);
+  s.used = fmaf((float)(t * tb), 1.0f - s.used, s.used);
+  const double gn = sqrt(dot(gx64, gx64));
+  bool tir = false;
+  if (gn > 0.0 && isfinite(gn)) {
+    const V3 N = mk(gx64.x / gn, gx64.y / gn, gx64.z / gn);
+    V3 d = dir64(s);
+    mg_take<C>(s, 1, (float)fabs(dot(N, d)));
+    const double nk = m.lvl_lo + ((double)k + 0.5) * m.lvl_span / L;
+    const double nk2 = m.lvl_lo + ((double)k2 + 0.5) * m.lvl_span / L;
+    double cm = INFINITY;
+    tir = refract64(d, N, nk / nk2, C::kMG ? &cm : nullptr);
+    mg_take<C>(s, 0, (float)cm);
+    set_dir(s, d);
+  }
+  if (tir) {
+    ++s.tir_i;
+  } else {
+    s.lvl_prev = k2;
+    if (!set_index(m, s, C::shell_nu(m, k2))) {
+      fin<C>(a, r, s, pos64(s), dir64(s), GRIN_EXIT_INVALID);
+      return false;
+    }
+  }
+  // the rest of the step's optical path in the (new) shell
+  s.h = (1.0f - s.used) * dopl_f * s.inv_prev;
+  return true;
+}
+
 // One VRT step of an active ray, every case tested in order; returns false
 // when the ray finished.  Taken only when the fast step below meets a case
 // it does not handle.
@@ -656,6 +937,9 @@ __device__ __noinline__ bool step_slow(const DevMedium& m, const TraceArgs& a, i
     ql[k] = y - (t - s.ph[k]);
     qh[k] = t;
   }
+  if constexpr (LAYERED)
+    if (a.flags & GRIN_TRACE_LEVEL_ROOT) return level_root_step<C>(m, a, r, s, dopl_f, qh, ql);
+  mg_take<C>(s, 2, bnd_margin<C>(m, qh, s.h));
   if (GRIN_UNLIKELY(!C::inside(m, qh))) {
     int rc = surface_event<C>(m, a, r, s, dopl_f, qh);
     if (rc == 2) return false;
@@ -667,12 +951,14 @@ __device__ __noinline__ bool step_slow(const DevMedium& m, const TraceArgs& a, i
     s.pl[k] = ql[k];
   }
   ++s.steps;
-  float nu_i, g[3];
+  float nu_i, g[3], u_i;
   int lvl_i;
-  C::eval(m, qh[0], qh[1], qh[2], ql[0], ql[1], ql[2], nu_i, g[0], g[1], g[2], lvl_i);
+  C::eval(m, qh[0], qh[1], qh[2], ql[0], ql[1], ql[2], nu_i, g[0], g[1], g[2], lvl_i,
+          C::kMG ? &u_i : nullptr);
+  if (LAYERED) mg_take<C>(s, 3, lvl_margin(m, u_i));
   const float n_i = m.base_f + nu_i;
   if (GRIN_UNLIKELY(!(isfinite(n_i) && n_i > 0.0f))) {
-    finish(a, r, s, pos64(s), dir64(s), GRIN_EXIT_INVALID);
+    fin<C>(a, r, s, pos64(s), dir64(s), GRIN_EXIT_INVALID);
     return false;
   }
   const float inv_n = 1.0f / n_i;
@@ -683,6 +969,7 @@ __device__ __noinline__ bool step_slow(const DevMedium& m, const TraceArgs& a, i
     float ri = rsqrtf(gn2);
     float N[3] = {g[0] * ri, g[1] * ri, g[2] * ri};
     float c = fmaf(N[0], s.d[0], fmaf(N[1], s.d[1], N[2] * s.d[2]));
+    mg_take<C>(s, 1, fabsf(c));
     if (GRIN_UNLIKELY(c == 0.0f)) {
       // Sec. II (iv): circular arc from one extra index sample along N.
       float hi = dopl_f * inv_n;
@@ -714,6 +1001,7 @@ __device__ __noinline__ bool step_slow(const DevMedium& m, const TraceArgs& a, i
       const float omm = om * (2.0f - om);    // 1 - mu^2
       const float mc = mu * c;
       const float D = fmaf(mc, mc, omm);
+      mg_take<C>(s, 0, crit_margin(c, mu, omm, D));
       bool tir = D <= 0.0f;
       float gamma = (c > 0.0f ? omm : -omm) / (sqrtf(fmaxf(D, 0.0f)) + fabsf(mc));
       if (GRIN_UNLIKELY(fabsf(D) <= kCritBand * (fabsf(omm) + mc * mc)))
@@ -735,7 +1023,7 @@ __device__ __noinline__ bool step_slow(const DevMedium& m, const TraceArgs& a, i
   s.gp[1] = g[1];
   s.gp[2] = g[2];
   if (GRIN_UNLIKELY(s.steps >= a.max_steps)) {
-    finish(a, r, s, pos64(s), dir64(s), GRIN_EXIT_MAXSTEPS);
+    fin<C>(a, r, s, pos64(s), dir64(s), GRIN_EXIT_MAXSTEPS);
     return false;
   }
   return true;
@@ -766,7 +1054,7 @@ template <class C, bool LAYERED>
 __device__ __forceinline__ bool step_from(const DevMedium& m, const TraceArgs& a, int64_t r,
                                           RayF& s, float dopl_f, const float* qh,
                                           const float* ql, const float* dv, float nu_i,
-                                          const float* g, int lvl_i) {
+                                          const float* g, int lvl_i, float u_i = 0.5f) {
   const bool in = C::inside(m, qh);
   const float n_i = m.base_f + nu_i;
   const float inv_n = 1.0f / n_i;
@@ -789,14 +1077,23 @@ __device__ __forceinline__ bool step_from(const DevMedium& m, const TraceArgs& a
   // overflows while its components stay finite gives N = 0 and c == 0.
   const bool special =
       !in || !(n_i > 0.0f && n_i < INFINITY) || s.steps + 1 >= a.max_steps ||
-      (!homog && (c == 0.0f || !(D > kCritBand * (fabsf(omm) + mc * mc))));
+      (!homog && (c == 0.0f || !(D > kCritBand * (fabsf(omm) + mc * mc)))) ||
+      (LAYERED && !homog && (a.flags & GRIN_TRACE_LEVEL_ROOT));
   if (GRIN_UNLIKELY(special)) {
     // out of line, on a copy: only the copy's address escapes, the live
     // state stays in registers
-    RayF t = s;
+    typename C::State t = static_cast<typename C::State&>(s);
     bool alive = step_slow<C, LAYERED>(m, a, r, t, dopl_f);
-    s = t;
+    static_cast<typename C::State&>(s) = t;
     return alive;
+  }
+  if constexpr (C::kMG) {
+    mg_take<C>(s, 2, bnd_margin<C>(m, qh, s.h));
+    if (LAYERED && !(a.flags & GRIN_TRACE_LEVEL_ROOT)) mg_take<C>(s, 3, lvl_margin(m, u_i));
+    if (!homog) {
+      mg_take<C>(s, 1, fabsf(c));
+      mg_take<C>(s, 0, crit_margin(c, mu, omm, D));
+    }
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -811,6 +1108,10 @@ __device__ __forceinline__ bool step_from(const DevMedium& m, const TraceArgs& a
 #pragma unroll
   for (int j = 0; j < 3; ++j) add_ff(s.d[j], s.dl[j], fmaf(kn, N[j], kd * s.d[j]));
   s.h = dopl_f * inv_n;
+  if constexpr (LAYERED) {
+    s.used = 0.0f;
+    s.xc = 0;
+  }
   s.nu_prev = nu_i;
   s.inv_prev = inv_n;
   s.lvl_prev = lvl_i;
@@ -825,10 +1126,11 @@ __device__ __forceinline__ bool step_ray(const DevMedium& m, const TraceArgs& a,
                                          RayF& s, float dopl_f) {
   float qh[3], ql[3], dv[3];
   step_point(s, qh, ql, dv);
-  float nu_i, g[3];
+  float nu_i, g[3], u_i = 0.5f;
   int lvl_i;
-  C::eval(m, qh[0], qh[1], qh[2], ql[0], ql[1], ql[2], nu_i, g[0], g[1], g[2], lvl_i);
-  return step_from<C, LAYERED>(m, a, r, s, dopl_f, qh, ql, dv, nu_i, g, lvl_i);
+  C::eval(m, qh[0], qh[1], qh[2], ql[0], ql[1], ql[2], nu_i, g[0], g[1], g[2], lvl_i,
+          C::kMG ? &u_i : nullptr);
+  return step_from<C, LAYERED>(m, a, r, s, dopl_f, qh, ql, dv, nu_i, g, lvl_i, u_i);
 }
 
 // Warp-collective: the lanes in `need` get their column of the tap cache
@@ -900,13 +1202,13 @@ __device__ __forceinline__ unsigned run_quantum(const DevMedium& m, const TraceA
       }
       tap_fill(m, need, key, lb, taps, lane);
       if (active) {
-        float nu_i, g[3];
+        float nu_i, g[3], u_i = 0.5f;
         int lvl_i;
-        C::eval_taps(m, fr, col, lb, nu_i, g[0], g[1], g[2], lvl_i);
+        C::eval_taps(m, fr, col, lb, nu_i, g[0], g[1], g[2], lvl_i, C::kMG ? &u_i : nullptr);
         // the step vector again here, so it is not held across the refill
 #pragma unroll
         for (int k = 0; k < 3; ++k) dv[k] = s.h * s.d[k];
-        active = step_from<C, LAYERED>(m, a, ray, s, dopl_f, qh, ql, dv, nu_i, g, lvl_i);
+        active = step_from<C, LAYERED>(m, a, ray, s, dopl_f, qh, ql, dv, nu_i, g, lvl_i, u_i);
         if (!active) ++ended;
       }
     }
@@ -922,7 +1224,7 @@ __global__ void __launch_bounds__(128, C::kMinBlocks) k_trace_mixed(DevMedium m,
   __shared__ __align__(16) float taps[C::kGrid ? 16 * kTapRow : 4];
   int key[3] = {INT_MIN, INT_MIN, INT_MIN};
   float lb = 0.0f;  // centre tap of the cached cell
-  RayF s;
+  typename C::State s;
   bool active = false;
   bool exhausted = false;
   int64_t ray = 0;
@@ -951,10 +1253,10 @@ __global__ void __launch_bounds__(128, C::kMinBlocks) k_trace_mixed(DevMedium m,
   }
 }
 
-template <int PC, bool GRID, bool LAYERED, int BK, int FORM>
+template <int PC, bool GRID, bool LAYERED, int BK, int FORM, bool MG = false>
 static int launch_t(const DevMedium& m, const TraceArgs& a, unsigned long long* queue,
                     cudaStream_t st, int sm_count) {
-  using C = Cfg<PC, GRID, LAYERED, BK, FORM>;
+  using C = Cfg<PC, GRID, LAYERED, BK, FORM, MG>;
   auto kern = k_trace_mixed<C, LAYERED>;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0) != cudaSuccess ||
@@ -977,6 +1279,11 @@ static int launch_t(const DevMedium& m, const TraceArgs& a, unsigned long long* 
 template <int PC, bool GRID>
 static int launch_pc(const DevMedium& m, const TraceArgs& a, unsigned long long* q,
                      cudaStream_t s, int sm) {
+  // decision margins: the kernels with run-time boundary and form, which
+  // also keep the margins
+  if (a.margin)
+    return m.n_levels > 0 ? launch_t<PC, GRID, true, -1, -1, true>(m, a, q, s, sm)
+                          : launch_t<PC, GRID, false, -1, -1, true>(m, a, q, s, sm);
   if (m.n_levels > 0) {
     if constexpr (GRID)
       if (m.bkind == GRIN_BOUNDARY_BOX)

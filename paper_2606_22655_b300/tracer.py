@@ -173,11 +173,15 @@ def _rays_struct(r: RayBatch) -> N.Rays:
     return s
 
 
-def empty_result(n: int, device) -> Dict[str, torch.Tensor]:
+def empty_result(n: int, device, margins: bool = False) -> Dict[str, torch.Tensor]:
+    """Output tensors of a trace; margins=True adds the (n, 4) decision
+    margins ("margin")."""
     pin = device == "cpu" and torch.cuda.is_available()
     kw = dict(device=device, pin_memory=pin) if pin else dict(device=device)
     out = {k: torch.empty(n, dtype=torch.float64, **kw) for k in OUT_FIELDS}
     out.update({k: torch.empty(n, dtype=torch.int32, **kw) for k in INT_FIELDS})
+    if margins:
+        out["margin"] = torch.empty((n, 4), dtype=torch.float64, **kw)
     return out
 
 
@@ -185,25 +189,30 @@ def _out_struct(out: Dict[str, torch.Tensor]) -> N.Out:
     s = N.Out()
     for k in OUT_FIELDS + INT_FIELDS:
         setattr(s, k, out[k].data_ptr())
+    s.margin = out["margin"].data_ptr() if "margin" in out else None
     return s
 
 
-def _params(dopl: float, max_steps: int, precision: str) -> N.Params:
+def _params(dopl: float, max_steps: int, precision: str, level_root: bool = False) -> N.Params:
     if precision not in PRECISION:
         raise ValueError(f"precision must be one of {sorted(PRECISION)}")
-    return N.Params(float(dopl), int(max_steps), PRECISION[precision], 0)
+    return N.Params(float(dopl), int(max_steps), PRECISION[precision],
+                    N.TRACE_LEVEL_ROOT if level_root else 0)
 
 
 def trace(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_steps: int,
           precision: str = "mixed", stream: Optional[torch.cuda.Stream] = None,
-          out: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
+          out: Optional[Dict[str, torch.Tensor]] = None, margins: bool = False,
+          level_root: bool = False) -> Dict[str, torch.Tensor]:
     """grin_trace on device tensors; asynchronous on `stream` (default: the
-    current torch stream)."""
+    current torch stream).  margins=True also returns the decision margins;
+    level_root=True refracts layered media at the exact shell crossings
+    (GRIN_TRACE_LEVEL_ROOT)."""
     if out is None:
-        out = empty_result(rays.count, rays.ox.device)
+        out = empty_result(rays.count, rays.ox.device, margins)
     if stream is None:
         stream = torch.cuda.current_stream(rays.ox.device)
-    rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, precision)
+    rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, precision, level_root)
     N.check("grin_trace", ctx.lib.grin_trace(ctx.handle, medium.handle, ctypes.byref(rs), ctypes.byref(ps),
                                              ctypes.byref(os_), ctypes.c_void_p(stream.cuda_stream)))
     return out
@@ -211,14 +220,15 @@ def trace(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_steps: 
 
 def trace_host(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_steps: int,
                precision: str = "mixed", stream: Optional[torch.cuda.Stream] = None,
-               out: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
+               out: Optional[Dict[str, torch.Tensor]] = None, margins: bool = False,
+               level_root: bool = False) -> Dict[str, torch.Tensor]:
     """grin_trace_host: rays and results in host memory (copies and the
     synchronisation happen inside the call)."""
     if out is None:
-        out = empty_result(rays.count, "cpu")
+        out = empty_result(rays.count, "cpu", margins)
     if stream is None:
         stream = torch.cuda.current_stream(ctx.device)
-    rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, precision)
+    rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, precision, level_root)
     N.check("grin_trace_host", ctx.lib.grin_trace_host(ctx.handle, medium.handle, ctypes.byref(rs),
                                                        ctypes.byref(ps), ctypes.byref(os_),
                                                        ctypes.c_void_p(stream.cuda_stream)))
@@ -226,7 +236,7 @@ def trace_host(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_st
 
 
 def trace_path(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_steps: int, cap: int,
-               stream: Optional[torch.cuda.Stream] = None):
+               stream: Optional[torch.cuda.Stream] = None, level_root: bool = False):
     """grin_trace_path (plain FP64) on device tensors: returns (result dict,
     points (count, cap, 3) float64, point counts (count,) int64).  Ray r's
     polyline is points[r, :min(counts[r], cap)]."""
@@ -236,7 +246,7 @@ def trace_path(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_st
     cnt = torch.zeros(rays.count, dtype=torch.int64, device=dev)
     if stream is None:
         stream = torch.cuda.current_stream(dev)
-    rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, "fp64")
+    rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, "fp64", level_root)
     N.check("grin_trace_path", ctx.lib.grin_trace_path(
         ctx.handle, medium.handle, ctypes.byref(rs), ctypes.byref(ps), ctypes.byref(os_),
         ctypes.c_void_p(pts.data_ptr()), int(cap), ctypes.c_void_p(cnt.data_ptr()),
@@ -245,11 +255,15 @@ def trace_path(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_st
 
 
 def to_numpy(res: Dict[str, torch.Tensor]) -> Dict[str, np.ndarray]:
-    """Results as numpy with P and d stacked to (n, 3), the oracle's layout."""
+    """Results as numpy with P and d stacked to (n, 3), the oracle's layout
+    (and the (n, 4) margins as "margins" when present)."""
     h = {k: v.cpu().numpy() for k, v in res.items()}
-    return dict(P=np.stack([h["px"], h["py"], h["pz"]], 1), d=np.stack([h["dx"], h["dy"], h["dz"]], 1),
-                opl=h["opl"], exit_id=h["exit_id"], steps=h["steps"], tir_internal=h["tir_internal"],
-                tir_boundary=h["tir_boundary"])
+    r = dict(P=np.stack([h["px"], h["py"], h["pz"]], 1), d=np.stack([h["dx"], h["dy"], h["dz"]], 1),
+             opl=h["opl"], exit_id=h["exit_id"], steps=h["steps"], tir_internal=h["tir_internal"],
+             tir_boundary=h["tir_boundary"])
+    if "margin" in h:
+        r["margins"] = h["margin"]
+    return r
 
 
 class Server:

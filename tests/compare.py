@@ -37,20 +37,22 @@ FP32_PROBE_TOL = 1e-5          # probe change (half the 2e-5 gate) that flags a 
 FP32_PROBE_SEEDS = (1, 2, 3)
 
 
-def fp32_flags(o: dict, medium, origins, dirs, dopl: float, max_steps: int, l_ref: float) -> np.ndarray:
+def fp32_flags(o: dict, medium, origins, dirs, dopl: float, max_steps: int, l_ref: float,
+               flags: int = 0) -> np.ndarray:
     """Rays the FP32 path is excused on, from the oracle result o of the same
     rays: a margin inside the path's drift (surface: below 2^-20 S steps for a
     ray of S steps; level: below 1e-5; critical distance or |N.I|: below
     2^-19), or a ray whose oracle trace changes an integer outcome or moves by
     more than 1e-5 when traced with the trapezoid index difference and a
-    2e-6 relative perturbation of every normal (three seeds)."""
+    2e-6 relative perturbation of every normal (three seeds).  flags are the
+    oracle trace flags o was traced with."""
     import oracle  # test infrastructure
 
     m = o["margins"]
     S = np.maximum(np.asarray(o["steps"], float), 1.0)
     f = (m[:, 2] < FP32_STEP_DRIFT * S) | (m[:, 3] < FP32_LEVEL) | (m[:, 0] < FP32_NI) | (m[:, 1] < FP32_NI)
     for seed in FP32_PROBE_SEEDS:
-        p = oracle.trace(medium, origins, dirs, dopl, max_steps, index_rule=1,
+        p = oracle.trace(medium, origins, dirs, dopl, max_steps, flags=flags, index_rule=1,
                          perturb=FP32_PROBE_PERTURB, seed=seed)
         same = np.ones(len(S), bool)
         for k in INT_KEYS:

@@ -34,6 +34,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_status_strings_and_poly_terms(lib):
     assert lib.grin_status_string(0) == b"ok"
     assert lib.grin_status_string(-1) == b"invalid argument"
+    assert lib.grin_status_string(-9) == b"index out of bounds (checked build)"
     assert [lib.grin_poly_terms(d) for d in range(7)] == [1, 4, 10, 20, 35, 56, 84]
     assert lib.grin_poly_terms(7) == 0
 
@@ -46,8 +47,26 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert lib.grin_trace_host(None, None, None, None, None, None) == -1
 
 
-def test_struct_sizes_match_c_layout():
-    # sizes computed from the header's field lists with natural alignment
-    assert ctypes.sizeof(N.Rays) == 6 * 8 + 8 + 8
-    assert ctypes.sizeof(N.Out) == 11 * 8
-    assert ctypes.sizeof(N.Params) == 8 + 4 + 4 + 4 + 4
+def test_struct_sizes_match_c_layout(tmp_path):
+    """The binding's structs have the sizes and field offsets the C compiler
+    gives the header's (a small program built against include/grin.h)."""
+    import subprocess
+    structs = {"grin_rays": (N.Rays, ["count", "dtype"]), "grin_out": (N.Out, ["tir_boundary", "margin"]),
+               "grin_params": (N.Params, ["precision", "flags"]),
+               "grin_medium_desc": (N.MediumDesc, ["grid_on_device", "n_levels", "boundary", "n_ext"]),
+               "grin_serve_config": (N.ServeConfig, ["max_slots_per_job"]),
+               "grin_serve_counters": (N.ServeCounters, ["ray_steps", "jobs_running"])}
+    src = ["#include <stdio.h>", "#include <stddef.h>", '#include "grin.h"', "int main(void) {"]
+    for c, (_, fields) in structs.items():
+        src.append(f'  printf("{c} %zu\\n", sizeof({c}));')
+        for f in fields:
+            src.append(f'  printf("{c}.{f} %zu\\n", offsetof({c}, {f}));')
+    src += ["  return 0;", "}"]
+    (tmp_path / "layout.c").write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(tmp_path / "layout.c"), "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for c, (py, fields) in structs.items():
+        assert ctypes.sizeof(py) == int(got[c]), c
+        for f in fields:
+            assert getattr(py, f).offset == int(got[f"{c}.{f}"]), (c, f)

@@ -829,19 +829,21 @@ def test_tangent_margin_is_smallest_normal_cosine():
     assert r["margins"][oracle.M_TAN] == pytest.approx(math.sin(b), rel=1e-14)
 
 
-@pytest.mark.parametrize("z0", [0.3, 0.9])
-def test_level_margin_is_distance_to_next_shell(z0):
-    """With f = 1.5 + 0.2 (z - 1) in two shells on [1.3, 1.7] the level
-    coordinate L (f - lo) / (hi - lo) equals z; a ray along x at height z0
-    stays at level coordinate z0, whose distance to the nearest shell
-    boundary (an integer) is min(z0, 1 - z0)."""
+@pytest.mark.parametrize("levels,z0,expect", [(2, 0.3, 0.7), (2, 0.9, 0.1), (2, 1.6, 0.6),
+                                               (4, 0.9, 0.2), (4, 0.2, 0.6)])
+def test_level_margin_is_distance_to_next_shell(levels, z0, expect):
+    """With f = 1.5 + 0.2 (z - 1) in L shells on [1.3, 1.7] the level
+    coordinate L (f - lo) / (hi - lo) is L z / 2; a ray along x at height z0
+    keeps it, and its margin is the distance to the nearest shell boundary
+    among u = 1 .. L - 1 (u = 0 and u = L bound no shell: the levels
+    clamp)."""
     c = W.coeffs_from_terms(1, {(0, 0, 0): 1.5, (0, 0, 1): 0.2})
     m = W.Medium(kind=W.KIND_POLY, form=W.FORM_LINEAR, degree=1, coeffs=c, off=(0, 0, 1),
-                 n_levels=2, level_lo=1.3, level_hi=1.7, bkind=W.BOUNDARY_BOX,
+                 n_levels=levels, level_lo=1.3, level_hi=1.7, bkind=W.BOUNDARY_BOX,
                  bparams=(-1, -1, 0, 1, 1, 2, 0, 0), n_ext=1.0)
     r = _one(m, (-0.5, 0, z0), (1, 0, 0), 1e-3, 5000)
     assert r["exit_id"] == 1
-    assert r["margins"][oracle.M_LEVEL] == pytest.approx(min(z0, 1 - z0), rel=1e-12)
+    assert r["margins"][oracle.M_LEVEL] == pytest.approx(expect, rel=1e-12)
 
 
 # --------------------------------------------- edge-clamped tricubic (Keys 1981)
@@ -941,9 +943,9 @@ def test_level_root_planar_stack_closed_form(levels):
     textbook one: in shell k (thickness T = 2/L, index n_k) it runs straight
     at sin(theta_k) = sin(theta_0) / n_k (Snell at every interface), so it
     leaves at the lateral offset tan(theta_0) + sum T tan(theta_k) along its
-    input direction, with OPL 1/cos(theta_0) + sum n_k T / cos(theta_k), in
-    sum ceil(n_k l_k / dL0) steps (each shell's last step cut at its upper
-    plane)."""
+    input direction, with OPL 1/cos(theta_0) + sum n_k T / cos(theta_k); a
+    crossing does not end a step, so the steps are ceil(inner OPL / dL0)
+    (the last one cut at the exit face)."""
     dopl = 1e-3
     m = _planar_shells(levels)
     th0 = math.radians(35.0)
@@ -953,16 +955,16 @@ def test_level_root_planar_stack_closed_form(levels):
                        flags=oracle.LEVEL_ROOT)
     r = {k: v[0] for k, v in res.items()}
     T = 2.0 / levels
-    lat, opl, steps = math.tan(th0), 1.0 / math.cos(th0), 0
+    lat, opl = math.tan(th0), 1.0 / math.cos(th0)
     for k in range(levels):
         nk = 1.3 + (k + 0.5) * 0.4 / levels
         tk = math.asin(math.sin(th0) / nk)
         lk = T / math.cos(tk)
         lat += T * math.tan(tk)
         opl += nk * lk
-        q = nk * lk / dopl
-        assert 1e-6 < q % 1 < 1 - 1e-6  # no rounding ambiguity in the count
-        steps += math.ceil(q)
+    q = (opl - 1.0 / math.cos(th0)) / dopl
+    assert 1e-6 < q % 1 < 1 - 1e-6  # no rounding ambiguity in the count
+    steps = math.ceil(q)
     assert r["exit_id"] == 5 and r["tir_internal"] == 0 and r["tir_boundary"] == 0
     np.testing.assert_allclose(r["P"], lat * u + np.array([0, 0, 2.0]), atol=1e-12)
     np.testing.assert_allclose(r["d"], d0, atol=1e-13)
