@@ -220,7 +220,7 @@ def serve_load(ctx, dev_index: int, rates, jobs_per_rate: int, seed: int = 7):
     media = [tracer.Medium(ctx, wl.medium) for wl in pool]
     rays = [tracer.RayBatch.from_numpy(wl.rays.origins, wl.rays.dirs, device="cpu", dtype=torch.float32, pin=True)
             for wl in pool]
-    n_out = 24
+    n_out = 48
     outs = [tracer.empty_result(1 << 20, "cpu") for _ in range(n_out)]
     srv = tracer.Server(ctx, 16 << 30)
     results = []
@@ -232,7 +232,7 @@ def serve_load(ctx, dev_index: int, rates, jobs_per_rate: int, seed: int = 7):
         counts = np.minimum(counts, [pool[k].rays.n for k in kinds])
         gaps = rng.exponential(1.0 / rate, jobs_per_rate)
         t0 = time.perf_counter()
-        inflight, lat, steps = [], [], 0.0
+        inflight, lat, steps, qr = [], [], 0.0, []
         next_t = t0
         free = list(range(n_out))
         for j in range(jobs_per_rate):
@@ -244,6 +244,7 @@ def serve_load(ctx, dev_index: int, rates, jobs_per_rate: int, seed: int = 7):
                     st, l = srv.poll(x[0])
                     lat.append(l)
                     steps += float(outs[x[1]]["steps"][: x[2]].sum())
+                    qr.append(srv.timing(x[0]))
                     free.append(x[1])
                     inflight.remove(x)
                 if now >= next_t and free:
@@ -259,16 +260,20 @@ def serve_load(ctx, dev_index: int, rates, jobs_per_rate: int, seed: int = 7):
             st, l = srv.poll(x[0])
             lat.append(l)
             steps += float(outs[x[1]]["steps"][: x[2]].sum())
+            qr.append(srv.timing(x[0]))
         wall = time.perf_counter() - t0
         lat = np.array(lat)
-        results.append({"rate_jobs_per_s": rate, "jobs": jobs_per_rate, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                        "p99_ms": 1e3 * float(np.percentile(lat, 99)), "ray_steps_per_s": steps / wall,
-                        "wall_s": wall})
+        qr = np.array(qr)
+        pc = lambda v, q: 1e3 * float(np.percentile(v, q))
+        results.append({"rate": rate, "jobs": jobs_per_rate, "p50_ms": pc(lat, 50), "p99_ms": pc(lat, 99),
+                        "queue_p50_ms": pc(qr[:, 0], 50), "queue_p99_ms": pc(qr[:, 0], 99),
+                        "run_p50_ms": pc(qr[:, 1], 50), "run_p99_ms": pc(qr[:, 1], 99),
+                        "ray_steps_per_s": steps / wall, "wall_s": wall})
     st = srv.stats()
     srv.close()
-    return {"media": names, "dL0": dopls,
-            "ray_count": "log-uniform [1e3, 1e6]", "arrivals": "Poisson", "step_quantum": 1024,
-            "sweep": results, "ticks": st["ticks"], "failed": st["failed"]}
+    return {"sweep": results, "media": names, "dL0": dopls, "ray_count": "log-uniform [1e3, 1e6]",
+            "arrivals": "Poisson", "latency": "submit to results in host memory = queue (to admission) + run",
+            "ticks": st["ticks"], "failed": st["failed"]}
 
 
 def adjoint_timing(ctx, dev, n_rays=1 << 18):
@@ -327,16 +332,18 @@ def media_rates(ctx, dev):
              ("spherical_freeform_262144", W.spherical_workload(1 << 18)),
              ("n2p_lens_65536", W.Workload("n2p", W.n2p_lens_medium(0.770, 4.462, 0.3), fan, 1e-4, 400000, 1.0)),
              ("grid_256_1048576", W.blob_workload(n_rays=1 << 20, res=256)),
-             ("layered_256_1048576", W.blob_workload(n_rays=1 << 20, res=256, n_levels=32))]
+             ("layered_256_1048576", W.blob_workload(n_rays=1 << 20, res=256, n_levels=32)),
+             ("layered_crossings_256_1048576", W.blob_workload(n_rays=1 << 20, res=256, n_levels=32))]
     res = {}
     for name, wl in cases:
+        lr = "crossings" in name  # shells with their crossings solved
         med = tracer.Medium(ctx, wl.medium)
         rays = tracer.RayBatch.from_numpy(wl.rays.origins, wl.rays.dirs, device=dev, dtype=torch.float32)
         out = tracer.empty_result(rays.count, dev)
-        tracer.trace(ctx, med, rays, wl.dopl, wl.max_steps, "mixed", out=out)
+        tracer.trace(ctx, med, rays, wl.dopl, wl.max_steps, "mixed", out=out, level_root=lr)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        tracer.trace(ctx, med, rays, wl.dopl, wl.max_steps, "mixed", out=out)
+        tracer.trace(ctx, med, rays, wl.dopl, wl.max_steps, "mixed", out=out, level_root=lr)
         e1.record()
         torch.cuda.synchronize(dev)
         t = e0.elapsed_time(e1) / 1e3
@@ -355,6 +362,90 @@ def design_sweep(ctx):
             "wall_s": res["wall_s"], "jobs": res["jobs"], "jobs_per_s": res["jobs"] / res["wall_s"],
             "round_wall_s": [h["wall_s"] for h in res["rounds"]],
             "beta": res["beta"], "gamma": res["gamma"], "rmse_lsa_over_R": res["rmse_lsa"]}
+
+
+def measured_peaks(ctx, dev_index: int):
+    """FP32 FMA rate of the CUDA cores and read bandwidth of an L2-resident
+    64 MiB buffer, measured on this GPU by the library's probes (CUDA events
+    around one launch each), with the SM clock sampled during the FMA run."""
+    import ctypes
+    from paper_2606_22655_b300 import _native as N
+    lib = ctx.lib
+    flops, secs = ctypes.c_double(), ctypes.c_double()
+    with ClockSampler(dev_index) as clk:
+        N.check("grin_probe_fp32_fma", lib.grin_probe_fp32_fma(6_000_000, ctypes.byref(flops), ctypes.byref(secs)))
+    l2 = ctypes.c_double()
+    N.check("grin_probe_l2_read", lib.grin_probe_l2_read(64 << 20, 40, ctypes.byref(l2)))
+    c = clk.summary()
+    return {"fp32_tflops": flops.value / 1e12, "fma_seconds": secs.value, "fma_sm_mhz": c["sm_mhz"],
+            "fp32_tflops_derived": FP32_PEAK_TFLOPS, "l2_read_gbs": l2.value / 1e9,
+            "how": "grin_probe_fp32_fma (8 FMA chains a thread, 8 x 256-thread blocks an SM) and "
+                   "grin_probe_l2_read (64 MiB, 40 reads), CUDA events"}
+
+
+def grid_flops_per_step() -> int:
+    """FP32 FLOPs of one ray-step on a gridded medium (FMA = 2): the
+    Catmull-Rom weights and derivatives of the three axes (3 x 10 FMA), the
+    tap-cache sums of value and gradient (16 rows x 8, 16 x 3, 4 x 4 FMA),
+    the compensated cell fraction (3 x 9) and the rest of a refracting step."""
+    return 2 * (30 + 16 * 8 + 16 * 3 + 4 * 4) + 27 + STEP_FIXED_FLOPS
+
+
+def timed_trace(ctx, med, rays, wl, precision, out, reps: int = 1):
+    """Mean event time of reps grin_trace calls after one warm-up call."""
+    import torch
+    from paper_2606_22655_b300 import tracer
+    tracer.trace(ctx, med, rays, wl.dopl, wl.max_steps, precision, out=out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        tracer.trace(ctx, med, rays, wl.dopl, wl.max_steps, precision, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def config_rates(ctx, dev, peaks):
+    """Config 1 (Luneburg lens, 4,096 rays): the mixed tracer against the
+    plain and fast FP64 tracers.  Config 3 (256^3 blob grid and its 32
+    shells, 4,194,304 rays): the mixed tracer's rate, its FP32 FLOP rate
+    against the measured FMA peak, and the cache traffic of its tap cache:
+    256 B of shared memory a ray-step, and from L2 the 256 B of a refill on
+    the 4.8 % of ray-steps that enter a new cell (ncu, 262,144 rays)."""
+    import torch
+    from paper_2606_22655_b300 import tracer
+    from paper_2606_22655_b300 import workloads as W
+    res = {}
+    wl = W.luneburg_workload()
+    med = tracer.Medium(ctx, wl.medium)
+    rays = tracer.RayBatch.from_numpy(wl.rays.origins, wl.rays.dirs, device=dev, dtype=torch.float32)
+    out = tracer.empty_result(rays.count, dev)
+    rate = {}
+    for prec in ("mixed", "fp64", "fp64-fast"):
+        t = timed_trace(ctx, med, rays, wl, prec, out, reps=5 if prec == "mixed" else 1)
+        rate[prec] = float(out["steps"].sum()) / t
+    res["luneburg_4096"] = {"mixed": rate["mixed"], "fp64": rate["fp64"], "fp64_fast": rate["fp64-fast"],
+                            "speedup_vs_fp64": rate["mixed"] / rate["fp64"],
+                            "speedup_vs_fp64_fast": rate["mixed"] / rate["fp64-fast"]}
+    med.close()
+    for levels in (0, 32):
+        wl = W.blob_workload(n_rays=1 << 22, res=256, n_levels=levels)
+        med = tracer.Medium(ctx, wl.medium)
+        rays = tracer.RayBatch.from_numpy(wl.rays.origins, wl.rays.dirs, device=dev, dtype=torch.float32)
+        out = tracer.empty_result(rays.count, dev)
+        t = timed_trace(ctx, med, rays, wl, "mixed", out)
+        r = float(out["steps"].sum()) / t
+        entry = {"ray_steps_per_s": r, "ms": 1e3 * t}
+        if not levels:
+            tflops = grid_flops_per_step() * r / 1e12
+            entry.update({"flops_per_ray_step": grid_flops_per_step(), "achieved_tflops": tflops,
+                          "fp32_frac_of_measured": tflops / peaks["fp32_tflops"],
+                          "shared_bytes_per_ray_step": 256, "l2_bytes_per_ray_step": 0.048 * 256,
+                          "l2_gbs": 0.048 * 256 * r / 1e9,
+                          "l2_frac_of_measured": 0.048 * 256 * r / 1e9 / peaks["l2_read_gbs"]})
+        res[("grid" if not levels else "layered") + "_256_4194304"] = entry
+        med.close()
+    return res
 
 
 def run_reference(args):
@@ -523,44 +614,56 @@ def run_ours(args):
 
     if rank != 0:
         return 0
+    peaks = measured_peaks(ctx, local)
+    configs = config_rates(ctx, dev, peaks) if not args.no_serve else None
     flops_launch = flops_per_step(4) * steps_per_trace
     achieved = flops_launch / mean_kern / 1e12
+    fp64_rate = float(res64["steps"].sum()) / fp64_s
+    fast_rate = float(res64["steps"].sum()) / fast_s
+    gate_pass = gate_s is not None and gate_s["int_mismatch_unflagged"] == 0 and \
+        max(gate_s["pos"], gate_s["dir"], gate_s["opl"]) <= 2e-5
+    # the keys a reader needs first (a log tail may keep only the start of
+    # this long line): the metric, the precision gate, the speed-up over the
+    # FP64 tracers, the workload and the roofline
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * region_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
+        "precision_gate": None if gate_s is None else {
+            "pass": gate_pass, "tolerance": 2e-5, "vs": "FP64 oracle on the same float32 rays",
+            "rays": gate_s["n"], "flagged": gate_s["n_flagged"], "flagged_frac": gate_s["n_flagged"] / gate_s["n"],
+            "int_mismatch_unflagged": gate_s["int_mismatch_unflagged"],
+            "max_rel_pos": gate_s["pos"], "max_dir": gate_s["dir"], "max_rel_opl": gate_s["opl"],
+            "p99_rel_pos": gate_s["pos_p99"], "p99_dir": gate_s["dir_p99"],
+            "sample": "every 16th ray of the batch",
+            "flag_rule": "oracle margin inside the FP32 drift (surface < 2^-20 S steps, level < 1e-5, "
+                         "critical or |N.I| < 2^-19) or oracle unstable under the trapezoid index "
+                         "difference and a 2e-6 normal perturbation (tests/compare.py)"},
+        "speedup_vs_fp64": value / ws / fp64_rate, "speedup_vs_fp64_fast": value / ws / fast_rate,
         "config": {"workload": wl.name, "rays": wl.rays.n, "medium": "degree-4 polynomial, 35 monomials",
                    "dopl_mm": wl.dopl, "max_steps": wl.max_steps, "precision": "fp32-mixed",
                    "ray_steps_per_step": steps_per_trace,
                    "l2": "256 MiB buffer zeroed before every step, inside the timed region"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+                     "frac": achieved / peaks["fp32_tflops"],
                      "traffic": profiled_traffic() if args.rays == N_RAYS and args.workload == "freeform" else None,
                      "kernel": KERNEL, "kernel_ms": 1e3 * mean_kern,
                      "flops_per_ray_step": flops_per_step(4),
-                     "peak_note": "148 SMs x 128 FP32 lanes x 2 FLOP x 2.032 GHz (derived)",
+                     "peak_source": "measured: FP32 FMA probe on this GPU (grin_probe_fp32_fma)",
+                     "peak_derived": FP32_PEAK_TFLOPS, "frac_of_derived": achieved / FP32_PEAK_TFLOPS,
                      "fp32_issue": fp32_issue(steps_per_trace / mean_kern)
                      if args.rays == N_RAYS and args.workload == "freeform" else None},
-        "precision_gate": {
-            "vs": "plain FP64 GPU tracer on the same float32 input rays",
-            "fp64_ms": 1e3 * fp64_s, "fp64_ray_steps_per_s": float(res64["steps"].sum()) / fp64_s,
-            "speedup_vs_fp64": value / ws / (float(res64["steps"].sum()) / fp64_s),
-            "fp64_fast_ms": 1e3 * fast_s, "speedup_vs_fp64_fast": value / ws / (float(res64["steps"].sum()) / fast_s),
-            "all_rays": {"rays": gate["n"], "int_mismatch": gate["int_mismatch_unflagged"],
-                         "p99_rel_pos": gate["pos_p99"], "p99_dir": gate["dir_p99"],
-                         "max_rel_pos": gate["pos"], "max_dir": gate["dir"], "max_rel_opl": gate["opl"]},
-            "oracle_sample": None if gate_s is None else {
-                "rays": gate_s["n"], "flagged": gate_s["n_flagged"],
-                "vs": "FP64 oracle on the same float32 rays",
-                "flag_rule": "FP32 drift margins (surface < 2^-20 S steps, level < 1e-5, critical or |N.I| < 2^-19) or unstable under the trapezoid index difference and 2e-6 normal perturbation (tests/compare.py)",
-                "int_mismatch_unflagged": gate_s["int_mismatch_unflagged"],
-                "max_rel_pos": gate_s["pos"], "max_dir": gate_s["dir"], "max_rel_opl": gate_s["opl"],
-                "pass": max(gate_s["pos"], gate_s["dir"], gate_s["opl"]) <= 2e-5}},
+        "configs": configs,
         "e2e": {"value": e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk.summary(),
+        "measured_peaks": peaks,
         "cpu_baseline": cpu,
+        "all_rays_vs_fp64": {"rays": gate["n"], "int_mismatch": gate["int_mismatch_unflagged"],
+                             "p99_rel_pos": gate["pos_p99"], "p99_dir": gate["dir_p99"],
+                             "max_rel_pos": gate["pos"], "max_dir": gate["dir"],
+                             "fp64_ray_steps_per_s": fp64_rate, "fp64_fast_ray_steps_per_s": fast_rate},
         "serve": serve,
         "adjoint": adjoint,
         "design_sweep": design,
@@ -581,7 +684,7 @@ def main():
     ap.add_argument("--ref-stride", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-latency sweep")
-    ap.add_argument("--serve-jobs", type=int, default=60, help="jobs per arrival rate in the sweep")
+    ap.add_argument("--serve-jobs", type=int, default=500, help="jobs per arrival rate in the sweep")
     ap.add_argument("--rays", type=int, default=N_RAYS,
                     help="ray count (profiling of a smaller case; the line then names it)")
     ap.add_argument("--workload", choices=["freeform", "grid", "layered", "luneburg"], default="freeform",

@@ -388,12 +388,41 @@ int grin_serve_submit(grin_server server, grin_medium medium, const grin_rays* r
 /* State of a job and its latency: submit to completion once DONE, else the
  * time since submission.  GRIN_ERR_NOT_FOUND for an unknown id. */
 int grin_serve_poll(grin_server server, uint64_t job_id, int32_t* state, double* latency_s);
+/* Where a job's latency went: *queued_s from submission to admission (to
+ * now while it is still queued, to its end if it ended unadmitted), *run_s
+ * from admission to completion (to now while it runs).
+ * GRIN_ERR_NOT_FOUND for an unknown id. */
+int grin_serve_timing(grin_server server, uint64_t job_id, double* queued_s, double* run_s);
 /* Wait up to timeout_s seconds for the job to end (DONE, FAILED or
  * CANCELLED); GRIN_ERR_TIMEOUT if it has not. */
 int grin_serve_wait(grin_server server, uint64_t job_id, double timeout_s, int32_t* state);
 /* Cancel a queued or running job (takes effect at the next tick). */
 int grin_serve_cancel(grin_server server, uint64_t job_id);
 int grin_serve_stats(grin_server server, grin_serve_counters* stats);
+
+/* ------------------------------------------------- bounds-checked build
+ *
+ * The library is also built with every device array index of its kernels
+ * range-checked (lib/libgrin_vrt_checked.so, same ABI; a stand-in for a
+ * memory checker): the grid samples of every gather, the slots of the mixed
+ * tracer's tap cache in shared memory, the claim order and the ray indices,
+ * the adjoint's samples and gradient entries.  An index out of range is
+ * replaced by 0, so the access stays in bounds and the kernel runs on, and
+ * the site of the first one is recorded per device.  The paper has no
+ * counterpart.
+ * grin_build_checked: 1 in the checked build, 0 in the ordinary one.
+ * grin_checked_status: the recorded site on `device` (0 if none; 1 a ray
+ *   index, 2 a grid sample of the mixed tracer, 3 a tap-cache slot, 4 a grid
+ *   sample of the FP64 tracers, 5 the adjoint), read after synchronising the
+ *   device and cleared; returns GRIN_ERR_CHECKED_BOUNDS when a site was
+ *   recorded, else GRIN_OK (always GRIN_OK with 0 in the ordinary build).
+ * grin_checked_selftest: in the checked build, runs a one-thread kernel that
+ *   forms an out-of-range grid index on purpose (the check redirects it, no
+ *   memory outside the array is touched) and leaves site 4 to be read;
+ *   GRIN_ERR_NOT_IMPLEMENTED in the ordinary build, which runs nothing. */
+int grin_build_checked(void);
+int grin_checked_status(int device, int32_t* site);
+int grin_checked_selftest(int device);
 
 /* Largest batch grin_trace_host_static accepts. */
 #define GRIN_STATIC_MAX_RAYS 65536

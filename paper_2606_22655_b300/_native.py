@@ -11,7 +11,10 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 # GRIN_LIB may name another build of the same library (e.g. one compiled
 # with different launch bounds); it must export the same C ABI
-LIB_PATH = os.environ.get("GRIN_LIB") or os.path.join(HERE, "lib", "libgrin_vrt.so")
+# GRIN_CHECKED=1 loads the bounds-checked build (every kernel array index
+# range-checked; grin_checked_status reports a violation)
+LIB_PATH = os.environ.get("GRIN_LIB") or os.path.join(
+    HERE, "lib", "libgrin_vrt_checked.so" if os.environ.get("GRIN_CHECKED") == "1" else "libgrin_vrt.so")
 
 GRIN_OK = 0
 (GRIN_ERR_INVALID_ARG, GRIN_ERR_OOM, GRIN_ERR_CUDA, GRIN_ERR_NOT_IMPLEMENTED, GRIN_ERR_TIMEOUT,
@@ -115,7 +118,13 @@ def load() -> ctypes.CDLL:
         "grin_serve_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, P(ctypes.c_int32), P(ctypes.c_double)]),
         "grin_serve_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_double, P(ctypes.c_int32)]),
         "grin_serve_cancel": (ctypes.c_int, [_vp, ctypes.c_uint64]),
+        "grin_serve_timing": (ctypes.c_int, [_vp, ctypes.c_uint64, P(ctypes.c_double), P(ctypes.c_double)]),
         "grin_serve_stats": (ctypes.c_int, [_vp, P(ServeCounters)]),
+        "grin_build_checked": (ctypes.c_int, []),
+        "grin_checked_status": (ctypes.c_int, [ctypes.c_int, P(ctypes.c_int32)]),
+        "grin_checked_selftest": (ctypes.c_int, [ctypes.c_int]),
+        "grin_probe_fp32_fma": (ctypes.c_int, [ctypes.c_int64, P(ctypes.c_double), P(ctypes.c_double)]),
+        "grin_probe_l2_read": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, P(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

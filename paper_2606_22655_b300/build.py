@@ -1,4 +1,5 @@
-"""Build the CUDA library libgrin_vrt.so in-tree for sm_103a (B300).
+"""Build the CUDA library libgrin_vrt.so in-tree for sm_103a (B300), and
+the same library with range-checked kernel indices, libgrin_vrt_checked.so.
 
     python -m paper_2606_22655_b300.build [--verbose-ptxas]
 
@@ -22,6 +23,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIB_DIR, "libgrin_vrt.so")
+# the same library with every kernel array index range-checked (-DGRIN_CHECKED)
+LIB_CHECKED = os.path.join(LIB_DIR, "libgrin_vrt_checked.so")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # per-source extra flags: the plain FP64 tracer must not contract a*b+c; the
@@ -53,9 +56,11 @@ def _flags(ptxas_verbose: bool):
     return f
 
 
-def _compile(src: str, ptxas_verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    cmd = [_nvcc()] + _flags(ptxas_verbose) + EXTRA.get(os.path.basename(src), []) + ["-c", src, "-o", obj]
+def _compile(src: str, ptxas_verbose: bool, checked: bool = False) -> str:
+    out_dir = os.path.join(BUILD, "checked") if checked else BUILD
+    obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
+    cmd = [_nvcc()] + _flags(ptxas_verbose) + EXTRA.get(os.path.basename(src), []) + \
+        (["-DGRIN_CHECKED"] if checked else []) + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -64,26 +69,33 @@ def _compile(src: str, ptxas_verbose: bool) -> str:
     return obj
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+def needs_build(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _sources() + _headers())
 
 
-def build(force: bool = False, ptxas_verbose: bool = False) -> str:
-    if not force and not ptxas_verbose and not needs_build():
+def build(force: bool = False, ptxas_verbose: bool = False, checked: bool = True) -> str:
+    """Build libgrin_vrt.so and (checked=True) libgrin_vrt_checked.so; both
+    variants' sources compile in one pool of nvcc processes."""
+    variants = [False] + ([True] if checked else [])
+    todo = [c for c in variants if force or ptxas_verbose or needs_build(LIB_CHECKED if c else LIB)]
+    if not todo:
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(os.path.join(BUILD, "checked"), exist_ok=True)
     os.makedirs(LIB_DIR, exist_ok=True)
+    jobs = [(src, c) for c in todo for src in _sources()]
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, ptxas_verbose), _sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+        objs = list(ex.map(lambda j: (j[1], _compile(j[0], ptxas_verbose, j[1])), jobs))
+    for c in todo:
+        lib = LIB_CHECKED if c else LIB
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for cc, o in objs if cc == c]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
     return LIB
 
 

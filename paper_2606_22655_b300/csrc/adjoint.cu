@@ -199,11 +199,11 @@ __device__ void field_h(const DevMedium& m, const double* P, double& n, double* 
       double y00 = 0.0, y10 = 0.0, y20 = 0.0, y01 = 0.0, y11 = 0.0, y02 = 0.0;
       for (int b = 0; b < 4; ++b) {
         int jj = min(max(b0[1] - 1 + b, 0), nn[1] - 1);
-        const float* row = m.grid + (kk * nn[1] + jj) * nn[0];
+        const int64_t row = ((int64_t)kk * nn[1] + jj) * nn[0];
         double x0 = 0.0, x1 = 0.0, x2 = 0.0;  // row sums with w, w', w'' in x
         for (int a = 0; a < 4; ++a) {
           int ii = min(max(b0[0] - 1 + a, 0), nn[0] - 1);
-          const double s = (double)row[ii];
+          const double s = (double)m.grid[GRIN_IDX(m, row + ii, m.grid_n, kSiteGridAdjoint)];
           x0 = fma(w[0][a], s, x0);
           x1 = fma(dw[0][a], s, x1);
           x2 = fma(ddw[0][a], s, x2);
@@ -310,7 +310,8 @@ __device__ void param_adj(const DevMedium& m, const double* P, double nb, const 
         for (int a = 0; a < 4; ++a) {
           int ii = min(max(b0[0] - 1 + a, 0), nn[0] - 1);
           const double v = fma(w[0][a], A, dw[0][a] * B);
-          if (v != 0.0) atomicAdd(grad + ((int64_t)kk * nn[1] + jj) * nn[0] + ii, v);
+          if (v != 0.0)
+            atomicAdd(grad + GRIN_IDX(m, ((int64_t)kk * nn[1] + jj) * nn[0] + ii, m.grid_n, kSiteGridAdjoint), v);
         }
       }
     }

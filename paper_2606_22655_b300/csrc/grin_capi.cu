@@ -144,6 +144,7 @@ int grin::describe_medium(const grin_medium_desc* d, DevMedium* mp, std::vector<
     m.nx = d->nx;
     m.ny = d->ny;
     m.nz = d->nz;
+    m.grid_n = cnt;
     m.rows16 = d->nx % 4 == 0;  // the device copy is cudaMalloc'd (256-byte aligned)
     try {
       samples->resize((size_t)cnt);
@@ -217,6 +218,98 @@ int grin_poly_terms(int degree) {
   return (degree + 1) * (degree + 2) * (degree + 3) / 6;
 }
 
+// The per-device word of the bounds-checked build (allocated with the first
+// context on the device; 4 bytes, also in the ordinary build).
+static unsigned int* g_oob[256] = {};
+static std::mutex g_oob_mutex;
+
+static unsigned int* oob_word(int device) {
+  std::lock_guard<std::mutex> lock(g_oob_mutex);
+  if (device < 0 || device >= 256) return nullptr;
+  if (!g_oob[device]) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(p, 0, sizeof(unsigned int)) != cudaSuccess) {
+      cudaGetLastError();
+      if (p) cudaFree(p);
+      return nullptr;
+    }
+    g_oob[device] = (unsigned int*)p;
+  }
+  return g_oob[device];
+}
+
+int grin_build_checked(void) {
+#ifdef GRIN_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+int grin_checked_status(int device, int32_t* site) {
+  if (!site) return GRIN_ERR_INVALID_ARG;
+  *site = 0;
+  unsigned int* w = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_oob_mutex);
+    if (device < 0 || device >= 256) return GRIN_ERR_INVALID_ARG;
+    w = g_oob[device];
+  }
+  int dev_prev = 0;
+  if (cudaGetDevice(&dev_prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return GRIN_ERR_CUDA;
+  }
+  int st = GRIN_OK;
+  unsigned int v = 0;
+  if (w) {
+    if (cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(w, 0, sizeof(unsigned int)) != cudaSuccess)
+      st = GRIN_ERR_CUDA;
+  }
+  unsigned int vs = 0;
+  if (st == GRIN_OK && grin::static_oob_take(&vs) != GRIN_OK) st = GRIN_ERR_CUDA;
+  cudaSetDevice(dev_prev);
+  if (st != GRIN_OK) {
+    cudaGetLastError();
+    return st;
+  }
+  *site = (int32_t)(v ? v : vs);
+  return *site ? GRIN_ERR_CHECKED_BOUNDS : GRIN_OK;
+}
+
+namespace {
+// Forms the index one past the end of a one-sample grid; the check records
+// site kSiteGridFP64 and redirects it to 0 (nothing is read or written).
+__global__ void k_checked_selftest(grin::DevMedium m, int64_t* sink) {
+  const int64_t i = GRIN_IDX(m, m.grid_n + (int64_t)threadIdx.x, m.grid_n, kSiteGridFP64);
+  if (i != 0) *sink = i;  // never taken; keeps the index computed
+}
+}  // namespace
+
+int grin_checked_selftest(int device) {
+#ifdef GRIN_CHECKED
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return GRIN_ERR_INVALID_ARG;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return GRIN_ERR_CUDA;
+  grin::DevMedium m;
+  std::memset(&m, 0, sizeof(m));
+  m.grid_n = 1;
+  m.oob = oob_word(device);
+  if (!m.oob) return GRIN_ERR_OOM;
+  if (grin::launch_kernel(k_checked_selftest, 1, 1, nullptr, m, (int64_t*)nullptr) < 0)
+    return GRIN_ERR_CUDA;
+  return cudaDeviceSynchronize() == cudaSuccess ? GRIN_OK : GRIN_ERR_CUDA;
+#else
+  (void)device;
+  return GRIN_ERR_NOT_IMPLEMENTED;
+#endif
+}
+
 int grin_ctx_create(int device, grin_ctx* out) {
   if (!out) return GRIN_ERR_INVALID_ARG;
   *out = nullptr;
@@ -288,6 +381,8 @@ int grin_medium_create(grin_ctx ctx, const grin_medium_desc* d, grin_medium* out
   const int st = grin::describe_medium(d, &m, &samples);
   if (st != GRIN_OK) return st;
 
+  m.oob = oob_word(ctx->device);
+  if (!m.oob) return GRIN_ERR_OOM;
   grin_medium med = new (std::nothrow) grin_medium_s;
   if (!med) return GRIN_ERR_OOM;
   med->ctx = ctx;

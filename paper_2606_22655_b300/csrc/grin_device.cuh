@@ -201,8 +201,9 @@ __device__ __forceinline__ void grid_vg(const DevMedium& m, const T* u_in, T sub
       T sv = T(0), sx = T(0), sy = T(0);
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        const float4* __restrict__ row4 =
-            reinterpret_cast<const float4*>(g + (idx[2][c] * n[1] + idx[1][b]) * n[0] + ax);
+        const int64_t rb = ((int64_t)idx[2][c] * n[1] + idx[1][b]) * n[0] + ax;
+        const float4* __restrict__ row4 = reinterpret_cast<const float4*>(
+            g + GRIN_IDX(m, rb, m.grid_n - (o ? 7 : 3), kSiteGridFP64));
         const float4 A = __ldg(row4);
         const float4 B = o ? __ldg(row4 + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float q[8] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w};
@@ -228,11 +229,11 @@ __device__ __forceinline__ void grid_vg(const DevMedium& m, const T* u_in, T sub
       T sv = T(0), sx = T(0), sy = T(0);
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        const float* __restrict__ row = g + (idx[2][c] * n[1] + idx[1][b]) * n[0];
+        const int64_t rb = ((int64_t)idx[2][c] * n[1] + idx[1][b]) * n[0];
         T r = T(0), rx = T(0);
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-          T s = (T)__ldg(row + idx[0][a]) - sub;
+          T s = (T)__ldg(g + GRIN_IDX(m, rb + idx[0][a], m.grid_n, kSiteGridFP64)) - sub;
           r = fmadd(w[0][a], s, r);
           rx = fmadd(dw[0][a], s, rx);
         }

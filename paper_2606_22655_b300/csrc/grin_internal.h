@@ -13,6 +13,33 @@
 
 namespace grin {
 
+// Bounds-checked build (-DGRIN_CHECKED, built beside the library as
+// lib/libgrin_vrt_checked.so): every index a kernel forms into a device array
+// of the call -- grid samples, the tap cache in shared memory, the claim
+// order, the ray arrays -- goes through GRIN_IDX.  An index outside [0, n)
+// records its site in the device word DevMedium::oob (the first one wins;
+// grin_checked_status reads and clears it) and is replaced by 0, so the
+// access stays inside the array and the kernel runs on.  The ordinary build
+// compiles GRIN_IDX to the bare index.
+enum CheckSite : unsigned {
+  kSiteRay = 1,         // a ray index (claim order value) outside the batch
+  kSiteGridMixed = 2,   // a grid sample of the mixed tracer's gathers
+  kSiteTapCache = 3,    // a slot of the mixed tracer's tap cache
+  kSiteGridFP64 = 4,    // a grid sample of the FP64 tracers
+  kSiteGridAdjoint = 5  // a grid sample or gradient entry of the adjoint
+};
+#ifdef GRIN_CHECKED
+__device__ __forceinline__ int64_t checked_index(unsigned int* word, int64_t i, int64_t n,
+                                                 unsigned site) {
+  if (i >= 0 && i < n) return i;
+  if (word) atomicCAS(word, 0u, site);
+  return 0;
+}
+#define GRIN_IDX(m, i, n, site) ::grin::checked_index((m).oob, (int64_t)(i), (int64_t)(n), ::grin::site)
+#else
+#define GRIN_IDX(m, i, n, site) (i)
+#endif
+
 // Largest supported polynomial: C(GRIN_MAX_DEGREE + 3, 3) coefficients.
 constexpr int kMaxTerms = 84;
 
@@ -43,6 +70,10 @@ struct DevMedium {
   double lvl_lo, lvl_hi, lvl_span;  // level_lo, level_hi, level_hi - level_lo
   double b[8];                    // boundary parameters (grin_medium_desc)
   const float* grid;              // device samples (x fastest)
+  int64_t grid_n;                 // nx * ny * nz
+  // bounds-checked build: the device word recording the first out-of-range
+  // index (a CheckSite), one per device (see checked_index)
+  unsigned int* oob;
   double scale[3], spacing[3];    // as given (the plain FP64 tracer divides)
   double cglex[kMaxTerms];        // coefficients in graded-lex order, zero padded
   double c64[kMaxTerms];          // coefficients in Horner layout (see hidx)
@@ -76,6 +107,9 @@ struct TraceArgs {
 // Validated device record of a medium description (grin_capi.cu); a grid's
 // samples go to *samples for the caller to upload (nullptr refuses grids).
 int describe_medium(const grin_medium_desc* d, DevMedium* m, std::vector<float>* samples);
+// The allocation-free entry point's own bounds word (in its static array):
+// read and clear it on the current device (grin_static.cu).
+int static_oob_take(unsigned int* value);
 
 // Number of kernel launches made; negative grin_status on failure.
 int launch_fp64(const DevMedium& m, const TraceArgs& a, cudaStream_t s, int sm_count);

@@ -95,7 +95,7 @@ struct Job {
   grin_params prm{};
   grin_out out{};
   int state = GRIN_JOB_QUEUED;  // written with the server lock held
-  double t_submit = 0.0, t_done = 0.0;
+  double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
   std::atomic<bool> cancel{false};  // set by grin_serve_cancel
   bool copying = false, failed = false;  // scheduler thread only
   // device resources while admitted
@@ -202,6 +202,7 @@ void admit(grin_server s) {
     size_t off;
     if (!s->arena->alloc(L.total, &off)) break;  // first come first served: wait
     s->queue.pop_front();
+    j.t_admit = now_s();
     j.off = off;
     j.bytes = L.total;
     j.host_done = s->pinned + s->pinned_free.back();
@@ -293,9 +294,11 @@ void scheduler(grin_server s) {
     std::vector<std::shared_ptr<Job>> run = s->running;
     lock.unlock();
     // ticks
+    int ticked = 0;
     for (auto& jp : run) {
       Job& j = *jp;
       if (j.copying || j.cancel || j.failed) continue;
+      ++ticked;
       int rc = grin::launch_serve_tick(j.med->dm, j.args, j.slots, j.nslots, j.counters, s->quantum,
                                        j.stream);
       if (rc < 0) {
@@ -337,6 +340,10 @@ void scheduler(grin_server s) {
     }
     if (keep.size() != s->running.size()) s->cv.notify_all();
     s->running.swap(keep);
+    // every running job is copying its results out: wait a little (a new
+    // submission wakes the loop) instead of polling the copies at once
+    if (!ticked && !s->running.empty() && s->queue.empty())
+      s->cv.wait_for(lock, std::chrono::microseconds(200));
   }
   // shutdown: everything still here is cancelled
   for (auto& jp : s->running) retire(s, *jp, GRIN_JOB_CANCELLED);
@@ -445,6 +452,20 @@ int grin_serve_submit(grin_server s, grin_medium med, const grin_rays* rays, con
   }
   *job_id = j->id;
   s->cv.notify_all();
+  return GRIN_OK;
+}
+
+int grin_serve_timing(grin_server s, uint64_t id, double* queued_s, double* run_s) {
+  if (!s || !queued_s || !run_s) return GRIN_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->jobs.find(id);
+  if (it == s->jobs.end()) return GRIN_ERR_NOT_FOUND;
+  const Job& j = *it->second;
+  const double now = now_s();
+  const bool admitted = j.t_admit > 0.0;
+  const double end = finished(j.state) ? j.t_done : now;
+  *queued_s = (admitted ? j.t_admit : end) - j.t_submit;
+  *run_s = admitted ? end - j.t_admit : 0.0;
   return GRIN_OK;
 }
 

@@ -31,7 +31,8 @@ namespace {
 // FP64 inputs and seven FP64 plus four int32 outputs.
 constexpr int64_t kMaxRays = GRIN_STATIC_MAX_RAYS;
 constexpr size_t kPerRay = 6 * 8 + 7 * 8 + 4 * 4;
-constexpr size_t kHeader = 256;  // the ray-queue counter, padded
+constexpr size_t kHeader = 256;  // the ray-queue counter, the bounds word, padding
+constexpr size_t kOobOffset = 8;  // the bounds-checked build's word (see grin_checked_status)
 constexpr size_t kScratchBytes = kHeader + kPerRay * (size_t)kMaxRays;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -60,6 +61,21 @@ int scratch_for_current_device(unsigned char** ptr, int* sms) {
 }
 
 }  // namespace
+
+// The bounds word in the static array: read and clear it (current device).
+int grin::static_oob_take(unsigned int* value) {
+  *value = 0;
+  unsigned char* base = nullptr;
+  int sms = 0;
+  if (scratch_for_current_device(&base, &sms) != GRIN_OK) return GRIN_ERR_CUDA;
+  if (cudaMemcpy(value, base + kOobOffset, sizeof(unsigned int), cudaMemcpyDeviceToHost) !=
+          cudaSuccess ||
+      cudaMemset(base + kOobOffset, 0, sizeof(unsigned int)) != cudaSuccess) {
+    cudaGetLastError();
+    return GRIN_ERR_CUDA;
+  }
+  return GRIN_OK;
+}
 
 extern "C" int grin_trace_host_static(const grin_medium_desc* desc, const grin_rays* rays,
                                       const grin_params* p, const grin_out* out,
@@ -104,6 +120,7 @@ extern "C" int grin_trace_host_static(const grin_medium_desc* desc, const grin_r
   if (st != GRIN_OK) return st;
   const size_t esz = rays->dtype == GRIN_F64 ? 8 : 4;
   unsigned long long* queue = (unsigned long long*)base;
+  m.oob = (unsigned int*)(base + kOobOffset);
   unsigned char* in = base + kHeader;
   const void* hin[6] = {rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz};
   void* din[6];

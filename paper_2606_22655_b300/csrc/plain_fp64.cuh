@@ -94,11 +94,11 @@ __device__ __forceinline__ void tricubic(const DevMedium& m, const double* P, do
     int kk = min(max(b0[2] - 1 + c, 0), n[2] - 1);
     for (int b = 0; b < 4; ++b) {
       int jj = min(max(b0[1] - 1 + b, 0), n[1] - 1);
-      const float* row = m.grid + (kk * n[1] + jj) * n[0];
+      const int64_t row = ((int64_t)kk * n[1] + jj) * n[0];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         int ii = min(max(b0[0] - 1 + a, 0), n[0] - 1);
-        double s = (double)__ldg(row + ii);
+        double s = (double)__ldg(m.grid + GRIN_IDX(m, row + ii, m.grid_n, kSiteGridFP64));
         v += w[0][a] * w[1][b] * w[2][c] * s;
         gx += dw[0][a] * w[1][b] * w[2][c] * s;
         gy += w[0][a] * dw[1][b] * w[2][c] * s;

@@ -211,7 +211,7 @@ struct Cfg {
   static __device__ __forceinline__ float centre_tap(const DevMedium& m, const int* i0) {
     const int ix = min(max(i0[0], 0), m.nx - 1), iy = min(max(i0[1], 0), m.ny - 1),
               iz = min(max(i0[2], 0), m.nz - 1);
-    return __ldg(m.grid + ((int64_t)iz * m.ny + iy) * m.nx + ix);
+    return __ldg(m.grid + GRIN_IDX(m, ((int64_t)iz * m.ny + iy) * m.nx + ix, m.grid_n, kSiteGridMixed));
   }
 
   // Catmull-Rom value (f = n - base) and gradient (physical units) at cell
@@ -235,11 +235,11 @@ struct Cfg {
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const int iy = min(max(i0[1] - 1 + b, 0), m.ny - 1);
-        const float* __restrict__ row = m.grid + ((int64_t)iz * m.ny + iy) * m.nx;
+        const int64_t row = ((int64_t)iz * m.ny + iy) * m.nx;
         float r = 0.0f, rx = 0.0f;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const float t = __ldg(row + ix[k]) - lb;
+          const float t = __ldg(m.grid + GRIN_IDX(m, row + ix[k], m.grid_n, kSiteGridMixed)) - lb;
           r = fmadd(w[0][k], t, r);
           rx = fmadd(dw[0][k], t, rx);
         }
@@ -270,6 +270,10 @@ struct Cfg {
 #pragma unroll
     for (int k = 0; k < 3; ++k) cr_w(fr[k], w[k], dw[k]);
     float V = 0.0f, GX = 0.0f, GY = 0.0f, GZ = 0.0f;
+#ifdef GRIN_CHECKED
+    // the column must lie in the block's cache (16 rows of kTapRow floats)
+    col = col - (int64_t)threadIdx.x * 4 + GRIN_IDX(m, (int64_t)threadIdx.x * 4, kTapRow - 4, kSiteTapCache);
+#endif
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       float sv = 0.0f, sx = 0.0f, sy = 0.0f;
@@ -1156,11 +1160,13 @@ __device__ __forceinline__ void tap_fill(const DevMedium& m, bool need, const in
     const int iy = min(max(ky - 1 + b, 0), m.ny - 1);
     const int ix0 = min(max(kx - 1 + 2 * h, 0), m.nx - 1);
     const int ix1 = min(max(kx + 2 * h, 0), m.nx - 1);
-    const float* __restrict__ g = m.grid + ((int64_t)iz * m.ny + iy) * m.nx;
-    const float v0 = __ldg(g + ix0), v1 = __ldg(g + ix1);
+    const int64_t row_i = ((int64_t)iz * m.ny + iy) * m.nx;
+    const float v0 = __ldg(m.grid + GRIN_IDX(m, row_i + ix0, m.grid_n, kSiteGridMixed));
+    const float v1 = __ldg(m.grid + GRIN_IDX(m, row_i + ix1, m.grid_n, kSiteGridMixed));
     const float sub = __shfl_sync(0xffffffffu, v1, 10);  // row 5 = (c, b) = (1, 1), x = kx
     if ((int)lane == src) lb = sub;
-    *reinterpret_cast<float2*>(taps + row * kTapRow + (wbase + src) * 4 + 2 * h) =
+    *reinterpret_cast<float2*>(
+        taps + GRIN_IDX(m, row * kTapRow + (wbase + src) * 4 + 2 * h, 16 * kTapRow - 1, kSiteTapCache)) =
         make_float2(v0 - sub, v1 - sub);
   }
   __syncwarp();
@@ -1240,7 +1246,7 @@ __global__ void __launch_bounds__(128, C::kMinBlocks) k_trace_mixed(DevMedium m,
       if (!active) {
         const unsigned long long rr = base + __popc(need & ((1u << lane) - 1u));
         if (rr < (unsigned long long)a.count) {
-          ray = a.perm ? (int64_t)a.perm[rr] : (int64_t)rr;
+          ray = a.perm ? (int64_t)GRIN_IDX(m, a.perm[rr], a.count, kSiteRay) : (int64_t)rr;
           active = init_ray<C>(m, a, ray, s);
         }
       }
@@ -1352,7 +1358,7 @@ __global__ void __launch_bounds__(128, C::kMinBlocks) k_serve_tick(DevMedium m, 
       if (!active) {
         const unsigned long long rr = base + __popc(need & ((1u << lane) - 1u));
         if (rr < (unsigned long long)a.count) {
-          ray = a.perm ? (int64_t)a.perm[rr] : (int64_t)rr;
+          ray = a.perm ? (int64_t)GRIN_IDX(m, a.perm[rr], a.count, kSiteRay) : (int64_t)rr;
           active = init_ray<C>(m, a, ray, s);
           if (!active) ++done;
         }

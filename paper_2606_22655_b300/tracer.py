@@ -282,11 +282,11 @@ class Server:
         ctx._servers.add(self)
 
     def submit(self, medium: Medium, rays: RayBatch, dopl: float, max_steps: int,
-               out: Optional[Dict[str, torch.Tensor]] = None):
+               out: Optional[Dict[str, torch.Tensor]] = None, level_root: bool = False):
         """Queue a job; returns (job id, result dict filled when it is DONE)."""
         if out is None:
             out = empty_result(rays.count, "cpu")
-        rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, "mixed")
+        rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, "mixed", level_root)
         jid = ctypes.c_uint64()
         N.check("grin_serve_submit", self.ctx.lib.grin_serve_submit(
             self.handle, medium.handle, ctypes.byref(rs), ctypes.byref(ps), ctypes.byref(os_), ctypes.byref(jid)))
@@ -299,6 +299,13 @@ class Server:
         if st.value >= N.JOB_DONE:
             self._keep.pop(job_id, None)
         return st.value, lat.value
+
+    def timing(self, job_id: int):
+        """(seconds queued before admission, seconds from admission to completion)."""
+        q, r = ctypes.c_double(), ctypes.c_double()
+        N.check("grin_serve_timing", self.ctx.lib.grin_serve_timing(self.handle, job_id, ctypes.byref(q),
+                                                                     ctypes.byref(r)))
+        return q.value, r.value
 
     def wait(self, job_id: int, timeout_s: float = 60.0) -> int:
         st = ctypes.c_int32()

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    text = open(os.path.join(ROOT, "include", "grin.h")).read()
+    text = "".join(open(os.path.join(ROOT, "include", h)).read() for h in ("grin.h", "grin_probe.h"))
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(grin_[a-z0-9_]+)\s*\(", text)))
 
@@ -70,3 +70,17 @@ def test_struct_sizes_match_c_layout(tmp_path):
         assert ctypes.sizeof(py) == int(got[c]), c
         for f in fields:
             assert getattr(py, f).offset == int(got[f"{c}.{f}"]), (c, f)
+
+
+def test_checked_build_exports_the_same_abi():
+    """The bounds-checked build (libgrin_vrt_checked.so) exports every
+    declared function and says so; the ordinary build runs no self-test."""
+    build.build()
+    names = declared_functions()
+    checked = ctypes.CDLL(build.LIB_CHECKED)
+    for n in names:
+        assert hasattr(checked, n), n
+    assert checked.grin_build_checked() == 1
+    plain = ctypes.CDLL(build.LIB)
+    assert plain.grin_build_checked() == 0
+    assert plain.grin_checked_selftest(0) == N.GRIN_ERR_NOT_IMPLEMENTED
