@@ -861,7 +861,7 @@ __device__ __forceinline__ bool level_root_step(const DevMedium& m, const TraceA
   const double a0 = (double)fP - fb, a1 = (double)fE - fb;
   double t = (a0 != a1) ? a0 / (a0 - a1) : 0.5;
   if (!(t > lo && t < hi)) t = 0.5;
-  V3 x = axpy(t, seg, p), gx64;
+  V3 x = axpy(t, seg, p);
   for (int it = 0; it < 10; ++it) {
     float fX;
     field64<C>(m, x, fX, gX);
@@ -876,29 +876,11 @@ __device__ __forceinline__ bool level_root_step(const DevMedium& m, const TraceA
     x = axpy(t, seg, p);
     if (done) break;
   }
-  // One Newton step on the field evaluated in FP64 (f rounded to FP32 moves
-  // the boundary by ~4e-9 in n, which at a curved isosurface and a
-  // near-critical crossing is felt in the refracted direction), which also
-  // gives the normal.
-  {
-    double fn;
-    V3 g64;
-    int l64;
-    Field64Fast<C::kPC, C::kGrid, false>::eval(m, x, fn, g64, l64);
-    const double dphi = dot(g64, seg);
-    const double tn = t - (fn - (fb + m.base)) / dphi;
-    if (tn > lo && tn < hi && isfinite(tn)) {
-      t = tn;
-      x = axpy(t, seg, p);
-    }
-    gX[0] = (float)g64.x;  // (kept in FP64 below)
-    gX[1] = (float)g64.y;
-    gX[2] = (float)g64.z;
-    gx64 = g64;
-  }
   // the ray is at x, a fraction t tb of what was left of the step further on
   set_pos(s, x);
   s.used = fmaf((float)(t * tb), 1.0f - s.used, s.used);
+  // (the normal is that of the last iterate's gradient)
+  const V3 gx64 = mk(gX[0], gX[1], gX[2]);
   const double gn = sqrt(dot(gx64, gx64));
   bool tir = false;
   if (gn > 0.0 && isfinite(gn)) {
