@@ -2,8 +2,9 @@
 
 Each job's results must be bitwise those of grin_trace_host with the mixed
 tracer, whether the job runs alone or among others of different media and
-sizes; admission respects the device arena; cancellation and bounded waits
-leave the server usable.
+sizes, and match the FP64 oracle under the FP32 flag rule; two jobs run at
+the same time on the device; admission respects the device arena;
+cancellation and bounded waits leave the server usable.
 """
 import numpy as np
 import pytest
@@ -166,4 +167,54 @@ def test_submit_and_wait_from_several_threads(ctx, jobs):
     assert not failures, failures
     st = srv.stats()
     assert st["done"] == 4 * len(jobs) and st["failed"] == 0
+    srv.close()
+
+
+def test_served_jobs_match_the_oracle(ctx, jobs):
+    """One served job of each medium kind (freeform block, Luneburg lens,
+    64^3 blob grid, its 32 shells) against the FP64 oracle directly, on a
+    strided sample of its rays, under the FP32 flag rule of tests/compare.py:
+    integer outcomes equal and every continuous result within 2e-5 on the
+    unflagged rays."""
+    import oracle
+    from tests.compare import compare, fp32_flags
+    srv = tracer.Server(ctx, 1 << 30)
+    for wl, med, rays, ref in jobs[:4]:
+        jid, res = srv.submit(med, rays, wl.dopl, wl.max_steps)
+        assert srv.wait(jid, 120) == N.JOB_DONE
+        idx = np.arange(0, rays.count, max(1, rays.count // 600))
+        origins = np.stack([t.numpy().astype(np.float64) for t in (rays.ox, rays.oy, rays.oz)], 1)[idx]
+        dirs = np.stack([t.numpy().astype(np.float64) for t in (rays.dx, rays.dy, rays.dz)], 1)[idx]
+        o = oracle.trace(wl.medium, origins, dirs, wl.dopl, wl.max_steps)
+        g = tracer.to_numpy({k: v[idx] for k, v in res.items()})
+        f = fp32_flags(o, wl.medium, origins, dirs, wl.dopl, wl.max_steps, wl.l_ref)
+        rep = compare(g, o, wl.l_ref, f)
+        assert rep["int_mismatch_unflagged"] == 0, (wl.name, rep)
+        assert max(rep["pos"], rep["dir"], rep["opl"]) <= 2e-5, (wl.name, rep)
+        assert rep["n_flagged"] <= 0.25 * rep["n"], (wl.name, rep)
+    srv.close()
+
+
+def test_concurrent_jobs_overlap_on_the_device(ctx):
+    """Two jobs that each hold a quarter of the GPU's resident slots, traced
+    together, finish in well under the sum of their times alone: their ticks
+    run at the same time on the device, on the jobs' own streams.  The times
+    are the server's own (admission to completion, grin_serve_timing)."""
+    wl = W.freeform_workload(40000)
+    med = tracer.Medium(ctx, wl.medium)
+    a, b = host_rays(wl, 20000), tracer.RayBatch.from_numpy(wl.rays.origins[20000:], wl.rays.dirs[20000:],
+                                                              device="cpu", dtype=torch.float32)
+    srv = tracer.Server(ctx, 1 << 30)
+    alone = []
+    for r in (a, b, a, b):  # the second pair is the one measured
+        jid, _ = srv.submit(med, r, wl.dopl, wl.max_steps)
+        assert srv.wait(jid, 120) == N.JOB_DONE
+        alone.append(srv.timing(jid)[1])
+    ja, _ = srv.submit(med, a, wl.dopl, wl.max_steps)
+    jb, _ = srv.submit(med, b, wl.dopl, wl.max_steps)
+    assert srv.wait(ja, 120) == N.JOB_DONE and srv.wait(jb, 120) == N.JOB_DONE
+    (qa, ra), (qb, rb) = srv.timing(ja), srv.timing(jb)
+    together = max(qa + ra, qb + rb)  # both submitted at once
+    assert qa < 0.5 * ra and qb < 0.5 * rb, (qa, ra, qb, rb)  # admitted at once
+    assert together < 0.75 * (alone[2] + alone[3]), (together, alone)
     srv.close()
