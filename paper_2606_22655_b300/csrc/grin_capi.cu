@@ -186,6 +186,7 @@ int grin::describe_medium(const grin_medium_desc* d, DevMedium* mp, std::vector<
   for (int k = 0; k < 3; ++k) {
     m.off_f[k] = (float)m.off[k];
     m.inv_scale_f[k] = (float)m.inv_scale[k];
+    m.noff_f[k] = (float)(-m.off[k] * m.inv_scale[k]);
     m.origin_f[k] = (float)m.origin[k];
     m.inv_spacing_f[k] = (float)m.inv_spacing[k];
     m.origin_lo_f[k] = (float)(m.origin[k] - (double)m.origin_f[k]);

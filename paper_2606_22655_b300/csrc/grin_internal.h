@@ -80,6 +80,9 @@ struct DevMedium {
   float c32[kMaxTerms];           // same, constant term shifted for nu
   float base_f, form_c_f, n_ext_f;
   float off_f[3], inv_scale_f[3], origin_f[3], inv_spacing_f[3];
+  // -off / scale, so that the normalised coordinate is one FMA,
+  // x = p inv_scale_f + noff_f
+  float noff_f[3];
   // residuals of origin_f and inv_spacing_f: origin = origin_f + origin_lo_f and
   // 1 / spacing = inv_spacing_f + inv_spacing_lo_f to about 2^-48 relative
   float origin_lo_f[3], inv_spacing_lo_f[3];

@@ -2,11 +2,12 @@
 //
 // The VRT step (Chavez-Islas et al., Sec. II; Eq. 1-9) runs in FP32:
 //   - the point is kept as an unevaluated sum ph + pl of two floats and each
-//     step's increment h d is added with Dekker's Fast2Sum, so rounding does
-//     not pile up over thousands of steps;
+//     step's increment h d is added with Dekker's Fast2Sum (on polynomial
+//     media, into pl alone, the pair normalised every kStepQuantum steps),
+//     so rounding does not pile up over thousands of steps;
 //   - the unit direction is kept the same way (dh + dl): a refraction adds
 //     the small vector R - I = gamma N - (1 - mu) I, a reflection -2 c N, by
-//     Knuth's TwoSum, so the direction does not random-walk by one FP32
+//     Fast2Sum, so the direction does not random-walk by one FP32
 //     rounding per step (that walk, a few 1e-6 after 3000 steps, would decide
 //     on which side of a turning point of n the discrete map kinks); R is a
 //     unit vector whenever I and N are, so no per-step renormalisation;
@@ -70,17 +71,19 @@ constexpr float kCritBand = 1.0e-5f;  // relative |D| below which FP64 decides
 #define GRIN_UNLIKELY(x) __builtin_expect(!!(x), 0)
 
 struct RayF;
-struct RayFM;
 
-// MG: the kernel also keeps each ray's decision margins (grin_out.margin),
-// in the state type RayFM.
+// MG: the kernel also keeps each ray's decision margins (grin_out.margin).
 template <int PC, bool GRID, bool LAYERED, int BK, int FORM, bool MG = false>
 struct Cfg {
   static constexpr bool kGrid = GRID;
   static constexpr int kPC = PC;
   static constexpr bool kLayered = LAYERED;
   static constexpr bool kMG = MG;
-  using State = typename std::conditional<MG, RayFM, RayF>::type;
+  // Polynomial media read only the hi part of a point, so their fast step
+  // carries it lazily: ph stays put for a quantum of steps while pl
+  // accumulates them (see step_point); a gridded medium's cell needs the
+  // pair normalised after every step.
+  static constexpr bool kLazyPos = !GRID;
   static constexpr int kMinBlocks = GRID ? GRIN_MIXED_MIN_BLOCKS_GRID : GRIN_MIXED_MIN_BLOCKS;
   static __device__ __forceinline__ int bk(const DevMedium& m) { return BK >= 0 ? BK : m.bkind; }
   static __device__ __forceinline__ int form(const DevMedium& m) { return FORM >= 0 ? FORM : m.form; }
@@ -108,9 +111,9 @@ struct Cfg {
       cell(m, ph, pl, i0, fr);
       grid_gather(m, i0, fr, f, gx, gy, gz);
     } else {
-      float x = (px - m.off_f[0]) * m.inv_scale_f[0];
-      float y = (py - m.off_f[1]) * m.inv_scale_f[1];
-      float z = (pz - m.off_f[2]) * m.inv_scale_f[2];
+      float x = fmaf(px, m.inv_scale_f[0], m.noff_f[0]);
+      float y = fmaf(py, m.inv_scale_f[1], m.noff_f[1]);
+      float z = fmaf(pz, m.inv_scale_f[2], m.noff_f[2]);
       float q, qx, qy, qz;
       field_vg<PC, float>(m.c32, x, y, z, q, qx, qy, qz);
       qx *= m.inv_scale_f[0];
@@ -328,29 +331,24 @@ struct RayF {
   // step's dL0 spent before its shell crossings, and their number
   float used;
   int xc;
-};
-
-// The state with the ray's decision margins (grin_out.margin, in FP32 on this
-// path's own trajectory): the minimum over the trace of [0] |N.I| minus its
-// critical value at refractions with mu > 1, [1] |N.I| at gradient steps,
-// [2] the distance of a step end to the surface in steps, [3] the distance
-// of the level coordinate to the nearest shell boundary.
-struct RayFM : RayF {
+  // kernels with MG: the ray's decision margins (grin_out.margin, in FP32 on
+  // this path's own trajectory), the minimum over the trace of [0] |N.I|
+  // minus its critical value at refractions with mu > 1, [1] |N.I| at
+  // gradient steps, [2] the distance of a step end to the surface in steps,
+  // [3] the distance of the level coordinate to the nearest shell boundary
+  // (the other kernels never touch them, and they take no registers there)
   float mg[4];
 };
 
 template <class C>
 __device__ __forceinline__ void mg_init(RayF& s) {
   if constexpr (C::kMG)
-    for (int k = 0; k < 4; ++k) static_cast<RayFM&>(s).mg[k] = INFINITY;
+    for (int k = 0; k < 4; ++k) s.mg[k] = INFINITY;
 }
 
 template <class C>
 __device__ __forceinline__ void mg_take(RayF& s, int k, float v) {
-  if constexpr (C::kMG) {
-    float& x = static_cast<RayFM&>(s).mg[k];
-    x = fminf(x, v);
-  }
+  if constexpr (C::kMG) s.mg[k] = fminf(s.mg[k], v);
 }
 
 // |N.I| minus its critical value for a refraction test with
@@ -417,15 +415,32 @@ __device__ __forceinline__ void set_dir(RayF& s, V3 d) {
   s.dl[2] = (float)(d.z - (double)s.d[2]);
 }
 
-// (hi, lo) += x: the carried residual lo is folded into x, then Knuth's
-// TwoSum (exact for any magnitudes) leaves hi = fl(hi + x) and the new
-// residual in lo, so hi stays the rounded value of the pair.
+// (hi, lo) += x: the carried residual lo is folded into x, then Dekker's
+// Fast2Sum leaves hi = fl(hi + x) and the new residual in lo, so hi stays the
+// rounded value of the pair.  Fast2Sum is exact when |hi| >= |x|; when a
+// component of the unit direction is smaller than the step's increment (it
+// passes through zero) the residual it returns is off by at most about one
+// ulp of x, the size of the rounding of x + lo itself, so Knuth's six-operation
+// TwoSum would buy nothing here.
 __device__ __forceinline__ void add_ff(float& hi, float& lo, float x) {
   x += lo;
-  float s = hi + x;
-  float bp = s - hi;
-  lo = (hi - (s - bp)) + (x - bp);
+  const float s = hi + x;
+  lo = x - (s - hi);
   hi = s;
+}
+
+// (hi, lo) <- TwoSum(hi, lo): an unevaluated pair normalised again, exactly.
+__device__ __forceinline__ void two_sum(float& hi, float& lo) {
+  const float s = hi + lo;
+  const float bp = s - hi;
+  lo = (hi - (s - bp)) + (lo - bp);
+  hi = s;
+}
+
+// A lazily carried position (Cfg::kLazyPos) as a normalised pair again.
+__device__ __forceinline__ void norm_pos(RayF& s) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) two_sum(s.ph[k], s.pl[k]);
 }
 
 __device__ __forceinline__ void finish(const TraceArgs& a, int64_t r, const RayF& s, V3 p, V3 d,
@@ -442,7 +457,7 @@ __device__ __forceinline__ void fin(const TraceArgs& a, int64_t r, const RayF& s
   finish(a, r, s, p, d, exit_id);
   if constexpr (C::kMG)
     if (a.margin)
-      for (int k = 0; k < 4; ++k) a.margin[4 * r + k] = (double)static_cast<const RayFM&>(s).mg[k];
+      for (int k = 0; k < 4; ++k) a.margin[4 * r + k] = (double)s.mg[k];
 }
 
 // (n_{i-1} - base) -> the state's index fields; false if n is not usable.
@@ -914,6 +929,8 @@ __device__ __forceinline__ bool level_root_step(const DevMedium& m, const TraceA
 template <class C, bool LAYERED>
 __device__ __noinline__ bool step_slow(const DevMedium& m, const TraceArgs& a, int64_t r,
                                        RayF& s, float dopl_f) {
+  // the exact pair form of step_point, on a normalised position
+  if constexpr (C::kLazyPos) norm_pos(s);
   float qh[3], ql[3], dv[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -1023,40 +1040,69 @@ __device__ __noinline__ bool step_slow(const DevMedium& m, const TraceArgs& a, i
 // D at or below the near-critical band, the step limit) to step_slow, which
 // redoes the step from the unchanged state.
 //
-// step_point gives the end point Q = P + h I as a hi + lo pair and the step
-// vector h I; step_from finishes the step from n and grad n at Q.
-__device__ __forceinline__ void step_point(const RayF& s, float* qh, float* ql, float* dv) {
+// step_point gives the end point Q = P + h I; step_from finishes the step from n and grad n at Q, and commit_point makes
+// Q the ray's point.  Q is the pair qh + ql by Fast2Sum, or, with a lazily
+// carried position, the low part alone moves: ql = pl + h I and qh =
+// fl(ph + ql), the rounded point the field is read at.  The low part then
+// grows by a quantum's steps at most (run_quantum normalises the pair at
+// each quantum's start, step_slow before it steps), so each step rounds at
+// an ulp of that sum instead of an ulp of the step: still well below the
+// rounding of qh itself.
+template <class C>
+__device__ __forceinline__ void step_point(const RayF& s, float* qh, float* ql) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    dv[k] = s.h * s.d[k];
     float y = fmaf(s.h, s.d[k], fmaf(s.h, s.dl[k], s.pl[k]));
-    float t = s.ph[k] + y;
-    ql[k] = y - (t - s.ph[k]);
-    qh[k] = t;
+    if constexpr (C::kLazyPos) {
+      ql[k] = y;
+      qh[k] = s.ph[k] + y;
+    } else {
+      float t = s.ph[k] + y;
+      ql[k] = y - (t - s.ph[k]);
+      qh[k] = t;
+    }
+  }
+}
+
+template <class C>
+__device__ __forceinline__ void commit_point(RayF& s, const float* qh, const float* ql) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if constexpr (!C::kLazyPos) s.ph[k] = qh[k];
+    s.pl[k] = ql[k];
   }
 }
 
 template <class C, bool LAYERED>
 __device__ __forceinline__ bool step_from(const DevMedium& m, const TraceArgs& a, int64_t r,
                                           RayF& s, float dopl_f, const float* qh,
-                                          const float* ql, const float* dv, float nu_i,
+                                          const float* ql, float nu_i,
                                           const float* g, int lvl_i, float u_i = 0.5f) {
   const bool in = C::inside(m, qh);
   const float n_i = m.base_f + nu_i;
-  const float inv_n = 1.0f / n_i;
+  // (the fast step's two divisions take the approximate reciprocal without
+  // the full-range scaling of '/': both divisors are of order one here, and
+  // any other value routes the step to step_slow)
+  const float inv_n = __fdividef(1.0f, n_i);
   const float gn2 = fmaf(g[0], g[0], fmaf(g[1], g[1], g[2] * g[2]));
   const bool homog = LAYERED && lvl_i == s.lvl_prev;
   const float ri = rsqrtf(gn2);
   float N[3] = {g[0] * ri, g[1] * ri, g[2] * ri};
   const float c = fmaf(N[0], s.d[0], fmaf(N[1], s.d[1], N[2] * s.d[2]));
-  float dn = nu_i - s.nu_prev;
-  if (!LAYERED) dn = trapezoid(s.gp, g, dv);
-  const float om = dn * inv_n;         // 1 - mu
+  // 1 - mu = (n_i - n_{i-1}) / n_i, the index difference by the trapezoid
+  // rule as (grad n_{i-1} + grad n_i) . I times h / 2 (layered media: the
+  // level values)
+  float om;
+  if constexpr (!LAYERED)
+    om = fmaf(s.gp[0] + g[0], s.d[0], fmaf(s.gp[1] + g[1], s.d[1], (s.gp[2] + g[2]) * s.d[2])) *
+         (0.5f * s.h) * inv_n;
+  else
+    om = (nu_i - s.nu_prev) * inv_n;
   const float mu = 1.0f - om;
   const float omm = om * (2.0f - om);  // 1 - mu^2
   const float mc = mu * c;
   const float D = fmaf(mc, mc, omm);
-  const float gamma = (c > 0.0f ? omm : -omm) / (sqrtf(D) + fabsf(mc));
+  const float gamma = __fdividef(c > 0.0f ? omm : -omm, sqrtf(D) + fabsf(mc));
   // A zero, infinite or undefined gradient, or an undefined index
   // difference, makes D a NaN (rsqrt(0) = inf and 0 * inf, or inf - inf),
   // which fails the comparison with the near-critical band; a gradient that
@@ -1068,9 +1114,9 @@ __device__ __forceinline__ bool step_from(const DevMedium& m, const TraceArgs& a
   if (GRIN_UNLIKELY(special)) {
     // out of line, on a copy: only the copy's address escapes, the live
     // state stays in registers
-    typename C::State t = static_cast<typename C::State&>(s);
+    RayF t = s;
     bool alive = step_slow<C, LAYERED>(m, a, r, t, dopl_f);
-    static_cast<typename C::State&>(s) = t;
+    s = t;
     return alive;
   }
   if constexpr (C::kMG) {
@@ -1081,11 +1127,7 @@ __device__ __forceinline__ bool step_from(const DevMedium& m, const TraceArgs& a
       mg_take<C>(s, 0, crit_margin(c, mu, omm, D));
     }
   }
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    s.ph[k] = qh[k];
-    s.pl[k] = ql[k];
-  }
+  commit_point<C>(s, qh, ql);
   ++s.steps;
   // Eq. 8, R = I + (gamma N - (1 - mu) I); Sec. II (v), R = I - 2 c N with a
   // step of dL0 / n_{i-1}; inside one shell of a layered medium, straight on
@@ -1110,13 +1152,13 @@ __device__ __forceinline__ bool step_from(const DevMedium& m, const TraceArgs& a
 template <class C, bool LAYERED>
 __device__ __forceinline__ bool step_ray(const DevMedium& m, const TraceArgs& a, int64_t r,
                                          RayF& s, float dopl_f) {
-  float qh[3], ql[3], dv[3];
-  step_point(s, qh, ql, dv);
+  float qh[3], ql[3];
+  step_point<C>(s, qh, ql);
   float nu_i, g[3], u_i = 0.5f;
   int lvl_i;
   C::eval(m, qh[0], qh[1], qh[2], ql[0], ql[1], ql[2], nu_i, g[0], g[1], g[2], lvl_i,
           C::kMG ? &u_i : nullptr);
-  return step_from<C, LAYERED>(m, a, r, s, dopl_f, qh, ql, dv, nu_i, g, lvl_i, u_i);
+  return step_from<C, LAYERED>(m, a, r, s, dopl_f, qh, ql, nu_i, g, lvl_i, u_i);
 }
 
 // Warp-collective: the lanes in `need` get their column of the tap cache
@@ -1166,7 +1208,9 @@ __device__ __forceinline__ unsigned run_quantum(const DevMedium& m, const TraceA
                                                 unsigned lane) {
   unsigned ended = 0;
   if constexpr (!C::kGrid) {
-#pragma unroll 1
+    if (active) norm_pos(s);
+    // (four steps an iteration: the measured optimum of 1, 2, 4 and 8)
+#pragma unroll 4
     for (int j = 0; j < kStepQuantum; ++j) {
       if (active) {
         active = step_ray<C, LAYERED>(m, a, ray, s, dopl_f);
@@ -1177,10 +1221,10 @@ __device__ __forceinline__ unsigned run_quantum(const DevMedium& m, const TraceA
     const float* col = taps + threadIdx.x * 4;
 #pragma unroll 1
     for (int j = 0; j < kStepQuantum; ++j) {
-      float qh[3], ql[3], dv[3], fr[3];
+      float qh[3], ql[3], fr[3];
       bool need = false;
       if (active) {
-        step_point(s, qh, ql, dv);
+        step_point<C>(s, qh, ql);
         int i0[3];
         C::cell(m, qh, ql, i0, fr);
         need = i0[0] != key[0] || i0[1] != key[1] || i0[2] != key[2];
@@ -1193,10 +1237,7 @@ __device__ __forceinline__ unsigned run_quantum(const DevMedium& m, const TraceA
         float nu_i, g[3], u_i = 0.5f;
         int lvl_i;
         C::eval_taps(m, fr, col, lb, nu_i, g[0], g[1], g[2], lvl_i, C::kMG ? &u_i : nullptr);
-        // the step vector again here, so it is not held across the refill
-#pragma unroll
-        for (int k = 0; k < 3; ++k) dv[k] = s.h * s.d[k];
-        active = step_from<C, LAYERED>(m, a, ray, s, dopl_f, qh, ql, dv, nu_i, g, lvl_i, u_i);
+        active = step_from<C, LAYERED>(m, a, ray, s, dopl_f, qh, ql, nu_i, g, lvl_i, u_i);
         if (!active) ++ended;
       }
     }
@@ -1212,7 +1253,7 @@ __global__ void __launch_bounds__(128, C::kMinBlocks) k_trace_mixed(DevMedium m,
   __shared__ __align__(16) float taps[C::kGrid ? 16 * kTapRow : 4];
   int key[3] = {INT_MIN, INT_MIN, INT_MIN};
   float lb = 0.0f;  // centre tap of the cached cell
-  typename C::State s;
+  RayF s;
   bool active = false;
   bool exhausted = false;
   int64_t ray = 0;
