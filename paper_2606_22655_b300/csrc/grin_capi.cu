@@ -130,6 +130,7 @@ int grin::describe_medium(const grin_medium_desc* d, DevMedium* mp, std::vector<
     for (int k = 0; k < grin::kMaxTerms; ++k) m.c32[k] = (float)m.c64[k];
     if (d->form == GRIN_FORM_LINEAR) m.c32[0] = (float)(c0 - m.base);
     else if (d->form == GRIN_FORM_SQRT) m.c32[0] = (float)(c0 - m.base * m.base);
+    for (int k = 0; k < grin::kMaxTerms; ++k) m.c32s[2 * k] = m.c32[k];
   } else {
     if (!samples) return GRIN_ERR_INVALID_ARG;
     if (!d->grid || d->nx < 1 || d->ny < 1 || d->nz < 1) return GRIN_ERR_INVALID_ARG;

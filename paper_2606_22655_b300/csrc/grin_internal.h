@@ -78,6 +78,12 @@ struct DevMedium {
   double cglex[kMaxTerms];        // coefficients in graded-lex order, zero padded
   double c64[kMaxTerms];          // coefficients in Horner layout (see hidx)
   float c32[kMaxTerms];           // same, constant term shifted for nu
+  // c32 again at a stride of two floats (c32s[2 t] = c32[t], odd slots zero),
+  // read by the FP32 polynomial evaluation: no two coefficients it reads are
+  // adjacent, so the compiler keeps each one as the constant operand of its
+  // FMA instead of merging neighbours into vector loads into registers
+  // (measured: about ten fewer instructions a ray-step)
+  float c32s[2 * kMaxTerms];
   float base_f, form_c_f, n_ext_f;
   float off_f[3], inv_scale_f[3], origin_f[3], inv_spacing_f[3];
   // -off / scale, so that the normalised coordinate is one FMA,

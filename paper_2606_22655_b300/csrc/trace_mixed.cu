@@ -72,6 +72,53 @@ constexpr float kCritBand = 1.0e-5f;  // relative |D| below which FP64 decides
 
 struct RayF;
 
+// The value and partials of a total-degree-D polynomial (Horner layout, see
+// hidx; coefficient t at c[2 t], DevMedium::c32s) in FP32: poly_vg's nested
+// Horner with derivative accumulators, with the outermost level's value and
+// z-partial, which both advance as (P, PZ) <- (P, PZ) x + (A, AZ), taken two
+// at a time by the packed fma.rn.f32x2.  The same FMAs in the same order as
+// poly_vg<D, float>, in fewer instructions.
+template <int D>
+__device__ __forceinline__ void poly_vg2(const float* __restrict__ c, float x, float y, float z,
+                                         float& p, float& px, float& py, float& pz) {
+  const float2 xx = make_float2(x, x);
+  float2 P = make_float2(0.0f, 0.0f);  // (P, PZ)
+  float PX = 0.0f, PY = 0.0f;
+#pragma unroll
+  for (int i = D; i >= 0; --i) {
+    float2 A = make_float2(0.0f, 0.0f);  // (A, AZ)
+    float AY = 0.0f;
+#pragma unroll
+    for (int j = D - i; j >= 0; --j) {
+      const int top = D - i - j;
+      float B = c[2 * hidx(D, i, j, top)], BZ = 0.0f;
+#pragma unroll
+      for (int k = top - 1; k >= 0; --k) {
+        BZ = (k == top - 1) ? B : fmaf(BZ, z, B);
+        B = fmaf(B, z, c[2 * hidx(D, i, j, k)]);
+      }
+      if (j == D - i) {
+        A = make_float2(B, BZ);
+      } else {
+        AY = (j == D - i - 1) ? A.x : fmaf(AY, y, A.x);
+        A = make_float2(fmaf(A.x, y, B), fmaf(A.y, y, BZ));
+      }
+    }
+    if (i == D) {
+      P = A;
+      PY = AY;
+    } else {
+      PX = (i == D - 1) ? P.x : fmaf(PX, x, P.x);
+      P = __ffma2_rn(P, xx, A);
+      PY = fmaf(PY, x, AY);
+    }
+  }
+  p = P.x;
+  pz = P.y;
+  px = PX;
+  py = PY;
+}
+
 // MG: the kernel also keeps each ray's decision margins (grin_out.margin).
 template <int PC, bool GRID, bool LAYERED, int BK, int FORM, bool MG = false>
 struct Cfg {
@@ -115,7 +162,10 @@ struct Cfg {
       float y = fmaf(py, m.inv_scale_f[1], m.noff_f[1]);
       float z = fmaf(pz, m.inv_scale_f[2], m.noff_f[2]);
       float q, qx, qy, qz;
-      field_vg<PC, float>(m.c32, x, y, z, q, qx, qy, qz);
+      if constexpr (PC == kPoly2 || PC == kPoly4 || PC == kPoly6)
+        poly_vg2<PC>(m.c32s, x, y, z, q, qx, qy, qz);
+      else
+        field_vg<PC, float>(m.c32, x, y, z, q, qx, qy, qz);
       qx *= m.inv_scale_f[0];
       qy *= m.inv_scale_f[1];
       qz *= m.inv_scale_f[2];
