@@ -101,15 +101,16 @@ FP32_ISSUE_PEAK = 148 * 128 * 2.032e9
 
 def fp32_issue(rate: float):
     """FP32 issue rate against the CUDA-core peak: the executed FFMA + FADD +
-    FMUL lane operations per ray-step that ncu counted for this kernel
-    (committed summary) times the measured ray-steps/s."""
+    FMUL lane operations per ray-step, two for each packed FFMA2, that ncu
+    counted for this kernel (committed summary) times the measured
+    ray-steps/s."""
     ops = profiled_value("fp32_lane_ops_per_ray_step")
     if ops is None:
         return None
     achieved = ops * rate
     return {"achieved": achieved / 1e12, "peak": FP32_ISSUE_PEAK / 1e12, "unit": "T lane-ops/s",
             "frac": achieved / FP32_ISSUE_PEAK, "fp32_lane_ops_per_ray_step": ops,
-            "source": "ncu sass op counts (FFMA + FADD + FMUL) of " + PROFILE}
+            "source": "ncu sass op counts (FFMA + FADD + FMUL + 2 FFMA2) of " + PROFILE}
 
 
 def rank_ray_seed(rank: int) -> int:
@@ -143,20 +144,58 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """SM clock and clock-event (throttle) sampling during the timed region:
+    NVML read every 10 ms from a thread (reads only), else nvidia-smi at its
+    shortest period."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits
+    REASONS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+               "hw_thermal_slowdown": 0x40}
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.thread = None
+        self.samples = []  # (sm_mhz, max_mhz, reasons bitmask)
+
+    def _nvml_handle(self):
+        import pynvml
+        pynvml.nvmlInit()
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(self.index).uuid)
+            return pynvml.nvmlDeviceGetHandleByUUID(("GPU-" + uuid) if not uuid.startswith("GPU-") else uuid)
+        except Exception:
+            return pynvml.nvmlDeviceGetHandleByIndex(self.index)
 
     def __enter__(self):
+        import threading
+        try:
+            import pynvml
+            h = self._nvml_handle()
+            self.stop = threading.Event()
+
+            def run():
+                while True:
+                    try:
+                        self.samples.append((pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM),
+                                             pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM),
+                                             pynvml.nvmlDeviceGetCurrentClocksThrottleReasons(h)))
+                    except Exception:
+                        break
+                    if self.stop.wait(0.01):
+                        break
+            self.thread = threading.Thread(target=run, daemon=True)
+            self.thread.start()
+            return self
+        except Exception:
+            self.thread = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
@@ -164,6 +203,10 @@ class ClockSampler:
 
     def __exit__(self, *exc):
         self.rows = []
+        if self.thread is not None:
+            self.stop.set()
+            self.thread.join(timeout=2)
+            return
         if self.proc is None:
             return
         self.proc.terminate()
@@ -178,6 +221,11 @@ class ClockSampler:
                 self.rows.append(parts)
 
     def summary(self):
+        if self.samples:
+            sm = [float(a) for a, _, _ in self.samples]
+            reasons = sorted({n for _, _, r in self.samples for n, b in self.REASONS.items() if r & b})
+            return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(max(b for _, b, _ in self.samples)),
+                    "reasons": reasons, "samples": len(self.samples), "source": "nvml, 10 ms"}
         rows = getattr(self, "rows", [])
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
@@ -186,7 +234,7 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "source": "nvidia-smi"}
 
 
 def oracle_rate(wl, stride: int, threads: int, rays=None):
