@@ -362,9 +362,35 @@ def adjoint_timing(ctx, dev, n_rays=1 << 18):
         same = bool(torch.allclose(grad1, grad, rtol=1e-12, atol=1e-15 * float(grad.abs().max())))
         stored = {"checkpoint_every": 1, "seconds": t1, "ray_steps_per_s_fwd_plus_bwd": steps / t1,
                   "workspace_gb": ws1 / 1e9, "gradient_equals_k64": same}
+    # one design iteration through the autograd function (grin_trace_adjoint
+    # _forward in forward, _backward in backward: the rays traced forward
+    # once), against a plain FP64 trace for the loss followed by the one-call
+    # adjoint (two forward traces)
+    targets = torch.tensor(W.design_targets(n) + 10.0, device=dev)
+    theta = torch.tensor(wl.medium.grid.astype(np.float64).ravel(), device=dev, requires_grad=True)
+
+    def design_step():
+        theta.grad = None
+        P, d, opl, ex = tracer.traced_exit(theta, ctx, wl.medium, rays, 0.02, 2000, 64)
+        tracer.image_plane_loss(P, d, ex, targets, 30.0).backward()
+
+    def two_trace_step():
+        tracer.trace(ctx, med, rays, 0.02, 2000, "fp64")
+        tracer.trace_adjoint(ctx, med, rays, 0.02, 2000, g, wl.medium.grid.size, 64)
+
+    design = {}
+    for name, fn in (("autograd_step_seconds", design_step), ("trace_then_adjoint_seconds", two_trace_step)):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        design[name] = e0.elapsed_time(e1) / 1e3
     return {"workload": f"grid_128 adjoint, {n} rays, dL0 0.02 mm, K=64", "seconds": t,
             "forward_ray_steps": steps, "ray_steps_per_s_fwd_plus_bwd": steps / t,
-            "precision": "fp64", "gradient_params": int(wl.medium.grid.size), "stored_steps": stored}
+            "precision": "fp64", "gradient_params": int(wl.medium.grid.size), "stored_steps": stored,
+            "design_iteration": design}
 
 
 def media_rates(ctx, dev):

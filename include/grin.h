@@ -337,6 +337,28 @@ int grin_trace_adjoint(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
                        int32_t checkpoint_every, void* workspace, size_t workspace_bytes,
                        void* cuda_stream);
 
+/* The two sweeps of grin_trace_adjoint as separate calls, for a caller that
+ * needs the exit states before it knows dL/dout (an autograd forward and
+ * backward): together they do what one grin_trace_adjoint call does, with
+ * the forward trace done once.
+ *   grin_trace_adjoint_forward writes `out` (bitwise grin_trace with
+ *   GRIN_PREC_FP64) and leaves the checkpoints and each ray's exit id and step
+ *   count in `workspace`;
+ *   grin_trace_adjoint_backward runs the backward sweep from that workspace
+ *   and adds dL/d(parameters) into dL_dmedium.  It must get the same
+ *   medium, rays, params and checkpoint_every as the forward call, and the
+ *   workspace unchanged in between (nothing checks this: other contents give
+ *   a meaningless gradient).  Both are asynchronous on cuda_stream; argument
+ *   errors and unsupported media as for grin_trace_adjoint. */
+int grin_trace_adjoint_forward(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
+                               const grin_params* params, const grin_out* out,
+                               int32_t checkpoint_every, void* workspace, size_t workspace_bytes,
+                               void* cuda_stream);
+int grin_trace_adjoint_backward(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
+                                const grin_params* params, const grin_out_grad* dL_dout,
+                                double* dL_dmedium, int32_t checkpoint_every, void* workspace,
+                                size_t workspace_bytes, void* cuda_stream);
+
 /* ------------------------------------------------------------ serving
  *
  * A server batches trace jobs continuously on one GPU.  A job is a batch of

@@ -112,6 +112,10 @@ def load() -> ctypes.CDLL:
                                                              P(ctypes.c_size_t)]),
         "grin_trace_adjoint": (ctypes.c_int, [_vp, _vp, P(Rays), P(Params), P(Out), P(OutGrad), _vp, ctypes.c_int32,
                                               _vp, ctypes.c_size_t, _vp]),
+        "grin_trace_adjoint_forward": (ctypes.c_int, [_vp, _vp, P(Rays), P(Params), P(Out), ctypes.c_int32,
+                                                      _vp, ctypes.c_size_t, _vp]),
+        "grin_trace_adjoint_backward": (ctypes.c_int, [_vp, _vp, P(Rays), P(Params), P(OutGrad), _vp,
+                                                       ctypes.c_int32, _vp, ctypes.c_size_t, _vp]),
         "grin_serve_create": (ctypes.c_int, [_vp, P(ServeConfig), P(_vp)]),
         "grin_serve_destroy": (ctypes.c_int, [_vp]),
         "grin_serve_submit": (ctypes.c_int, [_vp, _vp, P(Rays), P(Params), P(Out), P(ctypes.c_uint64)]),

@@ -86,8 +86,23 @@ def build(force: bool = False, ptxas_verbose: bool = False, checked: bool = True
     os.makedirs(os.path.join(BUILD, "checked"), exist_ok=True)
     os.makedirs(LIB_DIR, exist_ok=True)
     jobs = [(src, c) for c in todo for src in _sources()]
+    newest_header = max([os.path.getmtime(h) for h in _headers()] + [0.0])
+
+    def obj_of(src: str, checked: bool) -> str:
+        return os.path.join(BUILD, "checked" if checked else "", os.path.basename(src)[:-3] + ".o")
+
+    def fresh(src: str, checked: bool) -> bool:
+        # an object newer than its source and every header is reused
+        o = obj_of(src, checked)
+        return (not force and not ptxas_verbose and os.path.exists(o) and
+                os.path.getmtime(o) > max(os.path.getmtime(src), newest_header))
+
+    def one(j):
+        src, c = j
+        return (c, obj_of(src, c) if fresh(src, c) else _compile(src, ptxas_verbose, c))
+
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        objs = list(ex.map(lambda j: (j[1], _compile(j[0], ptxas_verbose, j[1])), jobs))
+        objs = list(ex.map(one, jobs))
     for c in todo:
         lib = LIB_CHECKED if c else LIB
         tmp = lib + f".tmp{os.getpid()}"

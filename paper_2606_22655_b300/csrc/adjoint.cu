@@ -168,9 +168,17 @@ __device__ bool start(const DevMedium& m, const TraceArgs& a, int64_t r, St& s, 
 
 // ------------------------------------------------------ field derivatives
 
-// n, grad n and the Hessian (xx, yy, zz, xy, xz, yz) at P.
+// At P: n, grad n and the Hessian (xx, yy, zz, xy, xz, yz), then, with the
+// same weights (grid) or powers (polynomial),
+//   theta_bar += nb dn/dtheta + gb . d(grad n)/dtheta
+// (polynomial: into the thread's accumulator acc[term]; grid: atomically
+// into grad).  gb may be null (zero).  The cell choice takes the forward
+// sweep's division; nothing after it feeds a decision, so the rest uses
+// explicit fused multiply-adds and products by stored reciprocals.
 template <int PC, bool GRID>
-__device__ void field_h(const DevMedium& m, const double* P, double& n, double* g, double* H) {
+__device__ void field_h_adj(const DevMedium& m, const double* P, double nb, const double* gbp,
+                            double& n, double* g, double* H, double* acc, double* grad) {
+  const double gb[3] = {gbp ? gbp[0] : 0.0, gbp ? gbp[1] : 0.0, gbp ? gbp[2] : 0.0};
   for (int k = 0; k < 3; ++k) g[k] = 0.0;
   for (int k = 0; k < 6; ++k) H[k] = 0.0;
   n = 0.0;
@@ -185,15 +193,14 @@ __device__ void field_h(const DevMedium& m, const double* P, double& n, double* 
       double fl = floor(u), t = u - fl;
       b0[a] = (int)fl;
       plain::keys(t, w[a], dw[a]);
-      ddw[a][0] = 2.0 - 3.0 * t;
-      ddw[a][1] = 9.0 * t - 5.0;
-      ddw[a][2] = 4.0 - 9.0 * t;
-      ddw[a][3] = 3.0 * t - 1.0;
+      ddw[a][0] = fma(-3.0, t, 2.0);
+      ddw[a][1] = fma(9.0, t, -5.0);
+      ddw[a][2] = fma(-9.0, t, 4.0);
+      ddw[a][3] = fma(3.0, t, -1.0);
     }
     // The tensor-product stencil separates: sums along x of the samples
     // weighted by w, w', w'' (per row), then along y, then along z, keeping
-    // only the weight combinations of total derivative order <= 2.  Fused
-    // multiply-adds (explicit fma; this file is otherwise built unfused).
+    // only the weight combinations of total derivative order <= 2.
     for (int c = 0; c < 4; ++c) {
       int kk = min(max(b0[2] - 1 + c, 0), nn[2] - 1);
       double y00 = 0.0, y10 = 0.0, y20 = 0.0, y01 = 0.0, y11 = 0.0, y02 = 0.0;
@@ -203,10 +210,10 @@ __device__ void field_h(const DevMedium& m, const double* P, double& n, double* 
         double x0 = 0.0, x1 = 0.0, x2 = 0.0;  // row sums with w, w', w'' in x
         for (int a = 0; a < 4; ++a) {
           int ii = min(max(b0[0] - 1 + a, 0), nn[0] - 1);
-          const double s = (double)m.grid[GRIN_IDX(m, row + ii, m.grid_n, kSiteGridAdjoint)];
-          x0 = fma(w[0][a], s, x0);
-          x1 = fma(dw[0][a], s, x1);
-          x2 = fma(ddw[0][a], s, x2);
+          const double sv = (double)m.grid[GRIN_IDX(m, row + ii, m.grid_n, kSiteGridAdjoint)];
+          x0 = fma(w[0][a], sv, x0);
+          x1 = fma(dw[0][a], sv, x1);
+          x2 = fma(ddw[0][a], sv, x2);
         }
         y00 = fma(w[1][b], x0, y00);
         y10 = fma(w[1][b], x1, y10);
@@ -226,8 +233,6 @@ __device__ void field_h(const DevMedium& m, const double* P, double& n, double* 
       H[4] = fma(dw[2][c], y10, H[4]);
       H[5] = fma(dw[2][c], y01, H[5]);
     }
-    // to physical units by the stored reciprocals: nothing here feeds a
-    // decision, so products replace the divisions
     const double* is = m.inv_spacing;
     for (int k = 0; k < 3; ++k) g[k] *= is[k];
     H[0] *= is[0] * is[0];
@@ -236,39 +241,62 @@ __device__ void field_h(const DevMedium& m, const double* P, double& n, double* 
     H[3] *= is[0] * is[1];
     H[4] *= is[0] * is[2];
     H[5] *= is[1] * is[2];
+    // d(n, grad n)/d(sample) = the tap's weight products; factored per row
+    // (b, c): v = w0 A + w0' B with A = w1 (nb w2 + gb2 w2') + gb1 w1' w2 and
+    // B = gb0 w1 w2 (the derivative weights in physical units)
+    const double g0 = gb[0] * is[0], g1 = gb[1] * is[1], g2 = gb[2] * is[2];
+    for (int c = 0; c < 4; ++c) {
+      int kk = min(max(b0[2] - 1 + c, 0), nn[2] - 1);
+      const double zc = fma(nb, w[2][c], g2 * dw[2][c]);
+      const double g1w2 = g1 * w[2][c], g0w2 = g0 * w[2][c];
+      for (int b = 0; b < 4; ++b) {
+        int jj = min(max(b0[1] - 1 + b, 0), nn[1] - 1);
+        const double A = fma(w[1][b], zc, g1w2 * dw[1][b]);
+        const double B = g0w2 * w[1][b];
+        const int64_t row = ((int64_t)kk * nn[1] + jj) * nn[0];
+        for (int a = 0; a < 4; ++a) {
+          int ii = min(max(b0[0] - 1 + a, 0), nn[0] - 1);
+          const double v = fma(w[0][a], A, dw[0][a] * B);
+          if (v != 0.0) atomicAdd(grad + GRIN_IDX(m, row + ii, m.grid_n, kSiteGridAdjoint), v);
+        }
+      }
+    }
   } else {
+    const double* is = m.inv_scale;
     double x[3];
-    for (int k = 0; k < 3; ++k) x[k] = (P[k] - m.off[k]) / m.scale[k];
+    for (int k = 0; k < 3; ++k) x[k] = (P[k] - m.off[k]) * is[k];
     double pw[3][PC + 1];
     for (int k = 0; k < 3; ++k) {
       pw[k][0] = 1.0;
       for (int e = 1; e <= PC; ++e) pw[k][e] = pw[k][e - 1] * x[k];
     }
+    const double gx = gb[0] * is[0], gy = gb[1] * is[1], gz = gb[2] * is[2];
     int idx = 0;
     for (int s = 0; s <= PC; ++s)
       for (int i = s; i >= 0; --i)
         for (int j = s - i; j >= 0; --j) {
           const int k = s - i - j;
-          const double c = m.cglex[idx++];
-          if (c == 0.0) continue;
           const double X = pw[0][i], Y = pw[1][j], Z = pw[2][k];
           const double dX = i ? i * pw[0][i - 1] : 0.0, dY = j ? j * pw[1][j - 1] : 0.0,
                        dZ = k ? k * pw[2][k - 1] : 0.0;
+          const double YZ = Y * Z, XZ = X * Z, XY = X * Y;
+          acc[idx] += fma(nb, X * YZ, fma(gx, dX * YZ, fma(gy, dY * XZ, gz * dZ * XY)));
+          const double c = m.cglex[idx++];
+          if (c == 0.0) continue;
           const double ddX = i > 1 ? i * (i - 1) * pw[0][i - 2] : 0.0;
           const double ddY = j > 1 ? j * (j - 1) * pw[1][j - 2] : 0.0;
           const double ddZ = k > 1 ? k * (k - 1) * pw[2][k - 2] : 0.0;
-          n += c * X * Y * Z;
-          g[0] += c * dX * Y * Z;
-          g[1] += c * X * dY * Z;
-          g[2] += c * X * Y * dZ;
-          H[0] += c * ddX * Y * Z;
-          H[1] += c * X * ddY * Z;
-          H[2] += c * X * Y * ddZ;
-          H[3] += c * dX * dY * Z;
-          H[4] += c * dX * Y * dZ;
-          H[5] += c * X * dY * dZ;
+          n = fma(c, X * YZ, n);
+          g[0] = fma(c, dX * YZ, g[0]);
+          g[1] = fma(c, dY * XZ, g[1]);
+          g[2] = fma(c, dZ * XY, g[2]);
+          H[0] = fma(c, ddX * YZ, H[0]);
+          H[1] = fma(c, ddY * XZ, H[1]);
+          H[2] = fma(c, ddZ * XY, H[2]);
+          H[3] = fma(c, dX * dY * Z, H[3]);
+          H[4] = fma(c, dX * dZ * Y, H[4]);
+          H[5] = fma(c, dY * dZ * X, H[5]);
         }
-    const double* is = m.inv_scale;
     for (int k = 0; k < 3; ++k) g[k] *= is[k];
     H[0] *= is[0] * is[0];
     H[1] *= is[1] * is[1];
@@ -276,67 +304,6 @@ __device__ void field_h(const DevMedium& m, const double* P, double& n, double* 
     H[3] *= is[0] * is[1];
     H[4] *= is[0] * is[2];
     H[5] *= is[1] * is[2];
-  }
-}
-
-// theta_bar += nb dn/dtheta + gb . d(grad n)/dtheta at P.  Polynomial:
-// into the thread's accumulator acc[term]; grid: atomically into grad.
-template <int PC, bool GRID>
-__device__ void param_adj(const DevMedium& m, const double* P, double nb, const double* gb,
-                          double* acc, double* grad) {
-  if (GRID) {
-    const int nn[3] = {m.nx, m.ny, m.nz};
-    int b0[3];
-    double w[3][4], dw[3][4];
-    for (int a = 0; a < 3; ++a) {
-      double u = (P[a] - m.origin[a]) / m.spacing[a];
-      if (!(u > -2.0)) u = -2.0;
-      if (u > (double)nn[a] + 1.0) u = (double)nn[a] + 1.0;
-      double fl = floor(u);
-      b0[a] = (int)fl;
-      plain::keys(u - fl, w[a], dw[a]);
-      for (int t = 0; t < 4; ++t) dw[a][t] *= m.inv_spacing[a];
-    }
-    // d(n, grad n)/d(sample) = the tap's weight products; factored per row
-    // (b, c): v = w0 A + w0' B with A = w1 (nb w2 + gb2 w2') + gb1 w1' w2 and
-    // B = gb0 w1 w2.
-    for (int c = 0; c < 4; ++c) {
-      int kk = min(max(b0[2] - 1 + c, 0), nn[2] - 1);
-      const double zc = fma(nb, w[2][c], gb[2] * dw[2][c]);
-      for (int b = 0; b < 4; ++b) {
-        int jj = min(max(b0[1] - 1 + b, 0), nn[1] - 1);
-        const double A = fma(w[1][b], zc, gb[1] * dw[1][b] * w[2][c]);
-        const double B = gb[0] * w[1][b] * w[2][c];
-        for (int a = 0; a < 4; ++a) {
-          int ii = min(max(b0[0] - 1 + a, 0), nn[0] - 1);
-          const double v = fma(w[0][a], A, dw[0][a] * B);
-          if (v != 0.0)
-            atomicAdd(grad + GRIN_IDX(m, ((int64_t)kk * nn[1] + jj) * nn[0] + ii, m.grid_n, kSiteGridAdjoint), v);
-        }
-      }
-    }
-  } else {
-    double x[3];
-    for (int k = 0; k < 3; ++k) x[k] = (P[k] - m.off[k]) / m.scale[k];
-    double pw[3][PC + 1];
-    for (int k = 0; k < 3; ++k) {
-      pw[k][0] = 1.0;
-      for (int e = 1; e <= PC; ++e) pw[k][e] = pw[k][e - 1] * x[k];
-    }
-    const double gx = gb[0] * m.inv_scale[0], gy = gb[1] * m.inv_scale[1],
-                 gz = gb[2] * m.inv_scale[2];
-    int idx = 0;
-    for (int s = 0; s <= PC; ++s)
-      for (int i = s; i >= 0; --i)
-        for (int j = s - i; j >= 0; --j) {
-          const int k = s - i - j;
-          const double X = pw[0][i], Y = pw[1][j], Z = pw[2][k];
-          double v = nb * X * Y * Z;
-          if (i) v += gx * i * pw[0][i - 1] * Y * Z;
-          if (j) v += gy * X * j * pw[1][j - 1] * Z;
-          if (k) v += gz * X * Y * k * pw[2][k - 1];
-          acc[idx++] += v;
-        }
   }
 }
 
@@ -346,35 +313,41 @@ struct Adj {
   double P[3], d[3], n, h;  // dL/dP, dL/dI, dL/dn_{i-1}, dL/dh
 };
 
-// Back through R -> R / |R| given the unit result u and |R|.
-__device__ __forceinline__ void unit_back(const double* u, double Rn, const double* ub, double* Rb) {
-  double s = plain::dot3(u, ub);
-  for (int k = 0; k < 3; ++k) Rb[k] = (ub[k] - u[k] * s) / Rn;
+// a . b with fused multiply-adds (reverse-mode arithmetic only: the forward
+// sweep keeps plain::dot3's unfused rounding)
+__device__ __forceinline__ double fdot3(const double* a, const double* b) {
+  return fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
+}
+
+// Back through R -> R / |R| given the unit result u and 1 / |R|.
+__device__ __forceinline__ void unit_back(const double* u, double inv_Rn, const double* ub, double* Rb) {
+  double s = fdot3(u, ub);
+  for (int k = 0; k < 3; ++k) Rb[k] = fma(-u[k], s, ub[k]) * inv_Rn;
 }
 
 // Back through the Snell refraction R = mu I + gamma N (Eq. 8-9) at fixed
 // branch; adds into Ib, Nb and returns mub.
 __device__ __forceinline__ double snell_back(const double* I, const double* N, double mu,
                                              const double* Rb, double* Ib, double* Nb) {
+  // c, D and gamma exactly as the forward step formed them (unfused): near
+  // critical incidence D is tiny, and 1 / sqrt(D) below would amplify any
+  // other rounding of it (or take the square root of a negative one)
   double c = plain::dot3(N, I);
-  double D = 1.0 - mu * mu * (1.0 - c * c);
+  const double omc2 = 1.0 - c * c;
+  double D = 1.0 - mu * mu * omc2;
   double s = c > 0.0 ? 1.0 : (c < 0.0 ? -1.0 : 0.0);
   double sq = sqrt(D);
   double gamma = -mu * c + s * sq;
-  double mub = plain::dot3(Rb, I);
-  double gammab = plain::dot3(Rb, N);
-  for (int k = 0; k < 3; ++k) {
-    Ib[k] += mu * Rb[k];
-    Nb[k] += gamma * Rb[k];
-  }
-  mub += -c * gammab;
+  double mub = fdot3(Rb, I);
+  double gammab = fdot3(Rb, N);
+  mub = fma(-c, gammab, mub);
   double cb = -mu * gammab;
-  double Db = sq > 0.0 ? s * gammab / (2.0 * sq) : 0.0;
-  mub += -2.0 * mu * (1.0 - c * c) * Db;
-  cb += 2.0 * mu * mu * c * Db;
+  double Db = sq > 0.0 ? s * gammab * (0.5 / sq) : 0.0;
+  mub = fma(-2.0 * mu * omc2, Db, mub);
+  cb = fma(2.0 * mu * mu * c, Db, cb);
   for (int k = 0; k < 3; ++k) {
-    Nb[k] += cb * I[k];
-    Ib[k] += cb * N[k];
+    Ib[k] = fma(cb, N[k], fma(mu, Rb[k], Ib[k]));
+    Nb[k] = fma(cb, I[k], fma(gamma, Rb[k], Nb[k]));
   }
   return mub;
 }
@@ -428,6 +401,8 @@ __device__ void normal_back(const DevMedium& m, double dopl, const double* rec, 
   const double n_prev = rec[6], h = rec[7];
   double Pn[3];
   for (int k = 0; k < 3; ++k) Pn[k] = P[k] + h * I[k];
+  // n and grad n at P' with the forward step's arithmetic, so that the
+  // branch decisions below are the forward sweep's
   double n, g[3];
   int lvl;
   plain::sample<PC, GRID, false>(m, Pn, n, g, lvl);
@@ -438,57 +413,61 @@ __device__ void normal_back(const DevMedium& m, double dopl, const double* rec, 
   out.n = out.h = 0.0;
   double nb = in.n;
   double gb[3] = {0.0, 0.0, 0.0};
+  const double inv_n = 1.0 / n;
   if (gn == 0.0 || !isfinite(gn)) {
-    nb += -in.h * (dopl / n) / n;
+    nb = fma(-in.h * dopl, inv_n * inv_n, nb);
     for (int k = 0; k < 3; ++k) out.d[k] += in.d[k];
   } else {
+    // (the decisions take the forward sweep's arithmetic: N, c and D as the
+    // plain step forms them; the rest is reverse-mode only)
     double N[3] = {g[0] / gn, g[1] / gn, g[2] / gn};
     double c = plain::dot3(N, I);
     double mu = n_prev / n;
     if (c == 0.0) {
       // tangential incidence (case iv, measure zero): the arc's direction is
       // held fixed
-      nb += -in.h * (dopl / n) / n;
+      nb = fma(-in.h * dopl, inv_n * inv_n, nb);
       for (int k = 0; k < 3; ++k) out.d[k] += in.d[k];
     } else {
       double D = 1.0 - mu * mu * (1.0 - c * c);
       bool tir = D <= 0.0;
       double R[3];
-      double Rn = fwd_R(I, N, mu, tir, R);
-      double u[3] = {R[0] / Rn, R[1] / Rn, R[2] / Rn};
+      const double inv_Rn = 1.0 / fwd_R(I, N, mu, tir, R);
+      double u[3] = {R[0] * inv_Rn, R[1] * inv_Rn, R[2] * inv_Rn};
       double Rb[3];
-      unit_back(u, Rn, in.d, Rb);
+      unit_back(u, inv_Rn, in.d, Rb);
       double Nb[3] = {0.0, 0.0, 0.0};
       if (tir) {
-        out.n += -in.h * (dopl / n_prev) / n_prev;
-        double cb = -2.0 * plain::dot3(Rb, N);
+        const double inv_p = 1.0 / n_prev;
+        out.n = fma(-in.h * dopl, inv_p * inv_p, out.n);
+        double cb = -2.0 * fdot3(Rb, N);
         for (int k = 0; k < 3; ++k) {
-          out.d[k] += Rb[k] + cb * N[k];
-          Nb[k] += -2.0 * c * Rb[k] + cb * I[k];
+          out.d[k] += fma(cb, N[k], Rb[k]);
+          Nb[k] += fma(-2.0 * c, Rb[k], cb * I[k]);
         }
       } else {
-        nb += -in.h * (dopl / n) / n;
+        nb = fma(-in.h * dopl, inv_n * inv_n, nb);
         double mub = snell_back(I, N, mu, Rb, out.d, Nb);
-        out.n += mub / n;
-        nb += -mub * mu / n;
+        out.n = fma(mub, inv_n, out.n);
+        nb = fma(-mub * mu, inv_n, nb);
       }
-      double s = plain::dot3(N, Nb);
-      for (int k = 0; k < 3; ++k) gb[k] = (Nb[k] - N[k] * s) / gn;
+      double s = fdot3(N, Nb);
+      const double inv_gn = 1.0 / gn;
+      for (int k = 0; k < 3; ++k) gb[k] = fma(-N[k], s, Nb[k]) * inv_gn;
     }
   }
   // field at P': dL/dP' = in.P + nb grad n + H gb; parameters
   double nh, gh[3], H[6];
-  field_h<PC, GRID>(m, Pn, nh, gh, H);
+  field_h_adj<PC, GRID>(m, Pn, nb, gb, nh, gh, H, acc, grad);
   double Pb[3];
-  Pb[0] = in.P[0] + nb * gh[0] + H[0] * gb[0] + H[3] * gb[1] + H[4] * gb[2];
-  Pb[1] = in.P[1] + nb * gh[1] + H[3] * gb[0] + H[1] * gb[1] + H[5] * gb[2];
-  Pb[2] = in.P[2] + nb * gh[2] + H[4] * gb[0] + H[5] * gb[1] + H[2] * gb[2];
-  param_adj<PC, GRID>(m, Pn, nb, gb, acc, grad);
+  Pb[0] = fma(H[4], gb[2], fma(H[3], gb[1], fma(H[0], gb[0], fma(nb, gh[0], in.P[0]))));
+  Pb[1] = fma(H[5], gb[2], fma(H[1], gb[1], fma(H[3], gb[0], fma(nb, gh[1], in.P[1]))));
+  Pb[2] = fma(H[2], gb[2], fma(H[5], gb[1], fma(H[4], gb[0], fma(nb, gh[2], in.P[2]))));
   // P' = P + h I
   for (int k = 0; k < 3; ++k) {
     out.P[k] += Pb[k];
-    out.h += Pb[k] * I[k];
-    out.d[k] += h * Pb[k];
+    out.h = fma(Pb[k], I[k], out.h);
+    out.d[k] = fma(h, Pb[k], out.d[k]);
   }
   lam = out;
 }
@@ -507,22 +486,21 @@ __device__ void reflect_back(const DevMedium& m, double dopl, const double* rec,
   plain::leave(m, P, Q, t, Pb, NB, f2);
   double R[3] = {I[0], I[1], I[2]};
   R[ax] = -I[ax];
-  double Rn = sqrt(plain::dot3(R, R));
-  double u[3] = {R[0] / Rn, R[1] / Rn, R[2] / Rn};
+  const double inv_Rn = 1.0 / sqrt(plain::dot3(R, R));
+  double u[3] = {R[0] * inv_Rn, R[1] * inv_Rn, R[2] * inv_Rn};
   Adj in = lam;
   Adj out;
   for (int k = 0; k < 3; ++k) out.P[k] = out.d[k] = 0.0;
-  out.n = -in.h * (dopl / n_prev) / n_prev;
+  const double inv_p = 1.0 / n_prev;
+  out.n = -in.h * dopl * inv_p * inv_p;
   out.h = 0.0;
   // n'_{i-1} = n(P_b)
   double nh, gh[3], H[6];
-  field_h<PC, GRID>(m, Pb, nh, gh, H);
+  field_h_adj<PC, GRID>(m, Pb, in.n, nullptr, nh, gh, H, acc, grad);
   double Pbb[3];
-  for (int k = 0; k < 3; ++k) Pbb[k] = in.P[k] + in.n * gh[k];
-  double zero[3] = {0.0, 0.0, 0.0};
-  param_adj<PC, GRID>(m, Pb, in.n, zero, acc, grad);
+  for (int k = 0; k < 3; ++k) Pbb[k] = fma(in.n, gh[k], in.P[k]);
   double Rb[3];
-  unit_back(u, Rn, in.d, Rb);
+  unit_back(u, inv_Rn, in.d, Rb);
   for (int k = 0; k < 3; ++k) out.d[k] += k == ax ? -Rb[k] : Rb[k];
   cross_back(m, P, I, h, face, Pbb, fb, out);
   lam = out;
@@ -539,10 +517,10 @@ __device__ void exit_back(const DevMedium& m, const double* rec, int face, const
   N[ax] = (face & 1) ? 1.0 : -1.0;
   const double mu = n_prev / m.n_ext;
   double R[3];
-  double Rn = fwd_R(I, N, mu, false, R);
-  double u[3] = {R[0] / Rn, R[1] / Rn, R[2] / Rn};
+  const double inv_Rn = 1.0 / fwd_R(I, N, mu, false, R);
+  double u[3] = {R[0] * inv_Rn, R[1] * inv_Rn, R[2] * inv_Rn};
   double Rb[3];
-  unit_back(u, Rn, dob, Rb);
+  unit_back(u, inv_Rn, dob, Rb);
   for (int k = 0; k < 3; ++k) lam.P[k] = lam.d[k] = 0.0;
   lam.h = 0.0;
   double Nb[3] = {0.0, 0.0, 0.0};
@@ -562,15 +540,15 @@ __device__ void entry_back(const DevMedium& m, double dopl, const St& s0, bool e
   if (entered) {
     double mu = m.n_ext / n0;
     double R[3];
-    double Rn = fwd_R(d_in, NB, mu, false, R);
-    double u[3] = {R[0] / Rn, R[1] / Rn, R[2] / Rn};
+    const double inv_Rn = 1.0 / fwd_R(d_in, NB, mu, false, R);
+    double u[3] = {R[0] * inv_Rn, R[1] * inv_Rn, R[2] * inv_Rn};
     double Rb[3], Ib[3] = {0.0, 0.0, 0.0}, Nb[3] = {0.0, 0.0, 0.0};
-    unit_back(u, Rn, lam.d, Rb);
+    unit_back(u, inv_Rn, lam.d, Rb);
     double mub = snell_back(d_in, NB, mu, Rb, Ib, Nb);
     nb += -mub * mu / n0;
   }
-  double zero[3] = {0.0, 0.0, 0.0};
-  param_adj<PC, GRID>(m, s0.P, nb, zero, acc, grad);
+  double nh, gh[3], H[6];
+  field_h_adj<PC, GRID>(m, s0.P, nb, nullptr, nh, gh, H, acc, grad);
 }
 
 // ---------------------------------------------------------------- kernels
@@ -709,9 +687,12 @@ __global__ void __launch_bounds__(128) k_adj_backward(DevMedium m, AdjArgs A) {
 }
 
 template <int PC, bool GRID>
-static int run_t(const DevMedium& m, const AdjArgs& A, cudaStream_t st) {
+static int run_t(const DevMedium& m, const AdjArgs& A, cudaStream_t st, int phase) {
   const unsigned blocks = (unsigned)((A.a.count + 127) / 128);
-  if (launch_kernel(k_adj_forward<PC, GRID>, blocks, 128, st, m, A) < 0) return GRIN_ERR_CUDA;
+  if (phase != kAdjBackward &&
+      launch_kernel(k_adj_forward<PC, GRID>, blocks, 128, st, m, A) < 0)
+    return GRIN_ERR_CUDA;
+  if (phase == kAdjForward) return 1;
   // The backward sweep walks each ray back through all its steps, one
   // thread a ray: in a gridded medium, where path lengths vary with the exit
   // face, take the rays longest first, bucketed by step count, so the threads
@@ -728,7 +709,7 @@ static int run_t(const DevMedium& m, const AdjArgs& A, cudaStream_t st) {
     }
   }
   if (launch_kernel(k_adj_backward<PC, GRID>, blocks, 128, st, m, B) < 0) return GRIN_ERR_CUDA;
-  return 2 + lo;
+  return (phase == kAdjBackward ? 1 : 2) + lo;
 }
 
 }  // namespace adj
@@ -754,13 +735,15 @@ size_t adjoint_workspace(int64_t rays, int32_t max_steps, int32_t k) {
 }
 
 int launch_adjoint(const DevMedium& m, const TraceArgs& a, int32_t k, void* ws, const double* const* gout,
-                   double* grad, int nterms, cudaStream_t st) {
+                   double* grad, int nterms, cudaStream_t st, int phase) {
   adj::AdjArgs A;
   A.a = a;
   A.k = k;
   A.nseg = a.max_steps / k + 1;
   A.ckpt = (double*)ws;
   A.meta = (int32_t*)((char*)ws + (size_t)a.count * A.nseg * adj::kCk * sizeof(double));
+  static const double* const kNone[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (!gout) gout = kNone;  // the forward sweep alone reads no gradients
   A.gpx = gout[0];
   A.gpy = gout[1];
   A.gpz = gout[2];
@@ -772,11 +755,11 @@ int launch_adjoint(const DevMedium& m, const TraceArgs& a, int32_t k, void* ws, 
   A.nterms = nterms;
   if (a.count < (int64_t(1) << 31))
     A.order_ws = (char*)ws + adjoint_order_offset(a.count, a.max_steps, k);
-  if (m.kind == GRIN_MEDIUM_GRID) return adj::run_t<0, true>(m, A, st);
+  if (m.kind == GRIN_MEDIUM_GRID) return adj::run_t<0, true>(m, A, st, phase);
   switch (m.pclass) {
-    case kPoly2: return adj::run_t<2, false>(m, A, st);
-    case kPoly4: return adj::run_t<4, false>(m, A, st);
-    default: return adj::run_t<6, false>(m, A, st);
+    case kPoly2: return adj::run_t<2, false>(m, A, st, phase);
+    case kPoly4: return adj::run_t<4, false>(m, A, st, phase);
+    default: return adj::run_t<6, false>(m, A, st, phase);
   }
 }
 

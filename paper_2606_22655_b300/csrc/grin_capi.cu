@@ -428,8 +428,11 @@ int grin_medium_device_bytes(grin_medium medium, size_t* bytes) {
   return GRIN_OK;
 }
 
+// out == nullptr: a call that writes no results (the adjoint's backward sweep)
 static int check_trace_args(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
-                            const grin_params* p, const grin_out* out) {
+                            const grin_params* p, const grin_out* out, bool need_out = true) {
+  static const grin_out kNoOut = {};
+  if (!need_out && !out) out = &kNoOut;
   if (!ctx || !medium || !rays || !p || !out) return GRIN_ERR_INVALID_ARG;
   if (medium->ctx != ctx) return GRIN_ERR_INVALID_ARG;
   if (rays->count < 0) return GRIN_ERR_INVALID_ARG;
@@ -445,6 +448,7 @@ static int check_trace_args(grin_ctx ctx, grin_medium medium, const grin_rays* r
   if (rays->count == 0) return GRIN_OK;
   if (!rays->ox || !rays->oy || !rays->oz || !rays->dx || !rays->dy || !rays->dz)
     return GRIN_ERR_INVALID_ARG;
+  if (!need_out) return GRIN_OK;
   if (!out->px || !out->py || !out->pz || !out->dx || !out->dy || !out->dz || !out->opl ||
       !out->exit_id || !out->steps || !out->tir_internal || !out->tir_boundary)
     return GRIN_ERR_INVALID_ARG;
@@ -708,21 +712,32 @@ int grin_trace_adjoint_workspace_size(grin_medium medium, int64_t ray_count, con
   return GRIN_OK;
 }
 
-int grin_trace_adjoint(grin_ctx ctx, grin_medium medium, const grin_rays* rays, const grin_params* p,
-                       const grin_out* out, const grin_out_grad* g, double* grad, int32_t k,
-                       void* ws, size_t ws_bytes, void* cuda_stream) {
-  int st = check_trace_args(ctx, medium, rays, p, out);
+// The forward sweep, the backward sweep or both (grin::AdjPhase); out and g
+// as the phase needs them.
+static int trace_adjoint_phase(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
+                               const grin_params* p, const grin_out* out, const grin_out_grad* g,
+                               double* grad, int32_t k, void* ws, size_t ws_bytes, void* cuda_stream,
+                               int phase) {
+  static const grin_out kNoOut = {};
+  const bool backward_only = phase == grin::kAdjBackward;
+  int st = check_trace_args(ctx, medium, rays, p, backward_only ? nullptr : out, !backward_only);
   if (st != GRIN_OK) return st;
-  if (!g || !grad || !ws || k < 1 || k > 64 || p->precision != GRIN_PREC_FP64)
-    return GRIN_ERR_INVALID_ARG;
+  if (backward_only) out = &kNoOut;  // the backward sweep writes no results
+  if (!ws || k < 1 || k > 64 || p->precision != GRIN_PREC_FP64) return GRIN_ERR_INVALID_ARG;
+  if (phase != grin::kAdjForward && (!g || !grad)) return GRIN_ERR_INVALID_ARG;
   if (p->flags || out->margin) return GRIN_ERR_NOT_IMPLEMENTED;
   if (!grin::adjoint_supported(medium->dm)) return GRIN_ERR_NOT_IMPLEMENTED;
   ctx->last_launches = 0;
   if (rays->count == 0) return GRIN_OK;
   if (ws_bytes < grin::adjoint_workspace(rays->count, p->max_steps, k)) return GRIN_ERR_INVALID_ARG;
-  const double* gout[7] = {g->px, g->py, g->pz, g->dx, g->dy, g->dz, g->opl};
-  for (int q = 0; q < 7; ++q)
-    if (!gout[q]) return GRIN_ERR_INVALID_ARG;
+  const double* gout[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (phase != grin::kAdjForward) {
+    const double* gg[7] = {g->px, g->py, g->pz, g->dx, g->dy, g->dz, g->opl};
+    for (int q = 0; q < 7; ++q) {
+      if (!gg[q]) return GRIN_ERR_INVALID_ARG;
+      gout[q] = gg[q];
+    }
+  }
   grin::TraceArgs a;
   a.ox = rays->ox;
   a.oy = rays->oy;
@@ -749,10 +764,33 @@ int grin_trace_adjoint(grin_ctx ctx, grin_medium medium, const grin_rays* rays, 
   a.margin = out->margin;
   const grin::DevMedium& m = medium->dm;
   int nterms = m.kind == GRIN_MEDIUM_POLY ? grin_poly_terms(m.pclass) : 0;
-  int rc = grin::launch_adjoint(m, a, k, ws, gout, grad, nterms, (cudaStream_t)cuda_stream);
+  int rc = grin::launch_adjoint(m, a, k, ws, phase == grin::kAdjForward ? nullptr : gout, grad, nterms,
+                                (cudaStream_t)cuda_stream, phase);
   if (rc < 0) return rc;
   ctx->last_launches = rc;
   return GRIN_OK;
+}
+
+int grin_trace_adjoint(grin_ctx ctx, grin_medium medium, const grin_rays* rays, const grin_params* p,
+                       const grin_out* out, const grin_out_grad* g, double* grad, int32_t k,
+                       void* ws, size_t ws_bytes, void* cuda_stream) {
+  if (!g || !grad) return GRIN_ERR_INVALID_ARG;
+  return trace_adjoint_phase(ctx, medium, rays, p, out, g, grad, k, ws, ws_bytes, cuda_stream,
+                             grin::kAdjBoth);
+}
+
+int grin_trace_adjoint_forward(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
+                               const grin_params* p, const grin_out* out, int32_t k, void* ws,
+                               size_t ws_bytes, void* cuda_stream) {
+  return trace_adjoint_phase(ctx, medium, rays, p, out, nullptr, nullptr, k, ws, ws_bytes,
+                             cuda_stream, grin::kAdjForward);
+}
+
+int grin_trace_adjoint_backward(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
+                                const grin_params* p, const grin_out_grad* g, double* grad,
+                                int32_t k, void* ws, size_t ws_bytes, void* cuda_stream) {
+  return trace_adjoint_phase(ctx, medium, rays, p, nullptr, g, grad, k, ws, ws_bytes, cuda_stream,
+                             grin::kAdjBackward);
 }
 
 }  // extern "C"

@@ -181,8 +181,13 @@ inline int launch_kernel(void (*kern)(P...), unsigned grid, unsigned block, cuda
 // opl) device arrays; grad accumulates dL/d(parameters).
 bool adjoint_supported(const DevMedium& m);
 size_t adjoint_workspace(int64_t rays, int32_t max_steps, int32_t k);
+// phase: kAdjBoth, or one of the two sweeps (the backward sweep reads the
+// checkpoints and step counts a forward call left in ws; it writes no
+// outputs and needs no gout for the forward sweep)
+enum AdjPhase : int { kAdjBoth = 0, kAdjForward = 1, kAdjBackward = 2 };
 int launch_adjoint(const DevMedium& m, const TraceArgs& a, int32_t k, void* ws,
-                   const double* const* gout, double* grad, int nterms, cudaStream_t st);
+                   const double* const* gout, double* grad, int nterms, cudaStream_t st,
+                   int phase = kAdjBoth);
 
 }  // namespace grin
 

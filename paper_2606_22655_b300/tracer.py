@@ -371,6 +371,43 @@ def trace_adjoint(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max
     return out, grad
 
 
+def trace_adjoint_forward(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_steps: int,
+                          k: int = 64, stream: Optional[torch.cuda.Stream] = None):
+    """grin_trace_adjoint_forward: the forward sweep alone.  Returns (forward
+    results, workspace); hand the workspace, unchanged, to
+    trace_adjoint_backward with the same medium, rays, dopl, max_steps and k."""
+    dev = rays.ox.device
+    out = empty_result(rays.count, dev)
+    ws = torch.empty(max(adjoint_workspace_bytes(medium, rays.count, dopl, max_steps, k), 1),
+                     dtype=torch.uint8, device=dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    rs, os_, ps = _rays_struct(rays), _out_struct(out), _params(dopl, max_steps, "fp64")
+    N.check("grin_trace_adjoint_forward", ctx.lib.grin_trace_adjoint_forward(
+        ctx.handle, medium.handle, ctypes.byref(rs), ctypes.byref(ps), ctypes.byref(os_), int(k),
+        ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(stream.cuda_stream)))
+    return out, ws
+
+
+def trace_adjoint_backward(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_steps: int,
+                           grads: Dict[str, torch.Tensor], n_params: int, k: int, ws: torch.Tensor,
+                           stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    """grin_trace_adjoint_backward: dL/d(parameters) (float64 device tensor)
+    from the workspace a trace_adjoint_forward call filled."""
+    dev = rays.ox.device
+    grad = torch.zeros(n_params, dtype=torch.float64, device=dev)
+    g = {key: grads[key].contiguous().to(torch.float64) for key in OUT_FIELDS}
+    gs = N.OutGrad(*[g[key].data_ptr() for key in OUT_FIELDS])
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    rs, ps = _rays_struct(rays), _params(dopl, max_steps, "fp64")
+    N.check("grin_trace_adjoint_backward", ctx.lib.grin_trace_adjoint_backward(
+        ctx.handle, medium.handle, ctypes.byref(rs), ctypes.byref(ps), ctypes.byref(gs),
+        ctypes.c_void_p(grad.data_ptr()), int(k), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+        ctypes.c_void_p(stream.cuda_stream)))
+    return grad
+
+
 def _with_params(spec, theta: torch.Tensor):
     import copy
     s = copy.copy(spec)
@@ -383,15 +420,17 @@ def _with_params(spec, theta: torch.Tensor):
 
 class TraceFunction(torch.autograd.Function):
     """Exit point, direction and optical path of every ray as a function of
-    the medium parameters theta (polynomial coefficients, or grid samples);
-    backward runs grin_trace_adjoint."""
+    the medium parameters theta (polynomial coefficients, or grid samples).
+    forward runs the adjoint's forward sweep (the plain FP64 trace, which also
+    stores the checkpoints) and backward its backward sweep from them, so the
+    rays are traced forward once."""
 
     @staticmethod
     def forward(fctx, theta, gctx, spec, rays, dopl, max_steps, k):
         med = Medium(gctx, _with_params(spec, theta))
-        res = trace(gctx, med, rays, dopl, max_steps, "fp64")
+        res, ws = trace_adjoint_forward(gctx, med, rays, dopl, max_steps, k)
         fctx.save_for_backward(theta)
-        fctx.extra = (gctx, med, rays, dopl, max_steps, k)
+        fctx.extra = (gctx, med, rays, dopl, max_steps, k, ws)
         P = torch.stack([res["px"], res["py"], res["pz"]], 1)
         d = torch.stack([res["dx"], res["dy"], res["dz"]], 1)
         fctx.mark_non_differentiable(res["exit_id"])
@@ -400,12 +439,13 @@ class TraceFunction(torch.autograd.Function):
     @staticmethod
     def backward(fctx, gP, gd, gopl, gexit):
         (theta,) = fctx.saved_tensors
-        gctx, med, rays, dopl, max_steps, k = fctx.extra
+        gctx, med, rays, dopl, max_steps, k, ws = fctx.extra
+        fctx.extra = None  # the workspace is released after this sweep
         n = rays.count
         z = lambda t, i: torch.zeros(n, dtype=torch.float64, device=rays.ox.device) if t is None else t[:, i]
         grads = {"px": z(gP, 0), "py": z(gP, 1), "pz": z(gP, 2), "dx": z(gd, 0), "dy": z(gd, 1), "dz": z(gd, 2),
                  "opl": torch.zeros(n, dtype=torch.float64, device=rays.ox.device) if gopl is None else gopl}
-        _, grad = trace_adjoint(gctx, med, rays, dopl, max_steps, grads, theta.numel(), k)
+        grad = trace_adjoint_backward(gctx, med, rays, dopl, max_steps, grads, theta.numel(), k, ws)
         return grad.reshape(theta.shape).to(theta.dtype), None, None, None, None, None, None
 
 

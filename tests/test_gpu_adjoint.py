@@ -25,6 +25,18 @@ pytestmark = pytest.mark.gpu
 Z_IMG = 30.0
 H = 1e-6
 REL = 1e-4
+# Rays left out of a coordinate's finite difference: those whose +-h traces
+# change an integer outcome (a step-count tie at the exit face, a TIR that
+# appears or goes), and those whose differences at the two step sizes
+# disagree by more than 1e-4 (a kink of the discrete map within the step:
+# Eq. 9's sgn(N.I) flips where a ray turns, N.I through zero).  The gridded
+# medium loses 0.4 % of ray-coordinate pairs this way; the freeform block,
+# whose rays turn in the field, about 47 % to kinks (and 2 % to integer
+# changes at h = 1e-6): there the oracle's forward-mode tangents, exact
+# derivatives of the same map, check every ray instead (the tangent tests
+# below keep all of them).
+KEPT_FLOOR_GRID = 0.95
+KEPT_FLOOR_POLY = 0.45
 INT_KEYS = ("exit_id", "steps", "tir_internal", "tir_boundary")
 
 
@@ -77,29 +89,43 @@ def per_ray_loss(res, targets):
 def smooth_fd(trace_at, base, targets, steps):
     """Per-ray central differences at the two perturbation sizes `steps`
     (realised parameter deltas returned by trace_at) and the rays whose
-    differences agree to 1e-4; returns (fd per ray at the smaller size,
+    differences agree to 1e-4 beyond their rounding noise (a few ulps of the
+    ray's loss over the step); returns (fd per ray at the smaller size,
     keep)."""
-    fds = []
+    fds, noise = [], []
     keep = np.ones(len(base["exit_id"]), bool)
+    smooth_fd.counts = getattr(smooth_fd, "counts", np.zeros(3, np.int64))
+    eps = np.finfo(np.float64).eps
     for h in steps:
         rp, vp = trace_at(+h)
         rm, vm = trace_at(-h)
         keep &= stable(rp, base) & stable(rm, base)
-        fds.append((per_ray_loss(rp, targets) - per_ray_loss(rm, targets)) / (vp - vm))
+        lp, lm = per_ray_loss(rp, targets), per_ray_loss(rm, targets)
+        fds.append((lp - lm) / (vp - vm))
+        noise.append(64 * eps * (np.abs(lp) + np.abs(lm)) / abs(vp - vm))
     a, b = fds
-    scale = max(np.abs(b).max(), 1e-300)
-    keep &= np.abs(a - b) <= 1e-4 * np.maximum(np.abs(b), 1e-6 * scale)
+    agree = np.abs(a - b) <= 1e-4 * np.abs(b) + noise[0] + noise[1]
+    # tally: rays kept, rays whose integer outcomes change, rays whose two
+    # differences disagree (a kink of the discrete map within the step)
+    smooth_fd.counts += [int((keep & agree).sum()), int((~keep).sum()), int((keep & ~agree).sum())]
+    smooth_fd.kink_margin = np.where(keep & ~agree, base["margins"][:, 1], np.nan)
+    keep &= agree
     return b, keep
 
 
 def check_coordinates(ctx, spec, theta0, rays, targets, dopl, max_steps, coords, trace_at_factory, steps):
     """Per coordinate: FD over the rays smooth for it, and the adjoint of the
-    loss over the same rays.  Returns the largest |adjoint - FD| / sum |FD_r|
-    and the mean fraction of rays kept."""
+    loss over the same rays.  Returns (the largest |adjoint - FD| / sum_r
+    |FD_r|, the largest full-loss error |adjoint - FD| / |FD| over the
+    coordinates whose FD does not cancel, |FD| >= 0.1 sum_r |FD_r|, and the
+    mean fraction of rays kept)."""
     base = oracle.trace(spec, rays.origins, rays.dirs, dopl, max_steps)
     rows = []
+    smooth_fd.counts = np.zeros(3, np.int64)
+    kink_margins = []
     for i in coords:
         fd_ray, keep = smooth_fd(trace_at_factory(i), base, targets, steps)
+        kink_margins.append(smooth_fd.kink_margin)
         fd = float(fd_ray[keep].sum()) / rays.n
         mag = float(np.abs(fd_ray[keep]).sum()) / rays.n
         L, g = adjoint_grad(ctx, spec, theta0, rays, targets, dopl, max_steps, 64, keep)
@@ -107,9 +133,18 @@ def check_coordinates(ctx, spec, theta0, rays, targets, dopl, max_steps, coords,
         rows.append((int(i), fd, float(g[i]), mag, float(keep.mean())))
     rows = [r for r in rows if r[3] > 0]
     errs = [abs(a - f) / m_ for _, f, a, m_, _ in rows]
+    full = [abs(a - f) / abs(f) for _, f, a, m_, _ in rows if abs(f) >= 0.1 * m_]
     k = int(np.argmax(errs))
-    print("worst coordinate (index, fd, adjoint, sum|fd_r|, kept):", rows[k], "error", errs[k])
-    return max(errs), float(np.mean([r[4] for r in rows]))
+    c = smooth_fd.counts / smooth_fd.counts.sum()
+    km = np.concatenate(kink_margins)
+    print("ray-coordinate pairs: kept %.3f, integer outcome changed %.3f, kink within the step %.3f;"
+          " min |N.I| over the kinked rays' steps: median %.2e (all rays: %.2e)"
+          % (c[0], c[1], c[2], np.nanmedian(km) if np.isfinite(km).any() else np.nan,
+             np.median(base["margins"][:, 1])))
+    print("worst coordinate (index, fd, adjoint, sum|fd_r|, kept):", rows[k], "error", errs[k],
+          "| full-loss error over", len(full), "coordinates:", max(full) if full else None,
+          "| kept min", min(r[4] for r in rows))
+    return max(errs), (max(full) if full else 0.0), float(np.mean([r[4] for r in rows]))
 
 
 def test_polynomial_coefficients_against_oracle_fd(ctx):
@@ -127,10 +162,11 @@ def test_polynomial_coefficients_against_oracle_fd(ctx):
             return oracle.trace(mm, rays.origins, rays.dirs, dopl, max_steps), c[i]
         return at
 
-    worst, kept = check_coordinates(ctx, m, m.coeffs, rays, targets, dopl, max_steps,
-                                    range(len(m.coeffs)), factory, (1e-7, 1e-8))
-    assert kept > 0.5, kept
+    worst, full, kept = check_coordinates(ctx, m, m.coeffs, rays, targets, dopl, max_steps,
+                                          range(len(m.coeffs)), factory, (1e-6, 2.5e-7))
+    assert kept > KEPT_FLOOR_POLY, kept
     assert worst <= REL, (worst, kept)
+    assert full <= REL, (full, kept)
 
 
 def test_polynomial_coefficients_against_oracle_tangents(ctx):
@@ -218,10 +254,11 @@ def test_grid_samples_against_oracle_fd(ctx):
         return at
 
     ulp = float(np.spacing(np.float32(1.5)))
-    worst, kept = check_coordinates(ctx, m, theta0, wl.rays, targets, dopl, max_steps, coords, factory,
-                                    (8 * ulp, 2 * ulp))
-    assert kept > 0.5, kept
+    worst, full, kept = check_coordinates(ctx, m, theta0, wl.rays, targets, dopl, max_steps, coords, factory,
+                                          (8 * ulp, 2 * ulp))
+    assert kept > KEPT_FLOOR_GRID, kept
     assert worst <= REL, (worst, kept)
+    assert full <= REL, (full, kept)
 
 
 def test_checkpoint_interval_does_not_change_the_gradient(ctx):
@@ -270,3 +307,28 @@ def test_optical_path_gradient_against_oracle_tangents(ctx):
     print("worst coefficient", int(err.argmax()), "error", float(err.max()), "kept", float(keep.mean()))
     assert keep.mean() > 0.95
     assert err.max() <= 1e-10, (float(err.max()), int(err.argmax()))
+
+
+def test_split_sweeps_equal_the_one_call(ctx):
+    """grin_trace_adjoint_forward then grin_trace_adjoint_backward (what the
+    autograd function runs) against one grin_trace_adjoint call: the forward
+    results bitwise, and equal to grin_trace FP64; the gradient to rounding
+    (its per-ray terms are summed atomically, in no fixed order)."""
+    for spec, rays, n_params in ((W.freeform_block_medium(), W.point_source_rays(2048, W.BASE_SEED + 4), 35),
+                                 (W.blob_workload(n_rays=1024, res=32).medium,
+                                  W.blob_workload(n_rays=1024, res=32).rays, 32 ** 3)):
+        med = tracer.Medium(ctx, spec)
+        rb = tracer.RayBatch.from_numpy(rays.origins, rays.dirs, device="cuda", dtype=torch.float64)
+        gen = torch.Generator(device="cuda").manual_seed(5)
+        grads = {k: torch.randn(rays.n, dtype=torch.float64, device="cuda", generator=gen)
+                 for k in tracer.OUT_FIELDS}
+        out1, g1 = tracer.trace_adjoint(ctx, med, rb, 0.02, 20000, grads, n_params, 16)
+        out2, ws = tracer.trace_adjoint_forward(ctx, med, rb, 0.02, 20000, 16)
+        g2 = tracer.trace_adjoint_backward(ctx, med, rb, 0.02, 20000, grads, n_params, 16, ws)
+        ref = tracer.trace(ctx, med, rb, 0.02, 20000, "fp64")
+        for k in out1:
+            assert torch.equal(out1[k], out2[k]), k
+            assert torch.equal(out2[k], ref[k]), k
+        g1, g2 = g1.cpu().numpy(), g2.cpu().numpy()
+        np.testing.assert_allclose(g2, g1, rtol=1e-12, atol=1e-14 * np.abs(g1).max())
+        med.close()
