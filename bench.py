@@ -143,6 +143,38 @@ def dist_env():
     return ws, rank, local
 
 
+class _Nvml:
+    """The few read-only NVML calls the clock sampler needs, through ctypes on
+    the driver's libnvidia-ml (no Python binding needed)."""
+
+    def __init__(self, cuda_index: int):
+        import ctypes
+        self.c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        bus = None
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(cuda_index)
+            bus = b"%08x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        except Exception:
+            pass
+        if bus is None or self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(self.h)) != 0:
+            if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(cuda_index), ctypes.byref(self.h)) != 0:
+                raise OSError("no NVML handle")
+
+    def sample(self):
+        c = self.c
+        sm, mx, why = c.c_uint(), c.c_uint(), c.c_ulonglong()
+        if (self.lib.nvmlDeviceGetClockInfo(self.h, 1, c.byref(sm)) != 0 or
+                self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, c.byref(mx)) != 0 or
+                self.lib.nvmlDeviceGetCurrentClocksThrottleReasons(self.h, c.byref(why)) != 0):
+            raise OSError("NVML read failed")
+        return sm.value, mx.value, why.value
+
+
 class ClockSampler:
     """SM clock and clock-event (throttle) sampling during the timed region:
     NVML read every 10 ms from a thread (reads only), else nvidia-smi at its
@@ -161,38 +193,25 @@ class ClockSampler:
         self.thread = None
         self.samples = []  # (sm_mhz, max_mhz, reasons bitmask)
 
-    def _nvml_handle(self):
-        import pynvml
-        pynvml.nvmlInit()
-        try:
-            import torch
-            uuid = str(torch.cuda.get_device_properties(self.index).uuid)
-            return pynvml.nvmlDeviceGetHandleByUUID(("GPU-" + uuid) if not uuid.startswith("GPU-") else uuid)
-        except Exception:
-            return pynvml.nvmlDeviceGetHandleByIndex(self.index)
-
     def __enter__(self):
         import threading
         try:
-            import pynvml
-            h = self._nvml_handle()
+            nv = _Nvml(self.index)
+            self.samples.append(nv.sample())
             self.stop = threading.Event()
 
             def run():
-                while True:
+                while not self.stop.wait(0.01):
                     try:
-                        self.samples.append((pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM),
-                                             pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM),
-                                             pynvml.nvmlDeviceGetCurrentClocksThrottleReasons(h)))
-                    except Exception:
-                        break
-                    if self.stop.wait(0.01):
+                        self.samples.append(nv.sample())
+                    except OSError:
                         break
             self.thread = threading.Thread(target=run, daemon=True)
             self.thread.start()
             return self
-        except Exception:
+        except OSError:
             self.thread = None
+            self.samples = []
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
