@@ -39,12 +39,14 @@ enum Kind : int { kNormal = 0, kCrossReflect = 1, kExit = 2 };
 
 struct St {
   double P[3], d[3], n_prev, h;
+  double n_end, g_end[3];  // n and grad n at the last normal step's end point
   int lvl, steps, full, ti, tb, exit_id;
   double frac, opl_ext;
   bool done;
 };
 
-// One iteration of the plain tracer's loop (trace_fp64.cu), on St.
+// One iteration of the plain tracer's loop (trace_fp64.cu), on St.  A
+// normal step leaves n and grad n at its end point in s.n_end and s.g_end.
 template <int PC, bool GRID>
 __device__ __forceinline__ int advance(const DevMedium& m, double dopl, St& s, int& face) {
   using namespace plain;
@@ -77,6 +79,10 @@ __device__ __forceinline__ int advance(const DevMedium& m, double dopl, St& s, i
   double n_i;
   int lvl_i;
   sample<PC, GRID, false>(m, s.P, n_i, g, lvl_i);
+  s.n_end = n_i;
+  s.g_end[0] = g[0];
+  s.g_end[1] = g[1];
+  s.g_end[2] = g[2];
   if (!(isfinite(n_i) && n_i > 0.0)) {
     s.exit_id = GRIN_EXIT_INVALID;
     s.done = true;
@@ -393,19 +399,29 @@ __device__ void cross_back(const DevMedium& m, const double* P, const double* I,
 }
 
 // Back through one normal step from its input state rec (P, I, n_{i-1}, h).
+// have: n0 and (g0, g1, g2) are n and grad n at the step's end point as the
+// forward recompute sampled them (taken by value), else they are sampled
+// here with the same arithmetic; either way the branch decisions below are
+// the forward sweep's.
 template <int PC, bool GRID>
 __device__ void normal_back(const DevMedium& m, double dopl, const double* rec, Adj& lam,
-                            double* acc, double* grad) {
+                            double* acc, double* grad, bool have = false, double n0 = 0.0,
+                            double g0 = 0.0, double g1 = 0.0, double g2 = 0.0) {
   const double* P = rec;
   const double* I = rec + 3;
   const double n_prev = rec[6], h = rec[7];
   double Pn[3];
   for (int k = 0; k < 3; ++k) Pn[k] = P[k] + h * I[k];
-  // n and grad n at P' with the forward step's arithmetic, so that the
-  // branch decisions below are the forward sweep's
   double n, g[3];
-  int lvl;
-  plain::sample<PC, GRID, false>(m, Pn, n, g, lvl);
+  if (have) {
+    n = n0;
+    g[0] = g0;
+    g[1] = g1;
+    g[2] = g2;
+  } else {
+    int lvl;
+    plain::sample<PC, GRID, false>(m, Pn, n, g, lvl);
+  }
   double gn = sqrt(plain::dot3(g, g));
   Adj in = lam;  // adjoint of the state after the step
   Adj out;
@@ -620,7 +636,9 @@ __global__ void __launch_bounds__(128) k_adj_backward(DevMedium m, AdjArgs A) {
   }
   lam.n = lam.h = 0.0;
   const double* ck = A.ckpt + (size_t)r * A.nseg * kCk;
-  double rec[kMaxK][kCk];
+  // each recomputed step's start state (kCk words, the last unused here) and
+  // n, grad n at its end point (4 words)
+  double rec[kMaxK][kCk + 4];
   int kind[kMaxK], fc[kMaxK];
   if (nsteps > 0 && A.k == 1) {
     // every step's start state, case and face were stored: no recompute
@@ -662,6 +680,10 @@ __global__ void __launch_bounds__(128) k_adj_backward(DevMedium m, AdjArgs A) {
         int face = 0;
         kind[i - s0] = advance<PC, GRID>(m, dopl, s, face);
         fc[i - s0] = face;
+        rr[kCk] = s.n_end;
+        rr[kCk + 1] = s.g_end[0];
+        rr[kCk + 2] = s.g_end[1];
+        rr[kCk + 3] = s.g_end[2];
       }
       int i = s1 - 1;
       if (seg == last && exit_id >= 0) {
@@ -672,7 +694,8 @@ __global__ void __launch_bounds__(128) k_adj_backward(DevMedium m, AdjArgs A) {
         if (kind[i - s0] == kCrossReflect)
           reflect_back<PC, GRID>(m, dopl, rec[i - s0], fc[i - s0], fb, lam, acc, A.grad);
         else
-          normal_back<PC, GRID>(m, dopl, rec[i - s0], lam, acc, A.grad);
+          normal_back<PC, GRID>(m, dopl, rec[i - s0], lam, acc, A.grad, true, rec[i - s0][kCk],
+                                rec[i - s0][kCk + 1], rec[i - s0][kCk + 2], rec[i - s0][kCk + 3]);
       }
     }
   }

@@ -332,3 +332,23 @@ def test_split_sweeps_equal_the_one_call(ctx):
         g1, g2 = g1.cpu().numpy(), g2.cpu().numpy()
         np.testing.assert_allclose(g2, g1, rtol=1e-12, atol=1e-14 * np.abs(g1).max())
         med.close()
+
+
+@pytest.mark.parametrize("degree", [2, 6])
+def test_checkpoint_interval_does_not_change_the_gradient_degrees(ctx, degree):
+    """The polynomial classes other than the freeform block's degree 4: the
+    gradient with a checkpoint every 64 steps (segments recomputed), every 7
+    and every step (stored, nothing recomputed) agree to rounding."""
+    base = W.freeform_block_medium()
+    c = W.normal(W.BASE_SEED + 9, degree, W.n_monomials(degree), 0.01)
+    c *= min(1.0, 0.1 / float(np.abs(c).sum()))
+    c[0] += 1.55
+    m = W.Medium(**{**base.__dict__, "degree": degree, "coeffs": c})
+    rays = W.point_source_rays(512, W.BASE_SEED + 4)
+    targets = W.design_targets(rays.n)
+    _, g64 = adjoint_grad(ctx, m, m.coeffs, rays, targets, 0.02, 20000, 64)
+    _, g7 = adjoint_grad(ctx, m, m.coeffs, rays, targets, 0.02, 20000, 7)
+    _, g1 = adjoint_grad(ctx, m, m.coeffs, rays, targets, 0.02, 20000, 1)
+    assert np.abs(g64).max() > 0
+    np.testing.assert_allclose(g7, g64, rtol=1e-12, atol=1e-15 * np.abs(g64).max())
+    np.testing.assert_allclose(g1, g64, rtol=1e-12, atol=1e-15 * np.abs(g64).max())
