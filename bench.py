@@ -651,6 +651,10 @@ def run_ours(args):
         rate, n, dt, orc_idx, orc_res = oracle_rate(wl, 16, threads, rays32)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"every 16th ray of the {wl.rays.n}-ray batch ({n} rays, {dt:.1f} s)"}
+        # the same oracle on one core, on every 256th ray
+        rate1, n1, dt1, _, _ = oracle_rate(wl, 256, 1, rays32)
+        cpu["single_core"] = {"value": rate1, "cores": 1,
+                              "sample": f"every 256th ray ({n1} rays, {dt1:.1f} s)"}
 
     # precision gate: this run's outputs against the plain FP64 GPU tracer
     res32 = tracer.to_numpy(out)
