@@ -301,12 +301,12 @@ int grin_ctx_last_launches(grin_ctx ctx, int32_t* launches);
  * mode through the discrete VRT map of the plain FP64 tracer with its
  * branch decisions held fixed (refraction or TIR at each point, surface
  * crossings, exit).  The forward sweep saves the ray state every
- * checkpoint_every steps in `workspace` (72 bytes a checkpoint); the
+ * checkpoint_every steps in `workspace` (104 bytes a checkpoint); the
  * backward sweep recomputes each segment from its checkpoint and carries the
  * adjoint back through it.  checkpoint_every = 1 stores every step with its
- * case, so the backward sweep recomputes nothing: about twice as fast, for
- * 72 bytes a ray-step of workspace (38 GB for 262,144 rays of up to 2,000
- * steps).  The gradient is the same for every checkpoint_every.
+ * case and the field at its end point, so the backward sweep recomputes
+ * nothing, for 104 bytes a ray-step of workspace (55 GB for 262,144 rays of
+ * up to 2,000 steps).  The gradient is the same for every checkpoint_every.
  * Supported media: box boundary, not layered, and either a polynomial with
  * n = p (gradient w.r.t. its C(degree+3,3) graded-lex coefficients) or a
  * grid (gradient w.r.t. its nx*ny*nz samples, x fastest); others give

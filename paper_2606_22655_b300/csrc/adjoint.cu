@@ -34,7 +34,10 @@ namespace adj {
 constexpr int kMaxK = 64;
 // checkpoint words: P[3], I[3], n_{i-1}, h at the start of a step; with a
 // checkpoint every step (K = 1) also the step's case and face, kind + 4 face
-constexpr int kCk = 9;
+// (word 8), and n, grad n at the end point of a normal step (words kNg ..
+// kNg + 3), which the backward step then takes instead of sampling the field
+constexpr int kCk = 13;
+constexpr int kNg = 9;
 enum Kind : int { kNormal = 0, kCrossReflect = 1, kExit = 2 };
 
 struct St {
@@ -604,7 +607,13 @@ __global__ void __launch_bounds__(128) k_adj_forward(DevMedium m, AdjArgs A) {
         c[7] = s.h;
       }
       const int kind = advance<PC, GRID>(m, A.a.dopl, s, face);
-      if (A.k == 1) c[8] = (double)(kind + 4 * face);
+      if (A.k == 1) {
+        c[8] = (double)(kind + 4 * face);
+        c[kNg] = s.n_end;
+        c[kNg + 1] = s.g_end[0];
+        c[kNg + 2] = s.g_end[1];
+        c[kNg + 3] = s.g_end[2];
+      }
     }
   }
   double opl = s.opl_ext + A.a.dopl * (double)s.full + A.a.dopl * s.frac;
@@ -636,9 +645,9 @@ __global__ void __launch_bounds__(128) k_adj_backward(DevMedium m, AdjArgs A) {
   }
   lam.n = lam.h = 0.0;
   const double* ck = A.ckpt + (size_t)r * A.nseg * kCk;
-  // each recomputed step's start state (kCk words, the last unused here) and
-  // n, grad n at its end point (4 words)
-  double rec[kMaxK][kCk + 4];
+  // each recomputed step's start state and n, grad n at its end point, in
+  // the checkpoint's word layout
+  double rec[kMaxK][kCk];
   int kind[kMaxK], fc[kMaxK];
   if (nsteps > 0 && A.k == 1) {
     // every step's start state, case and face were stored: no recompute
@@ -650,7 +659,8 @@ __global__ void __launch_bounds__(128) k_adj_backward(DevMedium m, AdjArgs A) {
       else if (kd == kCrossReflect)
         reflect_back<PC, GRID>(m, dopl, c, face, fb, lam, acc, A.grad);
       else
-        normal_back<PC, GRID>(m, dopl, c, lam, acc, A.grad);
+        normal_back<PC, GRID>(m, dopl, c, lam, acc, A.grad, true, c[kNg], c[kNg + 1], c[kNg + 2],
+                              c[kNg + 3]);
     }
   } else if (nsteps > 0) {
     const int last = (nsteps - 1) / A.k;
@@ -680,10 +690,10 @@ __global__ void __launch_bounds__(128) k_adj_backward(DevMedium m, AdjArgs A) {
         int face = 0;
         kind[i - s0] = advance<PC, GRID>(m, dopl, s, face);
         fc[i - s0] = face;
-        rr[kCk] = s.n_end;
-        rr[kCk + 1] = s.g_end[0];
-        rr[kCk + 2] = s.g_end[1];
-        rr[kCk + 3] = s.g_end[2];
+        rr[kNg] = s.n_end;
+        rr[kNg + 1] = s.g_end[0];
+        rr[kNg + 2] = s.g_end[1];
+        rr[kNg + 3] = s.g_end[2];
       }
       int i = s1 - 1;
       if (seg == last && exit_id >= 0) {
@@ -694,8 +704,8 @@ __global__ void __launch_bounds__(128) k_adj_backward(DevMedium m, AdjArgs A) {
         if (kind[i - s0] == kCrossReflect)
           reflect_back<PC, GRID>(m, dopl, rec[i - s0], fc[i - s0], fb, lam, acc, A.grad);
         else
-          normal_back<PC, GRID>(m, dopl, rec[i - s0], lam, acc, A.grad, true, rec[i - s0][kCk],
-                                rec[i - s0][kCk + 1], rec[i - s0][kCk + 2], rec[i - s0][kCk + 3]);
+          normal_back<PC, GRID>(m, dopl, rec[i - s0], lam, acc, A.grad, true, rec[i - s0][kNg],
+                                rec[i - s0][kNg + 1], rec[i - s0][kNg + 2], rec[i - s0][kNg + 3]);
       }
     }
   }
