@@ -499,9 +499,9 @@ def timed_trace(ctx, med, rays, wl, precision, out, reps: int = 1):
 
 
 def config_rates(ctx, dev, peaks):
-    """Config 1 (Luneburg lens, 4,096 rays): the mixed tracer against the
-    plain and fast FP64 tracers.  Config 3 (256^3 blob grid and its 32
-    shells, 4,194,304 rays): the mixed tracer's rate, its FP32 FLOP rate
+    """The Luneburg lens (4,096 rays): the mixed tracer against the plain
+    and fast FP64 tracers.  The 256^3 blob grid and its 32 shells
+    (4,194,304 rays): the mixed tracer's rate, its FP32 FLOP rate
     against the measured FMA peak, and the cache traffic of its tap cache:
     256 B of shared memory a ray-step, and from L2 the 256 B of a refill on
     the 4.8 % of ray-steps that enter a new cell (ncu, 262,144 rays)."""
