@@ -319,6 +319,16 @@ struct Cfg {
                                                    const float* col, float lb, float& nu,
                                                    float& gx, float& gy, float& gz, int& lvl,
                                                    float* uo = nullptr) {
+    float f;
+    taps_field(m, fr, col, lb, f, gx, gy, gz);
+    level(m, f, nu, lvl, uo);
+  }
+
+  // The smooth field f = n - base and its gradient from the cached taps (the
+  // part of eval_taps before the level).
+  static __device__ __forceinline__ void taps_field(const DevMedium& m, const float* fr,
+                                                    const float* col, float lb, float& f,
+                                                    float& gx, float& gy, float& gz) {
     float w[3][4], dw[3][4];
 #pragma unroll
     for (int k = 0; k < 3; ++k) cr_w(fr[k], w[k], dw[k]);
@@ -352,7 +362,7 @@ struct Cfg {
     gx = GX * m.inv_spacing_f[0];
     gy = GY * m.inv_spacing_f[1];
     gz = GZ * m.inv_spacing_f[2];
-    level(m, V + (lb - m.base_f), nu, lvl, uo);
+    f = V + (lb - m.base_f);
   }
 
   static __device__ __forceinline__ bool inside(const DevMedium& m, const float* q) {
@@ -844,6 +854,37 @@ __device__ __forceinline__ void field64(const DevMedium& m, V3 p, float& f, floa
            (float)(p.z - (double)hz), f, g[0], g[1], g[2]);
 }
 
+// The thread's tap cache as the out-of-line step sees it: its column, the
+// centre tap and the cell it holds (col == nullptr: no cache).
+struct TapView {
+  const float* col = nullptr;
+  float lb = 0.0f;
+  int kx = 0, ky = 0, kz = 0;
+};
+
+// field64 from the tap cache when the point lies in the cached cell (the
+// same bits, see eval_taps), else from the grid.
+template <class C>
+__device__ __forceinline__ void field64c(const DevMedium& m, V3 p, float& f, float* g,
+                                         const TapView& tv) {
+  if constexpr (C::kGrid) {
+    if (tv.col) {
+      const float ph[3] = {(float)p.x, (float)p.y, (float)p.z};
+      const float pl[3] = {(float)(p.x - (double)ph[0]), (float)(p.y - (double)ph[1]),
+                           (float)(p.z - (double)ph[2])};
+      int i0[3];
+      float fr[3];
+      C::cell(m, ph, pl, i0, fr);
+      if (i0[0] == tv.kx && i0[1] == tv.ky && i0[2] == tv.kz)
+        C::taps_field(m, fr, tv.col, tv.lb, f, g[0], g[1], g[2]);
+      else
+        C::grid_gather(m, i0, fr, f, g[0], g[1], g[2]);
+      return;
+    }
+  }
+  field64<C>(m, p, f, g);
+}
+
 // Shell crossings within one step, at most (GRIN_TRACE_LEVEL_ROOT): a ray
 // grazing a curved shell boundary can cross it back and forth at ever shorter
 // intervals; after this many the rest of the step runs straight into the
@@ -864,7 +905,7 @@ constexpr int kMaxCrossings = 16;
 template <class C>
 __device__ __forceinline__ bool level_root_step(const DevMedium& m, const TraceArgs& a, int64_t r,
                                                 RayF& s, float dopl_f, const float* qh,
-                                                const float* ql) {
+                                                const float* ql, const TapView& tv) {
   const V3 p = pos64(s);
   const V3 q = mk((double)qh[0] + (double)ql[0], (double)qh[1] + (double)ql[1],
                   (double)qh[2] + (double)ql[2]);
@@ -879,7 +920,7 @@ __device__ __forceinline__ bool level_root_step(const DevMedium& m, const TraceA
   }
   float fE, gE[3], nuE;
   int lE;
-  field64<C>(m, e, fE, gE);
+  field64c<C>(m, e, fE, gE, tv);
   C::level(m, fE, nuE, lE);
   if (lE != s.lvl_prev && s.xc == kMaxCrossings) {
     s.lvl_prev = lE;
@@ -920,7 +961,7 @@ __device__ __forceinline__ bool level_root_step(const DevMedium& m, const TraceA
   const double L = (double)m.n_levels;
   const double fb = (m.lvl_lo - m.base) + (double)(up ? k + 1 : k) * m.lvl_span / L;
   float fP, gX[3];
-  field64<C>(m, p, fP, gX);
+  field64c<C>(m, p, fP, gX, tv);
   const V3 seg = mk(e.x - p.x, e.y - p.y, e.z - p.z);
   double lo = 0.0, hi = 1.0;
   const double a0 = (double)fP - fb, a1 = (double)fE - fb;
@@ -929,7 +970,7 @@ __device__ __forceinline__ bool level_root_step(const DevMedium& m, const TraceA
   V3 x = axpy(t, seg, p);
   for (int it = 0; it < 10; ++it) {
     float fX;
-    field64<C>(m, x, fX, gX);
+    field64c<C>(m, x, fX, gX, tv);
     const double phi = (double)fX - fb;
     if (up ? phi < 0.0 : phi >= 0.0) lo = t;
     else hi = t;
@@ -978,7 +1019,7 @@ __device__ __forceinline__ bool level_root_step(const DevMedium& m, const TraceA
 // it does not handle.
 template <class C, bool LAYERED>
 __device__ __noinline__ bool step_slow(const DevMedium& m, const TraceArgs& a, int64_t r,
-                                       RayF& s, float dopl_f) {
+                                       RayF& s, float dopl_f, TapView tv = TapView()) {
   // the exact pair form of step_point, on a normalised position
   if constexpr (C::kLazyPos) norm_pos(s);
   float qh[3], ql[3], dv[3];
@@ -991,7 +1032,7 @@ __device__ __noinline__ bool step_slow(const DevMedium& m, const TraceArgs& a, i
     qh[k] = t;
   }
   if constexpr (LAYERED)
-    if (a.flags & GRIN_TRACE_LEVEL_ROOT) return level_root_step<C>(m, a, r, s, dopl_f, qh, ql);
+    if (a.flags & GRIN_TRACE_LEVEL_ROOT) return level_root_step<C>(m, a, r, s, dopl_f, qh, ql, tv);
   mg_take<C>(s, 2, bnd_margin<C>(m, qh, s.h));
   if (GRIN_UNLIKELY(!C::inside(m, qh))) {
     int rc = surface_event<C>(m, a, r, s, dopl_f, qh);
@@ -1127,7 +1168,8 @@ template <class C, bool LAYERED>
 __device__ __forceinline__ bool step_from(const DevMedium& m, const TraceArgs& a, int64_t r,
                                           RayF& s, float dopl_f, const float* qh,
                                           const float* ql, float nu_i,
-                                          const float* g, int lvl_i, float u_i = 0.5f) {
+                                          const float* g, int lvl_i, float u_i = 0.5f,
+                                          const TapView& tv = TapView()) {
   const bool in = C::inside(m, qh);
   const float n_i = m.base_f + nu_i;
   // (the fast step's two divisions take the approximate reciprocal without
@@ -1165,7 +1207,7 @@ __device__ __forceinline__ bool step_from(const DevMedium& m, const TraceArgs& a
     // out of line, on a copy: only the copy's address escapes, the live
     // state stays in registers
     RayF t = s;
-    bool alive = step_slow<C, LAYERED>(m, a, r, t, dopl_f);
+    bool alive = step_slow<C, LAYERED>(m, a, r, t, dopl_f, tv);
     s = t;
     return alive;
   }
@@ -1287,7 +1329,16 @@ __device__ __forceinline__ unsigned run_quantum(const DevMedium& m, const TraceA
         float nu_i, g[3], u_i = 0.5f;
         int lvl_i;
         C::eval_taps(m, fr, col, lb, nu_i, g[0], g[1], g[2], lvl_i, C::kMG ? &u_i : nullptr);
-        active = step_from<C, LAYERED>(m, a, ray, s, dopl_f, qh, ql, nu_i, g, lvl_i, u_i);
+        TapView tv;
+        if constexpr (LAYERED) {
+          // (only the shell-crossing solve reads it)
+          tv.col = col;
+          tv.lb = lb;
+          tv.kx = key[0];
+          tv.ky = key[1];
+          tv.kz = key[2];
+        }
+        active = step_from<C, LAYERED>(m, a, ray, s, dopl_f, qh, ql, nu_i, g, lvl_i, u_i, tv);
         if (!active) ++ended;
       }
     }
