@@ -294,6 +294,35 @@ int grin_trace_path(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
  * grin_trace_path call on this context (for accounting). */
 int grin_ctx_last_launches(grin_ctx ctx, int32_t* launches);
 
+/* Summary of a trace's results, for logging and monitoring.  `out` holds
+ * the results of `count` rays (device arrays, as grin_trace wrote them);
+ * they are reduced on the device on cuda_stream and the totals copied back,
+ * so the call synchronises that stream.
+ *   rays, ray_steps: count and the sum of the step counts;
+ *   exit_face[f]: rays that left through face f (exit id 0..5), and the
+ *     rays of each other exit id;
+ *   tir_internal, tir_boundary: sums of the TIR counts;
+ *   flagged: rays with any of the four decision margins (grin_out.margin,
+ *     which must then be set) below the matching entry of margin_min (four
+ *     thresholds), or -1 when margin_min is NULL;
+ *   elapsed_ms: device time of the most recent grin_trace call on this
+ *     context (for grin_trace_host, the trace of its last chunk), from CUDA
+ *     events recorded on its stream around its kernels (-1 if it recorded
+ *     none: a capturing stream, or no call yet).
+ * Errors: GRIN_ERR_INVALID_ARG for a null pointer among the arrays it
+ * reads, a negative count, or margin_min without out->margin. */
+typedef struct {
+  int64_t rays, ray_steps;
+  int64_t exit_face[6];
+  int64_t exit_miss, exit_entry_reflect, exit_max_steps, exit_invalid;
+  int64_t tir_internal, tir_boundary;
+  int64_t flagged;
+  double elapsed_ms;
+} grin_trace_stats;
+int grin_trace_stats_compute(grin_ctx ctx, const grin_out* out, int64_t count,
+                             const double* margin_min, grin_trace_stats* stats,
+                             void* cuda_stream);
+
 /* ------------------------------------------------------------ adjoint
  *
  * Gradient of a loss of the exit states with respect to the medium

@@ -66,6 +66,14 @@ class OutGrad(ctypes.Structure):
     _fields_ = [("px", _vp), ("py", _vp), ("pz", _vp), ("dx", _vp), ("dy", _vp), ("dz", _vp), ("opl", _vp)]
 
 
+class TraceStats(ctypes.Structure):
+    _fields_ = [("rays", ctypes.c_int64), ("ray_steps", ctypes.c_int64), ("exit_face", ctypes.c_int64 * 6),
+                ("exit_miss", ctypes.c_int64), ("exit_entry_reflect", ctypes.c_int64),
+                ("exit_max_steps", ctypes.c_int64), ("exit_invalid", ctypes.c_int64),
+                ("tir_internal", ctypes.c_int64), ("tir_boundary", ctypes.c_int64),
+                ("flagged", ctypes.c_int64), ("elapsed_ms", ctypes.c_double)]
+
+
 class ServeConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("step_quantum", ctypes.c_int32),
                 ("max_slots_per_job", ctypes.c_int32)]
@@ -107,6 +115,8 @@ def load() -> ctypes.CDLL:
         "grin_trace_path": (ctypes.c_int, [_vp, _vp, P(Rays), P(Params), P(Out), _vp, ctypes.c_int64,
                                            _vp, _vp]),
         "grin_ctx_last_launches": (ctypes.c_int, [_vp, P(ctypes.c_int32)]),
+        "grin_trace_stats_compute": (ctypes.c_int, [_vp, P(Out), ctypes.c_int64, P(ctypes.c_double),
+                                                    P(TraceStats), _vp]),
         "grin_trace_host_static": (ctypes.c_int, [P(MediumDesc), P(Rays), P(Params), P(Out), _vp]),
         "grin_trace_adjoint_workspace_size": (ctypes.c_int, [_vp, ctypes.c_int64, P(Params), ctypes.c_int32,
                                                              P(ctypes.c_size_t)]),

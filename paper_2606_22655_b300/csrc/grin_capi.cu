@@ -365,6 +365,9 @@ int grin_ctx_destroy(grin_ctx ctx) {
     if (h) cudaStreamDestroy(h);
   for (cudaEvent_t e : ctx->hev)
     if (e) cudaEventDestroy(e);
+  if (ctx->stats) cudaFree(ctx->stats);
+  for (cudaEvent_t e : ctx->tev)
+    if (e) cudaEventDestroy(e);
   delete ctx;
   return GRIN_OK;
 }
@@ -495,12 +498,45 @@ int grin_trace_path(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
   return GRIN_OK;
 }
 
+// The timing events of grin_trace (created once); false if unavailable.
+static bool trace_events(grin_ctx ctx) {
+  if (ctx->tev[0]) return true;
+  if (cudaEventCreate(&ctx->tev[0]) == cudaSuccess && cudaEventCreate(&ctx->tev[1]) == cudaSuccess)
+    return true;
+  cudaGetLastError();
+  for (cudaEvent_t& e : ctx->tev)
+    if (e) cudaEventDestroy(e), e = nullptr;
+  return false;
+}
+
+static int trace_launches(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
+                          const grin_params* p, const grin_out* out, cudaStream_t s);
+
 int grin_trace(grin_ctx ctx, grin_medium medium, const grin_rays* rays, const grin_params* p,
                const grin_out* out, void* cuda_stream) {
   int st = check_trace_args(ctx, medium, rays, p, out);
   if (st != GRIN_OK) return st;
   ctx->last_launches = 0;
+  ctx->timed = false;
   if (rays->count == 0) return GRIN_OK;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // device time of the call, from events around its kernels (not on a
+  // capturing stream, where a recorded event would become part of a graph)
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const bool timed = cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
+                     cap == cudaStreamCaptureStatusNone && trace_events(ctx) &&
+                     cudaEventRecord(ctx->tev[0], s) == cudaSuccess;
+  cudaGetLastError();
+  const int rc = trace_launches(ctx, medium, rays, p, out, s);
+  if (rc < 0) return rc;
+  ctx->timed = timed && cudaEventRecord(ctx->tev[1], s) == cudaSuccess;
+  ctx->last_launches = rc;
+  return GRIN_OK;
+}
+
+// grin_trace's kernels: the number launched, or a negative grin_status.
+static int trace_launches(grin_ctx ctx, grin_medium medium, const grin_rays* rays,
+                          const grin_params* p, const grin_out* out, cudaStream_t s) {
   grin::TraceArgs a;
   a.ox = rays->ox;
   a.oy = rays->oy;
@@ -525,7 +561,6 @@ int grin_trace(grin_ctx ctx, grin_medium medium, const grin_rays* rays, const gr
   a.max_steps = p->max_steps;
   a.flags = p->flags;
   a.margin = out->margin;
-  cudaStream_t s = (cudaStream_t)cuda_stream;
   int rc;
   if (p->precision == GRIN_PREC_FP64) {
     rc = grin::launch_fp64(medium->dm, a, s, ctx->sm_count);
@@ -557,8 +592,52 @@ int grin_trace(grin_ctx ctx, grin_medium medium, const grin_rays* rays, const gr
     if (order) cudaFreeAsync(order, s);
     if (rc >= 0) rc += lo;
   }
-  if (rc < 0) return rc;
-  ctx->last_launches = rc;
+  return rc;
+}
+
+int grin_trace_stats_compute(grin_ctx ctx, const grin_out* out, int64_t count,
+                             const double* margin_min, grin_trace_stats* stats,
+                             void* cuda_stream) {
+  if (!ctx || !out || !stats || count < 0) return GRIN_ERR_INVALID_ARG;
+  if (count > 0 && (!out->exit_id || !out->steps || !out->tir_internal || !out->tir_boundary))
+    return GRIN_ERR_INVALID_ARG;
+  if (margin_min && !out->margin) return GRIN_ERR_INVALID_ARG;
+  cudaSetDevice(ctx->device);
+  if (!ctx->stats &&
+      cudaMalloc(&ctx->stats, grin::kStatWords * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->stats = nullptr;
+    return GRIN_ERR_OOM;
+  }
+  grin::TraceArgs a{};
+  a.count = count;
+  a.exit_id = out->exit_id;
+  a.steps = out->steps;
+  a.tir_i = out->tir_internal;
+  a.tir_b = out->tir_boundary;
+  a.margin = out->margin;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (grin::launch_stats(a, margin_min, ctx->stats, s) < 0) return GRIN_ERR_CUDA;
+  unsigned long long w[grin::kStatWords];
+  if (cudaMemcpyAsync(w, ctx->stats, sizeof(w), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return GRIN_ERR_CUDA;
+  stats->rays = (int64_t)w[0];
+  stats->ray_steps = (int64_t)w[1];
+  for (int f = 0; f < 6; ++f) stats->exit_face[f] = (int64_t)w[2 + f];
+  stats->exit_miss = (int64_t)w[8];
+  stats->exit_entry_reflect = (int64_t)w[9];
+  stats->exit_max_steps = (int64_t)w[10];
+  stats->exit_invalid = (int64_t)w[11];
+  stats->tir_internal = (int64_t)w[12];
+  stats->tir_boundary = (int64_t)w[13];
+  stats->flagged = margin_min ? (int64_t)w[14] : -1;
+  stats->elapsed_ms = -1.0;
+  float ms = 0.0f;
+  if (ctx->timed && cudaEventSynchronize(ctx->tev[1]) == cudaSuccess &&
+      cudaEventElapsedTime(&ms, ctx->tev[0], ctx->tev[1]) == cudaSuccess)
+    stats->elapsed_ms = ms;
+  cudaGetLastError();
   return GRIN_OK;
 }
 

@@ -185,6 +185,11 @@ size_t adjoint_workspace(int64_t rays, int32_t max_steps, int32_t k);
 // checkpoints and step counts a forward call left in ws; it writes no
 // outputs and needs no gout for the forward sweep)
 enum AdjPhase : int { kAdjBoth = 0, kAdjForward = 1, kAdjBackward = 2 };
+// grin_trace_stats_compute's reduction: kStatWords totals (see grin_stats.cu)
+// into the zeroed device words `acc`
+constexpr int kStatWords = 16;
+int launch_stats(const TraceArgs& a, const double* margin_min, unsigned long long* acc,
+                 cudaStream_t st);
 int launch_adjoint(const DevMedium& m, const TraceArgs& a, int32_t k, void* ws,
                    const double* const* gout, double* grad, int nterms, cudaStream_t st,
                    int phase = kAdjBoth);
@@ -214,6 +219,11 @@ struct grin_ctx_s {
   // and an event marking the caller's stream
   cudaStream_t hs[4] = {};
   cudaEvent_t hev[2 * grin::kHostChunks + 1] = {};
+  // grin_trace_stats_compute: its device totals, and the timing events of
+  // the last grin_trace call (created on first use; timed = both recorded)
+  unsigned long long* stats = nullptr;
+  cudaEvent_t tev[2] = {};
+  bool timed = false;
 };
 
 struct grin_medium_s {

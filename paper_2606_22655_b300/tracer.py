@@ -371,6 +371,26 @@ def trace_adjoint(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max
     return out, grad
 
 
+def trace_stats(ctx: Context, out: Dict[str, torch.Tensor], margin_min=None,
+                stream: Optional[torch.cuda.Stream] = None) -> Dict[str, object]:
+    """grin_trace_stats_compute on a result dict of trace(): totals of the
+    rays' outcomes (and, with margin_min, four thresholds, the rays flagged
+    by their margins), plus the device time of the context's last trace."""
+    n = int(out["exit_id"].numel())
+    dev = out["exit_id"].device
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    st = N.TraceStats()
+    mm = None if margin_min is None else (ctypes.c_double * 4)(*[float(v) for v in margin_min])
+    N.check("grin_trace_stats_compute", ctx.lib.grin_trace_stats_compute(
+        ctx.handle, ctypes.byref(_out_struct(out)), n, mm, ctypes.byref(st), ctypes.c_void_p(stream.cuda_stream)))
+    return {"rays": st.rays, "ray_steps": st.ray_steps, "exit_face": list(st.exit_face),
+            "exit_miss": st.exit_miss, "exit_entry_reflect": st.exit_entry_reflect,
+            "exit_max_steps": st.exit_max_steps, "exit_invalid": st.exit_invalid,
+            "tir_internal": st.tir_internal, "tir_boundary": st.tir_boundary,
+            "flagged": st.flagged, "elapsed_ms": st.elapsed_ms}
+
+
 def trace_adjoint_forward(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_steps: int,
                           k: int = 64, stream: Optional[torch.cuda.Stream] = None):
     """grin_trace_adjoint_forward: the forward sweep alone.  Returns (forward

@@ -45,6 +45,7 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert lib.grin_medium_destroy(None) == -1
     assert lib.grin_trace(None, None, None, None, None, None) == -1
     assert lib.grin_trace_host(None, None, None, None, None, None) == -1
+    assert lib.grin_trace_stats_compute(None, None, 0, None, None, None) == -1
 
 
 def test_struct_sizes_match_c_layout(tmp_path):
@@ -55,7 +56,8 @@ def test_struct_sizes_match_c_layout(tmp_path):
                "grin_params": (N.Params, ["precision", "flags"]),
                "grin_medium_desc": (N.MediumDesc, ["grid_on_device", "n_levels", "boundary", "n_ext"]),
                "grin_serve_config": (N.ServeConfig, ["max_slots_per_job"]),
-               "grin_serve_counters": (N.ServeCounters, ["ray_steps", "jobs_running"])}
+               "grin_serve_counters": (N.ServeCounters, ["ray_steps", "jobs_running"]),
+               "grin_trace_stats": (N.TraceStats, ["exit_face", "exit_invalid", "flagged", "elapsed_ms"])}
     src = ["#include <stdio.h>", "#include <stddef.h>", '#include "grin.h"', "int main(void) {"]
     for c, (_, fields) in structs.items():
         src.append(f'  printf("{c} %zu\\n", sizeof({c}));')
