@@ -336,10 +336,11 @@ int grin_trace_stats_compute(grin_ctx ctx, const grin_out* out, int64_t count,
  * case and the field at its end point, so the backward sweep recomputes
  * nothing, for 104 bytes a ray-step of workspace (55 GB for 262,144 rays of
  * up to 2,000 steps).  The gradient is the same for every checkpoint_every.
- * Supported media: box boundary, not layered, and either a polynomial with
- * n = p (gradient w.r.t. its C(degree+3,3) graded-lex coefficients) or a
- * grid (gradient w.r.t. its nx*ny*nz samples, x fastest); others give
- * GRIN_ERR_NOT_IMPLEMENTED. */
+ * Supported media: a box, sphere or cylinder boundary, not layered, and
+ * either a polynomial with n = p, sqrt(p) or form_c / p (gradient w.r.t. its
+ * C(degree+3,3) graded-lex coefficients) or a grid (gradient w.r.t. its
+ * nx*ny*nz samples, x fastest); layered, spherical-freeform and N2P media
+ * give GRIN_ERR_NOT_IMPLEMENTED. */
 
 /* dL/d(exit state): device FP64 arrays of `count` entries each (the same
  * fields as grin_out; any may be NULL for zero). */

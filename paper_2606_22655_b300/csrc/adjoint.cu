@@ -175,6 +175,12 @@ __device__ bool start(const DevMedium& m, const TraceArgs& a, int64_t r, St& s, 
   return true;
 }
 
+// a . b with fused multiply-adds (reverse-mode arithmetic only: the forward
+// sweep keeps plain::dot3's unfused rounding)
+__device__ __forceinline__ double fdot3(const double* a, const double* b) {
+  return fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
+}
+
 // ------------------------------------------------------ field derivatives
 
 // At P: n, grad n and the Hessian (xx, yy, zz, xy, xz, yz), then, with the
@@ -270,7 +276,7 @@ __device__ void field_h_adj(const DevMedium& m, const double* P, double nb, cons
         }
       }
     }
-  } else {
+  } else if (m.form == GRIN_FORM_LINEAR) {
     const double* is = m.inv_scale;
     double x[3];
     for (int k = 0; k < 3; ++k) x[k] = (P[k] - m.off[k]) * is[k];
@@ -313,6 +319,84 @@ __device__ void field_h_adj(const DevMedium& m, const double* P, double nb, cons
     H[3] *= is[0] * is[1];
     H[4] *= is[0] * is[2];
     H[5] *= is[1] * is[2];
+  } else {
+    // n = sqrt(p) or n = form_c / p: p, grad p and its Hessian first (the
+    // first pass), then n's, and the adjoints of p and grad p that n's value
+    // and gradient give (the second pass puts them on the coefficients)
+    const double* is = m.inv_scale;
+    double x[3];
+    for (int k = 0; k < 3; ++k) x[k] = (P[k] - m.off[k]) * is[k];
+    double pw[3][PC + 1];
+    for (int k = 0; k < 3; ++k) {
+      pw[k][0] = 1.0;
+      for (int e = 1; e <= PC; ++e) pw[k][e] = pw[k][e - 1] * x[k];
+    }
+    double p = 0.0, gp[3] = {0.0, 0.0, 0.0}, Hp[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    int idx = 0;
+    for (int s = 0; s <= PC; ++s)
+      for (int i = s; i >= 0; --i)
+        for (int j = s - i; j >= 0; --j) {
+          const int k = s - i - j;
+          const double c = m.cglex[idx++];
+          if (c == 0.0) continue;
+          const double X = pw[0][i], Y = pw[1][j], Z = pw[2][k];
+          const double dX = i ? i * pw[0][i - 1] : 0.0, dY = j ? j * pw[1][j - 1] : 0.0,
+                       dZ = k ? k * pw[2][k - 1] : 0.0;
+          const double ddX = i > 1 ? i * (i - 1) * pw[0][i - 2] : 0.0;
+          const double ddY = j > 1 ? j * (j - 1) * pw[1][j - 2] : 0.0;
+          const double ddZ = k > 1 ? k * (k - 1) * pw[2][k - 2] : 0.0;
+          const double YZ = Y * Z, XZ = X * Z, XY = X * Y;
+          p = fma(c, X * YZ, p);
+          gp[0] = fma(c, dX * YZ, gp[0]);
+          gp[1] = fma(c, dY * XZ, gp[1]);
+          gp[2] = fma(c, dZ * XY, gp[2]);
+          Hp[0] = fma(c, ddX * YZ, Hp[0]);
+          Hp[1] = fma(c, ddY * XZ, Hp[1]);
+          Hp[2] = fma(c, ddZ * XY, Hp[2]);
+          Hp[3] = fma(c, dX * dY * Z, Hp[3]);
+          Hp[4] = fma(c, dX * dZ * Y, Hp[4]);
+          Hp[5] = fma(c, dY * dZ * X, Hp[5]);
+        }
+    for (int k = 0; k < 3; ++k) gp[k] *= is[k];
+    Hp[0] *= is[0] * is[0];
+    Hp[1] *= is[1] * is[1];
+    Hp[2] *= is[2] * is[2];
+    Hp[3] *= is[0] * is[1];
+    Hp[4] *= is[0] * is[2];
+    Hp[5] *= is[1] * is[2];
+    const int hi[6] = {0, 1, 2, 0, 0, 1}, hj[6] = {0, 1, 2, 1, 2, 2};
+    const double gbp = fdot3(gb, gp);
+    double pb, gscale;  // dL/dp, and dL/d(grad p) = gscale * gb
+    if (m.form == GRIN_FORM_SQRT) {
+      // n = sqrt(p): grad n = grad p / 2n, H_n = H_p / 2n - grad p grad p^T / 4n^3
+      n = sqrt(p);
+      const double i2n = 0.5 / n, i4n3 = 0.25 / (n * n * n);
+      for (int k = 0; k < 3; ++k) g[k] = gp[k] * i2n;
+      for (int q = 0; q < 6; ++q) H[q] = fma(Hp[q], i2n, -gp[hi[q]] * gp[hj[q]] * i4n3);
+      pb = fma(nb, i2n, -gbp * i4n3);
+      gscale = i2n;
+    } else {
+      // n = C / p: grad n = -C grad p / p^2, H_n = -C H_p / p^2 + 2 C grad p grad p^T / p^3
+      const double C = m.form_c, ip = 1.0 / p, cp2 = C * ip * ip, c2p3 = 2.0 * cp2 * ip;
+      n = C * ip;
+      for (int k = 0; k < 3; ++k) g[k] = -cp2 * gp[k];
+      for (int q = 0; q < 6; ++q) H[q] = fma(-cp2, Hp[q], c2p3 * gp[hi[q]] * gp[hj[q]]);
+      pb = fma(-cp2, nb, c2p3 * gbp);
+      gscale = -cp2;
+    }
+    const double gx = gscale * gb[0] * is[0], gy = gscale * gb[1] * is[1],
+                 gz = gscale * gb[2] * is[2];
+    idx = 0;
+    for (int s = 0; s <= PC; ++s)
+      for (int i = s; i >= 0; --i)
+        for (int j = s - i; j >= 0; --j) {
+          const int k = s - i - j;
+          const double X = pw[0][i], Y = pw[1][j], Z = pw[2][k];
+          const double dX = i ? i * pw[0][i - 1] : 0.0, dY = j ? j * pw[1][j - 1] : 0.0,
+                       dZ = k ? k * pw[2][k - 1] : 0.0;
+          const double YZ = Y * Z, XZ = X * Z, XY = X * Y;
+          acc[idx++] += fma(pb, X * YZ, fma(gx, dX * YZ, fma(gy, dY * XZ, gz * dZ * XY)));
+        }
   }
 }
 
@@ -321,12 +405,6 @@ __device__ void field_h_adj(const DevMedium& m, const double* P, double nb, cons
 struct Adj {
   double P[3], d[3], n, h;  // dL/dP, dL/dI, dL/dn_{i-1}, dL/dh
 };
-
-// a . b with fused multiply-adds (reverse-mode arithmetic only: the forward
-// sweep keeps plain::dot3's unfused rounding)
-__device__ __forceinline__ double fdot3(const double* a, const double* b) {
-  return fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
-}
 
 // Back through R -> R / |R| given the unit result u and 1 / |R|.
 __device__ __forceinline__ void unit_back(const double* u, double inv_Rn, const double* ub, double* Rb) {
@@ -398,6 +476,78 @@ __device__ void cross_back(const DevMedium& m, const double* P, const double* I,
   for (int k = 0; k < 3; ++k) {
     lam.h += Db[k] * I[k];
     lam.d[k] += h * Db[k];
+  }
+}
+
+// The surface geometry of a crossing at P_b on face `face`: r, a normal
+// direction of the surface's implicit function there (so that r . dP_b = 0
+// along the surface), |r|, and for a plane face its axis, whose coordinate
+// the forward sweep sets to the plane's exactly (-1 for a curved face, whose
+// unit normal N = r / |r| moves with P_b).
+struct CrossGeom {
+  double r[3];
+  double rn;
+  int plane_axis;
+  bool z_free = false;  // r does not depend on P_b's z (a cylinder side)
+};
+
+__device__ __forceinline__ CrossGeom cross_geom(const DevMedium& m, const double* Pb, int face) {
+  CrossGeom g;
+  const double* b = m.b;
+  g.r[0] = g.r[1] = g.r[2] = 0.0;
+  g.rn = 1.0;
+  if (m.bkind == GRIN_BOUNDARY_BOX) {
+    g.plane_axis = face >> 1;
+    g.r[g.plane_axis] = (face & 1) ? 1.0 : -1.0;
+  } else if (m.bkind == GRIN_BOUNDARY_SPHERE) {
+    g.plane_axis = -1;
+    for (int k = 0; k < 3; ++k) g.r[k] = Pb[k] - b[k];
+    g.rn = sqrt(plain::dot3(g.r, g.r));
+  } else if (face == 0) {  // cylinder side
+    g.plane_axis = -1;
+    g.z_free = true;
+    g.r[0] = Pb[0] - b[0];
+    g.r[1] = Pb[1] - b[1];
+    g.rn = sqrt(g.r[0] * g.r[0] + g.r[1] * g.r[1]);
+  } else {  // cylinder end planes
+    g.plane_axis = 2;
+    g.r[2] = face == 2 ? 1.0 : -1.0;
+  }
+  return g;
+}
+
+// Back through the unit normal N = r / |r| of a curved face: dL/dN into
+// dL/dP_b, (1 - N N^T) dL/dN / |r| on the coordinates r depends on.
+__device__ __forceinline__ void surface_normal_back(const CrossGeom& g, const double* N,
+                                                    const double* Nb, double* Pbb) {
+  if (g.plane_axis >= 0) return;
+  const double s = fdot3(N, Nb), inv = 1.0 / g.rn;
+  for (int k = 0; k < (g.z_free ? 2 : 3); ++k) Pbb[k] = fma(fma(-N[k], s, Nb[k]), inv, Pbb[k]);
+}
+
+// Back through a step that crossed the surface at the fraction t of D = h I
+// from P (P_b = P + t D, t the root of the surface's implicit function along
+// the segment): takes dL/dP_b (a plane face's own coordinate ignored, as the
+// forward sweep sets it) and dL/dt; adds into lam.  With r the surface normal
+// direction at P_b, dt = -(r . dP + t r . dD) / (r . D).
+__device__ void cross_back_general(const double* P, const double* I, double h, double t,
+                                   const CrossGeom& g, const double* Pbb, double tb, Adj& lam) {
+  double D[3], Db[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < 3; ++k) D[k] = h * I[k];
+  for (int k = 0; k < 3; ++k) {
+    if (k == g.plane_axis) continue;
+    tb = fma(Pbb[k], D[k], tb);
+    Db[k] = fma(t, Pbb[k], Db[k]);
+    lam.P[k] += Pbb[k];
+  }
+  const double inv_rD = 1.0 / fdot3(g.r, D);
+  for (int k = 0; k < 3; ++k) {
+    lam.P[k] = fma(-tb * inv_rD, g.r[k], lam.P[k]);
+    Db[k] = fma(-tb * t * inv_rD, g.r[k], Db[k]);
+  }
+  for (int k = 0; k < 3; ++k) {
+    lam.h = fma(Db[k], I[k], lam.h);
+    lam.d[k] = fma(h, Db[k], lam.d[k]);
   }
 }
 
@@ -498,13 +648,14 @@ __device__ void reflect_back(const DevMedium& m, double dopl, const double* rec,
   const double* P = rec;
   const double* I = rec + 3;
   const double n_prev = rec[6], h = rec[7];
-  const int ax = face >> 1;
   double Q[3], t, Pb[3], NB[3];
   int f2;
   for (int k = 0; k < 3; ++k) Q[k] = P[k] + h * I[k];
   plain::leave(m, P, Q, t, Pb, NB, f2);
-  double R[3] = {I[0], I[1], I[2]};
-  R[ax] = -I[ax];
+  // R = I - 2 (I.N) N, as the forward reflection forms it
+  const double cI = plain::dot3(NB, I);
+  double R[3];
+  for (int k = 0; k < 3; ++k) R[k] = I[k] - 2.0 * cI * NB[k];
   const double inv_Rn = 1.0 / sqrt(plain::dot3(R, R));
   double u[3] = {R[0] * inv_Rn, R[1] * inv_Rn, R[2] * inv_Rn};
   Adj in = lam;
@@ -520,8 +671,20 @@ __device__ void reflect_back(const DevMedium& m, double dopl, const double* rec,
   for (int k = 0; k < 3; ++k) Pbb[k] = fma(in.n, gh[k], in.P[k]);
   double Rb[3];
   unit_back(u, inv_Rn, in.d, Rb);
-  for (int k = 0; k < 3; ++k) out.d[k] += k == ax ? -Rb[k] : Rb[k];
-  cross_back(m, P, I, h, face, Pbb, fb, out);
+  // dR = (1 - 2 N N^T) dI - 2 ((I.N) dN + N (I . dN))
+  const double rN = fdot3(Rb, NB);
+  double Nb[3];
+  for (int k = 0; k < 3; ++k) {
+    out.d[k] += fma(-2.0 * rN, NB[k], Rb[k]);
+    Nb[k] = -2.0 * fma(cI, Rb[k], rN * I[k]);
+  }
+  if (m.bkind == GRIN_BOUNDARY_BOX) {
+    cross_back(m, P, I, h, face, Pbb, fb, out);
+  } else {
+    const CrossGeom g = cross_geom(m, Pb, face);
+    surface_normal_back(g, NB, Nb, Pbb);
+    cross_back_general(P, I, h, t, g, Pbb, fb, out);
+  }
   lam = out;
 }
 
@@ -531,9 +694,16 @@ __device__ void exit_back(const DevMedium& m, const double* rec, int face, const
   const double* P = rec;
   const double* I = rec + 3;
   const double n_prev = rec[6], h = rec[7];
-  double N[3] = {0.0, 0.0, 0.0};
-  const int ax = face >> 1;
-  N[ax] = (face & 1) ? 1.0 : -1.0;
+  double N[3] = {0.0, 0.0, 0.0}, t = 0.0, Pb[3];
+  if (m.bkind == GRIN_BOUNDARY_BOX) {
+    const int ax = face >> 1;
+    N[ax] = (face & 1) ? 1.0 : -1.0;
+  } else {
+    double Q[3];
+    int f2;
+    for (int k = 0; k < 3; ++k) Q[k] = P[k] + h * I[k];
+    plain::leave(m, P, Q, t, Pb, N, f2);
+  }
   const double mu = n_prev / m.n_ext;
   double R[3];
   const double inv_Rn = 1.0 / fwd_R(I, N, mu, false, R);
@@ -545,7 +715,15 @@ __device__ void exit_back(const DevMedium& m, const double* rec, int face, const
   double Nb[3] = {0.0, 0.0, 0.0};
   double mub = snell_back(I, N, mu, Rb, lam.d, Nb);
   lam.n = mub / m.n_ext;
-  cross_back(m, P, I, h, face, Pob, fb, lam);
+  if (m.bkind == GRIN_BOUNDARY_BOX) {
+    cross_back(m, P, I, h, face, Pob, fb, lam);
+  } else {
+    // the exit normal moves with the exit point
+    const CrossGeom g = cross_geom(m, Pb, face);
+    double Pbb[3] = {Pob[0], Pob[1], Pob[2]};
+    surface_normal_back(g, N, Nb, Pbb);
+    cross_back_general(P, I, h, t, g, Pbb, fb, lam);
+  }
 }
 
 // Back through the ray's start: the entry refraction (mu = n_ext / n(P_b))
@@ -748,8 +926,13 @@ static int run_t(const DevMedium& m, const AdjArgs& A, cudaStream_t st, int phas
 }  // namespace adj
 
 bool adjoint_supported(const DevMedium& m) {
-  if (m.n_levels > 0 || m.bkind != GRIN_BOUNDARY_BOX) return false;
-  return m.kind == GRIN_MEDIUM_GRID || (m.kind == GRIN_MEDIUM_POLY && m.form == GRIN_FORM_LINEAR);
+  if (m.n_levels > 0) return false;
+  if (m.bkind != GRIN_BOUNDARY_BOX && m.bkind != GRIN_BOUNDARY_SPHERE &&
+      m.bkind != GRIN_BOUNDARY_CYLINDER)
+    return false;
+  if (m.kind == GRIN_MEDIUM_GRID) return true;
+  return m.kind == GRIN_MEDIUM_POLY && (m.form == GRIN_FORM_LINEAR || m.form == GRIN_FORM_SQRT ||
+                                        m.form == GRIN_FORM_RECIP);
 }
 
 // Workspace: checkpoints [ray][segment][kCk] | meta [ray][2] | (256-byte
