@@ -346,9 +346,12 @@ def serve_load(ctx, dev_index: int, rates, jobs_per_rate: int, seed: int = 7):
 def adjoint_timing(ctx, dev, n_rays=1 << 18):
     """One gradient of the image-plane design loss (16 target spots on
     z = 30 mm) with respect to the 128^3 blob grid: 262,144 collimated rays
-    (or n_rays, to profile a smaller case), dL0 = 0.02 mm (up to 2000 steps),
-    checkpoints every 64 steps; the FP64 forward sweep with checkpoints plus
-    the backward sweep."""
+    (or n_rays, to profile a smaller case), dL0 = 0.02 mm (up to 2000 steps);
+    the FP64 forward sweep with checkpoints plus the backward sweep.  The
+    checkpoint interval is the library's choice for half the free device
+    memory (every step stored when that fits: 55 GB here); the same gradient
+    with a checkpoint every 64 steps (segments recomputed) is timed beside
+    it."""
     import torch
     from paper_2606_22655_b300 import tracer
     from paper_2606_22655_b300 import workloads as W
@@ -356,49 +359,47 @@ def adjoint_timing(ctx, dev, n_rays=1 << 18):
     med = tracer.Medium(ctx, wl.medium)
     rays = tracer.RayBatch.from_numpy(wl.rays.origins, wl.rays.dirs, device=dev, dtype=torch.float64)
     n = rays.count
+    n_par = wl.medium.grid.size
     g = {k: torch.randn(n, dtype=torch.float64, device=dev) * 1e-3 for k in tracer.OUT_FIELDS}
-    out, grad = tracer.trace_adjoint(ctx, med, rays, 0.02, 2000, g, wl.medium.grid.size, 64)
-    torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    out, grad = tracer.trace_adjoint(ctx, med, rays, 0.02, 2000, g, wl.medium.grid.size, 64)
-    e1.record()
-    torch.cuda.synchronize(dev)
-    t = e0.elapsed_time(e1) / 1e3
-    steps = float(out["steps"].sum())
-    # every step stored (K = 1): no recompute in the backward sweep, 72 B a
-    # ray-step of workspace (38 GB here); skipped if the device lacks room
-    ws1 = tracer.adjoint_workspace_bytes(med, n, 0.02, 2000, 1)
-    stored = None
-    if ws1 < 0.8 * torch.cuda.mem_get_info(dev)[0]:
-        tracer.trace_adjoint(ctx, med, rays, 0.02, 2000, g, wl.medium.grid.size, 1)
+
+    def timed(k):
+        tracer.trace_adjoint(ctx, med, rays, 0.02, 2000, g, n_par, k)  # warm-up
         torch.cuda.synchronize(dev)
         e0.record()
-        _, grad1 = tracer.trace_adjoint(ctx, med, rays, 0.02, 2000, g, wl.medium.grid.size, 1)
+        out, grad = tracer.trace_adjoint(ctx, med, rays, 0.02, 2000, g, n_par, k)
         e1.record()
         torch.cuda.synchronize(dev)
-        t1 = e0.elapsed_time(e1) / 1e3
-        same = bool(torch.allclose(grad1, grad, rtol=1e-12, atol=1e-15 * float(grad.abs().max())))
-        stored = {"checkpoint_every": 1, "seconds": t1, "ray_steps_per_s_fwd_plus_bwd": steps / t1,
-                  "workspace_gb": ws1 / 1e9, "gradient_equals_k64": same}
+        return out, grad, e0.elapsed_time(e1) / 1e3
+
+    out, g64, t64 = timed(64)
+    steps = float(out["steps"].sum())
+    k = tracer.adjoint_interval(med, n, 0.02, 2000)
+    if k != 64:
+        _, gk, t = timed(k)
+    else:
+        gk, t = g64, t64
+    same = bool(torch.allclose(gk, g64, rtol=1e-12, atol=1e-15 * float(g64.abs().max())))
     # one design iteration through the autograd function (grin_trace_adjoint
     # _forward in forward, _backward in backward: the rays traced forward
-    # once), against a plain FP64 trace for the loss followed by the one-call
-    # adjoint (two forward traces)
+    # once), at the chosen interval and at K = 64, against a plain FP64
+    # trace for the loss followed by the one-call adjoint at K = 64
     targets = torch.tensor(W.design_targets(n) + 10.0, device=dev)
     theta = torch.tensor(wl.medium.grid.astype(np.float64).ravel(), device=dev, requires_grad=True)
 
-    def design_step():
+    def design_step(kk):
         theta.grad = None
-        P, d, opl, ex = tracer.traced_exit(theta, ctx, wl.medium, rays, 0.02, 2000, 64)
+        P, d, opl, ex = tracer.traced_exit(theta, ctx, wl.medium, rays, 0.02, 2000, kk)
         tracer.image_plane_loss(P, d, ex, targets, 30.0).backward()
 
     def two_trace_step():
         tracer.trace(ctx, med, rays, 0.02, 2000, "fp64")
-        tracer.trace_adjoint(ctx, med, rays, 0.02, 2000, g, wl.medium.grid.size, 64)
+        tracer.trace_adjoint(ctx, med, rays, 0.02, 2000, g, n_par, 64)
 
     design = {}
-    for name, fn in (("autograd_step_seconds", design_step), ("trace_then_adjoint_seconds", two_trace_step)):
+    for name, fn in (("autograd_step_seconds", lambda: design_step(0)),
+                     ("autograd_step_k64_seconds", lambda: design_step(64)),
+                     ("trace_then_adjoint_k64_seconds", two_trace_step)):
         fn()
         torch.cuda.synchronize(dev)
         e0.record()
@@ -406,9 +407,14 @@ def adjoint_timing(ctx, dev, n_rays=1 << 18):
         e1.record()
         torch.cuda.synchronize(dev)
         design[name] = e0.elapsed_time(e1) / 1e3
-    return {"workload": f"grid_128 adjoint, {n} rays, dL0 0.02 mm, K=64", "seconds": t,
-            "forward_ray_steps": steps, "ray_steps_per_s_fwd_plus_bwd": steps / t,
-            "precision": "fp64", "gradient_params": int(wl.medium.grid.size), "stored_steps": stored,
+    return {"workload": f"grid_128 adjoint, {n} rays, dL0 0.02 mm, checkpoint interval by free memory",
+            "checkpoint_every": k,
+            "workspace_gb": tracer.adjoint_workspace_bytes(med, n, 0.02, 2000, k) / 1e9,
+            "seconds": t, "forward_ray_steps": steps, "ray_steps_per_s_fwd_plus_bwd": steps / t,
+            "precision": "fp64", "gradient_params": int(n_par),
+            "recomputed_k64": {"seconds": t64, "ray_steps_per_s_fwd_plus_bwd": steps / t64,
+                               "workspace_gb": tracer.adjoint_workspace_bytes(med, n, 0.02, 2000, 64) / 1e9,
+                               "gradient_equals": same},
             "design_iteration": design}
 
 

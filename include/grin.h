@@ -355,6 +355,15 @@ int grin_trace_adjoint_workspace_size(grin_medium medium, int64_t ray_count,
                                       const grin_params* params, int32_t checkpoint_every,
                                       size_t* bytes);
 
+/* The checkpoint interval for a workspace of at most budget_bytes: 1 (every
+ * step stored, so the backward sweep recomputes nothing: the fastest) when
+ * its workspace fits, else the smallest K <= 64 whose workspace fits (every
+ * K >= 2 recomputes each step once).  GRIN_ERR_OOM if not even K = 64 fits;
+ * GRIN_ERR_NOT_IMPLEMENTED for media the adjoint does not support.  Host
+ * arithmetic only; no device memory is touched. */
+int grin_trace_adjoint_interval(grin_medium medium, int64_t ray_count, const grin_params* params,
+                                size_t budget_bytes, int32_t* checkpoint_every);
+
 /* Forward sweep (writes `out`, bitwise the results of grin_trace with
  * GRIN_PREC_FP64) then backward sweep, adding dL/d(parameters) into the
  * device FP64 array dL_dmedium (the caller zeroes it).  params->precision

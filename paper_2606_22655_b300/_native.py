@@ -120,6 +120,8 @@ def load() -> ctypes.CDLL:
         "grin_trace_host_static": (ctypes.c_int, [P(MediumDesc), P(Rays), P(Params), P(Out), _vp]),
         "grin_trace_adjoint_workspace_size": (ctypes.c_int, [_vp, ctypes.c_int64, P(Params), ctypes.c_int32,
                                                              P(ctypes.c_size_t)]),
+        "grin_trace_adjoint_interval": (ctypes.c_int, [_vp, ctypes.c_int64, P(Params), ctypes.c_size_t,
+                                                       P(ctypes.c_int32)]),
         "grin_trace_adjoint": (ctypes.c_int, [_vp, _vp, P(Rays), P(Params), P(Out), P(OutGrad), _vp, ctypes.c_int32,
                                               _vp, ctypes.c_size_t, _vp]),
         "grin_trace_adjoint_forward": (ctypes.c_int, [_vp, _vp, P(Rays), P(Params), P(Out), ctypes.c_int32,

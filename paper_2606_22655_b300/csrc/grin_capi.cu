@@ -791,6 +791,25 @@ int grin_trace_adjoint_workspace_size(grin_medium medium, int64_t ray_count, con
   return GRIN_OK;
 }
 
+int grin_trace_adjoint_interval(grin_medium medium, int64_t ray_count, const grin_params* p,
+                                size_t budget_bytes, int32_t* k_out) {
+  if (!medium || !p || !k_out || ray_count < 0 || p->max_steps < 0) return GRIN_ERR_INVALID_ARG;
+  if (!grin::adjoint_supported(medium->dm)) return GRIN_ERR_NOT_IMPLEMENTED;
+  // every step stored: the backward sweep recomputes nothing
+  if (grin::adjoint_workspace(ray_count, p->max_steps, 1) <= budget_bytes) {
+    *k_out = 1;
+    return GRIN_OK;
+  }
+  // otherwise every step is recomputed once whatever K is; the smallest K
+  // that fits keeps the thread's segment records shortest
+  for (int32_t k = 2; k <= 64; ++k)
+    if (grin::adjoint_workspace(ray_count, p->max_steps, k) <= budget_bytes) {
+      *k_out = k;
+      return GRIN_OK;
+    }
+  return GRIN_ERR_OOM;
+}
+
 // The forward sweep, the backward sweep or both (grin::AdjPhase); out and g
 // as the phase needs them.
 static int trace_adjoint_phase(grin_ctx ctx, grin_medium medium, const grin_rays* rays,

@@ -348,6 +348,24 @@ def adjoint_workspace_bytes(medium: Medium, count: int, dopl: float, max_steps: 
     return int(v.value)
 
 
+def adjoint_interval(medium: Medium, count: int, dopl: float, max_steps: int,
+                     budget_bytes: Optional[int] = None) -> int:
+    """grin_trace_adjoint_interval: the checkpoint interval whose workspace
+    fits in budget_bytes, 1 (every step stored) when it can.  The default
+    budget is half of the device memory free to this process (what the CUDA
+    driver reports free plus what torch's allocator holds unused)."""
+    if budget_bytes is None:
+        dev = torch.device("cuda", medium.ctx.device)
+        free = torch.cuda.mem_get_info(dev)[0]
+        cached = torch.cuda.memory_reserved(dev) - torch.cuda.memory_allocated(dev)
+        budget_bytes = (free + cached) // 2
+    v = ctypes.c_int32()
+    ps = _params(dopl, max_steps, "fp64")
+    N.check("grin_trace_adjoint_interval", medium.ctx.lib.grin_trace_adjoint_interval(
+        medium.handle, int(count), ctypes.byref(ps), int(budget_bytes), ctypes.byref(v)))
+    return int(v.value)
+
+
 def trace_adjoint(ctx: Context, medium: Medium, rays: RayBatch, dopl: float, max_steps: int,
                   grads: Dict[str, torch.Tensor], n_params: int, k: int = 64,
                   stream: Optional[torch.cuda.Stream] = None):
@@ -443,11 +461,14 @@ class TraceFunction(torch.autograd.Function):
     the medium parameters theta (polynomial coefficients, or grid samples).
     forward runs the adjoint's forward sweep (the plain FP64 trace, which also
     stores the checkpoints) and backward its backward sweep from them, so the
-    rays are traced forward once."""
+    rays are traced forward once.  k = 0 takes the checkpoint interval from
+    adjoint_interval (every step stored when half the free memory holds it)."""
 
     @staticmethod
     def forward(fctx, theta, gctx, spec, rays, dopl, max_steps, k):
         med = Medium(gctx, _with_params(spec, theta))
+        if not k:
+            k = adjoint_interval(med, rays.count, dopl, max_steps)
         res, ws = trace_adjoint_forward(gctx, med, rays, dopl, max_steps, k)
         fctx.save_for_backward(theta)
         fctx.extra = (gctx, med, rays, dopl, max_steps, k, ws)
@@ -470,8 +491,9 @@ class TraceFunction(torch.autograd.Function):
 
 
 def traced_exit(theta: torch.Tensor, ctx: Context, spec, rays: RayBatch, dopl: float, max_steps: int,
-                k: int = 64):
-    """(P, d, opl, exit_id) differentiable in theta (see TraceFunction)."""
+                k: int = 0):
+    """(P, d, opl, exit_id) differentiable in theta (see TraceFunction); k is
+    the checkpoint interval, 0 to choose it by the free device memory."""
     return TraceFunction.apply(theta, ctx, spec, rays, dopl, max_steps, k)
 
 

@@ -17,6 +17,7 @@ import pytest
 import torch
 
 import oracle
+from paper_2606_22655_b300 import _native as N
 from paper_2606_22655_b300 import tracer
 from paper_2606_22655_b300 import workloads as W
 
@@ -456,3 +457,28 @@ def test_curved_media_checkpoint_interval_and_split(ctx, name):
     assert np.abs(g64).max() > 0
     np.testing.assert_allclose(g7, g64, rtol=1e-12, atol=1e-13 * np.abs(g64).max())
     np.testing.assert_allclose(g1, g64, rtol=1e-12, atol=1e-13 * np.abs(g64).max())
+
+
+def test_checkpoint_interval_choice(ctx):
+    """grin_trace_adjoint_interval: 1 when every step's workspace fits the
+    budget, else the smallest K whose workspace fits, GRIN_ERR_OOM below
+    K = 64's; and the autograd function at the chosen interval (k = 0) gives
+    the gradient of K = 64."""
+    m = W.freeform_block_medium()
+    med = tracer.Medium(ctx, m)
+    n, dopl, ms = 4096, 0.02, 20000
+    ws = {k: tracer.adjoint_workspace_bytes(med, n, dopl, ms, k) for k in range(1, 65)}
+    assert all(ws[k] >= ws[k + 1] for k in range(1, 64))
+    assert tracer.adjoint_interval(med, n, dopl, ms, ws[1]) == 1
+    assert tracer.adjoint_interval(med, n, dopl, ms, ws[1] - 1) == 2
+    assert tracer.adjoint_interval(med, n, dopl, ms, ws[9]) == next(k for k in range(2, 65) if ws[k] <= ws[9])
+    assert tracer.adjoint_interval(med, n, dopl, ms, ws[64]) == min(k for k in range(2, 65) if ws[k] <= ws[64])
+    with pytest.raises(N.GrinError) as e:
+        tracer.adjoint_interval(med, n, dopl, ms, ws[64] - 1)
+    assert e.value.status == N.GRIN_ERR_OOM
+    med.close()
+    rays = W.point_source_rays(512, W.BASE_SEED + 4)
+    targets = W.design_targets(rays.n)
+    _, g64 = adjoint_grad(ctx, m, m.coeffs, rays, targets, dopl, ms, 64)
+    _, g0 = adjoint_grad(ctx, m, m.coeffs, rays, targets, dopl, ms, 0)
+    np.testing.assert_allclose(g0, g64, rtol=1e-12, atol=1e-15 * np.abs(g64).max())
