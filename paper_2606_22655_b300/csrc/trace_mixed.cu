@@ -312,9 +312,8 @@ struct Cfg {
   }
 
   // eval for a gridded medium from the cell's 64 taps (sample - lb, lb the
-  // centre tap; row c * 4 + b at col[(c * 4 + b) * kTapRow], x taps in
-  // .x .. .w): the same products summed in the same order as grid_gather's,
-  // so the same value and gradient bit for bit.
+  // centre tap; layout at tap_fill): the same products summed in the same
+  // order as grid_gather's, so the same value and gradient bit for bit.
   static __device__ __forceinline__ void eval_taps(const DevMedium& m, const float* fr,
                                                    const float* col, float lb, float& nu,
                                                    float& gx, float& gy, float& gz, int& lvl,
@@ -325,39 +324,66 @@ struct Cfg {
   }
 
   // The smooth field f = n - base and its gradient from the cached taps (the
-  // part of eval_taps before the level).
+  // part of eval_taps before the level).  Row 2 (4 p + b) + h of the column
+  // holds, for the z planes c = 2p and 2p + 1 of stencil row b, the taps
+  // x = 2h and 2h + 1 as (x: c, c + 1, x + 1: c, c + 1), so each float4 read
+  // gives two plane pairs: the x and y sums of planes 2p and 2p + 1 go
+  // together through packed FMAs (fma.rn.f32x2, each half an IEEE fma) with
+  // the weight in both halves, and each plane's sums keep grid_gather's order.
   static __device__ __forceinline__ void taps_field(const DevMedium& m, const float* fr,
                                                     const float* col, float lb, float& f,
                                                     float& gx, float& gy, float& gz) {
     float w[3][4], dw[3][4];
 #pragma unroll
     for (int k = 0; k < 3; ++k) cr_w(fr[k], w[k], dw[k]);
-    float V = 0.0f, GX = 0.0f, GY = 0.0f, GZ = 0.0f;
+    float2 wx[4], dwx[4], wy[4], dwy[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      wx[k] = make_float2(w[0][k], w[0][k]);
+      dwx[k] = make_float2(dw[0][k], dw[0][k]);
+      wy[k] = make_float2(w[1][k], w[1][k]);
+      dwy[k] = make_float2(dw[1][k], dw[1][k]);
+    }
+    const float2 z2 = make_float2(0.0f, 0.0f);
 #ifdef GRIN_CHECKED
     // the column must lie in the block's cache (16 rows of kTapRow floats)
     col = col - (int64_t)threadIdx.x * 4 + GRIN_IDX(m, (int64_t)threadIdx.x * 4, kTapRow - 4, kSiteTapCache);
 #endif
+    float sv[4], sx[4], sy[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      float sv = 0.0f, sx = 0.0f, sy = 0.0f;
+    for (int p = 0; p < 2; ++p) {
+      float2 SV = z2, SX = z2, SY = z2;
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        const float4 q = *reinterpret_cast<const float4*>(col + (c * 4 + b) * kTapRow);
-        const float t[4] = {q.x, q.y, q.z, q.w};
-        float r = 0.0f, rx = 0.0f;
+        const float* row = col + (2 * (4 * p + b)) * kTapRow;
+        const float4 q0 = *reinterpret_cast<const float4*>(row);
+        const float4 q1 = *reinterpret_cast<const float4*>(row + kTapRow);
+        const float2 t[4] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w),
+                             make_float2(q1.x, q1.y), make_float2(q1.z, q1.w)};
+        float2 r = z2, rx = z2;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          r = fmadd(w[0][k], t[k], r);
-          rx = fmadd(dw[0][k], t[k], rx);
+          r = __ffma2_rn(wx[k], t[k], r);
+          rx = __ffma2_rn(dwx[k], t[k], rx);
         }
-        sv = fmadd(w[1][b], r, sv);
-        sx = fmadd(w[1][b], rx, sx);
-        sy = fmadd(dw[1][b], r, sy);
+        SV = __ffma2_rn(wy[b], r, SV);
+        SX = __ffma2_rn(wy[b], rx, SX);
+        SY = __ffma2_rn(dwy[b], r, SY);
       }
-      V = fmadd(w[2][c], sv, V);
-      GX = fmadd(w[2][c], sx, GX);
-      GY = fmadd(w[2][c], sy, GY);
-      GZ = fmadd(dw[2][c], sv, GZ);
+      sv[2 * p] = SV.x;
+      sv[2 * p + 1] = SV.y;
+      sx[2 * p] = SX.x;
+      sx[2 * p + 1] = SX.y;
+      sy[2 * p] = SY.x;
+      sy[2 * p + 1] = SY.y;
+    }
+    float V = 0.0f, GX = 0.0f, GY = 0.0f, GZ = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      V = fmadd(w[2][c], sv[c], V);
+      GX = fmadd(w[2][c], sx[c], GX);
+      GY = fmadd(w[2][c], sy[c], GY);
+      GZ = fmadd(dw[2][c], sv[c], GZ);
     }
     gx = GX * m.inv_spacing_f[0];
     gy = GY * m.inv_spacing_f[1];
@@ -1256,15 +1282,19 @@ __device__ __forceinline__ bool step_ray(const DevMedium& m, const TraceArgs& a,
 // Warp-collective: the lanes in `need` get their column of the tap cache
 // refilled for the cell in their key[] (the 64 edge-clamped stencil samples
 // of grid_gather, minus the centre tap, which the lane keeps in lb).  The
-// whole warp loads one such lane's taps at a time, two x-adjacent taps of
-// one row a lane (lane 10 holds the centre tap (kx, ky, kz) as its second),
+// whole warp loads one such lane's taps at a time, lane 2 r + e filling the
+// pair of floats e of cache row r = 2 (4 p + b) + h: the samples at
+// x = 2 h + e of stencil row b in the z planes 2 p and 2 p + 1 (the layout
+// taps_field reads).  Lanes 4 j .. 4 j + 3 read four x-adjacent samples of
+// one grid row, and lane 5 holds the centre tap (kx, ky, kz) as its second,
 // so a refill costs the warp two gathers instead of the lane's 64.
 __device__ __forceinline__ void tap_fill(const DevMedium& m, bool need, const int* key,
                                          float& lb, float* taps, unsigned lane) {
   unsigned mask = __ballot_sync(0xffffffffu, need);
   if (!mask) return;
   __syncwarp();  // the owners' reads of their old taps come first
-  const int row = (int)(lane >> 1), c = row >> 2, b = row & 3, h = (int)(lane & 1u);
+  const int row = (int)(lane >> 1), e = (int)(lane & 1u);
+  const int p = row >> 3, b = (row >> 1) & 3, x = 2 * (row & 1) + e;
   const int wbase = (int)(threadIdx.x & ~31u);
   while (mask) {
     const int src = __ffs(mask) - 1;
@@ -1272,17 +1302,16 @@ __device__ __forceinline__ void tap_fill(const DevMedium& m, bool need, const in
     const int kx = __shfl_sync(0xffffffffu, key[0], src);
     const int ky = __shfl_sync(0xffffffffu, key[1], src);
     const int kz = __shfl_sync(0xffffffffu, key[2], src);
-    const int iz = min(max(kz - 1 + c, 0), m.nz - 1);
+    const int iz0 = min(max(kz - 1 + 2 * p, 0), m.nz - 1);
+    const int iz1 = min(max(kz + 2 * p, 0), m.nz - 1);
     const int iy = min(max(ky - 1 + b, 0), m.ny - 1);
-    const int ix0 = min(max(kx - 1 + 2 * h, 0), m.nx - 1);
-    const int ix1 = min(max(kx + 2 * h, 0), m.nx - 1);
-    const int64_t row_i = ((int64_t)iz * m.ny + iy) * m.nx;
-    const float v0 = __ldg(m.grid + GRIN_IDX(m, row_i + ix0, m.grid_n, kSiteGridMixed));
-    const float v1 = __ldg(m.grid + GRIN_IDX(m, row_i + ix1, m.grid_n, kSiteGridMixed));
-    const float sub = __shfl_sync(0xffffffffu, v1, 10);  // row 5 = (c, b) = (1, 1), x = kx
+    const int ix = min(max(kx - 1 + x, 0), m.nx - 1);
+    const float v0 = __ldg(m.grid + GRIN_IDX(m, ((int64_t)iz0 * m.ny + iy) * m.nx + ix, m.grid_n, kSiteGridMixed));
+    const float v1 = __ldg(m.grid + GRIN_IDX(m, ((int64_t)iz1 * m.ny + iy) * m.nx + ix, m.grid_n, kSiteGridMixed));
+    const float sub = __shfl_sync(0xffffffffu, v1, 5);  // plane 1, row 1, x = kx
     if ((int)lane == src) lb = sub;
     *reinterpret_cast<float2*>(
-        taps + GRIN_IDX(m, row * kTapRow + (wbase + src) * 4 + 2 * h, 16 * kTapRow - 1, kSiteTapCache)) =
+        taps + GRIN_IDX(m, row * kTapRow + (wbase + src) * 4 + 2 * e, 16 * kTapRow - 1, kSiteTapCache)) =
         make_float2(v0 - sub, v1 - sub);
   }
   __syncwarp();
