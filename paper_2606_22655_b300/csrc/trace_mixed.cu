@@ -53,13 +53,19 @@
 namespace grin {
 
 // Resident blocks of 128 threads per SM the register allocation aims for:
-// 5 (at most 102 registers a thread) for polynomial and grid media; the
-// measured optimum between register spills and resident warps.
+// 5 (at most 102 registers a thread) for polynomial and grid media, 4 (128
+// registers) for the shells of a layered grid, whose level logic spills at
+// 96; the measured optimum between register spills and resident warps
+// (256^3 grid at 1,048,576 rays: 4, 5, 6 blocks 5.26e10, 5.52e10, 5.33e10
+// ray-steps/s; its 32 shells 5.11e10, 4.94e10, 5.02e10).
 #ifndef GRIN_MIXED_MIN_BLOCKS
 #define GRIN_MIXED_MIN_BLOCKS 5
 #endif
 #ifndef GRIN_MIXED_MIN_BLOCKS_GRID
 #define GRIN_MIXED_MIN_BLOCKS_GRID 5
+#endif
+#ifndef GRIN_MIXED_MIN_BLOCKS_LAYERED_GRID
+#define GRIN_MIXED_MIN_BLOCKS_LAYERED_GRID 4
 #endif
 constexpr int kStepQuantum = 32;
 // Tap cache of the gridded fast step: 16 rows (one per (z, y) pair of the
@@ -132,6 +138,7 @@ struct Cfg {
   // pair normalised after every step.
   static constexpr bool kLazyPos = !GRID;
   static constexpr int kMinBlocks = GRID ? GRIN_MIXED_MIN_BLOCKS_GRID : GRIN_MIXED_MIN_BLOCKS;
+  static constexpr int kMinBlocksLayered = GRID ? GRIN_MIXED_MIN_BLOCKS_LAYERED_GRID : kMinBlocks;
   static __device__ __forceinline__ int bk(const DevMedium& m) { return BK >= 0 ? BK : m.bkind; }
   static __device__ __forceinline__ int form(const DevMedium& m) { return FORM >= 0 ? FORM : m.form; }
 
@@ -1376,7 +1383,7 @@ __device__ __forceinline__ unsigned run_quantum(const DevMedium& m, const TraceA
 }
 
 template <class C, bool LAYERED>
-__global__ void __launch_bounds__(128, C::kMinBlocks) k_trace_mixed(DevMedium m, TraceArgs a,
+__global__ void __launch_bounds__(128, LAYERED ? C::kMinBlocksLayered : C::kMinBlocks) k_trace_mixed(DevMedium m, TraceArgs a,
                                                      unsigned long long* queue) {
   const unsigned lane = threadIdx.x & 31u;
   const float dopl_f = (float)a.dopl;
@@ -1483,7 +1490,7 @@ struct SlotState {
 };
 
 template <class C, bool LAYERED>
-__global__ void __launch_bounds__(128, C::kMinBlocks) k_serve_tick(DevMedium m, TraceArgs a,
+__global__ void __launch_bounds__(128, LAYERED ? C::kMinBlocksLayered : C::kMinBlocks) k_serve_tick(DevMedium m, TraceArgs a,
                                                                    SlotState* slots,
                                                                    unsigned long long* counters,
                                                                    int quantum) {
