@@ -201,11 +201,12 @@ def trace_path(medium, origin, direction, dopl: float, max_steps: int, cap: Opti
 def trace_tangent(medium, origins, dirs, dopl: float, max_steps: int, samples=None,
                   threads: Optional[int] = None) -> Dict[str, np.ndarray]:
     """Exit state of every ray (as `trace`) and its forward-mode derivative
-    with respect to each polynomial coefficient (polynomial media with n = p)
-    or to each grid sample in `samples` (flat indices, x fastest; grid
-    media): tP, td (n, nc, 3), topl (n, nc); flag (n,) marks rays whose
-    tangents are not followed (tangential incidence, clamped crossing
-    fraction).  Box boundaries, no layering."""
+    with respect to each polynomial coefficient (polynomial media, n = p,
+    sqrt(p) or form_c / p) or to each grid sample in `samples` (flat
+    indices, x fastest; grid media): tP, td (n, nc, 3), topl (n, nc); flag
+    (n,) marks rays whose tangents are not followed (tangential incidence,
+    clamped crossing fraction).  Box, sphere or cylinder boundaries, no
+    layering."""
     lib = _load()
     b = _Bound(medium)
     o = np.ascontiguousarray(origins, dtype=np.float64).reshape(-1, 3)
@@ -229,5 +230,5 @@ def trace_tangent(medium, origins, dirs, dopl: float, max_steps: int, samples=No
                                ip(out["steps"]), _ptr(out["tP"]), _ptr(out["td"]), _ptr(out["topl"]),
                                ip(out["flag"]), int(threads or os.cpu_count() or 1))
     if rc != 0:
-        raise ValueError("trace_tangent: polynomial (n = p) or grid media in a box, samples in range")
+        raise ValueError("trace_tangent: polynomial or grid media, not layered, samples in range")
     return out

@@ -1070,17 +1070,44 @@ static void grid_second(const orc_medium* m, const double* P, int np, const int6
   }
 }
 
-/* n and grad n as trace_one samples them, and the second-order data of the
- * tangents: polynomial coefficients (all of them) or grid samples params[]. */
+/* n and grad n as trace_one samples them (field_eval: the polynomial's form
+ * applied, or the grid's interpolant), and the second-order data of the
+ * tangents: the Hessian of n and, per parameter (all polynomial
+ * coefficients, or the grid samples params[]), dn and d(grad n).  For
+ * n = sqrt(p): grad n = grad p / 2n, H_n = H_p / 2n - grad p grad p^T / 4n^3,
+ * dn = dp / 2n, d grad n = d grad p / 2n - grad p dp / 4n^3.  For n = C / p:
+ * grad n = -C grad p / p^2, H_n = -C H_p / p^2 + 2 C grad p grad p^T / p^3,
+ * dn = -C dp / p^2, d grad n = -C d grad p / p^2 + 2 C grad p dp / p^3. */
 static void ref_eval(const orc_medium* m, const double* P, double* n, double* g) {
-  if (m->kind == 1) grid_eval(m, P, n, g);
-  else poly_eval(m, P, n, g);
+  field_eval(m, P, n, g);
 }
 
 static void ref_second(const orc_medium* m, const double* P, int np, const int64_t* params,
                        double H[3][3], double* phi, double (*gphi)[3]) {
-  if (m->kind == 1) grid_second(m, P, np, params, H, phi, gphi);
-  else poly_second(m, P, H, phi, gphi);
+  if (m->kind == 1) {
+    grid_second(m, P, np, params, H, phi, gphi);
+    return;
+  }
+  poly_second(m, P, H, phi, gphi);
+  if (m->form == 0) return;
+  int nc = (m->degree + 1) * (m->degree + 2) * (m->degree + 3) / 6;
+  double p, gp[3];
+  poly_eval(m, P, &p, gp);
+  double a1, a2; /* n' and n'' of the form at p */
+  if (m->form == 1) {
+    double n = sqrt(p);
+    a1 = 1.0 / (2.0 * n);
+    a2 = -1.0 / (4.0 * n * n * n);
+  } else {
+    a1 = -m->form_c / (p * p);
+    a2 = 2.0 * m->form_c / (p * p * p);
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) H[a][b] = a1 * H[a][b] + a2 * gp[a] * gp[b];
+  for (int j = 0; j < nc; ++j) {
+    for (int a = 0; a < 3; ++a) gphi[j][a] = a1 * gphi[j][a] + a2 * gp[a] * phi[j];
+    phi[j] = a1 * phi[j];
+  }
 }
 
 /* Per parameter j the tangents carried along a ray. */
@@ -1088,12 +1115,14 @@ typedef struct {
   double P[3], d[3], Q[3], n_prev, h, opl;
 } tangent;
 
-/* One ray of a polynomial medium with n = p, or of a grid medium, in a box:
- * trace_one's values and decisions (the same operations, in the same order),
- * with every continuous quantity also carrying its derivative with respect to
- * each of the nc parameters (all polynomial coefficients, or the grid samples
- * params[]).  The entry point does not depend on the coefficients; at the
- * exit the crossing fraction t = (b - P_a) / (Q_a - P_a) carries one.
+/* One ray of a polynomial medium (n = p, sqrt(p) or C / p) or of a grid
+ * medium, in a box, sphere or cylinder: trace_one's values and decisions
+ * (the same operations, in the same order), with every continuous quantity
+ * also carrying its derivative with respect to each of the nc parameters
+ * (all polynomial coefficients, or the grid samples params[]).  The entry
+ * point does not depend on the parameters; at the exit the crossing fraction
+ * carries one (a plane face: t = (b - P_a) / (Q_a - P_a)), and on a curved
+ * face so does the normal.
  * Returns 1 when the ray met a case the tangents do not follow (tangential
  * incidence N.I == 0, or a crossing fraction clamped to [0, 1]). */
 static int tangent_one(const orc_medium* m, const orc_params* prm, const double* o,
@@ -1166,19 +1195,50 @@ static int tangent_one(const orc_medium* m, const orc_params* prm, const double*
       double t, Pb[3], NB[3], R[3], Dm;
       int face;
       exit_root(m, P, Q, &t, Pb, NB, &face);
-      int ax = face / 2;
-      double bv = (face & 1) ? m->b[3 + ax] : m->b[ax];
-      double Da = Q[ax] - P[ax];
-      double traw = (bv - P[ax]) / Da;
-      int clamped = !(traw > 0.0) || traw > 1.0;
+      /* a plane face (a box face, a cylinder's end) fixes its coordinate ax
+       * at bv; a curved face (the sphere, the cylinder's side) is met where
+       * its implicit function F(P + t (Q - P)) vanishes, so that
+       * dt = -r . (dP + t (dQ - dP)) / r . (Q - P) with r = grad F at P_b,
+       * and its unit normal N = r / |r| moves with P_b:
+       * dN = (dr - N (N . dr)) / |r|, dr = dP_b (its xy part on the side) */
+      int ax = -1;
+      double bv = 0.0;
+      if (m->bkind == 0) {
+        ax = face / 2;
+        bv = (face & 1) ? m->b[3 + ax] : m->b[ax];
+      } else if (m->bkind == 2 && face != 0) {
+        ax = 2;
+        bv = face == 2 ? m->b[4] : m->b[3];
+      }
+      double r[3] = {0.0, 0.0, 0.0}, rn = 1.0, rD = 1.0;
+      int clamped;
+      if (ax >= 0) {
+        double traw = (bv - P[ax]) / (Q[ax] - P[ax]);
+        clamped = !(traw > 0.0) || traw > 1.0;
+      } else {
+        clamped = !(t > 0.0) || !(t < 1.0);
+        for (int a = 0; a < 3; ++a) r[a] = Pb[a] - m->b[a];
+        if (m->bkind == 2) r[2] = 0.0;
+        rn = norm3(r);
+        rD = r[0] * (Q[0] - P[0]) + r[1] * (Q[1] - P[1]) + r[2] * (Q[2] - P[2]);
+      }
       if (clamped) flag = 1;
       for (int j = 0; j < nc; ++j) {
-        double dDa = T[j].Q[ax] - T[j].P[ax];
-        double dt = clamped ? 0.0 : (-T[j].P[ax] * Da - (bv - P[ax]) * dDa) / (Da * Da);
+        double dt;
+        if (clamped) {
+          dt = 0.0;
+        } else if (ax >= 0) {
+          double Da = Q[ax] - P[ax], dDa = T[j].Q[ax] - T[j].P[ax];
+          dt = (-T[j].P[ax] * Da - (bv - P[ax]) * dDa) / (Da * Da);
+        } else {
+          double s = 0.0;
+          for (int a = 0; a < 3; ++a) s += r[a] * (T[j].P[a] + t * (T[j].Q[a] - T[j].P[a]));
+          dt = -s / rD;
+        }
         double dPb[3];
         for (int a = 0; a < 3; ++a)
           dPb[a] = T[j].P[a] + dt * (Q[a] - P[a]) + t * (T[j].Q[a] - T[j].P[a]);
-        dPb[ax] = 0.0;
+        if (ax >= 0) dPb[ax] = 0.0;
         for (int a = 0; a < 3; ++a) T[j].P[a] = dPb[a];
         T[j].opl += dt * dopl;
       }
@@ -1188,8 +1248,13 @@ static int tangent_one(const orc_medium* m, const orc_params* prm, const double*
       double mu = n_prev / m->n_ext;
       int tir = refract_or_reflect(d, NB, mu, R, &Dm);
       for (int j = 0; j < nc; ++j) {
-        double dd[3];
-        refract_tangent(d, NB, mu, tir, T[j].d, zero, T[j].n_prev / m->n_ext, dd);
+        double dd[3], dNB[3] = {0.0, 0.0, 0.0};
+        if (ax < 0) {
+          double dr[3] = {T[j].P[0], T[j].P[1], m->bkind == 2 ? 0.0 : T[j].P[2]};
+          double Ndr = dot3(NB, dr);
+          for (int a = 0; a < 3; ++a) dNB[a] = (dr[a] - NB[a] * Ndr) / rn;
+        }
+        refract_tangent(d, NB, mu, tir, T[j].d, dNB, T[j].n_prev / m->n_ext, dd);
         for (int a = 0; a < 3; ++a) T[j].d[a] = dd[a];
       }
       for (int a = 0; a < 3; ++a) d[a] = R[a];
@@ -1338,9 +1403,9 @@ int orc_trace_tangent(const orc_medium* m, const orc_params* p, int64_t n, const
                       const double* d, int32_t nparams, const int64_t* params, double* P_out,
                       double* d_out, double* opl, int32_t* exit_id, int32_t* steps, double* tP,
                       double* td, double* topl, int32_t* flag, int32_t nthreads) {
-  if (m->bkind != 0 || m->n_levels != 0) return -1;
+  if (m->bkind < 0 || m->bkind > 2 || m->n_levels != 0) return -1;
   int nc;
-  if (m->kind == 0 && m->form == 0 && m->degree >= 0) {
+  if (m->kind == 0 && m->form >= 0 && m->form <= 2 && m->degree >= 0) {
     nc = (m->degree + 1) * (m->degree + 2) * (m->degree + 3) / 6;
   } else if (m->kind == 1 && nparams > 0 && params) {
     int64_t total = (int64_t)m->nx * m->ny * m->nz;

@@ -627,6 +627,80 @@ def test_tangents_match_central_differences_through_the_exit():
         assert e.max() <= 5e-5 and np.median(e) <= 1e-6, (e.max(), np.median(e))
 
 
+def _curved_tangent_case(name):
+    """(medium, rays, dL0, max steps) whose rays meet a curved surface or an
+    n = sqrt(p) or C / p field: the Luneburg lens (sqrt, collimated beam
+    through the unit sphere), Maxwell's fish-eye (C / p, rays from an
+    interior point refracting out of a sphere of radius 3), the Sec. V
+    corrector (n = p, total internal reflections on its cylinder's side) and
+    the parabolic fibre (sqrt, some rays leaving through the cylinder's
+    side)."""
+    if name == "luneburg":
+        return W.luneburg_medium(), W.luneburg_rays(8), 2e-3, 5000
+    if name == "fisheye":
+        th = W.uniform(7, 1, 256, 0.0, math.pi)
+        ph = W.uniform(7, 2, 256, 0.0, 2 * math.pi)
+        return (W.fisheye_medium(n0=2.0, a=1.0, r_bound=3.0),
+                W.Rays(np.tile([0.5, 0.0, 0.0], (256, 1)), W.direction(th, ph)), 2e-3, 5000)
+    if name == "corrector":
+        wl = W.corrector_workload(128)
+        return wl.medium, wl.rays, 5e-3, 20000
+    x = W.uniform(8, 1, 128, -4.0, 4.0)
+    y = W.uniform(8, 2, 128, -3.0, 3.0)
+    d = W.direction(W.uniform(8, 3, 128, 0.0, math.radians(40)), W.uniform(8, 4, 128, 0, 2 * math.pi))
+    return W.fiber_medium(length=8.0), W.Rays(np.stack([x, y, np.full(128, -1.0)], 1), d), 2e-3, 40000
+
+
+@pytest.mark.parametrize("name", ["luneburg", "fisheye", "corrector", "fiber"])
+def test_curved_surface_and_form_tangents_match_central_differences(name):
+    """The tangents on curved surfaces and through the n = sqrt(p) and C / p
+    forms: the crossing fraction of a sphere or cylinder side by implicit
+    differentiation of the surface along the step, the unit normal moving
+    with the crossing point, and dn = F'(p) dp for n = F(p).  Against
+    central differences as above (h = 1e-6 and 5e-7 on four nonzero
+    coefficients and the last one): within 5e-5, median 1e-6, with the
+    traced values equal to the oracle's trace.  Leaving out the moving
+    normal misses by 3e-3 to 0.4 (Luneburg, fish-eye, corrector), leaving out
+    F'(p) by O(1) (Luneburg, fish-eye, fibre)."""
+    m, rays, dopl, max_steps = _curved_tangent_case(name)
+    t = oracle.trace_tangent(m, rays.origins, rays.dirs, dopl, max_steps)
+    base = oracle.trace(m, rays.origins, rays.dirs, dopl, max_steps)
+    for k in ("P", "d", "opl", "exit_id", "steps"):
+        np.testing.assert_array_equal(t[k], base[k], err_msg=k)
+    # the surface events this case is there for
+    if name in ("luneburg", "fisheye"):
+        assert (base["exit_id"] == 0).sum() >= 50
+    elif name == "corrector":
+        assert base["tir_boundary"].sum() >= 2
+    else:
+        assert (base["exit_id"] == 0).sum() >= 5
+    nc = len(m.coeffs)
+    coords = [i for i in range(nc) if m.coeffs[i] != 0][:4] + [nc - 1]
+    h = 1e-6
+    for i in coords:
+        keep = (t["flag"] == 0) & (base["exit_id"] >= 0)
+        fds = []
+        for hh in (h, h / 2):
+            res = []
+            for s in (+hh, -hh):
+                c = m.coeffs.copy()
+                c[i] += s
+                mm = W.Medium(**{**m.__dict__, "coeffs": c})
+                res.append((oracle.trace(mm, rays.origins, rays.dirs, dopl, max_steps), c[i]))
+            (rp, vp), (rm, vm) = res
+            for k in ("exit_id", "steps", "tir_internal", "tir_boundary"):
+                keep &= (rp[k] == base[k]) & (rm[k] == base[k])
+            fds.append(np.concatenate([rp["P"] - rm["P"], rp["d"] - rm["d"],
+                                       (rp["opl"] - rm["opl"])[:, None]], 1) / (vp - vm))
+        a, b = fds
+        scale = np.abs(a).max(1) + 1e-300
+        keep &= np.abs(a - b).max(1) / scale <= 1e-6
+        tan = np.concatenate([t["tP"][:, i], t["td"][:, i], t["topl"][:, i][:, None]], 1)
+        e = (np.abs(tan - a).max(1) / scale)[keep]
+        assert e.size >= 10, (i, e.size)
+        assert e.max() <= 5e-5 and np.median(e) <= 1e-6, (i, e.max(), np.median(e))
+
+
 def test_grid_sample_tangents_match_central_differences():
     """Tangents with respect to grid samples (the weight of a sample at P is
     the product of its per-axis Catmull-Rom weights, summed over the taps the
