@@ -104,7 +104,7 @@ enum { GRIN_PREC_FP64 = 0, GRIN_PREC_FP32_MIXED = 1, GRIN_PREC_FP64_FAST = 2 };
  *     `coeffs` = R > 0, F > 0, beta, gamma (4 host doubles); form must be
  *     GRIN_FORM_LINEAR; degree and norm_scale are ignored.  The z extent is
  *     the boundary's (a cylinder, z0 = -L, z1 = 0, in the paper).
- *     grin_trace_adjoint returns GRIN_ERR_NOT_IMPLEMENTED for it.
+ *     grin_trace_adjoint's gradient is with respect to (R, F, beta, gamma).
  * n_levels > 0 turns the field into that many isoindicial shells (the
  * discretised media of Sec. I and the abstract): level
  * k = clamp(floor(n_levels (f - level_lo) / (level_hi - level_lo)), 0,
@@ -338,9 +338,11 @@ int grin_trace_stats_compute(grin_ctx ctx, const grin_out* out, int64_t count,
  * up to 2,000 steps).  The gradient is the same for every checkpoint_every.
  * Supported media: a box, sphere or cylinder boundary, not layered, and
  * either a polynomial with n = p, sqrt(p) or form_c / p (gradient w.r.t. its
- * C(degree+3,3) graded-lex coefficients) or a grid (gradient w.r.t. its
- * nx*ny*nz samples, x fastest); layered, spherical-freeform and N2P media
- * give GRIN_ERR_NOT_IMPLEMENTED. */
+ * C(degree+3,3) graded-lex coefficients), the N2P lens (gradient w.r.t.
+ * R, F, beta, gamma: 4 entries) or a grid (gradient w.r.t. its nx*ny*nz
+ * samples, x fastest); layered and spherical-freeform media give
+ * GRIN_ERR_NOT_IMPLEMENTED.  Tangential incidence (N.I == 0, Sec. II (iv))
+ * is differentiated through its arc, including the extra index sample. */
 
 /* dL/d(exit state): device FP64 arrays of `count` entries each (the same
  * fields as grin_out; any may be NULL for zero). */

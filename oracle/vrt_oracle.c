@@ -1082,10 +1082,52 @@ static void ref_eval(const orc_medium* m, const double* P, double* n, double* g)
   field_eval(m, P, n, g);
 }
 
+/* The N2P lens (Sec. VI), n = w^gamma, w = 1 + u^beta,
+ * u = (R^2 - rho^2 / 4) / F^2, rho from the axis through off[0], off[1]:
+ * with du = (-x / 2F^2, -y / 2F^2, 0), dn/du = gamma beta w^(gamma - 1)
+ * u^(beta - 1) =: nu and d nu / du = nuu, grad n = nu du and the Hessian
+ * nuu du du^T + nu diag(-1 / 2F^2, -1 / 2F^2, 0).  Per parameter (R, F,
+ * beta, gamma): dn/dR = nu 2R / F^2, dn/dF = -nu 2u / F,
+ * dn/dbeta = gamma w^(gamma - 1) u^beta ln u, dn/dgamma = w^gamma ln w,
+ * and grad n moves along du: d grad n/dR = nuu (2R / F^2) du,
+ * d grad n/dF = -(2 / F) (u nuu + nu) du, d grad n/dbeta = (d nu/dbeta) du,
+ * d grad n/dgamma = (d nu/dgamma) du. */
+static void n2p_second(const orc_medium* m, const double* P, double H[3][3], double* phi,
+                       double (*gphi)[3]) {
+  double R = m->coeffs[0], F = m->coeffs[1], be = m->coeffs[2], ga = m->coeffs[3];
+  double x = P[0] - m->off[0], y = P[1] - m->off[1];
+  double u = (R * R - (x * x + y * y) / 4.0) / (F * F);
+  double ub = pow(u, be), w = 1.0 + ub;
+  double nu = ga * be * pow(w, ga - 1.0) * pow(u, be - 1.0);
+  double nuu = ga * be * ((ga - 1.0) * be * pow(w, ga - 2.0) * pow(u, 2.0 * be - 2.0) +
+                          (be - 1.0) * pow(w, ga - 1.0) * pow(u, be - 2.0));
+  double du[3] = {-x / (2.0 * F * F), -y / (2.0 * F * F), 0.0};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) H[a][b] = nuu * du[a] * du[b];
+  H[0][0] += -nu / (2.0 * F * F);
+  H[1][1] += -nu / (2.0 * F * F);
+  /* d nu / dbeta and d nu / dgamma, differentiated term by term */
+  double dnu_dbe = ga * pow(w, ga - 1.0) * pow(u, be - 1.0) +
+                   ga * be * (ga - 1.0) * pow(w, ga - 2.0) * ub * log(u) * pow(u, be - 1.0) +
+                   ga * be * pow(w, ga - 1.0) * pow(u, be - 1.0) * log(u);
+  double dnu_dga = be * pow(w, ga - 1.0) * pow(u, be - 1.0) + nu * log(w);
+  double dn[4] = {nu * 2.0 * R / (F * F), -nu * 2.0 * u / F, ga * pow(w, ga - 1.0) * ub * log(u),
+                  pow(w, ga) * log(w)};
+  double c[4] = {nuu * 2.0 * R / (F * F), -(2.0 / F) * (u * nuu + nu), dnu_dbe, dnu_dga};
+  for (int j = 0; j < 4; ++j) {
+    phi[j] = dn[j];
+    for (int a = 0; a < 3; ++a) gphi[j][a] = c[j] * du[a];
+  }
+}
+
 static void ref_second(const orc_medium* m, const double* P, int np, const int64_t* params,
                        double H[3][3], double* phi, double (*gphi)[3]) {
   if (m->kind == 1) {
     grid_second(m, P, np, params, H, phi, gphi);
+    return;
+  }
+  if (m->kind == 3) {
+    n2p_second(m, P, H, phi, gphi);
     return;
   }
   poly_second(m, P, H, phi, gphi);
@@ -1115,19 +1157,20 @@ typedef struct {
   double P[3], d[3], Q[3], n_prev, h, opl;
 } tangent;
 
-/* One ray of a polynomial medium (n = p, sqrt(p) or C / p) or of a grid
- * medium, in a box, sphere or cylinder: trace_one's values and decisions
+/* One ray of a polynomial medium (n = p, sqrt(p) or C / p), of a grid
+ * medium or of the N2P lens, in a box, sphere or cylinder: trace_one's values and decisions
  * (the same operations, in the same order), with every continuous quantity
  * also carrying its derivative with respect to each of the nc parameters
  * (all polynomial coefficients, or the grid samples params[]).  The entry
  * point does not depend on the parameters; at the exit the crossing fraction
  * carries one (a plane face: t = (b - P_a) / (Q_a - P_a)), and on a curved
  * face so does the normal.
- * Returns 1 when the ray met a case the tangents do not follow (tangential
- * incidence N.I == 0, or a crossing fraction clamped to [0, 1]). */
+ * Returns 1 when the ray met a case the tangents do not follow (an arc of
+ * tangential incidence whose a0 = sqrt(1 - k^2) is clamped, or a crossing
+ * fraction clamped to [0, 1]). */
 static int tangent_one(const orc_medium* m, const orc_params* prm, const double* o,
                        const double* d0, ray_out* out, int nc, const int64_t* params, tangent* T,
-                       double* phi, double (*gphi)[3]) {
+                       double* phi, double (*gphi)[3], double* phi2, double (*gphi2)[3]) {
   double P[3] = {o[0], o[1], o[2]}, d[3] = {d0[0], d0[1], d0[2]};
   nsum opl = {0.0, 0.0};
   int flag = 0;
@@ -1305,15 +1348,42 @@ static int tangent_one(const orc_medium* m, const orc_params* prm, const double*
       double c = dot3(N, d);
       double mu = n_prev / n_i;
       if (c == 0.0) {
-        /* tangential incidence: trace_one's arc, value only */
-        flag = 1;
+        /* tangential incidence (Sec. II (iv)): trace_one's arc,
+         * d = normalize(a0 d + k N), k = (n(P'') - n_i) / 2 n_i,
+         * a0 = sqrt(1 - k^2), P'' = P + hi N, hi = dL0 / n_i, with its
+         * tangents: dk = dn'' / 2 n_i - n'' dn_i / 2 n_i^2,
+         * dn'' = dn(P'') + grad n(P'') . dP'', dP'' = dP + dhi N + hi dN,
+         * da0 = -k dk / a0 (not followed where the clamp a0 = 0 acts) */
         double hi = dopl / n_i;
         double Pn[3] = {P[0] + hi * N[0], P[1] + hi * N[1], P[2] + hi * N[2]};
-        double n2, g2[3];
+        double n2, g2[3], H2[3][3];
         ref_eval(m, Pn, &n2, g2);
+        ref_second(m, Pn, nc, params, H2, phi2, gphi2);
         double k = (n2 - n_i) / (2.0 * n_i);
         double w = 1.0 - k * k;
         double a0 = w > 0.0 ? sqrt(w) : 0.0;
+        if (!(w > 0.0)) flag = 1;
+        double Rr[3];
+        for (int a = 0; a < 3; ++a) Rr[a] = a0 * d[a] + k * N[a];
+        double L = norm3(Rr), R[3] = {Rr[0] / L, Rr[1] / L, Rr[2] / L};
+        for (int j = 0; j < nc; ++j) {
+          double dn_i = phi[j] + dot3(g, T[j].P);
+          double dg[3], dN[3], dPn[3], dRr[3];
+          for (int a = 0; a < 3; ++a)
+            dg[a] = gphi[j][a] + H[a][0] * T[j].P[0] + H[a][1] * T[j].P[1] + H[a][2] * T[j].P[2];
+          double Ndg = dot3(N, dg);
+          for (int a = 0; a < 3; ++a) dN[a] = (dg[a] - N[a] * Ndg) / gn;
+          double dhi = -dopl * dn_i / (n_i * n_i);
+          for (int a = 0; a < 3; ++a) dPn[a] = T[j].P[a] + dhi * N[a] + hi * dN[a];
+          double dn2 = phi2[j] + dot3(g2, dPn);
+          double dk = dn2 / (2.0 * n_i) - n2 * dn_i / (2.0 * n_i * n_i);
+          double da0 = w > 0.0 ? -k * dk / a0 : 0.0;
+          for (int a = 0; a < 3; ++a) dRr[a] = da0 * d[a] + a0 * T[j].d[a] + dk * N[a] + k * dN[a];
+          double pr = dot3(R, dRr);
+          for (int a = 0; a < 3; ++a) T[j].d[a] = (dRr[a] - R[a] * pr) / L;
+          T[j].h = dhi;
+          T[j].n_prev = dn_i;
+        }
         for (int a = 0; a < 3; ++a) d[a] = a0 * d[a] + k * N[a];
         normalize3(d);
         n_prev = n_i;
@@ -1374,10 +1444,12 @@ static void* tangent_worker(void* arg) {
   tangent* T = (tangent*)malloc((size_t)j->nc * sizeof(tangent));
   double* phi = (double*)malloc((size_t)j->nc * sizeof(double));
   double(*gphi)[3] = (double(*)[3])malloc((size_t)j->nc * sizeof(*gphi));
+  double* phi2 = (double*)malloc((size_t)j->nc * sizeof(double));
+  double(*gphi2)[3] = (double(*)[3])malloc((size_t)j->nc * sizeof(*gphi2));
   ray_out r;
   for (int64_t i = j->tid; i < j->n; i += j->nt) {
     j->flag[i] = tangent_one(j->m, j->p, j->o + 3 * i, j->d + 3 * i, &r, j->nc, j->params, T,
-                             phi, gphi);
+                             phi, gphi, phi2, gphi2);
     for (int a = 0; a < 3; ++a) {
       j->P_out[3 * i + a] = r.P[a];
       j->d_out[3 * i + a] = r.d[a];
@@ -1396,6 +1468,8 @@ static void* tangent_worker(void* arg) {
   free(T);
   free(phi);
   free(gphi);
+  free(phi2);
+  free(gphi2);
   return NULL;
 }
 
@@ -1407,6 +1481,8 @@ int orc_trace_tangent(const orc_medium* m, const orc_params* p, int64_t n, const
   int nc;
   if (m->kind == 0 && m->form >= 0 && m->form <= 2 && m->degree >= 0) {
     nc = (m->degree + 1) * (m->degree + 2) * (m->degree + 3) / 6;
+  } else if (m->kind == 3 && m->form == 0) {
+    nc = 4; /* R, F, beta, gamma */
   } else if (m->kind == 1 && nparams > 0 && params) {
     int64_t total = (int64_t)m->nx * m->ny * m->nz;
     for (int q = 0; q < nparams; ++q)

@@ -197,6 +197,35 @@ __device__ void field_h_adj(const DevMedium& m, const double* P, double nb, cons
   for (int k = 0; k < 3; ++k) g[k] = 0.0;
   for (int k = 0; k < 6; ++k) H[k] = 0.0;
   n = 0.0;
+  if constexpr (PC == kN2P) {
+    // N2P lens (Sec. VI): n = w^gamma, w = 1 + u^beta, u = (R^2 - rho^2 / 4) / F^2.
+    // With n_u = dn/du = gamma beta w^(gamma-1) u^(beta-1) and
+    // n_uu = n_u ((gamma - 1) beta u^beta / w + beta - 1) / u: grad n = n_u grad u,
+    // H = n_uu grad u grad u^T + n_u diag(-1/2F^2, -1/2F^2, 0).  The parameters
+    // theta = (R, F, beta, gamma) move n by dn/dtheta and grad n by
+    // c_theta grad u (every grad n derivative lies along grad u).
+    const double R = m.cglex[0], F = m.cglex[1], be = m.cglex[2], ga = m.cglex[3];
+    const double X = P[0] - m.off[0], Y = P[1] - m.off[1];
+    const double iF2 = 1.0 / (F * F);
+    const double u = (R * R - (X * X + Y * Y) * 0.25) * iF2;
+    const double lu = log(u), A = pow(u, be), w = 1.0 + A, lw = log(w);
+    n = pow(w, ga);
+    const double n0 = n * A / (w * u);  // n_u / (gamma beta)
+    const double nu = ga * be * n0;
+    const double nuu = nu * fma((ga - 1.0) * be, A / w, be - 1.0) / u;
+    const double ux = -0.5 * X * iF2, uy = -0.5 * Y * iF2, uxx = -0.5 * iF2;
+    g[0] = nu * ux;
+    g[1] = nu * uy;
+    H[0] = fma(nuu * ux, ux, nu * uxx);
+    H[1] = fma(nuu * uy, uy, nu * uxx);
+    H[3] = nuu * ux * uy;
+    const double gbu = fma(gb[0], ux, gb[1] * uy);
+    const double dn[4] = {nu * 2.0 * R * iF2, nu * (-2.0 * u / F), ga * n * A * lu / w, n * lw};
+    const double c[4] = {nuu * 2.0 * R * iF2, (-2.0 / F) * fma(u, nuu, nu),
+                         fma(nu, fma((ga - 1.0) * A, lu / w, lu), ga * n0), fma(nu, lw, be * n0)};
+    for (int q = 0; q < 4; ++q) acc[q] += fma(nb, dn[q], gbu * c[q]);
+    return;
+  }
   if (GRID) {
     const int nn[3] = {m.nx, m.ny, m.nz};
     int b0[3];
@@ -582,6 +611,7 @@ __device__ void normal_back(const DevMedium& m, double dopl, const double* rec, 
   out.n = out.h = 0.0;
   double nb = in.n;
   double gb[3] = {0.0, 0.0, 0.0};
+  double Pxb[3] = {0.0, 0.0, 0.0};  // dL/dP' through the arc's P'' (tangential incidence)
   const double inv_n = 1.0 / n;
   if (gn == 0.0 || !isfinite(gn)) {
     nb = fma(-in.h * dopl, inv_n * inv_n, nb);
@@ -592,11 +622,47 @@ __device__ void normal_back(const DevMedium& m, double dopl, const double* rec, 
     double N[3] = {g[0] / gn, g[1] / gn, g[2] / gn};
     double c = plain::dot3(N, I);
     double mu = n_prev / n;
+    double Nb[3] = {0.0, 0.0, 0.0};
     if (c == 0.0) {
-      // tangential incidence (case iv, measure zero): the arc's direction is
-      // held fixed
-      nb = fma(-in.h * dopl, inv_n * inv_n, nb);
-      for (int k = 0; k < 3; ++k) out.d[k] += in.d[k];
+      // tangential incidence (Sec. II (iv)): the arc's direction
+      // R = a0 I + k N, renormalised, with k = (n(P'') - n) / 2n,
+      // a0 = sqrt(1 - k^2), P'' = P' + hi N and the step hi = dL0 / n, as the
+      // forward sweep forms them; back through n(P''), n, N and I
+      const double hi = dopl / n;
+      double Pa[3];
+      for (int k = 0; k < 3; ++k) Pa[k] = Pn[k] + hi * N[k];
+      double n2, g2[3];
+      int l2;
+      plain::sample<PC, GRID, false>(m, Pa, n2, g2, l2);
+      const double kk = (n2 - n) / (2.0 * n);
+      const double w = 1.0 - kk * kk;
+      const double a0 = w > 0.0 ? sqrt(w) : 0.0;
+      double R[3];
+      for (int k = 0; k < 3; ++k) R[k] = fma(a0, I[k], kk * N[k]);
+      const double inv_Rn = 1.0 / sqrt(fdot3(R, R));
+      double u[3] = {R[0] * inv_Rn, R[1] * inv_Rn, R[2] * inv_Rn};
+      double Rb[3];
+      unit_back(u, inv_Rn, in.d, Rb);
+      const double a0b = fdot3(Rb, I);
+      double kb = fdot3(Rb, N);
+      if (w > 0.0) kb = fma(-a0b, kk / a0, kb);
+      for (int k = 0; k < 3; ++k) {
+        out.d[k] = fma(a0, Rb[k], out.d[k]);
+        Nb[k] = kk * Rb[k];
+      }
+      // k = (n2 - n) / 2n; n2 = n(P''): its parameters, dL/dP'' = n2b grad n(P'')
+      const double n2b = kb * (0.5 * inv_n);
+      nb = fma(-kb * n2 * 0.5, inv_n * inv_n, nb);
+      double nh2, gh2[3], H2[6];
+      field_h_adj<PC, GRID>(m, Pa, n2b, nullptr, nh2, gh2, H2, acc, grad);
+      double hib = in.h;  // the next step's length is hi
+      for (int k = 0; k < 3; ++k) {
+        const double pab = n2b * gh2[k];
+        Pxb[k] += pab;
+        hib = fma(pab, N[k], hib);
+        Nb[k] = fma(hi, pab, Nb[k]);
+      }
+      nb = fma(-hib * dopl, inv_n * inv_n, nb);
     } else {
       double D = 1.0 - mu * mu * (1.0 - c * c);
       bool tir = D <= 0.0;
@@ -605,7 +671,6 @@ __device__ void normal_back(const DevMedium& m, double dopl, const double* rec, 
       double u[3] = {R[0] * inv_Rn, R[1] * inv_Rn, R[2] * inv_Rn};
       double Rb[3];
       unit_back(u, inv_Rn, in.d, Rb);
-      double Nb[3] = {0.0, 0.0, 0.0};
       if (tir) {
         const double inv_p = 1.0 / n_prev;
         out.n = fma(-in.h * dopl, inv_p * inv_p, out.n);
@@ -620,18 +685,18 @@ __device__ void normal_back(const DevMedium& m, double dopl, const double* rec, 
         out.n = fma(mub, inv_n, out.n);
         nb = fma(-mub * mu, inv_n, nb);
       }
-      double s = fdot3(N, Nb);
-      const double inv_gn = 1.0 / gn;
-      for (int k = 0; k < 3; ++k) gb[k] = fma(-N[k], s, Nb[k]) * inv_gn;
     }
+    double s = fdot3(N, Nb);
+    const double inv_gn = 1.0 / gn;
+    for (int k = 0; k < 3; ++k) gb[k] = fma(-N[k], s, Nb[k]) * inv_gn;
   }
-  // field at P': dL/dP' = in.P + nb grad n + H gb; parameters
+  // field at P': dL/dP' = in.P + nb grad n + H gb (+ the arc's P''); parameters
   double nh, gh[3], H[6];
   field_h_adj<PC, GRID>(m, Pn, nb, gb, nh, gh, H, acc, grad);
   double Pb[3];
-  Pb[0] = fma(H[4], gb[2], fma(H[3], gb[1], fma(H[0], gb[0], fma(nb, gh[0], in.P[0]))));
-  Pb[1] = fma(H[5], gb[2], fma(H[1], gb[1], fma(H[3], gb[0], fma(nb, gh[1], in.P[1]))));
-  Pb[2] = fma(H[2], gb[2], fma(H[5], gb[1], fma(H[4], gb[0], fma(nb, gh[2], in.P[2]))));
+  Pb[0] = fma(H[4], gb[2], fma(H[3], gb[1], fma(H[0], gb[0], fma(nb, gh[0], in.P[0] + Pxb[0]))));
+  Pb[1] = fma(H[5], gb[2], fma(H[1], gb[1], fma(H[3], gb[0], fma(nb, gh[1], in.P[1] + Pxb[1]))));
+  Pb[2] = fma(H[2], gb[2], fma(H[5], gb[1], fma(H[4], gb[0], fma(nb, gh[2], in.P[2] + Pxb[2]))));
   // P' = P + h I
   for (int k = 0; k < 3; ++k) {
     out.P[k] += Pb[k];
@@ -930,7 +995,7 @@ bool adjoint_supported(const DevMedium& m) {
   if (m.bkind != GRIN_BOUNDARY_BOX && m.bkind != GRIN_BOUNDARY_SPHERE &&
       m.bkind != GRIN_BOUNDARY_CYLINDER)
     return false;
-  if (m.kind == GRIN_MEDIUM_GRID) return true;
+  if (m.kind == GRIN_MEDIUM_GRID || m.kind == GRIN_MEDIUM_N2P) return true;
   return m.kind == GRIN_MEDIUM_POLY && (m.form == GRIN_FORM_LINEAR || m.form == GRIN_FORM_SQRT ||
                                         m.form == GRIN_FORM_RECIP);
 }
@@ -972,6 +1037,7 @@ int launch_adjoint(const DevMedium& m, const TraceArgs& a, int32_t k, void* ws, 
   if (a.count < (int64_t(1) << 31))
     A.order_ws = (char*)ws + adjoint_order_offset(a.count, a.max_steps, k);
   if (m.kind == GRIN_MEDIUM_GRID) return adj::run_t<0, true>(m, A, st, phase);
+  if (m.kind == GRIN_MEDIUM_N2P) return adj::run_t<kN2P, false>(m, A, st, phase);
   switch (m.pclass) {
     case kPoly2: return adj::run_t<2, false>(m, A, st, phase);
     case kPoly4: return adj::run_t<4, false>(m, A, st, phase);

@@ -701,6 +701,50 @@ def test_curved_surface_and_form_tangents_match_central_differences(name):
         assert e.max() <= 5e-5 and np.median(e) <= 1e-6, (i, e.max(), np.median(e))
 
 
+def test_n2p_lens_tangents_through_the_arc_match_central_differences():
+    """The N2P lens (Sec. VI) with respect to R, F, beta, gamma, on the
+    design fan: rays parallel to the axis meet the radial gradient with
+    N.I = 0 exactly, so their first step is the tangential-incidence arc of
+    Sec. II (iv), whose tangent carries k = (n(P'') - n_i) / 2 n_i through the
+    extra sample at P'' = P + hi N.  The fan's rays stay nearly parallel to
+    the axis, where Eq. 9's D is formed by cancellation, so differences at
+    h = 1e-6 are rounding noise; at h = 1e-4 and 5e-5 they agree to about
+    1e-7, and the tangents lie within 5e-5 of them (median 1e-6) on every
+    ray whose two differences agree to 2e-5.  Without the arc's dk the
+    tangents miss by far more."""
+    from paper_2606_22655_b300 import n2p_design
+    m = W.n2p_lens_medium(0.770, 4.462, 0.3)
+    rays = n2p_design.fan(64, 0.3)
+    dopl, max_steps = 1e-3, 400000
+    t = oracle.trace_tangent(m, rays.origins, rays.dirs, dopl, max_steps)
+    base = oracle.trace(m, rays.origins, rays.dirs, dopl, max_steps)
+    for k in ("P", "d", "opl", "exit_id", "steps"):
+        np.testing.assert_array_equal(t[k], base[k], err_msg=k)
+    assert (t["flag"] == 0).all() and (base["exit_id"] == 2).all()
+    h = 1e-4
+    for i in range(4):
+        keep = np.ones(rays.n, bool)
+        fds = []
+        for hh in (h, h / 2):
+            res = []
+            for s in (+hh, -hh):
+                c = m.coeffs.copy()
+                c[i] += s
+                mm = W.Medium(**{**m.__dict__, "coeffs": c})
+                res.append(oracle.trace(mm, rays.origins, rays.dirs, dopl, max_steps))
+            for k in ("exit_id", "steps", "tir_internal", "tir_boundary"):
+                keep &= (res[0][k] == base[k]) & (res[1][k] == base[k])
+            fds.append(np.concatenate([res[0]["P"] - res[1]["P"], res[0]["d"] - res[1]["d"],
+                                       (res[0]["opl"] - res[1]["opl"])[:, None]], 1) / (2 * hh))
+        a, b = fds
+        scale = np.abs(a).max(1) + 1e-300
+        keep &= np.abs(a - b).max(1) / scale <= 2e-5
+        tan = np.concatenate([t["tP"][:, i], t["td"][:, i], t["topl"][:, i][:, None]], 1)
+        e = (np.abs(tan - b).max(1) / scale)[keep]
+        assert e.size >= 30, (i, e.size)
+        assert e.max() <= 5e-5 and np.median(e) <= 1e-6, (i, e.max(), np.median(e))
+
+
 def test_grid_sample_tangents_match_central_differences():
     """Tangents with respect to grid samples (the weight of a sample at P is
     the product of its per-axis Catmull-Rom weights, summed over the taps the
