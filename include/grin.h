@@ -97,7 +97,7 @@ enum { GRIN_PREC_FP64 = 0, GRIN_PREC_FP32_MIXED = 1, GRIN_PREC_FP64_FAST = 2 };
  *     coordinates x' (r = |x'|, theta from +z', phi the azimuth), a0..a3 the
  *     4 host doubles in `coeffs` (degree is ignored); `form` maps p to n as
  *     for polynomials.  At r = 0 the polar angle is taken as 0.
- *     grin_trace_adjoint returns GRIN_ERR_NOT_IMPLEMENTED for it;
+ *     grin_trace_adjoint's gradient is with respect to a0..a3;
  *   - GRIN_MEDIUM_N2P: the N2P-GRIN cylinder lens of Sec. VI,
  *     n = [1 + ((R^2 - (rho/2)^2) / F^2)^beta]^gamma with rho the distance
  *     from the axis through (norm_offset[0], norm_offset[1]) parallel to z;
@@ -338,10 +338,10 @@ int grin_trace_stats_compute(grin_ctx ctx, const grin_out* out, int64_t count,
  * up to 2,000 steps).  The gradient is the same for every checkpoint_every.
  * Supported media: a box, sphere or cylinder boundary, not layered, and
  * either a polynomial with n = p, sqrt(p) or form_c / p (gradient w.r.t. its
- * C(degree+3,3) graded-lex coefficients), the N2P lens (gradient w.r.t.
- * R, F, beta, gamma: 4 entries) or a grid (gradient w.r.t. its nx*ny*nz
- * samples, x fastest); layered and spherical-freeform media give
- * GRIN_ERR_NOT_IMPLEMENTED.  Tangential incidence (N.I == 0, Sec. II (iv))
+ * C(degree+3,3) graded-lex coefficients), the spherical freeform (a0..a3,
+ * with the same forms), the N2P lens (gradient w.r.t. R, F, beta, gamma: 4
+ * entries) or a grid (gradient w.r.t. its nx*ny*nz samples, x fastest);
+ * layered media give GRIN_ERR_NOT_IMPLEMENTED.  Tangential incidence (N.I == 0, Sec. II (iv))
  * is differentiated through its arc, including the extra index sample. */
 
 /* dL/d(exit state): device FP64 arrays of `count` entries each (the same

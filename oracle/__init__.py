@@ -202,7 +202,8 @@ def trace_tangent(medium, origins, dirs, dopl: float, max_steps: int, samples=No
                   threads: Optional[int] = None) -> Dict[str, np.ndarray]:
     """Exit state of every ray (as `trace`) and its forward-mode derivative
     with respect to each polynomial coefficient (polynomial media, n = p,
-    sqrt(p) or form_c / p), to R, F, beta, gamma (the N2P lens) or to each
+    sqrt(p) or form_c / p), to a0 .. a3 (the spherical freeform), to R, F,
+    beta, gamma (the N2P lens) or to each
     grid sample in `samples` (flat
     indices, x fastest; grid media): tP, td (n, nc, 3), topl (n, nc); flag
     (n,) marks rays whose tangents are not followed (tangential incidence,
@@ -214,8 +215,8 @@ def trace_tangent(medium, origins, dirs, dopl: float, max_steps: int, samples=No
     d = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
     n = o.shape[0]
     if samples is None:
-        # the N2P lens's parameters are (R, F, beta, gamma)
-        nc = 4 if medium.kind == 3 else (medium.degree + 1) * (medium.degree + 2) * (medium.degree + 3) // 6
+        # the spherical freeform's a0 .. a3, the N2P lens's (R, F, beta, gamma)
+        nc = 4 if medium.kind in (2, 3) else (medium.degree + 1) * (medium.degree + 2) * (medium.degree + 3) // 6
         par = np.zeros(1, np.int64)
     else:
         par = np.ascontiguousarray(samples, dtype=np.int64).ravel()

@@ -1120,6 +1120,62 @@ static void n2p_second(const orc_medium* m, const double* P, double H[3][3], dou
   }
 }
 
+/* The spherical freeform field (Sec. V) in sph_eval's forms: the Hessian of
+ * p = a0 + a1 G1 + a2 G2 + a3 G3 and, per coefficient a_k, dp = G_k and
+ * d grad p = grad G_k.  G1 = 0.3 (r^2 - 1) and G3 = x^2 - y^2 have the
+ * constant Hessians 0.6 I and diag(2, -2, 0).  For G2 = z q(t), t = z^2 s,
+ * s = 1 / r^2, q = 16 t^2 - 20 t + 5: s_ab = 8 x_a x_b s^3 - 2 delta_ab s^2,
+ * so t_xx = z^2 (8 x^2 s^3 - 2 s^2), t_xy = 8 x y z^2 s^3,
+ * t_xz = 8 x z^3 s^3 - 4 x z s^2, t_zz = 2 s - 10 z^2 s^2 + 8 z^4 s^3 (y as
+ * x), and G2_ab = z (q'' t_a t_b + q' t_ab) + q' (t_a [b = z] + t_b [a = z]),
+ * q' = 32 t - 20, q'' = 32.  At r = 0 t's derivatives are taken as 0, as
+ * sph_eval takes the polar angle there. */
+static void sph_second(const orc_medium* m, const double* P, double H[3][3], double* phi,
+                       double (*gphi)[3]) {
+  double X[3];
+  for (int a = 0; a < 3; ++a) X[a] = (P[a] - m->off[a]) / m->scale[a];
+  const double* c = m->coeffs;
+  double r2 = dot3(X, X);
+  double t = 1.0, dt[3] = {0.0, 0.0, 0.0}, ddt[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+  double z = X[2];
+  if (r2 > 0.0) {
+    double s = 1.0 / r2;
+    t = z * z * s;
+    dt[0] = -2.0 * X[0] * t / r2;
+    dt[1] = -2.0 * X[1] * t / r2;
+    dt[2] = 2.0 * z * (1.0 - t) / r2;
+    for (int a = 0; a < 2; ++a) {
+      for (int b = 0; b < 2; ++b)
+        ddt[a][b] = z * z * (8.0 * X[a] * X[b] * s * s * s - (a == b ? 2.0 * s * s : 0.0));
+      ddt[a][2] = ddt[2][a] = 8.0 * X[a] * z * z * z * s * s * s - 4.0 * X[a] * z * s * s;
+    }
+    ddt[2][2] = 2.0 * s - 10.0 * z * z * s * s + 8.0 * z * z * z * z * s * s * s;
+  }
+  double q = 16.0 * t * t - 20.0 * t + 5.0, q1 = 32.0 * t - 20.0, q2 = 32.0;
+  double G2H[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      G2H[a][b] = z * (q2 * dt[a] * dt[b] + q1 * ddt[a][b]);
+      if (b == 2) G2H[a][b] += q1 * dt[a];
+      if (a == 2) G2H[a][b] += q1 * dt[b];
+    }
+  double G3H[3] = {2.0, -2.0, 0.0};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      H[a][b] = (c[1] * (a == b ? 0.6 : 0.0) + c[2] * G2H[a][b] + c[3] * (a == b ? G3H[a] : 0.0)) /
+                (m->scale[a] * m->scale[b]);
+  double dG[4][3] = {{0.0, 0.0, 0.0},
+                     {0.6 * X[0], 0.6 * X[1], 0.6 * X[2]},
+                     {z * q1 * dt[0], z * q1 * dt[1], q + z * q1 * dt[2]},
+                     {2.0 * X[0], -2.0 * X[1], 0.0}};
+  phi[0] = 1.0;
+  phi[1] = 0.3 * (r2 - 1.0);
+  phi[2] = z * q;
+  phi[3] = X[0] * X[0] - X[1] * X[1];
+  for (int k = 0; k < 4; ++k)
+    for (int a = 0; a < 3; ++a) gphi[k][a] = dG[k][a] / m->scale[a];
+}
+
 static void ref_second(const orc_medium* m, const double* P, int np, const int64_t* params,
                        double H[3][3], double* phi, double (*gphi)[3]) {
   if (m->kind == 1) {
@@ -1130,11 +1186,18 @@ static void ref_second(const orc_medium* m, const double* P, int np, const int64
     n2p_second(m, P, H, phi, gphi);
     return;
   }
-  poly_second(m, P, H, phi, gphi);
-  if (m->form == 0) return;
-  int nc = (m->degree + 1) * (m->degree + 2) * (m->degree + 3) / 6;
+  int nc;
   double p, gp[3];
-  poly_eval(m, P, &p, gp);
+  if (m->kind == 2) {
+    sph_second(m, P, H, phi, gphi);
+    nc = 4;
+  } else {
+    poly_second(m, P, H, phi, gphi);
+    nc = (m->degree + 1) * (m->degree + 2) * (m->degree + 3) / 6;
+  }
+  if (m->form == 0) return;
+  if (m->kind == 2) sph_eval(m, P, &p, gp);
+  else poly_eval(m, P, &p, gp);
   double a1, a2; /* n' and n'' of the form at p */
   if (m->form == 1) {
     double n = sqrt(p);
@@ -1157,8 +1220,9 @@ typedef struct {
   double P[3], d[3], Q[3], n_prev, h, opl;
 } tangent;
 
-/* One ray of a polynomial medium (n = p, sqrt(p) or C / p), of a grid
- * medium or of the N2P lens, in a box, sphere or cylinder: trace_one's values and decisions
+/* One ray of a polynomial or spherical freeform medium (n = p, sqrt(p) or
+ * C / p), of a grid medium or of the N2P lens, in a box, sphere or
+ * cylinder: trace_one's values and decisions
  * (the same operations, in the same order), with every continuous quantity
  * also carrying its derivative with respect to each of the nc parameters
  * (all polynomial coefficients, or the grid samples params[]).  The entry
@@ -1483,6 +1547,8 @@ int orc_trace_tangent(const orc_medium* m, const orc_params* p, int64_t n, const
     nc = (m->degree + 1) * (m->degree + 2) * (m->degree + 3) / 6;
   } else if (m->kind == 3 && m->form == 0) {
     nc = 4; /* R, F, beta, gamma */
+  } else if (m->kind == 2 && m->form >= 0 && m->form <= 2) {
+    nc = 4; /* a0 .. a3 */
   } else if (m->kind == 1 && nparams > 0 && params) {
     int64_t total = (int64_t)m->nx * m->ny * m->nz;
     for (int q = 0; q < nparams; ++q)

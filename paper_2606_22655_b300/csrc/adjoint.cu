@@ -226,6 +226,77 @@ __device__ void field_h_adj(const DevMedium& m, const double* P, double nb, cons
     for (int q = 0; q < 4; ++q) acc[q] += fma(nb, dn[q], gbu * c[q]);
     return;
   }
+  if constexpr (PC == kSpherical) {
+    // Spherical freeform (Sec. V): p = a0 + a1 G1 + a2 G2 + a3 G3 in the
+    // normalised coordinates X, G1 = 0.3 (r^2 - 1), G2 = z q(t) with
+    // t = z^2 s, s = 1 / r^2, q = 16 t^2 - 20 t + 5, G3 = x^2 - y^2.  With
+    // t_a and t_ab from s_ab = 8 X_a X_b s^3 - 2 delta_ab s^2,
+    // G2_ab = z (32 t_a t_b + q' t_ab) + q' (t_a [b = z] + t_b [a = z]); G1 and
+    // G3 have the Hessians 0.6 I and diag(2, -2, 0).  dp/da_k = G_k; the form
+    // (n = p, sqrt(p), C / p) by the chain rule as for polynomials.
+    const double* a = m.cglex;
+    double X[3];
+    for (int k = 0; k < 3; ++k) X[k] = (P[k] - m.off[k]) * m.inv_scale[k];
+    const double z = X[2];
+    const double r2 = fdot3(X, X);
+    double t = 1.0, dt[3] = {0.0, 0.0, 0.0}, tt[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (r2 > 0.0) {
+      const double sv = 1.0 / r2, s2 = sv * sv, s3 = s2 * sv, zz = z * z;
+      t = zz * sv;
+      dt[0] = -2.0 * X[0] * t * sv;
+      dt[1] = -2.0 * X[1] * t * sv;
+      dt[2] = 2.0 * z * (1.0 - t) * sv;
+      tt[0] = zz * fma(8.0 * X[0] * X[0], s3, -2.0 * s2);
+      tt[1] = zz * fma(8.0 * X[1] * X[1], s3, -2.0 * s2);
+      tt[2] = fma(8.0 * zz * zz, s3, fma(-10.0 * zz, s2, 2.0 * sv));
+      tt[3] = 8.0 * X[0] * X[1] * zz * s3;
+      tt[4] = X[0] * z * fma(8.0 * zz, s3, -4.0 * s2);
+      tt[5] = X[1] * z * fma(8.0 * zz, s3, -4.0 * s2);
+    }
+    const double q = fma(fma(16.0, t, -20.0), t, 5.0), q1 = fma(32.0, t, -20.0);
+    const int hi[6] = {0, 1, 2, 0, 0, 1}, hj[6] = {0, 1, 2, 1, 2, 2};
+    const double* is = m.inv_scale;
+    const double G[4] = {1.0, 0.3 * (r2 - 1.0), z * q, fma(X[0], X[0], -X[1] * X[1])};
+    double dG[4][3] = {{0.0, 0.0, 0.0},
+                       {0.6 * X[0] * is[0], 0.6 * X[1] * is[1], 0.6 * X[2] * is[2]},
+                       {z * q1 * dt[0] * is[0], z * q1 * dt[1] * is[1], fma(z * q1, dt[2], q) * is[2]},
+                       {2.0 * X[0] * is[0], -2.0 * X[1] * is[1], 0.0}};
+    double pv = a[0], gp[3] = {0.0, 0.0, 0.0}, Hp[6];
+    for (int k = 1; k < 4; ++k) {
+      pv = fma(a[k], G[k], pv);
+      for (int c = 0; c < 3; ++c) gp[c] = fma(a[k], dG[k][c], gp[c]);
+    }
+    for (int e = 0; e < 6; ++e) {
+      const int i = hi[e], j = hj[e];
+      double h2 = z * fma(32.0 * dt[i], dt[j], q1 * tt[e]);
+      if (j == 2) h2 = fma(q1, dt[i], h2);
+      if (i == 2) h2 = fma(q1, dt[j], h2);
+      const double h1 = i == j ? 0.6 : 0.0, h3 = i == j ? (i == 0 ? 2.0 : (i == 1 ? -2.0 : 0.0)) : 0.0;
+      Hp[e] = fma(a[1], h1, fma(a[2], h2, a[3] * h3)) * is[i] * is[j];
+    }
+    double pb = nb, gscale = 1.0;
+    if (m.form == GRIN_FORM_LINEAR) {
+      n = pv;
+      for (int c = 0; c < 3; ++c) g[c] = gp[c];
+      for (int e = 0; e < 6; ++e) H[e] = Hp[e];
+    } else if (m.form == GRIN_FORM_SQRT) {
+      n = sqrt(pv);
+      const double i2n = 0.5 / n, i4n3 = 0.25 / (n * n * n);
+      for (int c = 0; c < 3; ++c) g[c] = gp[c] * i2n;
+      for (int e = 0; e < 6; ++e) H[e] = fma(Hp[e], i2n, -gp[hi[e]] * gp[hj[e]] * i4n3);
+      pb = fma(nb, i2n, -fdot3(gb, gp) * i4n3);
+      gscale = i2n;
+    } else {
+      const double C = m.form_c, ip = 1.0 / pv, cp2 = C * ip * ip, c2p3 = 2.0 * cp2 * ip;
+      n = C * ip;
+      for (int c = 0; c < 3; ++c) g[c] = -cp2 * gp[c];
+      for (int e = 0; e < 6; ++e) H[e] = fma(-cp2, Hp[e], c2p3 * gp[hi[e]] * gp[hj[e]]);
+      pb = fma(-cp2, nb, c2p3 * fdot3(gb, gp));
+      gscale = -cp2;
+    }
+    for (int k = 0; k < 4; ++k) acc[k] += fma(pb, G[k], gscale * fdot3(gb, dG[k]));
+    return;
+  }
   if (GRID) {
     const int nn[3] = {m.nx, m.ny, m.nz};
     int b0[3];
@@ -996,8 +1067,8 @@ bool adjoint_supported(const DevMedium& m) {
       m.bkind != GRIN_BOUNDARY_CYLINDER)
     return false;
   if (m.kind == GRIN_MEDIUM_GRID || m.kind == GRIN_MEDIUM_N2P) return true;
-  return m.kind == GRIN_MEDIUM_POLY && (m.form == GRIN_FORM_LINEAR || m.form == GRIN_FORM_SQRT ||
-                                        m.form == GRIN_FORM_RECIP);
+  return (m.kind == GRIN_MEDIUM_POLY || m.kind == GRIN_MEDIUM_SPHERICAL) &&
+         (m.form == GRIN_FORM_LINEAR || m.form == GRIN_FORM_SQRT || m.form == GRIN_FORM_RECIP);
 }
 
 // Workspace: checkpoints [ray][segment][kCk] | meta [ray][2] | (256-byte
@@ -1038,6 +1109,7 @@ int launch_adjoint(const DevMedium& m, const TraceArgs& a, int32_t k, void* ws, 
     A.order_ws = (char*)ws + adjoint_order_offset(a.count, a.max_steps, k);
   if (m.kind == GRIN_MEDIUM_GRID) return adj::run_t<0, true>(m, A, st, phase);
   if (m.kind == GRIN_MEDIUM_N2P) return adj::run_t<kN2P, false>(m, A, st, phase);
+  if (m.kind == GRIN_MEDIUM_SPHERICAL) return adj::run_t<kSpherical, false>(m, A, st, phase);
   switch (m.pclass) {
     case kPoly2: return adj::run_t<2, false>(m, A, st, phase);
     case kPoly4: return adj::run_t<4, false>(m, A, st, phase);

@@ -861,7 +861,9 @@ static int trace_adjoint_phase(grin_ctx ctx, grin_medium medium, const grin_rays
   a.flags = p->flags;
   a.margin = out->margin;
   const grin::DevMedium& m = medium->dm;
-  int nterms = m.kind == GRIN_MEDIUM_POLY ? grin_poly_terms(m.pclass) : (m.kind == GRIN_MEDIUM_N2P ? 4 : 0);
+  // polynomial: its coefficients; N2P lens: R, F, beta, gamma; spherical freeform: a0 .. a3
+  int nterms = m.kind == GRIN_MEDIUM_POLY ? grin_poly_terms(m.pclass)
+               : (m.kind == GRIN_MEDIUM_N2P || m.kind == GRIN_MEDIUM_SPHERICAL) ? 4 : 0;
   int rc = grin::launch_adjoint(m, a, k, ws, phase == grin::kAdjForward ? nullptr : gout, grad, nterms,
                                 (cudaStream_t)cuda_stream, phase);
   if (rc < 0) return rc;

@@ -379,7 +379,9 @@ def _curved_case(name):
       terms over 35 monomials) in its cylinder, entering through an end face,
       with total internal reflections on the side wall;
     - fiber: the parabolic fibre n^2 = nc^2 (1 - 2 delta rho^2 / R^2) in a
-      cylinder inside its cladding, many rays refracting out of the side."""
+      cylinder inside its cladding, many rays refracting out of the side;
+    - spherical: the spherical freeform of Sec. V (a0 .. a3, G2 = r cos 5
+      theta) in its unit sphere, rays from outside aimed inside it."""
     if name == "luneburg":
         m = W.luneburg_medium()
         return m, _heading_to_plane(m, W.luneburg_rays(24), 2e-3, 5000, 256), 2e-3, 5000
@@ -393,6 +395,9 @@ def _curved_case(name):
     if name == "corrector":
         wl = W.corrector_workload(1024)
         return wl.medium, _heading_to_plane(wl.medium, wl.rays, 5e-3, 20000, 256), 5e-3, 20000
+    if name == "spherical":
+        wl = W.spherical_workload(4096)
+        return wl.medium, _heading_to_plane(wl.medium, wl.rays, 1e-3, 20000, 256), 1e-3, 20000
     m = W.fiber_medium(length=8.0)
     x = W.uniform(8, 1, 2048, -4.0, 4.0)
     y = W.uniform(8, 2, 2048, -3.0, 3.0)
@@ -401,11 +406,12 @@ def _curved_case(name):
     return m, _heading_to_plane(m, rays, 2e-3, 40000, 256), 2e-3, 40000
 
 
-CURVED = ("luneburg", "fisheye", "corrector", "fiber")
-# Kept fraction of ray-coordinate pairs, measured 0.996, 0.996, 0.66 and
-# 0.80: in the corrector and the fibre most rays turn in the field (N.I
-# through zero inside a step, a kink of the discrete map within the FD step).
-KEPT_FLOOR_CURVED = {"luneburg": 0.95, "fisheye": 0.95, "corrector": 0.5, "fiber": 0.7}
+CURVED = ("luneburg", "fisheye", "corrector", "fiber", "spherical")
+# Kept fraction of ray-coordinate pairs, measured 0.996, 0.996, 0.66, 0.80
+# and 0.73: in the corrector, the fibre and the spherical freeform most rays
+# turn in the field (N.I through zero inside a step, a kink of the discrete
+# map within the FD step).
+KEPT_FLOOR_CURVED = {"luneburg": 0.95, "fisheye": 0.95, "corrector": 0.5, "fiber": 0.7, "spherical": 0.6}
 
 
 @pytest.mark.parametrize("name", CURVED)

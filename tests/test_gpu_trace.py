@@ -13,6 +13,7 @@ flagged fraction is bounded per medium.  The spherical freeform medium of
 Sec. V, whose r cos(5 theta) puts many turning points of n on every path, is
 stated (fraction within 2e-5 and the largest error) rather than gated.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -427,7 +428,8 @@ def test_new_media_argument_errors(ctx):
     rb = tracer.RayBatch.from_numpy(np.array([[0.0, 0.3, -1.0]]), np.array([[0.0, 0.0, 1.0]]),
                                     dtype=torch.float64)
     g = {k: torch.zeros(1, dtype=torch.float64, device="cuda") for k in tracer.OUT_FIELDS}
-    for spec in (sph,):  # the spherical freeform has no adjoint
+    layered = dataclasses.replace(W.luneburg_medium(), n_levels=8, level_lo=1.0, level_hi=math.sqrt(2.0))
+    for spec in (layered,):  # shells have no adjoint
         med = tracer.Medium(ctx, spec)
         with pytest.raises(N.GrinError) as e:
             tracer.trace_adjoint(ctx, med, rb, 1e-3, 100, g, 4, 8)

@@ -634,7 +634,8 @@ def _curved_tangent_case(name):
     interior point refracting out of a sphere of radius 3), the Sec. V
     corrector (n = p, total internal reflections on its cylinder's side) and
     the parabolic fibre (sqrt, some rays leaving through the cylinder's
-    side)."""
+    side); and the spherical freeform of Sec. V (coefficients a0 .. a3, the
+    Hessian of G2 = r cos 5 theta), rays through its unit sphere."""
     if name == "luneburg":
         return W.luneburg_medium(), W.luneburg_rays(8), 2e-3, 5000
     if name == "fisheye":
@@ -645,13 +646,16 @@ def _curved_tangent_case(name):
     if name == "corrector":
         wl = W.corrector_workload(128)
         return wl.medium, wl.rays, 5e-3, 20000
+    if name == "spherical":
+        wl = W.spherical_workload(128)
+        return wl.medium, wl.rays, 1e-3, 20000
     x = W.uniform(8, 1, 128, -4.0, 4.0)
     y = W.uniform(8, 2, 128, -3.0, 3.0)
     d = W.direction(W.uniform(8, 3, 128, 0.0, math.radians(40)), W.uniform(8, 4, 128, 0, 2 * math.pi))
     return W.fiber_medium(length=8.0), W.Rays(np.stack([x, y, np.full(128, -1.0)], 1), d), 2e-3, 40000
 
 
-@pytest.mark.parametrize("name", ["luneburg", "fisheye", "corrector", "fiber"])
+@pytest.mark.parametrize("name", ["luneburg", "fisheye", "corrector", "fiber", "spherical"])
 def test_curved_surface_and_form_tangents_match_central_differences(name):
     """The tangents on curved surfaces and through the n = sqrt(p) and C / p
     forms: the crossing fraction of a sphere or cylinder side by implicit
@@ -661,14 +665,15 @@ def test_curved_surface_and_form_tangents_match_central_differences(name):
     coefficients and the last one): within 5e-5, median 1e-6, with the
     traced values equal to the oracle's trace.  Leaving out the moving
     normal misses by 3e-3 to 0.4 (Luneburg, fish-eye, corrector), leaving out
-    F'(p) by O(1) (Luneburg, fish-eye, fibre)."""
+    F'(p) by O(1) (Luneburg, fish-eye, fibre), leaving out t's second
+    derivatives in G2's Hessian likewise (spherical)."""
     m, rays, dopl, max_steps = _curved_tangent_case(name)
     t = oracle.trace_tangent(m, rays.origins, rays.dirs, dopl, max_steps)
     base = oracle.trace(m, rays.origins, rays.dirs, dopl, max_steps)
     for k in ("P", "d", "opl", "exit_id", "steps"):
         np.testing.assert_array_equal(t[k], base[k], err_msg=k)
     # the surface events this case is there for
-    if name in ("luneburg", "fisheye"):
+    if name in ("luneburg", "fisheye", "spherical"):
         assert (base["exit_id"] == 0).sum() >= 50
     elif name == "corrector":
         assert base["tir_boundary"].sum() >= 2
