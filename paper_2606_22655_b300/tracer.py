@@ -458,7 +458,8 @@ def _with_params(spec, theta: torch.Tensor):
 
 class TraceFunction(torch.autograd.Function):
     """Exit point, direction and optical path of every ray as a function of
-    the medium parameters theta (polynomial coefficients, or grid samples).
+    the medium parameters theta (polynomial coefficients, the spherical
+    freeform's a0..a3, the N2P lens's R, F, beta, gamma, or grid samples).
     forward runs the adjoint's forward sweep (the plain FP64 trace, which also
     stores the checkpoints) and backward its backward sweep from them, so the
     rays are traced forward once.  k = 0 takes the checkpoint interval from
