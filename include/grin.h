@@ -336,12 +336,15 @@ int grin_trace_stats_compute(grin_ctx ctx, const grin_out* out, int64_t count,
  * case and the field at its end point, so the backward sweep recomputes
  * nothing, for 104 bytes a ray-step of workspace (55 GB for 262,144 rays of
  * up to 2,000 steps).  The gradient is the same for every checkpoint_every.
- * Supported media: a box, sphere or cylinder boundary, not layered, and
- * either a polynomial with n = p, sqrt(p) or form_c / p (gradient w.r.t. its
+ * Supported media: a box, sphere or cylinder boundary, and either a
+ * polynomial with n = p, sqrt(p) or form_c / p (gradient w.r.t. its
  * C(degree+3,3) graded-lex coefficients), the spherical freeform (a0..a3,
  * with the same forms), the N2P lens (gradient w.r.t. R, F, beta, gamma: 4
  * entries) or a grid (gradient w.r.t. its nx*ny*nz samples, x fastest);
- * layered media give GRIN_ERR_NOT_IMPLEMENTED.  Tangential incidence (N.I == 0, Sec. II (iv))
+ * continuous or in point-sampled shells (n_levels > 0: a shell's index is a
+ * constant, the parameters act through the refraction normal of the smooth
+ * field).  GRIN_TRACE_LEVEL_ROOT (exact shell crossings) and a margin output
+ * give GRIN_ERR_NOT_IMPLEMENTED.  Tangential incidence (N.I == 0, Sec. II (iv))
  * is differentiated through its arc, including the extra index sample. */
 
 /* dL/d(exit state): device FP64 arrays of `count` entries each (the same

@@ -207,8 +207,9 @@ def trace_tangent(medium, origins, dirs, dopl: float, max_steps: int, samples=No
     grid sample in `samples` (flat
     indices, x fastest; grid media): tP, td (n, nc, 3), topl (n, nc); flag
     (n,) marks rays whose tangents are not followed (tangential incidence,
-    clamped crossing fraction).  Box, sphere or cylinder boundaries, no
-    layering."""
+    clamped crossing fraction).  Box, sphere or cylinder boundaries;
+    continuous media or point-sampled shells (whose constant indices have
+    zero derivatives; the shells' refraction normals still move)."""
     lib = _load()
     b = _Bound(medium)
     o = np.ascontiguousarray(origins, dtype=np.float64).reshape(-1, 3)

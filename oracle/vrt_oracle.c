@@ -1070,17 +1070,13 @@ static void grid_second(const orc_medium* m, const double* P, int np, const int6
   }
 }
 
-/* n and grad n as trace_one samples them (field_eval: the polynomial's form
- * applied, or the grid's interpolant), and the second-order data of the
- * tangents: the Hessian of n and, per parameter (all polynomial
+/* The second-order data of the tangents at P (n and grad n themselves come
+ * from sample(), as trace_one takes them): the Hessian of n and, per parameter (all polynomial
  * coefficients, or the grid samples params[]), dn and d(grad n).  For
  * n = sqrt(p): grad n = grad p / 2n, H_n = H_p / 2n - grad p grad p^T / 4n^3,
  * dn = dp / 2n, d grad n = d grad p / 2n - grad p dp / 4n^3.  For n = C / p:
  * grad n = -C grad p / p^2, H_n = -C H_p / p^2 + 2 C grad p grad p^T / p^3,
  * dn = -C dp / p^2, d grad n = -C d grad p / p^2 + 2 C grad p dp / p^3. */
-static void ref_eval(const orc_medium* m, const double* P, double* n, double* g) {
-  field_eval(m, P, n, g);
-}
 
 /* The N2P lens (Sec. VI), n = w^gamma, w = 1 + u^beta,
  * u = (R^2 - rho^2 / 4) / F^2, rho from the axis through off[0], off[1]:
@@ -1215,13 +1211,29 @@ static void ref_second(const orc_medium* m, const double* P, int np, const int64
   }
 }
 
+/* n, grad n and the level as trace_one samples them (sample()), with the
+ * second-order data of ref_second.  In a layered medium n is a shell's
+ * constant index: its derivatives, dn/dtheta and its spatial gradient gd,
+ * are zero, while grad f still sets the refraction normal (Sec. I, Eq. 5). */
+static void tan_field(const orc_medium* m, const double* P, int nc, const int64_t* params,
+                      double* n, double* g, double* gd, int* lvl, double H[3][3], double* phi,
+                      double (*gphi)[3]) {
+  double u;
+  sample(m, P, n, g, lvl, &u);
+  ref_second(m, P, nc, params, H, phi, gphi);
+  for (int a = 0; a < 3; ++a) gd[a] = m->n_levels > 0 ? 0.0 : g[a];
+  if (m->n_levels > 0)
+    for (int j = 0; j < nc; ++j) phi[j] = 0.0;
+}
+
 /* Per parameter j the tangents carried along a ray. */
 typedef struct {
   double P[3], d[3], Q[3], n_prev, h, opl;
 } tangent;
 
 /* One ray of a polynomial or spherical freeform medium (n = p, sqrt(p) or
- * C / p), of a grid medium or of the N2P lens, in a box, sphere or
+ * C / p), of a grid medium or of the N2P lens, continuous or in
+ * point-sampled shells (not the exact level crossings), in a box, sphere or
  * cylinder: trace_one's values and decisions
  * (the same operations, in the same order), with every continuous quantity
  * also carrying its derivative with respect to each of the nc parameters
@@ -1249,10 +1261,10 @@ static int tangent_one(const orc_medium* m, const orc_params* prm, const double*
   normalize3(d);
   const double zero[3] = {0.0, 0.0, 0.0};
 
-  double n_prev, g[3], H[3][3];
+  double n_prev, g[3], gd[3], H[3][3];
+  int lvl_prev;
   if (inside(m, P)) {
-    ref_eval(m, P, &n_prev, g);
-    ref_second(m, P, nc, params, H, phi, gphi);
+    tan_field(m, P, nc, params, &n_prev, g, gd, &lvl_prev, H, phi, gphi);
     for (int j = 0; j < nc; ++j) T[j].n_prev = phi[j];
   } else {
     double t, Pb[3], NB[3], Dm;
@@ -1265,8 +1277,7 @@ static int tangent_one(const orc_medium* m, const orc_params* prm, const double*
     nsum_add(&opl, m->n_ext * t);
     for (int a = 0; a < 3; ++a) P[a] = Pb[a];
     double n_b;
-    ref_eval(m, P, &n_b, g);
-    ref_second(m, P, nc, params, H, phi, gphi);
+    tan_field(m, P, nc, params, &n_b, g, gd, &lvl_prev, H, phi, gphi);
     double R[3];
     double mu = m->n_ext / n_b;
     int tir = refract_or_reflect(d, NB, mu, R, &Dm);
@@ -1369,15 +1380,14 @@ static int tangent_one(const orc_medium* m, const orc_params* prm, const double*
         ++out->tir_bnd;
         h = dopl / n_prev;
         for (int j = 0; j < nc; ++j) T[j].h = -dopl * T[j].n_prev / (n_prev * n_prev);
-        ref_eval(m, P, &n_prev, g);
-        ref_second(m, P, nc, params, H, phi, gphi);
+        tan_field(m, P, nc, params, &n_prev, g, gd, &lvl_prev, H, phi, gphi);
         if (!(isfinite(n_prev) && n_prev > 0.0)) {
           out->exit_id = EXIT_INVALID;
           break;
         }
         for (int a = 0; a < 3; ++a) Q[a] = P[a] + h * d[a];
         for (int j = 0; j < nc; ++j) {
-          T[j].n_prev = phi[j] + dot3(g, T[j].P);
+          T[j].n_prev = phi[j] + dot3(gd, T[j].P);
           for (int a = 0; a < 3; ++a) T[j].Q[a] = T[j].P[a] + T[j].h * d[a] + h * T[j].d[a];
         }
         continue;
@@ -1392,16 +1402,17 @@ static int tangent_one(const orc_medium* m, const orc_params* prm, const double*
     ++steps;
 
     double n_i;
-    ref_eval(m, P, &n_i, g);
-    ref_second(m, P, nc, params, H, phi, gphi);
+    int lvl_i;
+    tan_field(m, P, nc, params, &n_i, g, gd, &lvl_i, H, phi, gphi);
     if (!(isfinite(n_i) && n_i > 0.0)) {
       out->exit_id = EXIT_INVALID;
       break;
     }
     double gn = norm3(g);
-    if (gn == 0.0 || !isfinite(gn)) {
+    if ((lvl_i >= 0 && lvl_i == lvl_prev) || gn == 0.0 || !isfinite(gn)) {
+      /* a step inside one shell, or no gradient: straight */
       for (int j = 0; j < nc; ++j) {
-        double dn_i = phi[j] + dot3(g, T[j].P);
+        double dn_i = phi[j] + dot3(gd, T[j].P);
         T[j].n_prev = dn_i;
         T[j].h = -dopl * dn_i / (n_i * n_i);
       }
@@ -1420,9 +1431,9 @@ static int tangent_one(const orc_medium* m, const orc_params* prm, const double*
          * da0 = -k dk / a0 (not followed where the clamp a0 = 0 acts) */
         double hi = dopl / n_i;
         double Pn[3] = {P[0] + hi * N[0], P[1] + hi * N[1], P[2] + hi * N[2]};
-        double n2, g2[3], H2[3][3];
-        ref_eval(m, Pn, &n2, g2);
-        ref_second(m, Pn, nc, params, H2, phi2, gphi2);
+        double n2, g2[3], g2d[3], H2[3][3];
+        int l2;
+        tan_field(m, Pn, nc, params, &n2, g2, g2d, &l2, H2, phi2, gphi2);
         double k = (n2 - n_i) / (2.0 * n_i);
         double w = 1.0 - k * k;
         double a0 = w > 0.0 ? sqrt(w) : 0.0;
@@ -1431,7 +1442,7 @@ static int tangent_one(const orc_medium* m, const orc_params* prm, const double*
         for (int a = 0; a < 3; ++a) Rr[a] = a0 * d[a] + k * N[a];
         double L = norm3(Rr), R[3] = {Rr[0] / L, Rr[1] / L, Rr[2] / L};
         for (int j = 0; j < nc; ++j) {
-          double dn_i = phi[j] + dot3(g, T[j].P);
+          double dn_i = phi[j] + dot3(gd, T[j].P);
           double dg[3], dN[3], dPn[3], dRr[3];
           for (int a = 0; a < 3; ++a)
             dg[a] = gphi[j][a] + H[a][0] * T[j].P[0] + H[a][1] * T[j].P[1] + H[a][2] * T[j].P[2];
@@ -1439,7 +1450,7 @@ static int tangent_one(const orc_medium* m, const orc_params* prm, const double*
           for (int a = 0; a < 3; ++a) dN[a] = (dg[a] - N[a] * Ndg) / gn;
           double dhi = -dopl * dn_i / (n_i * n_i);
           for (int a = 0; a < 3; ++a) dPn[a] = T[j].P[a] + dhi * N[a] + hi * dN[a];
-          double dn2 = phi2[j] + dot3(g2, dPn);
+          double dn2 = phi2[j] + dot3(g2d, dPn);
           double dk = dn2 / (2.0 * n_i) - n2 * dn_i / (2.0 * n_i * n_i);
           double da0 = w > 0.0 ? -k * dk / a0 : 0.0;
           for (int a = 0; a < 3; ++a) dRr[a] = da0 * d[a] + a0 * T[j].d[a] + dk * N[a] + k * dN[a];
@@ -1456,7 +1467,7 @@ static int tangent_one(const orc_medium* m, const orc_params* prm, const double*
         double R[3], Dm;
         int tir = refract_or_reflect(d, N, mu, R, &Dm);
         for (int j = 0; j < nc; ++j) {
-          double dn_i = phi[j] + dot3(g, T[j].P);
+          double dn_i = phi[j] + dot3(gd, T[j].P);
           double dg[3], dN[3], dd[3];
           for (int a = 0; a < 3; ++a)
             dg[a] = gphi[j][a] + H[a][0] * T[j].P[0] + H[a][1] * T[j].P[1] + H[a][2] * T[j].P[2];
@@ -1478,6 +1489,7 @@ static int tangent_one(const orc_medium* m, const orc_params* prm, const double*
         n_prev = n_i;
       }
     }
+    lvl_prev = lvl_i;
     for (int a = 0; a < 3; ++a) Q[a] = P[a] + h * d[a];
     for (int j = 0; j < nc; ++j)
       for (int a = 0; a < 3; ++a) T[j].Q[a] = T[j].P[a] + T[j].h * d[a] + h * T[j].d[a];
@@ -1541,7 +1553,7 @@ int orc_trace_tangent(const orc_medium* m, const orc_params* p, int64_t n, const
                       const double* d, int32_t nparams, const int64_t* params, double* P_out,
                       double* d_out, double* opl, int32_t* exit_id, int32_t* steps, double* tP,
                       double* td, double* topl, int32_t* flag, int32_t nthreads) {
-  if (m->bkind < 0 || m->bkind > 2 || m->n_levels != 0) return -1;
+  if (m->bkind < 0 || m->bkind > 2 || (p->flags & ORC_LEVEL_ROOT)) return -1;
   int nc;
   if (m->kind == 0 && m->form >= 0 && m->form <= 2 && m->degree >= 0) {
     nc = (m->degree + 1) * (m->degree + 2) * (m->degree + 3) / 6;

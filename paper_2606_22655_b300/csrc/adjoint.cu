@@ -50,7 +50,7 @@ struct St {
 
 // One iteration of the plain tracer's loop (trace_fp64.cu), on St.  A
 // normal step leaves n and grad n at its end point in s.n_end and s.g_end.
-template <int PC, bool GRID>
+template <int PC, bool GRID, bool LAY>
 __device__ __forceinline__ int advance(const DevMedium& m, double dopl, St& s, int& face) {
   using namespace plain;
   double Q[3];
@@ -65,7 +65,7 @@ __device__ __forceinline__ int advance(const DevMedium& m, double dopl, St& s, i
     if (snell(s.d, NB, s.n_prev / m.n_ext)) {
       ++s.tb;
       s.h = dopl / s.n_prev;
-      sample<PC, GRID, false>(m, s.P, s.n_prev, g, s.lvl);
+      sample<PC, GRID, LAY>(m, s.P, s.n_prev, g, s.lvl);
       if (!(isfinite(s.n_prev) && s.n_prev > 0.0)) {
         s.exit_id = GRIN_EXIT_INVALID;
         s.done = true;
@@ -81,7 +81,7 @@ __device__ __forceinline__ int advance(const DevMedium& m, double dopl, St& s, i
   ++s.steps;
   double n_i;
   int lvl_i;
-  sample<PC, GRID, false>(m, s.P, n_i, g, lvl_i);
+  sample<PC, GRID, LAY>(m, s.P, n_i, g, lvl_i);
   s.n_end = n_i;
   s.g_end[0] = g[0];
   s.g_end[1] = g[1];
@@ -92,7 +92,7 @@ __device__ __forceinline__ int advance(const DevMedium& m, double dopl, St& s, i
     return kNormal;
   }
   double gn = sqrt(dot3(g, g));
-  if (gn == 0.0 || !isfinite(gn)) {
+  if ((LAY && lvl_i == s.lvl) || gn == 0.0 || !isfinite(gn)) {
     s.h = dopl / n_i;
   } else {
     double N[3] = {g[0] / gn, g[1] / gn, g[2] / gn};
@@ -102,7 +102,7 @@ __device__ __forceinline__ int advance(const DevMedium& m, double dopl, St& s, i
       double Pn[3] = {s.P[0] + hi * N[0], s.P[1] + hi * N[1], s.P[2] + hi * N[2]};
       double n2, g2[3];
       int l2;
-      sample<PC, GRID, false>(m, Pn, n2, g2, l2);
+      sample<PC, GRID, LAY>(m, Pn, n2, g2, l2);
       double k = (n2 - n_i) / (2.0 * n_i);
       double w = 1.0 - k * k;
       double a0 = w > 0.0 ? sqrt(w) : 0.0;
@@ -124,7 +124,7 @@ __device__ __forceinline__ int advance(const DevMedium& m, double dopl, St& s, i
 // Start of a ray as in the plain tracer; false if it never steps (miss,
 // entry reflection, invalid).  Also returns the entry data the backward
 // sweep needs.
-template <int PC, bool GRID>
+template <int PC, bool GRID, bool LAY>
 __device__ bool start(const DevMedium& m, const TraceArgs& a, int64_t r, St& s, bool& entered,
                       double* d_in, double* NB) {
   using namespace plain;
@@ -147,7 +147,7 @@ __device__ bool start(const DevMedium& m, const TraceArgs& a, int64_t r, St& s, 
   normalize3(s.d);
   double g[3];
   if (inside(m, s.P)) {
-    sample<PC, GRID, false>(m, s.P, s.n_prev, g, s.lvl);
+    sample<PC, GRID, LAY>(m, s.P, s.n_prev, g, s.lvl);
   } else {
     double t, Pb[3];
     int face;
@@ -161,7 +161,7 @@ __device__ bool start(const DevMedium& m, const TraceArgs& a, int64_t r, St& s, 
       s.P[k] = Pb[k];
       d_in[k] = s.d[k];
     }
-    sample<PC, GRID, false>(m, s.P, s.n_prev, g, s.lvl);
+    sample<PC, GRID, LAY>(m, s.P, s.n_prev, g, s.lvl);
     if (snell(s.d, NB, m.n_ext / s.n_prev)) {
       s.exit_id = GRIN_EXIT_ENTRY_REFLECT;
       return false;
@@ -656,7 +656,7 @@ __device__ void cross_back_general(const double* P, const double* I, double h, d
 // forward recompute sampled them (taken by value), else they are sampled
 // here with the same arithmetic; either way the branch decisions below are
 // the forward sweep's.
-template <int PC, bool GRID>
+template <int PC, bool GRID, bool LAY>
 __device__ void normal_back(const DevMedium& m, double dopl, const double* rec, Adj& lam,
                             double* acc, double* grad, bool have = false, double n0 = 0.0,
                             double g0 = 0.0, double g1 = 0.0, double g2 = 0.0) {
@@ -666,25 +666,36 @@ __device__ void normal_back(const DevMedium& m, double dopl, const double* rec, 
   double Pn[3];
   for (int k = 0; k < 3; ++k) Pn[k] = P[k] + h * I[k];
   double n, g[3];
+  int lvl_i = -1, lvl_prev = -1;
   if (have) {
     n = n0;
     g[0] = g0;
     g[1] = g1;
     g[2] = g2;
   } else {
-    int lvl;
-    plain::sample<PC, GRID, false>(m, Pn, n, g, lvl);
+    plain::sample<PC, GRID, LAY>(m, Pn, n, g, lvl_i);
+  }
+  if (LAY) {
+    // shells: the levels at the step's two ends decide whether it stayed in
+    // one (the level of the current point is always the one sampled there)
+    double nx, gx[3];
+    if (have) plain::sample<PC, GRID, LAY>(m, Pn, nx, gx, lvl_i);
+    plain::sample<PC, GRID, LAY>(m, P, nx, gx, lvl_prev);
   }
   double gn = sqrt(plain::dot3(g, g));
   Adj in = lam;  // adjoint of the state after the step
   Adj out;
   for (int k = 0; k < 3; ++k) out.P[k] = out.d[k] = 0.0;
   out.n = out.h = 0.0;
-  double nb = in.n;
+  // a shell's index is a constant: nothing flows into n in a layered medium
+  double nb = LAY ? 0.0 : in.n;
   double gb[3] = {0.0, 0.0, 0.0};
   double Pxb[3] = {0.0, 0.0, 0.0};  // dL/dP' through the arc's P'' (tangential incidence)
   const double inv_n = 1.0 / n;
-  if (gn == 0.0 || !isfinite(gn)) {
+  if (LAY && lvl_i == lvl_prev) {
+    // inside one shell: straight, h = dL0 / n_i a constant
+    for (int k = 0; k < 3; ++k) out.d[k] += in.d[k];
+  } else if (gn == 0.0 || !isfinite(gn)) {
     nb = fma(-in.h * dopl, inv_n * inv_n, nb);
     for (int k = 0; k < 3; ++k) out.d[k] += in.d[k];
   } else {
@@ -704,7 +715,7 @@ __device__ void normal_back(const DevMedium& m, double dopl, const double* rec, 
       for (int k = 0; k < 3; ++k) Pa[k] = Pn[k] + hi * N[k];
       double n2, g2[3];
       int l2;
-      plain::sample<PC, GRID, false>(m, Pa, n2, g2, l2);
+      plain::sample<PC, GRID, LAY>(m, Pa, n2, g2, l2);
       const double kk = (n2 - n) / (2.0 * n);
       const double w = 1.0 - kk * kk;
       const double a0 = w > 0.0 ? sqrt(w) : 0.0;
@@ -722,18 +733,20 @@ __device__ void normal_back(const DevMedium& m, double dopl, const double* rec, 
         Nb[k] = kk * Rb[k];
       }
       // k = (n2 - n) / 2n; n2 = n(P''): its parameters, dL/dP'' = n2b grad n(P'')
-      const double n2b = kb * (0.5 * inv_n);
-      nb = fma(-kb * n2 * 0.5, inv_n * inv_n, nb);
-      double nh2, gh2[3], H2[6];
-      field_h_adj<PC, GRID>(m, Pa, n2b, nullptr, nh2, gh2, H2, acc, grad);
-      double hib = in.h;  // the next step's length is hi
-      for (int k = 0; k < 3; ++k) {
-        const double pab = n2b * gh2[k];
-        Pxb[k] += pab;
-        hib = fma(pab, N[k], hib);
-        Nb[k] = fma(hi, pab, Nb[k]);
+      if (!LAY) {  // (in shells k is a constant: n, n'' and hi are levels' indices)
+        const double n2b = kb * (0.5 * inv_n);
+        nb = fma(-kb * n2 * 0.5, inv_n * inv_n, nb);
+        double nh2, gh2[3], H2[6];
+        field_h_adj<PC, GRID>(m, Pa, n2b, nullptr, nh2, gh2, H2, acc, grad);
+        double hib = in.h;  // the next step's length is hi
+        for (int k = 0; k < 3; ++k) {
+          const double pab = n2b * gh2[k];
+          Pxb[k] += pab;
+          hib = fma(pab, N[k], hib);
+          Nb[k] = fma(hi, pab, Nb[k]);
+        }
+        nb = fma(-hib * dopl, inv_n * inv_n, nb);
       }
-      nb = fma(-hib * dopl, inv_n * inv_n, nb);
     } else {
       double D = 1.0 - mu * mu * (1.0 - c * c);
       bool tir = D <= 0.0;
@@ -762,6 +775,7 @@ __device__ void normal_back(const DevMedium& m, double dopl, const double* rec, 
     for (int k = 0; k < 3; ++k) gb[k] = fma(-N[k], s, Nb[k]) * inv_gn;
   }
   // field at P': dL/dP' = in.P + nb grad n + H gb (+ the arc's P''); parameters
+  if (LAY) nb = 0.0;
   double nh, gh[3], H[6];
   field_h_adj<PC, GRID>(m, Pn, nb, gb, nh, gh, H, acc, grad);
   double Pb[3];
@@ -778,7 +792,7 @@ __device__ void normal_back(const DevMedium& m, double dopl, const double* rec, 
 }
 
 // Back through a surface crossing with boundary reflection.
-template <int PC, bool GRID>
+template <int PC, bool GRID, bool LAY>
 __device__ void reflect_back(const DevMedium& m, double dopl, const double* rec, int face,
                              double fb, Adj& lam, double* acc, double* grad) {
   const double* P = rec;
@@ -802,9 +816,10 @@ __device__ void reflect_back(const DevMedium& m, double dopl, const double* rec,
   out.h = 0.0;
   // n'_{i-1} = n(P_b)
   double nh, gh[3], H[6];
-  field_h_adj<PC, GRID>(m, Pb, in.n, nullptr, nh, gh, H, acc, grad);
+  const double nbb = LAY ? 0.0 : in.n;  // (a shell's index: a constant)
+  field_h_adj<PC, GRID>(m, Pb, nbb, nullptr, nh, gh, H, acc, grad);
   double Pbb[3];
-  for (int k = 0; k < 3; ++k) Pbb[k] = fma(in.n, gh[k], in.P[k]);
+  for (int k = 0; k < 3; ++k) Pbb[k] = fma(nbb, gh[k], in.P[k]);
   double Rb[3];
   unit_back(u, inv_Rn, in.d, Rb);
   // dR = (1 - 2 N N^T) dI - 2 ((I.N) dN + N (I . dN))
@@ -864,7 +879,7 @@ __device__ void exit_back(const DevMedium& m, const double* rec, int face, const
 
 // Back through the ray's start: the entry refraction (mu = n_ext / n(P_b))
 // or, for a ray starting inside, n(P_0).
-template <int PC, bool GRID>
+template <int PC, bool GRID, bool LAY>
 __device__ void entry_back(const DevMedium& m, double dopl, const St& s0, bool entered,
                            const double* d_in, const double* NB, const Adj& lam, double* acc,
                            double* grad) {
@@ -881,6 +896,7 @@ __device__ void entry_back(const DevMedium& m, double dopl, const St& s0, bool e
     nb += -mub * mu / n0;
   }
   double nh, gh[3], H[6];
+  if (LAY) nb = 0.0;  // the entry shell's index is a constant
   field_h_adj<PC, GRID>(m, s0.P, nb, nullptr, nh, gh, H, acc, grad);
 }
 
@@ -898,14 +914,14 @@ struct AdjArgs {
   const uint32_t* order = nullptr;  // backward sweep: thread t takes ray order[t]
 };
 
-template <int PC, bool GRID>
+template <int PC, bool GRID, bool LAY>
 __global__ void __launch_bounds__(128) k_adj_forward(DevMedium m, AdjArgs A) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= A.a.count) return;
   St s;
   bool entered;
   double d_in[3], NB[3];
-  bool live = start<PC, GRID>(m, A.a, r, s, entered, d_in, NB);
+  bool live = start<PC, GRID, LAY>(m, A.a, r, s, entered, d_in, NB);
   double* ck = A.ckpt + (size_t)r * A.nseg * kCk;
   if (live) {
     int face = 0;
@@ -920,7 +936,7 @@ __global__ void __launch_bounds__(128) k_adj_forward(DevMedium m, AdjArgs A) {
         c[6] = s.n_prev;
         c[7] = s.h;
       }
-      const int kind = advance<PC, GRID>(m, A.a.dopl, s, face);
+      const int kind = advance<PC, GRID, LAY>(m, A.a.dopl, s, face);
       if (A.k == 1) {
         c[8] = (double)(kind + 4 * face);
         c[kNg] = s.n_end;
@@ -936,7 +952,7 @@ __global__ void __launch_bounds__(128) k_adj_forward(DevMedium m, AdjArgs A) {
   A.meta[2 * r + 1] = s.steps;
 }
 
-template <int PC, bool GRID>
+template <int PC, bool GRID, bool LAY>
 __global__ void __launch_bounds__(128) k_adj_backward(DevMedium m, AdjArgs A) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= A.a.count) return;
@@ -971,9 +987,9 @@ __global__ void __launch_bounds__(128) k_adj_backward(DevMedium m, AdjArgs A) {
       if (i == nsteps - 1 && exit_id >= 0)
         exit_back(m, c, face, Pob, dob, fb, lam);
       else if (kd == kCrossReflect)
-        reflect_back<PC, GRID>(m, dopl, c, face, fb, lam, acc, A.grad);
+        reflect_back<PC, GRID, LAY>(m, dopl, c, face, fb, lam, acc, A.grad);
       else
-        normal_back<PC, GRID>(m, dopl, c, lam, acc, A.grad, true, c[kNg], c[kNg + 1], c[kNg + 2],
+        normal_back<PC, GRID, LAY>(m, dopl, c, lam, acc, A.grad, true, c[kNg], c[kNg + 1], c[kNg + 2],
                               c[kNg + 3]);
     }
   } else if (nsteps > 0) {
@@ -993,6 +1009,10 @@ __global__ void __launch_bounds__(128) k_adj_backward(DevMedium m, AdjArgs A) {
       s.frac = 0.0;
       s.done = false;
       s.lvl = 0;
+      if (LAY) {  // the current point's level, as the forward sweep sampled it there
+        double nx, gx[3];
+        plain::sample<PC, GRID, LAY>(m, s.P, nx, gx, s.lvl);
+      }
       for (int i = s0; i < s1; ++i) {
         double* rr = rec[i - s0];
         for (int q = 0; q < 3; ++q) {
@@ -1002,7 +1022,7 @@ __global__ void __launch_bounds__(128) k_adj_backward(DevMedium m, AdjArgs A) {
         rr[6] = s.n_prev;
         rr[7] = s.h;
         int face = 0;
-        kind[i - s0] = advance<PC, GRID>(m, dopl, s, face);
+        kind[i - s0] = advance<PC, GRID, LAY>(m, dopl, s, face);
         fc[i - s0] = face;
         rr[kNg] = s.n_end;
         rr[kNg + 1] = s.g_end[0];
@@ -1016,9 +1036,9 @@ __global__ void __launch_bounds__(128) k_adj_backward(DevMedium m, AdjArgs A) {
       }
       for (; i >= s0; --i) {
         if (kind[i - s0] == kCrossReflect)
-          reflect_back<PC, GRID>(m, dopl, rec[i - s0], fc[i - s0], fb, lam, acc, A.grad);
+          reflect_back<PC, GRID, LAY>(m, dopl, rec[i - s0], fc[i - s0], fb, lam, acc, A.grad);
         else
-          normal_back<PC, GRID>(m, dopl, rec[i - s0], lam, acc, A.grad, true, rec[i - s0][kNg],
+          normal_back<PC, GRID, LAY>(m, dopl, rec[i - s0], lam, acc, A.grad, true, rec[i - s0][kNg],
                                 rec[i - s0][kNg + 1], rec[i - s0][kNg + 2], rec[i - s0][kNg + 3]);
       }
     }
@@ -1026,18 +1046,18 @@ __global__ void __launch_bounds__(128) k_adj_backward(DevMedium m, AdjArgs A) {
   St s;
   bool entered;
   double d_in[3], NB[3];
-  start<PC, GRID>(m, A.a, r, s, entered, d_in, NB);
-  entry_back<PC, GRID>(m, dopl, s, entered, d_in, NB, lam, acc, A.grad);
+  start<PC, GRID, LAY>(m, A.a, r, s, entered, d_in, NB);
+  entry_back<PC, GRID, LAY>(m, dopl, s, entered, d_in, NB, lam, acc, A.grad);
   if (!GRID)
     for (int q = 0; q < A.nterms; ++q)
       if (acc[q] != 0.0) atomicAdd(A.grad + q, acc[q]);
 }
 
-template <int PC, bool GRID>
+template <int PC, bool GRID, bool LAY>
 static int run_t(const DevMedium& m, const AdjArgs& A, cudaStream_t st, int phase) {
   const unsigned blocks = (unsigned)((A.a.count + 127) / 128);
   if (phase != kAdjBackward &&
-      launch_kernel(k_adj_forward<PC, GRID>, blocks, 128, st, m, A) < 0)
+      launch_kernel(k_adj_forward<PC, GRID, LAY>, blocks, 128, st, m, A) < 0)
     return GRIN_ERR_CUDA;
   if (phase == kAdjForward) return 1;
   // The backward sweep walks each ray back through all its steps, one
@@ -1055,14 +1075,13 @@ static int run_t(const DevMedium& m, const AdjArgs& A, cudaStream_t st, int phas
       lo = 0;
     }
   }
-  if (launch_kernel(k_adj_backward<PC, GRID>, blocks, 128, st, m, B) < 0) return GRIN_ERR_CUDA;
+  if (launch_kernel(k_adj_backward<PC, GRID, LAY>, blocks, 128, st, m, B) < 0) return GRIN_ERR_CUDA;
   return (phase == kAdjBackward ? 1 : 2) + lo;
 }
 
 }  // namespace adj
 
 bool adjoint_supported(const DevMedium& m) {
-  if (m.n_levels > 0) return false;
   if (m.bkind != GRIN_BOUNDARY_BOX && m.bkind != GRIN_BOUNDARY_SPHERE &&
       m.bkind != GRIN_BOUNDARY_CYLINDER)
     return false;
@@ -1086,6 +1105,19 @@ size_t adjoint_workspace(int64_t rays, int32_t max_steps, int32_t k) {
   return bytes + 256;
 }
 
+// The medium kinds, continuous (LAY = false) or in point-sampled shells.
+template <bool LAY>
+static int launch_adjoint_t(const DevMedium& m, const adj::AdjArgs& A, cudaStream_t st, int phase) {
+  if (m.kind == GRIN_MEDIUM_GRID) return adj::run_t<0, true, LAY>(m, A, st, phase);
+  if (m.kind == GRIN_MEDIUM_N2P) return adj::run_t<kN2P, false, LAY>(m, A, st, phase);
+  if (m.kind == GRIN_MEDIUM_SPHERICAL) return adj::run_t<kSpherical, false, LAY>(m, A, st, phase);
+  switch (m.pclass) {
+    case kPoly2: return adj::run_t<2, false, LAY>(m, A, st, phase);
+    case kPoly4: return adj::run_t<4, false, LAY>(m, A, st, phase);
+    default: return adj::run_t<6, false, LAY>(m, A, st, phase);
+  }
+}
+
 int launch_adjoint(const DevMedium& m, const TraceArgs& a, int32_t k, void* ws, const double* const* gout,
                    double* grad, int nterms, cudaStream_t st, int phase) {
   adj::AdjArgs A;
@@ -1107,14 +1139,9 @@ int launch_adjoint(const DevMedium& m, const TraceArgs& a, int32_t k, void* ws, 
   A.nterms = nterms;
   if (a.count < (int64_t(1) << 31))
     A.order_ws = (char*)ws + adjoint_order_offset(a.count, a.max_steps, k);
-  if (m.kind == GRIN_MEDIUM_GRID) return adj::run_t<0, true>(m, A, st, phase);
-  if (m.kind == GRIN_MEDIUM_N2P) return adj::run_t<kN2P, false>(m, A, st, phase);
-  if (m.kind == GRIN_MEDIUM_SPHERICAL) return adj::run_t<kSpherical, false>(m, A, st, phase);
-  switch (m.pclass) {
-    case kPoly2: return adj::run_t<2, false>(m, A, st, phase);
-    case kPoly4: return adj::run_t<4, false>(m, A, st, phase);
-    default: return adj::run_t<6, false>(m, A, st, phase);
-  }
+  if (m.n_levels > 0) return launch_adjoint_t<true>(m, A, st, phase);
+  return launch_adjoint_t<false>(m, A, st, phase);
 }
+
 
 }  // namespace grin

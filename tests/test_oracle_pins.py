@@ -750,6 +750,50 @@ def test_n2p_lens_tangents_through_the_arc_match_central_differences():
         assert e.max() <= 5e-5 and np.median(e) <= 1e-6, (i, e.max(), np.median(e))
 
 
+def test_layered_shell_tangents_match_central_differences():
+    """Point-sampled shells (Sec. I): the Luneburg field in 8 shells.  A
+    shell's index is a constant, so dn = 0 and the step lengths and mu do not
+    move; the parameters act through the refraction normal grad f / |grad f|
+    at each shell change.  Tangents against central differences (h = 1e-6
+    and 5e-7) on coefficients 1-4, on every ray whose integer outcomes hold
+    and whose differences agree: within 5e-5, median 1e-6; the constant
+    coefficient, which shifts f uniformly, has a zero tangent (to rounding).  Taking dn from
+    grad f instead (as for a continuous medium) misses by orders of
+    magnitude."""
+    m = dataclasses.replace(W.luneburg_medium(), n_levels=8, level_lo=1.0, level_hi=math.sqrt(2.0))
+    rays = W.luneburg_rays(8)
+    dopl, max_steps = 2e-3, 5000
+    t = oracle.trace_tangent(m, rays.origins, rays.dirs, dopl, max_steps)
+    base = oracle.trace(m, rays.origins, rays.dirs, dopl, max_steps)
+    for k in ("P", "d", "opl", "exit_id", "steps"):
+        np.testing.assert_array_equal(t[k], base[k], err_msg=k)
+    assert (t["flag"] == 0).all()
+    big = max(np.abs(t["tP"][:, 1:]).max(), np.abs(t["td"][:, 1:]).max())
+    assert max(np.abs(t["tP"][:, 0]).max(), np.abs(t["td"][:, 0]).max()) <= 1e-12 * big
+    h = 1e-6
+    for i in (1, 2, 3, 4):
+        keep = base["exit_id"] >= 0
+        fds = []
+        for hh in (h, h / 2):
+            res = []
+            for s in (+hh, -hh):
+                c = m.coeffs.copy()
+                c[i] += s
+                res.append((oracle.trace(W.Medium(**{**m.__dict__, "coeffs": c}), rays.origins, rays.dirs,
+                                         dopl, max_steps), c[i]))
+            (rp, vp), (rm, vm) = res
+            for k in ("exit_id", "steps", "tir_internal", "tir_boundary"):
+                keep &= (rp[k] == base[k]) & (rm[k] == base[k])
+            fds.append(np.concatenate([rp["P"] - rm["P"], rp["d"] - rm["d"]], 1) / (vp - vm))
+        a, b = fds
+        scale = np.abs(a).max(1) + 1e-300
+        keep &= np.abs(a - b).max(1) / scale <= 1e-6
+        tan = np.concatenate([t["tP"][:, i], t["td"][:, i]], 1)
+        e = (np.abs(tan - a).max(1) / scale)[keep]
+        assert e.size >= 40, (i, e.size)
+        assert e.max() <= 5e-5 and np.median(e) <= 1e-6, (i, e.max(), np.median(e))
+
+
 def test_grid_sample_tangents_match_central_differences():
     """Tangents with respect to grid samples (the weight of a sample at P is
     the product of its per-axis Catmull-Rom weights, summed over the taps the
