@@ -350,7 +350,8 @@ def adjoint_timing(ctx, dev, n_rays=1 << 18):
     checkpoint interval is the library's choice for half the free device
     memory (every step stored when that fits: 55 GB here); the same gradient
     with a checkpoint every 64 steps (segments recomputed) is timed beside
-    it."""
+    it, and so is the gradient with respect to the freeform block's 35
+    coefficients on as many point-source rays."""
     import torch
     from paper_2606_22655_b300 import tracer
     from paper_2606_22655_b300 import workloads as W
@@ -406,6 +407,26 @@ def adjoint_timing(ctx, dev, n_rays=1 << 18):
         e1.record()
         torch.cuda.synchronize(dev)
         design[name] = e0.elapsed_time(e1) / 1e3
+    # the same loss with respect to the freeform block's 35 coefficients (the
+    # point-source bundle, dL0 = 0.02 mm so that every ray leaves within 2000
+    # steps), at the interval chosen by free memory
+    fm = W.freeform_block_medium()
+    fr = W.point_source_rays(n, W.BASE_SEED + 4)
+    fmed = tracer.Medium(ctx, fm)
+    frays = tracer.RayBatch.from_numpy(fr.origins, fr.dirs, device=dev, dtype=torch.float64)
+    fk = tracer.adjoint_interval(fmed, n, 0.02, 2000)
+    tracer.trace_adjoint(ctx, fmed, frays, 0.02, 2000, g, len(fm.coeffs), fk)  # warm-up
+    torch.cuda.synchronize(dev)
+    e0.record()
+    fout, _ = tracer.trace_adjoint(ctx, fmed, frays, 0.02, 2000, g, len(fm.coeffs), fk)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    tf = e0.elapsed_time(e1) / 1e3
+    fsteps = float(fout["steps"].sum())
+    fmed.close()
+    coefficients = {"workload": f"freeform block adjoint, 35 coefficients, {n} rays, dL0 0.02 mm",
+                    "checkpoint_every": fk, "seconds": tf, "forward_ray_steps": fsteps,
+                    "ray_steps_per_s_fwd_plus_bwd": fsteps / tf}
     return {"workload": f"grid_128 adjoint, {n} rays, dL0 0.02 mm, checkpoint interval by free memory",
             "checkpoint_every": k,
             "workspace_gb": tracer.adjoint_workspace_bytes(med, n, 0.02, 2000, k) / 1e9,
@@ -414,7 +435,7 @@ def adjoint_timing(ctx, dev, n_rays=1 << 18):
             "recomputed_k64": {"seconds": t64, "ray_steps_per_s_fwd_plus_bwd": steps / t64,
                                "workspace_gb": tracer.adjoint_workspace_bytes(med, n, 0.02, 2000, 64) / 1e9,
                                "gradient_equals": same},
-            "design_iteration": design}
+            "design_iteration": design, "coefficients": coefficients}
 
 
 def media_rates(ctx, dev):
