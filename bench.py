@@ -623,8 +623,11 @@ def run_ours(args):
     stream = torch.cuda.Stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
+    level_root = bool(args.level_root and wl.medium.n_levels)
+
     def step():
-        tracer.trace(ctx, med, rays, wl.dopl, wl.max_steps, "mixed", stream=stream, out=out)
+        tracer.trace(ctx, med, rays, wl.dopl, wl.max_steps, "mixed", stream=stream, out=out,
+                     level_root=level_root)
 
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
@@ -660,7 +663,8 @@ def run_ours(args):
 
     if args.profile_only:
         if rank == 0:
-            print(json.dumps({"profile_only": True, "workload": wl.name, "value": value, "unit": UNIT,
+            print(json.dumps({"profile_only": True, "workload": wl.name + ("_crossings" if level_root else ""),
+                              "value": value, "unit": UNIT,
                               "kernel_ms": 1e3 * mean_kern, "gpu_launches": launches}), flush=True)
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -814,6 +818,8 @@ def main():
                     help="freeform (the benchmark), or another medium for profiling")
     ap.add_argument("--profile-only", action="store_true",
                     help="timed steps only: no precision gate, e2e or CPU baseline")
+    ap.add_argument("--level-root", action="store_true",
+                    help="with --workload layered: the shells with their crossings solved")
     ap.add_argument("--adjoint-only", type=int, default=0, metavar="RAYS",
                     help="only the adjoint timing, on RAYS rays (to profile its kernels)")
     args = ap.parse_args()
