@@ -29,9 +29,12 @@ Parity status per function (pins live in tests/test_oracle_pins.py):
   - the inner index at the exit face (n at the last interior point): pinned
     by the conserved transverse momentum of a z-stratified medium;
   - forward-mode tangents (trace_tangent; polynomial coefficients with
-    n = p, or grid samples, in a box): values and decisions bitwise those of
-    trace; derivatives pinned against central differences of trace, inside
-    the medium, through the exit and at edge-clamped samples;
+    n = p, sqrt(p) or C / p, the spherical freeform's a0..a3, the N2P lens's
+    R, F, beta, gamma, or grid samples; box, sphere or cylinder; continuous
+    or in point-sampled shells; through the tangential-incidence arc):
+    values and decisions bitwise those of trace; derivatives pinned against
+    central differences of trace, inside the medium, through the exit, on
+    curved surfaces, at edge-clamped samples and in shells;
   - freeform and blob media as a whole: parity unpinned beyond the
     invariants above (no closed form exists).
 """
